@@ -1,0 +1,68 @@
+"""Pins of the oracle's preconditioner K_d (CPU only)."""
+import numpy as np
+import pytest
+
+import pdhg_workloads as W
+from oracle import precond, spacetime
+
+
+@pytest.mark.parametrize("p", [
+    W.advection_upwind_be(nx=8, nt=5),
+    W.heat_table1(8, 4),
+    W.burgers_2d(n=6, nt=3),
+    W.burgers_dg_p2(ncell=6, nt=4),
+    W.viscous_burgers(nx=7, nt=3),
+], ids=lambda p: p.name)
+def test_kd_inverse_equals_dense_solve(p):
+    """FFT-in-x + Thomas-in-t equals a dense solve of K_d assembled in real space from
+    stencils (not from Fourier symbols); K_d is symmetric positive definite."""
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal((p.nt,) + p.slice_shape)
+    Kd = precond.dense_Kd(p)
+    zd = np.linalg.solve(Kd, r.ravel()).reshape(r.shape)
+    z = precond.kd_inverse(p, r)
+    assert np.max(np.abs(z - zd)) <= 1e-12 * np.max(np.abs(zd))
+    assert np.max(np.abs(Kd - Kd.T)) == 0.0
+    assert np.min(np.linalg.eigvalsh(Kd)) > 0.0
+
+
+def test_Tt_is_backward_euler_gram_matrix():
+    """T_t / h_t^2 = A_t A_t^T with A_t the backward-Euler difference acting on
+    u^1..u^nt (u^0 held fixed): the paper's H-norm with phi^{nt} = 0."""
+    p = W.advection_upwind_be(nx=4, nt=6).replace(beta=0.0)
+    n = p.ndof
+    u = np.zeros((p.nt + 1,) + p.slice_shape)
+    A = np.zeros((p.nt * n, p.nt * n))
+    for k in range(p.nt * n):
+        v = np.zeros_like(u)
+        v.reshape(-1)[n + k] = 1.0
+        A[:, k] = spacetime.jvp(p, u, v).ravel()
+    T = np.kron(precond.dense_Tt(p.nt), np.eye(n)) / p.ht ** 2
+    assert np.allclose(A @ A.T, T, rtol=1e-13, atol=1e-13 * np.max(T))
+
+
+def test_fd_symbol_equals_upwind_gram():
+    """For FD the symbol kappa = c^2 L(theta) equals |S(theta)|^2 of the upwind operator
+    of c u_x, the construction the DG preconditioner generalises."""
+    p = W.advection_upwind_be(nx=16, nt=2).replace(c=1.7)
+    k = np.arange(9)
+    theta = 2 * np.pi * k / 16
+    S = 1.7 * (1 - np.exp(-1j * theta)) / p.hx
+    assert np.allclose(np.abs(S) ** 2, precond.fd_kappa(p), rtol=1e-13)
+
+
+def test_dg_symbol_blocks_hermitian_psd():
+    p = W.burgers_dg_p2(ncell=8, nt=2)
+    K = precond.dg_Kx(p)
+    assert np.allclose(K, np.conj(np.swapaxes(K, -1, -2)), atol=1e-12)
+    assert np.min(np.linalg.eigvalsh(K)) > -1e-9 * np.max(np.abs(K))
+
+
+def test_thomas_kappa_zero_prefix_sums():
+    """For kappa = 0 every pivot is 1, so z is a suffix sum of prefix sums of h_t^2 r."""
+    nt = 7
+    r = np.random.default_rng(1).standard_normal((nt, 1)) + 0j
+    z = precond.thomas_t(r, np.zeros(1), 0.5)
+    y = np.cumsum(0.25 * r[:, 0])
+    zz = np.cumsum(y[::-1])[::-1]
+    assert np.allclose(z[:, 0], zz, atol=1e-14)

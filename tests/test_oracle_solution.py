@@ -1,0 +1,194 @@
+"""Pins of the oracle's discrete solution and of Algorithm 1 (CPU only).
+
+* the Newton time-stepper (the definition of the discrete solution) against
+  Fourier closed forms (BE upwind advection; BDF2 by its two-step recurrence);
+* the PDHG fixed point against the Newton time-stepper to 1e-10;
+* the proposition of Sec. 2.3: the iteration matrix has eigenvalues
+  (1-x) +- i sqrt(x(1-x)) for x in the spectrum of tau_u tau_phi J^T K_d^{-1} J;
+* Table 1 (Sec. 4.1) iteration counts;
+* mass conservation at convergence;
+* the signs printed in Algorithm 1 do not converge (a recorded reading).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import pdhg_workloads as W
+from oracle import newton, pdhg, precond, spacetime
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _mode_closed_form_be(p, k=1):
+    """u^l_j = Im(g^l e^{i k x_j}), g = 1/(1 + nu (1 - e^{-i theta})), nu = b h_t/h_x."""
+    x = W.fd_nodes(p.nx, p.lx)
+    theta = k * p.hx
+    nu = p.beta * p.ht / p.hx
+    g = 1.0 / (1.0 + nu * (1.0 - np.exp(-1j * theta)))
+    return np.array([np.imag(g ** l * np.exp(1j * k * x)) for l in range(p.nt + 1)])
+
+
+def _mode_closed_form_bdf2(p, k=1):
+    """BDF2 with a BE first step, per Fourier mode: a scalar two-step recurrence."""
+    x = W.fd_nodes(p.nx, p.lx)
+    s = p.beta * p.ht / p.hx * (1.0 - np.exp(-1j * k * p.hx))
+    a = [1.0 + 0j, 1.0 / (1.0 + s)]
+    for _ in range(2, p.nt + 1):
+        a.append((2.0 * a[-1] - 0.5 * a[-2]) / (1.5 + s))
+    return np.array([np.imag(al * np.exp(1j * k * x)) for al in a])
+
+
+def test_newton_matches_be_closed_form_config1():
+    p = W.advection_upwind_be()                      # 128 x 64, CFL 2, u0 = sin x
+    u = newton.solve(p)
+    assert np.max(np.abs(u - _mode_closed_form_be(p))) < 1e-12
+
+
+def test_newton_matches_bdf2_closed_form():
+    p = W.advection_upwind_be(nx=32, nt=24, cfl=3.0).replace(time="bdf2")
+    u = newton.solve(p)
+    assert np.max(np.abs(u - _mode_closed_form_bdf2(p))) < 1e-12
+
+
+def _with_steps(p, fac=0.6):
+    """tau_u = tau_phi = sqrt(fac / nu_max), nu_max from the oracle's power estimate;
+    tau_u0 = 0.1 for the initial row (the paper gives no tau_u0)."""
+    t = float(np.sqrt(fac / pdhg.power_estimate(p, iters=100)))
+    return p.replace(tau_u=t, tau_phi=t, tau_u0=0.1, tau_lambda=0.99)
+
+
+def _tiny_cases():
+    yield _with_steps(W.advection_upwind_be(nx=8, nt=4))
+    yield _with_steps(W.advection_upwind_be(nx=8, nt=4).replace(time="bdf2"))
+    yield W.heat_table1(8, 4)
+    yield _with_steps(W.burgers_dg_p2(ncell=8, nt=4, T=0.4).replace(c=0.5), 1.0)
+    yield _with_steps(W.burgers_dg_p2(ncell=8, nt=4, T=0.4, time="be").replace(c=0.5), 1.0)
+    yield _with_steps(W.burgers_2d(n=8, nt=3))
+    yield _with_steps(W.viscous_burgers(nx=8, nt=4, T=0.5, nu=0.05))
+    yield _with_steps(W.viscous_burgers(nx=8, nt=4, T=0.5, nu=0.05).replace(init="pinned"))
+
+
+@pytest.mark.parametrize("p", list(_tiny_cases()), ids=lambda p: f"{p.name}_{p.time}_{p.init}")
+def test_pdhg_fixed_point_equals_newton(p):
+    """The saddle point's u is the solution of the implicit scheme (Sec. 3.1): PDHG
+    converged to Res <= 1e-11 agrees with the Newton time-stepper to 1e-10, the dual
+    variables vanish, and the mass sum_j u^l_j is the same on every slice."""
+    un = newton.solve(p)
+    st, it, _ = pdhg.solve(p, max_iters=40000, tol=1e-11, check_every=20)
+    res = pdhg.residual_norms(p, st)
+    assert res[0] <= 1e-11 and res[1] <= 1e-11, (it, res)
+    assert np.max(np.abs(st["u"] - un)) <= 1e-10
+    assert np.max(np.abs(st["phi"])) <= 1e-8
+    if p.space == "dg_p2_lf":
+        mass = st["u"][:, 0].sum(axis=-1)
+    else:
+        mass = st["u"].reshape(p.nt + 1, -1).sum(axis=-1)
+    assert np.max(np.abs(mass - mass[0])) <= 1e-9 * max(1.0, np.abs(mass[0]))
+
+
+def test_pdhg_config1_against_closed_form():
+    """Config 1 (BE upwind advection 128 x 64, CFL 2): PDHG to absolute Res 1e-10
+    lands within 1e-9 of the closed-form discrete solution."""
+    p = W.advection_upwind_be().replace(tau_u=1.4, tau_u0=0.1, tau_phi=0.35, tau_lambda=0.99)
+    st, it, _ = pdhg.solve(p, max_iters=6000, tol=1e-10, check_every=10)
+    res = pdhg.residual_norms(p, st)
+    assert res[0] <= 1e-10 and res[1] <= 1e-10
+    assert np.max(np.abs(st["u"] - _mode_closed_form_be(p))) < 1e-9
+
+
+def test_proposition_eigenvalues():
+    """Sec. 2.3: for linear A the nonzero eigenvalues of the iteration matrix are
+    (1-x) +- i sqrt(x(1-x)), x the eigenvalues of tau_u tau_phi A^T K^{-1} A."""
+    p = W.advection_upwind_be(nx=8, nt=4).replace(init="pinned", tau_u=0.7, tau_phi=0.7)
+    p = p.replace(u0=np.zeros_like(p.u0))
+    n, nt = p.ndof, p.nt
+    u = np.zeros((nt + 1, n))
+    G = np.zeros((nt * n, nt * n))
+    for k in range(nt * n):
+        v = np.zeros_like(u)
+        v.reshape(-1)[n + k] = 1.0
+        G[:, k] = spacetime.jvp(p, u, v).ravel()
+    X = p.tau_u * p.tau_phi * G.T @ np.linalg.solve(precond.dense_Kd(p), G)
+    x = np.linalg.eigvals(X).real
+    assert np.all(x > 0) and np.all(x < 1)
+    pred = np.concatenate([(1 - x) + 1j * np.sqrt(x * (1 - x)), (1 - x) - 1j * np.sqrt(x * (1 - x))])
+
+    def step_vec(vec):
+        st = pdhg.initial_state(p)
+        st["u"][1:] = vec[: nt * n].reshape(nt, n)
+        st["phi"] = vec[nt * n: 2 * nt * n].reshape(nt, n).copy()
+        st["phit"] = vec[2 * nt * n:].reshape(nt, n).copy()
+        pdhg.step(p, st)
+        return np.concatenate([st["u"][1:].ravel(), st["phi"].ravel(), st["phit"].ravel()])
+
+    m = 3 * nt * n
+    M = np.stack([step_vec(e) for e in np.eye(m)], axis=1)
+    ev = np.linalg.eigvals(M)
+    ev = ev[np.abs(ev) > 1e-9]
+    assert len(ev) == len(pred)
+    assert max(np.min(np.abs(ev - q)) for q in pred) < 1e-12
+    assert max(np.min(np.abs(pred - e)) for e in ev) < 1e-12
+    # and the observed residual contraction follows rho = sqrt(1 - x_min)
+    rho = np.sqrt(1 - np.min(x))
+    q = p.replace(u0=np.sin(W.fd_nodes(8, p.lx)))
+    st = pdhg.initial_state(q)
+    hist = []
+    for _ in range(120):
+        pdhg.step(q, st)
+        hist.append(pdhg.residual_norms(q, st)[0])
+    obs = (hist[-1] / hist[-41]) ** (1.0 / 40)
+    assert abs(obs - rho) < 0.01 * rho
+
+
+def _table1():
+    rows = []
+    with open(os.path.join(HERE, "golden", "paper_table1_heat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(tuple(int(t) for t in line.split()))
+    return rows
+
+
+def _iters_to(p, tols, max_iters=600):
+    st = pdhg.initial_state(p)
+    first = {}
+    for it in range(1, max_iters + 1):
+        pdhg.step(p, st)
+        r = pdhg.residual_norms(p, st)
+        for tol in tols:
+            if tol not in first and r[0] <= tol and r[1] <= tol:
+                first[tol] = it
+        if len(first) == len(tols):
+            break
+    return first
+
+
+def test_table1_coarsest_mesh_exact():
+    """Table 1, N_x x N_t = 64 x 16: 90 iterations to 1e-6 and 144 to 1e-10, with the
+    reading tau_u0 = tau_u (the paper gives no tau_u0)."""
+    nx, nt, i6, i10 = _table1()[0]
+    got = _iters_to(W.heat_table1(nx, nt), (1e-6, 1e-10))
+    assert got[1e-6] == i6 and got[1e-10] == i10
+
+
+def test_table1_finer_meshes_loose():
+    """Finer Table 1 meshes: the counts stay within +25% of the printed ones (the
+    u^0/lambda sub-iteration, whose step tau_u0 is not given, drifts with the mesh)."""
+    for nx, nt, i6, i10 in _table1()[1:3]:
+        got = _iters_to(W.heat_table1(nx, nt), (1e-6, 1e-10))
+        assert i6 <= got[1e-6] <= 1.25 * i6
+        assert i10 <= got[1e-10] <= 1.25 * i10
+
+
+def test_paper_printed_signs_do_not_converge():
+    """Algorithm 1 as printed pairs u^0 <- u^0 - tau(phit^0 - lamt) with
+    lambda <- lambda + tau(u^0 - u0), which is positive feedback for lambda; the
+    standard Chambolle-Pock signs converge on the same problem."""
+    p = W.advection_upwind_be(nx=16, nt=8).replace(tau_u=0.7, tau_u0=0.1, tau_phi=0.7)
+    st_std, _, _ = pdhg.solve(p, max_iters=400, tol=0.0, check_every=400)
+    st_pap, _, _ = pdhg.solve(p, max_iters=400, tol=0.0, check_every=400, signs="paper")
+    r_std = pdhg.residual_norms(p, st_std)
+    r_pap = pdhg.residual_norms(p, st_pap)
+    assert r_std[0] < 1e-3
+    assert not (r_pap[0] < 1e-3)
