@@ -1,0 +1,393 @@
+"""Benchmark of the space-time PDHG iteration (Algorithm 1) on GB300.
+
+One "step" is one PDHG iteration over the whole space-time grid of the
+workload: primal step, residual, preconditioned dual step and extrapolation
+for every (dof, time slice) at once.  The metric is space-time
+cell-iterations per second (dofs x equation slices x iterations / s).
+
+Default workload (N = 1): 2D Burgers u_t + (u^2/2)_x + (u^2/2)_y = 0 on a
+periodic 1024 x 1024 grid, 256 time slices (268,435,456 space-time cells),
+backward Euler + global Lax-Friedrichs, float32 fields, u0 = 8 seeded random
+Fourier modes.  The state (u, phi, phit, spectrum: about 4.3 GB) is far larger
+than L2, so consecutive iterations stream it from HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs under torch.distributed.run: every rank solves its own replica of
+the workload (the method has no data-parallel split across GPUs here;
+"replicas only"), the timed region is bracketed by barriers and the slowest
+rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pdhg_workloads as W  # noqa: E402
+
+METRIC = "PDHG space-time cell-iters/s & HBM %peak; time-to-residual 1e-6 vs plain GPU"
+UNIT = "cell-iters/s"
+
+
+def workload(name: str):
+    if name == "burgers2d":
+        return W.burgers_2d(n=1024, nt=256, tau=(0.4, 0.1, 0.4, 0.99))
+    if name == "burgers2d_small":
+        return W.burgers_2d(n=256, nt=64, tau=(0.4, 0.1, 0.4, 0.99))
+    if name == "dg_p2":
+        return W.burgers_dg_p2(tau=(0.2, 0.1, 0.2, 0.99)).replace(c=0.5)
+    if name == "advection":
+        return W.advection_upwind_be(tau=(1.4, 0.1, 0.35, 0.99))
+    raise ValueError(name)
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(local_units: float, local_ms: float, group=None):
+    """Whole-job throughput: units summed over ranks / the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return local_units / (local_ms * 1e-3), local_ms
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+    return float(u.item()) / (float(t.item()) * 1e-3), float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str | None = None):
+        self.gpu = gpu_index
+        self.path = path
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        if self.path:
+            with open(self.path, "w") as f:
+                f.write(self.FIELDS + "\n" + "\n".join(self.lines) + "\n")
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            t = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(t[1]))
+                smax = float(t[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, t[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic bytes per launch of each stage
+# ---------------------------------------------------------------------------
+
+def stage_bytes(p, esz: int):
+    """Compulsory HBM bytes of one launch of each stage: every input read once,
+    every output written once (sizes from the array shapes)."""
+    S, nt = p.ndof, p.nt
+    lines = 3 if p.space == "dg_p2_lf" else (p.ny if p.dims == 2 else 1)
+    spec = nt * lines * (p.nx // 2 + 1) * 2 * esz          # complex spectrum, all slices
+    u = (nt + 1) * S * esz
+    f = nt * S * esz
+    lam = S * esz
+    return {
+        "primal": u + f + u + 3 * lam + 2 * lam,            # read u, phit; write u; lambda row
+        "residual_fft": u + spec,                           # read u; write spectrum
+        "fft_y": 2 * spec,                                  # read + write spectrum
+        "tsolve": 4 * spec,                                 # forward sweep r/w, backward r/w
+        "dual": spec + f + 2 * f,                           # read spectrum, phi; write phi, phit
+        "fused_rows": spec + f + f + u + u + spec,          # read Zx, phi; write phi; r/w u; write X
+        "fused_cols": spec + spec + 2 * spec,               # read X, write Zx, spill w/r
+    }
+
+
+KERNEL_SOURCES = {"primal": "kernels_plain.cu", "residual_fft": "kernels_plain.cu",
+                  "fft_y": "kernels_plain.cu", "tsolve": "kernels_plain.cu",
+                  "dual": "kernels_plain.cu", "fused_rows": "kernels_fused2d.cu",
+                  "fused_cols": "kernels_fused2d.cu"}
+
+
+def traffic_for(stage: str, workload_name: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        db = json.load(open(path))
+        ent = db.get(workload_name, {}).get(stage)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, "paper_2207_07234_gb300", "csrc", KERNEL_SOURCES[stage])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if ent.get("src_sha") != sha:
+            return None
+        return ent["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(p, nt_sample=8):
+    """The workload cut to its first nt_sample time slices (same grid, same u0)."""
+    return p.replace(nt=nt_sample, T=p.ht * nt_sample)
+
+
+def time_oracle(p, iters=3, warm=1):
+    from oracle import pdhg as opdhg
+    q = oracle_sample(p)
+    st = opdhg.initial_state(q)
+    for _ in range(warm):
+        opdhg.step(q, st)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        opdhg.step(q, st)
+    dt = time.perf_counter() - t0
+    return q.cells_per_iter * iters / dt, q, dt
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    p = workload(args.workload)
+    q = oracle_sample(p)
+    from oracle import pdhg as opdhg
+    st = opdhg.initial_state(q)
+    for _ in range(args.warmup):
+        opdhg.step(q, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        opdhg.step(q, st)
+    dt = time.perf_counter() - t0
+    value = q.cells_per_iter * args.steps / dt
+    sample = (f"{q.name.replace(str(p.nt), str(q.nt))}: the workload cut to its first {q.nt} "
+              f"time slices, {args.steps} oracle iterations")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": p.name, "oracle_sample_slices": q.nt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_07234_gb300 import binding
+
+    p = workload(args.workload)
+    esz = 4 if args.precision == "fp32" else 8
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(dev)
+    solver = binding.Solver(p, precision=args.precision, path=args.path, device=dev, stream=stream)
+    path = solver.info()["path"]
+    per_iter = solver.launches(reset=True)
+
+    # warm-up
+    solver.iterate(args.warmup)
+    torch.cuda.synchronize()
+    solver.launches(reset=True)
+    solver.set_profiling(True)
+    solver.stage_times()                      # clear
+
+    barrier()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk_path = os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+    with ClockSampler(gpu_index(local), clk_path) as clk:
+        start.record(stream)
+        solver.iterate(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    local_ms = start.elapsed_time(end)
+    launches = solver.launches(reset=True)
+    stages = solver.stage_times()
+    solver.set_profiling(False)
+    units = p.cells_per_iter * args.steps
+    value, max_ms = aggregate(units, local_ms)
+
+    # roofline of the dominant stage
+    sb = stage_bytes(p, esz)
+    dom = max(stages, key=lambda k: stages[k][0]) if stages else None
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if dom:
+        ms, n = stages[dom]
+        achieved = sb[dom] / (ms / n * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_for(dom, p.name),
+                "algorithmic_bytes_per_launch": sb[dom], "avg_launch_ms": ms / n,
+                "peak_source": peak_kind,
+                "stage_ms_share": {k: round(v[0] / sum(x[0] for x in stages.values()), 4)
+                                   for k, v in stages.items()}}
+    solver.close()
+    del solver
+    torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host buffers: upload u0 from pinned host
+    # memory, K iterations with one residual read-back, terminal slice to pinned host
+    e2e = None
+    if not args.no_e2e:
+        u0_host = torch.from_numpy(np.ascontiguousarray(p.u0, dtype=np.float64)).pin_memory()
+        out_host = torch.empty(p.slice_shape, dtype=torch.float32 if esz == 4 else torch.float64).pin_memory()
+        q = p.replace(u0=u0_host.numpy())
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = binding.Solver(q, precision=args.precision, path=args.path, device=dev, stream=stream)
+        s2.iterate(args.steps, tol=0.0, check_every=args.steps)
+        s2.get_host("u_terminal", out=out_host.numpy())
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        s2.close()
+        e2e_val, _ = aggregate(units, e2e_s * 1e3)
+        h2d = p.ndof * 8 + (p.nx if p.gamma_half is not None else 0) * 8
+        d2h = p.ndof * esz + 6 * 8
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+               "d2h_bytes_per_step": d2h / args.steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, q, dt = time_oracle(p)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{p.name} cut to its first {q.nt} time slices, 3 oracle iterations ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if esz == 4 else "f64",
+                "data": "synthetic",
+                "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nt": p.nt,
+                           "cells_per_iter": p.cells_per_iter, "scheme": f"{p.time}+{p.space}",
+                           "path": path, "l2": "state larger than L2 (no flush needed)",
+                           "parallelism": f"replicas{ws}"},
+                "gpu_launches": launches, "launches_per_iter": per_iter if per_iter else None,
+                "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="burgers2d")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

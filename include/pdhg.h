@@ -1,0 +1,179 @@
+/*
+ * pdhg.h -- C ABI of the GB300 space-time PDHG solver for implicit schemes of
+ * scalar conservation laws (Liu, Osher, Li, Shu, arXiv 2207.07234).
+ *
+ * The solver finds the saddle point of the discrete Lagrangian of Sec. 3.3
+ * (Eq. 3.10) with the preconditioned primal-dual iteration of Algorithm 1:
+ * every time slice of the implicit scheme (backward Euler or BDF2 in t,
+ * Sec. 3.1; upwind / Lax-Friedrichs finite differences or DG P2 in x,
+ * Sec. 3.2) is updated at once on the GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: PDHG_OK (0) or a negative pdhg_status.  Nothing aborts and
+ *   no kernel traps; pdhg_last_error() gives a message for the calling thread.
+ * - Memory: the library allocates NO device memory.  The caller owns one
+ *   device workspace of pdhg_workspace_size() bytes (256-byte aligned) and
+ *   passes it to pdhg_create(); the handle (host memory, owned by the
+ *   library) only points into it.  The workspace must stay alive and untouched
+ *   until pdhg_destroy().
+ * - Streams: every device operation is enqueued on the handle's stream (a
+ *   cudaStream_t passed as void*; NULL is the legacy default stream).
+ * - Layouts (one time slice, "dofs"): 1D finite differences: u[j], j = 0..nx-1,
+ *   x_j = j*lx/nx.  2D: u[y][x], x fastest.  DG P2: U[m][j], m = 0..2 Legendre
+ *   mode, j = cell, cell fastest.  Space-time fields are slice-major: u has
+ *   nt+1 slices (l = 0..nt), phi and phit have nt slices (one per equation).
+ * - Precision: fields are stored as double (PDHG_FP64) or float (PDHG_FP32);
+ *   buffers passed to pdhg_get_field/pdhg_set_field use that element type.
+ *   Residual norms are always accumulated in double.
+ * - Determinism: the same inputs on the same GPU give bitwise-identical results.
+ */
+#ifndef PDHG_H
+#define PDHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PDHG_OK = 0,
+    PDHG_ERR_INVALID_ARG = -1,          /* a size, step, pointer or enum is invalid */
+    PDHG_ERR_WORKSPACE_TOO_SMALL = -2,  /* workspace smaller than pdhg_workspace_size() */
+    PDHG_ERR_CUDA = -3,                 /* a CUDA runtime call failed (message has the cudaError) */
+    PDHG_ERR_NONFINITE = -4,            /* a residual norm became NaN or Inf */
+    PDHG_ERR_DIVERGED = -5,             /* the primal residual grew by more than 1e10 */
+    PDHG_ERR_TIMEOUT = -6,              /* a bounded device wait gave up */
+    PDHG_ERR_UNSUPPORTED = -7           /* valid but not implemented (e.g. nx not a power of two) */
+} pdhg_status;
+
+enum { PDHG_TIME_BE = 0, PDHG_TIME_BDF2 = 1 };
+enum { PDHG_SPACE_FD_UPWIND = 0, PDHG_SPACE_FD_LF = 1, PDHG_SPACE_DG_P2_LF = 2 };
+enum { PDHG_FP64 = 0, PDHG_FP32 = 1 };
+enum { PDHG_INIT_LAMBDA = 0, PDHG_INIT_PINNED = 1 };
+enum { PDHG_PATH_AUTO = 0, PDHG_PATH_PLAIN = 1, PDHG_PATH_FUSED = 2 };
+enum { PDHG_FIELD_U = 0, PDHG_FIELD_PHI = 1, PDHG_FIELD_PHIT = 2,
+       PDHG_FIELD_LAMBDA = 3, PDHG_FIELD_LAMBDAT = 4, PDHG_FIELD_U_TERMINAL = 5 };
+
+/* Stages of one iteration, for pdhg_stage_times(). */
+enum { PDHG_STAGE_PRIMAL = 0,      /* primal step + lambda update (Algorithm 1 steps 1, 2b) */
+       PDHG_STAGE_RESIDUAL_FFT = 1,/* R(u^n) and its forward x-transform */
+       PDHG_STAGE_FFT_Y = 2,       /* 2D: forward and inverse y-transforms */
+       PDHG_STAGE_TSOLVE = 3,      /* tridiagonal solve in t per Fourier mode */
+       PDHG_STAGE_DUAL = 4,        /* inverse x-transform, dual step and extrapolation */
+       PDHG_STAGE_CHECK = 5,       /* residual norms (every check_every iterations) */
+       PDHG_STAGE_FUSED_ROWS = 6,  /* fused path: dual update + primal + residual + x-FFT */
+       PDHG_STAGE_FUSED_COLS = 7,  /* fused path: y-FFT + t-solve + inverse y-FFT */
+       PDHG_NUM_STAGES = 8 };
+
+/*
+ * The conservation law u_t + f(u)_x - (gamma u_x)_x = 0 on a periodic domain
+ * (Eq. 2.1; 2D: f(u)_x + f(u)_y), the preconditioner and the step sizes.
+ *   f(u) = alpha*u^2 + beta*u                   (Sec. 3.2.3; linear: alpha = 0)
+ *   nu          constant viscosity: adds -nu * central second difference
+ *   gamma_half  host pointer to gamma_{j+1/2}, j = 0..nx-1 (1D FD only) or NULL;
+ *               adds -Lap(u) of Sec. 3.2.1.  Copied at create.
+ *   u0          host pointer to the initial slice (dof layout above). Copied at create.
+ *   lf_a        global Lax-Friedrichs constant (> 0 for FD_LF and DG_P2_LF)
+ *   c, gamma_hat  K = -d_tt - c^2 d_xx + gamma_hat^2 d_xxxx (Eq. 2.8, 2.10);
+ *                 DG uses c only.
+ *   tau_u, tau_u0, tau_phi, tau_lambda   step sizes of Algorithm 1 (> 0).
+ */
+typedef struct {
+    double alpha, beta;
+    double nu;
+    const double *gamma_half;
+    const double *u0;
+    double lf_a;
+    double c, gamma_hat;
+    double tau_u, tau_u0, tau_phi, tau_lambda;
+} pdhg_problem;
+
+/* Uniform space-time grid (Sec. 3.1, 3.2): h_x = lx/nx, h_y = ly/ny, h_t = T/nt.
+ * dims = 1 or 2; ny = 1 in 1D; for DG, nx is the number of cells. */
+typedef struct {
+    int32_t dims;
+    int64_t nx, ny;
+    double lx, ly;
+    double T;
+    int64_t nt;
+} pdhg_grid;
+
+/* time: PDHG_TIME_*; space: PDHG_SPACE_*; precision: PDHG_FP64 / PDHG_FP32;
+ * init: PDHG_INIT_LAMBDA (Algorithm 1's multiplier on u^0 = u0) or
+ * PDHG_INIT_PINNED (u^0 held at u0); path: PDHG_PATH_*; flags: 0. */
+typedef struct {
+    int32_t time, space, precision, init, path, flags;
+} pdhg_scheme;
+
+typedef struct pdhg_handle pdhg_handle;
+
+/* Bytes of device workspace that pdhg_create() needs for this problem. */
+pdhg_status pdhg_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                const pdhg_scheme *scheme, size_t *bytes);
+
+/* Validate, lay out the workspace, upload u0 and the preconditioner tables,
+ * and set the initial guess [u0 extended in t, 0, 0] (Sec. 3.3).  The
+ * workspace (device pointer, >= pdhg_workspace_size bytes, 256-byte aligned)
+ * stays owned by the caller.  Synchronises the stream before returning. */
+pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *grid,
+                        const pdhg_scheme *scheme, void *workspace, size_t bytes,
+                        void *stream, pdhg_handle **out);
+
+/* Free the host handle (the workspace is the caller's to free). NULL is a no-op. */
+pdhg_status pdhg_destroy(pdhg_handle *h);
+
+/* Change the stream used by later calls. */
+pdhg_status pdhg_set_stream(pdhg_handle *h, void *stream);
+
+/* Run iterations of Algorithm 1.
+ * check_every > 0: every check_every iterations compute Res (Eq. 2.12) and stop
+ *   once both entries are <= tol (absolute; relative to ||A(u_init)|| when
+ *   relative != 0); synchronises at each check.  Returns NONFINITE/DIVERGED on
+ *   a bad residual.
+ * check_every <= 0: enqueue max_iters iterations asynchronously (no host sync).
+ * *iters_done (may be NULL) receives the iterations performed by this call. */
+pdhg_status pdhg_iterate(pdhg_handle *h, int64_t max_iters, double tol, int32_t check_every,
+                         int32_t relative, int64_t *iters_done);
+
+/* Res of Eq. 2.12 at the current state, absolute, synchronously:
+ * out[0] = ||A(u)|| (equations and initial row), out[1] = ||grad_u L|| =
+ * ||J(u)^T phi|| (rows l >= 1, plus the u^0 row h_t (J^T phi)^0 + lambda with
+ * init LAMBDA), out[2] = ||u^0 - u0||, out[3] = the Lagrangian <phi, R(u)> +
+ * <lambda, u^0 - u0> (the duality-gap diagnostic; the objective is 0).
+ * Norms are discrete L2 with weights h_t*w_x per equation dof, w_x per
+ * initial-row dof (w_x = h_x, or h_x*h_y in 2D). */
+pdhg_status pdhg_residual(pdhg_handle *h, double out[4]);
+
+/* Copy a field (PDHG_FIELD_*) out of / into the state.  dst/src has the
+ * handle's element type; on_device != 0 means a device pointer.  Sizes in
+ * elements: U (nt+1)*ndof, U_TERMINAL ndof (get only), PHI/PHIT nt*ndof,
+ * LAMBDA/LAMBDAT ndof.  Synchronous. */
+pdhg_status pdhg_get_field(pdhg_handle *h, int32_t field, void *dst, int32_t on_device);
+pdhg_status pdhg_set_field(pdhg_handle *h, int32_t field, const void *src, int32_t on_device);
+
+/* Element counts and iteration counter of the handle. */
+pdhg_status pdhg_info(pdhg_handle *h, int64_t *ndof, int64_t *nt, int64_t *iterations,
+                      int32_t *precision, int32_t *path);
+
+/* Kernel launches issued by this handle since create (or the last reset). */
+pdhg_status pdhg_launch_count(pdhg_handle *h, int64_t *launches, int32_t reset);
+
+/* Per-stage timing with CUDA events on the handle's stream.  While enabled,
+ * pdhg_iterate records an event pair around every stage launch; stage_times
+ * returns accumulated milliseconds and launch counts per PDHG_STAGE_* and
+ * resets them.  Synchronises the stream. */
+pdhg_status pdhg_set_profiling(pdhg_handle *h, int32_t enable);
+pdhg_status pdhg_stage_times(pdhg_handle *h, double ms[PDHG_NUM_STAGES],
+                             int64_t launches[PDHG_NUM_STAGES]);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *pdhg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDHG_H */

@@ -1,0 +1,238 @@
+"""Thin ctypes binding of include/pdhg.h (argument marshalling only).
+
+Every step of the PDHG iteration runs in libpdhg.so's CUDA kernels; PyTorch is
+used here only to own the device workspace and to supply the CUDA stream.
+Importing this module loads the library and raises if it is missing: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpdhg.so")
+
+# ---- enums (mirror include/pdhg.h) ----
+OK = 0
+STATUS = {0: "PDHG_OK", -1: "PDHG_ERR_INVALID_ARG", -2: "PDHG_ERR_WORKSPACE_TOO_SMALL",
+          -3: "PDHG_ERR_CUDA", -4: "PDHG_ERR_NONFINITE", -5: "PDHG_ERR_DIVERGED",
+          -6: "PDHG_ERR_TIMEOUT", -7: "PDHG_ERR_UNSUPPORTED"}
+TIME = {"be": 0, "bdf2": 1}
+SPACE = {"fd_upwind": 0, "fd_lf": 1, "dg_p2_lf": 2}
+PRECISION = {"fp64": 0, "fp32": 1}
+INIT = {"lambda": 0, "pinned": 1}
+PATH = {"auto": 0, "plain": 1, "fused": 2}
+FIELD = {"u": 0, "phi": 1, "phit": 2, "lambda": 3, "lambdat": 4, "u_terminal": 5}
+STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_rows", "fused_cols"]
+
+# every symbol include/pdhg.h declares
+EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_stream", "pdhg_iterate",
+           "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_info", "pdhg_launch_count",
+           "pdhg_set_profiling", "pdhg_stage_times", "pdhg_last_error"]
+
+
+class PdhgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pdhg_problem(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("nu", ctypes.c_double),
+                ("gamma_half", ctypes.POINTER(ctypes.c_double)), ("u0", ctypes.POINTER(ctypes.c_double)),
+                ("lf_a", ctypes.c_double), ("c", ctypes.c_double), ("gamma_hat", ctypes.c_double),
+                ("tau_u", ctypes.c_double), ("tau_u0", ctypes.c_double), ("tau_phi", ctypes.c_double),
+                ("tau_lambda", ctypes.c_double)]
+
+
+class pdhg_grid(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("T", ctypes.c_double),
+                ("nt", ctypes.c_int64)]
+
+
+class pdhg_scheme(ctypes.Structure):
+    _fields_ = [("time", ctypes.c_int32), ("space", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("init", ctypes.c_int32), ("path", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpdhg.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P, G, S = ctypes.POINTER(pdhg_problem), ctypes.POINTER(pdhg_grid), ctypes.POINTER(pdhg_scheme)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "pdhg_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_create": [P, G, S, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "pdhg_destroy": [vp],
+        "pdhg_set_stream": [vp, vp],
+        "pdhg_iterate": [vp, i64, ctypes.c_double, i32, i32, ctypes.POINTER(i64)],
+        "pdhg_residual": [vp, ctypes.POINTER(ctypes.c_double)],
+        "pdhg_get_field": [vp, i32, vp, i32],
+        "pdhg_set_field": [vp, i32, vp, i32],
+        "pdhg_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                      ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "pdhg_launch_count": [vp, ctypes.POINTER(i64), i32],
+        "pdhg_set_profiling": [vp, i32],
+        "pdhg_stage_times": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.pdhg_last_error.argtypes = []
+    lib.pdhg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != OK:
+        raise PdhgError(status, load().pdhg_last_error().decode())
+
+
+def structs(p, precision="fp32", path="auto"):
+    """C structs for a pdhg_workloads.Problem; returns (prob, grid, scheme, keepalive)."""
+    u0 = np.ascontiguousarray(p.u0, dtype=np.float64).ravel()
+    keep = [u0]
+    prob = pdhg_problem()
+    prob.alpha, prob.beta, prob.nu = p.alpha, p.beta, p.nu
+    prob.u0 = u0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if p.gamma_half is not None:
+        g = np.ascontiguousarray(p.gamma_half, dtype=np.float64)
+        keep.append(g)
+        prob.gamma_half = g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    prob.lf_a, prob.c, prob.gamma_hat = p.lf_a, p.c, p.gamma_hat
+    prob.tau_u, prob.tau_u0, prob.tau_phi, prob.tau_lambda = p.tau_u, p.tau_u0, p.tau_phi, p.tau_lambda
+    grid = pdhg_grid(p.dims, p.nx, p.ny if p.dims == 2 else 1, p.lx, p.ly, p.T, p.nt)
+    scheme = pdhg_scheme(TIME[p.time], SPACE[p.space], PRECISION[precision], INIT[p.init], PATH[path], 0)
+    return prob, grid, scheme, keep
+
+
+def workspace_size(p, precision="fp32", path="auto") -> int:
+    prob, grid, scheme, _keep = structs(p, precision, path)
+    n = ctypes.c_size_t(0)
+    _check(load().pdhg_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                      ctypes.byref(n)))
+    return n.value
+
+
+class Solver:
+    """One space-time problem on the GPU (a pdhg_handle plus its torch-owned workspace)."""
+
+    def __init__(self, p, precision="fp32", path="auto", device=None, stream=None):
+        import torch
+        self._torch = torch
+        self.p = p
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.device = torch.device(device if device is not None else "cuda")
+        lib = load()
+        prob, grid, scheme, keep = structs(p, precision, path)
+        nbytes = ctypes.c_size_t(0)
+        _check(lib.pdhg_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                       ctypes.byref(nbytes)))
+        self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._stream = s
+        h = ctypes.c_void_p()
+        _check(lib.pdhg_create(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                               ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                               ctypes.c_void_p(s.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        self.ndof = p.ndof
+        self.nt = p.nt
+
+    # ---- lifecycle ----
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().pdhg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- iteration ----
+    def iterate(self, n, tol=0.0, check_every=0, relative=False) -> int:
+        done = ctypes.c_int64(0)
+        _check(load().pdhg_iterate(self.h, int(n), float(tol), int(check_every), int(bool(relative)),
+                                   ctypes.byref(done)))
+        return done.value
+
+    def residual(self) -> np.ndarray:
+        out = (ctypes.c_double * 4)()
+        _check(load().pdhg_residual(self.h, out))
+        return np.array(list(out))
+
+    def info(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        d, e = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().pdhg_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                ctypes.byref(d), ctypes.byref(e)))
+        return {"ndof": a.value, "nt": b.value, "iterations": c.value, "precision": d.value,
+                "path": {1: "plain", 2: "fused"}.get(e.value, e.value)}
+
+    def launches(self, reset=False) -> int:
+        n = ctypes.c_int64()
+        _check(load().pdhg_launch_count(self.h, ctypes.byref(n), int(bool(reset))))
+        return n.value
+
+    def set_profiling(self, on=True):
+        _check(load().pdhg_set_profiling(self.h, int(bool(on))))
+
+    def stage_times(self):
+        ms = (ctypes.c_double * 8)()
+        n = (ctypes.c_int64 * 8)()
+        _check(load().pdhg_stage_times(self.h, ms, n))
+        return {STAGES[i]: (ms[i], n[i]) for i in range(8) if n[i] > 0}
+
+    # ---- fields ----
+    def _shape(self, field):
+        sl = tuple(self.p.slice_shape)
+        return {"u": (self.nt + 1,) + sl, "u_terminal": sl, "phi": (self.nt,) + sl,
+                "phit": (self.nt,) + sl, "lambda": sl, "lambdat": sl}[field]
+
+    def get(self, field):
+        """Device copy of a field as a torch tensor of the handle's dtype."""
+        t = self._torch.empty(self._shape(field), dtype=self.dtype, device=self.device)
+        _check(load().pdhg_get_field(self.h, FIELD[field], ctypes.c_void_p(t.data_ptr()), 1))
+        return t
+
+    def get_host(self, field, out=None):
+        """Copy a field into a host numpy array (pinned or pageable)."""
+        np_dtype = np.float64 if self.precision == "fp64" else np.float32
+        a = out if out is not None else np.empty(self._shape(field), dtype=np_dtype)
+        _check(load().pdhg_get_field(self.h, FIELD[field], ctypes.c_void_p(a.ctypes.data), 0))
+        return a
+
+    def set(self, field, value):
+        t = self._torch.as_tensor(value, dtype=self.dtype, device=self.device).contiguous()
+        assert tuple(t.shape) == self._shape(field)
+        _check(load().pdhg_set_field(self.h, FIELD[field], ctypes.c_void_p(t.data_ptr()), 1))
+
+
+def solve(p, precision="fp32", max_iters=10000, tol=1e-6, check_every=50, relative=True, path="auto"):
+    """Convenience: run Algorithm 1 to tolerance; returns (u as numpy, iterations, Res)."""
+    with Solver(p, precision=precision, path=path) as s:
+        it = s.iterate(max_iters, tol=tol, check_every=check_every, relative=relative)
+        return s.get_host("u"), it, s.residual()

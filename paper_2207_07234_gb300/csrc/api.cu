@@ -1,0 +1,619 @@
+// api.cu -- the C ABI of include/pdhg.h: validation, workspace layout, host
+// preparation of the preconditioner tables, and the iteration driver of
+// Algorithm 1 (Sec. 3.3).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/pdhg.h"
+#include "fused2d.h"
+#include "plain.h"
+
+using namespace pdhg;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static pdhg_status fail(pdhg_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+static pdhg_status cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return PDHG_ERR_CUDA;
+}
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+extern "C" const char *pdhg_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// layout
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Layout {
+    size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, partials, scal, fused;
+    size_t total;
+};
+
+inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+inline int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Geom {
+    int dims, space, time, init, prec, path;
+    int64_t nx, ny, nt, S, nkx, lines, modes;
+    size_t esz;      // element size
+    bool has_gamma;
+    bool fused;
+};
+
+pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s, Geom *G) {
+    if (!p || !g || !s) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
+    if (g->dims != 1 && g->dims != 2) return fail(PDHG_ERR_INVALID_ARG, "dims must be 1 or 2");
+    if (s->time != PDHG_TIME_BE && s->time != PDHG_TIME_BDF2) return fail(PDHG_ERR_INVALID_ARG, "bad time scheme");
+    if (s->space < PDHG_SPACE_FD_UPWIND || s->space > PDHG_SPACE_DG_P2_LF)
+        return fail(PDHG_ERR_INVALID_ARG, "bad space scheme");
+    if (s->precision != PDHG_FP64 && s->precision != PDHG_FP32) return fail(PDHG_ERR_INVALID_ARG, "bad precision");
+    if (s->init != PDHG_INIT_LAMBDA && s->init != PDHG_INIT_PINNED) return fail(PDHG_ERR_INVALID_ARG, "bad init");
+    if (s->path < PDHG_PATH_AUTO || s->path > PDHG_PATH_FUSED) return fail(PDHG_ERR_INVALID_ARG, "bad path");
+    if (g->nt < 1 || g->nt > 65534) return fail(PDHG_ERR_INVALID_ARG, "nt must be in [1, 65534]");
+    if (g->nx < 1 || (g->dims == 2 && g->ny < 1)) return fail(PDHG_ERR_INVALID_ARG, "nx, ny must be positive");
+    if (!(g->T > 0) || !(g->lx > 0) || (g->dims == 2 && !(g->ly > 0)))
+        return fail(PDHG_ERR_INVALID_ARG, "T, lx, ly must be positive");
+    if (!p->u0) return fail(PDHG_ERR_INVALID_ARG, "u0 is NULL");
+    if (!(p->tau_u > 0) || !(p->tau_phi > 0)) return fail(PDHG_ERR_INVALID_ARG, "tau_u, tau_phi must be > 0");
+    if (s->init == PDHG_INIT_LAMBDA && (!(p->tau_u0 > 0) || !(p->tau_lambda > 0)))
+        return fail(PDHG_ERR_INVALID_ARG, "tau_u0, tau_lambda must be > 0");
+    if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !(p->nu >= 0) || !std::isfinite(p->nu) ||
+        !std::isfinite(p->c) || !std::isfinite(p->gamma_hat) || !(p->lf_a >= 0) || !std::isfinite(p->lf_a))
+        return fail(PDHG_ERR_INVALID_ARG, "non-finite or negative coefficient");
+    if (s->space == PDHG_SPACE_DG_P2_LF) {
+        if (g->dims != 1) return fail(PDHG_ERR_UNSUPPORTED, "DG P2 is 1D only");
+        if (p->gamma_half) return fail(PDHG_ERR_UNSUPPORTED, "DG P2 has no variable-coefficient Laplacian");
+        if (p->nu != 0) return fail(PDHG_ERR_UNSUPPORTED, "DG P2 has no viscous term");
+        if (p->gamma_hat != 0) return fail(PDHG_ERR_UNSUPPORTED, "DG P2 preconditioner uses c only");
+    }
+    if (g->dims == 2 && p->gamma_half) return fail(PDHG_ERR_UNSUPPORTED, "gamma_half is 1D only");
+    if (!is_pow2(g->nx) || g->nx < 4 || g->nx > 8192)
+        return fail(PDHG_ERR_UNSUPPORTED, "nx must be a power of two in [4, 8192]");
+    if (g->dims == 2 && (!is_pow2(g->ny) || g->ny < 4 || g->ny > 2048))
+        return fail(PDHG_ERR_UNSUPPORTED, "ny must be a power of two in [4, 2048]");
+    G->dims = g->dims; G->space = s->space; G->time = s->time; G->init = s->init;
+    G->prec = s->precision; G->path = s->path;
+    G->nx = g->nx; G->ny = g->dims == 2 ? g->ny : 1; G->nt = g->nt;
+    G->S = s->space == PDHG_SPACE_DG_P2_LF ? 3 * g->nx : g->nx * G->ny;
+    G->nkx = g->nx / 2 + 1;
+    G->lines = s->space == PDHG_SPACE_DG_P2_LF ? 3 : G->ny;
+    G->modes = s->space == PDHG_SPACE_DG_P2_LF ? 3 * G->nkx : G->lines * G->nkx;
+    G->esz = s->precision == PDHG_FP64 ? 8 : 4;
+    G->has_gamma = p->gamma_half != nullptr;
+    G->fused = false;
+    if (s->path == PDHG_PATH_FUSED || s->path == PDHG_PATH_AUTO) {
+        bool ok = fused2d_supported(g->dims, s->space, s->time, s->precision, g->nx, G->ny, g->nt, p->nu);
+        if (s->path == PDHG_PATH_FUSED && !ok)
+            return fail(PDHG_ERR_UNSUPPORTED, "the fused path needs 2D FD, FP32, nx = ny in {256..1024}");
+        G->fused = ok;
+    }
+    return PDHG_OK;
+}
+
+Layout layout_of(const Geom &G) {
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    const size_t e = G.esz;
+    L.u = take((G.nt + 1) * G.S * e);
+    L.phi = take(G.nt * G.S * e);
+    L.phit = take(G.nt * G.S * e);
+    L.lam = take(G.S * e);
+    L.lamt = take(G.S * e);
+    L.u0 = take(G.S * e);
+    L.gamma = take(G.has_gamma ? G.S * e : 0);
+    L.spec = take(G.fused ? 0 : (size_t)G.nt * G.lines * G.nkx * 2 * e);
+    L.twx = take(G.nkx * 2 * e);
+    L.twy = take(G.dims == 2 ? G.ny * 2 * e : 0);
+    L.theta = take(G.modes * e);
+    L.V = take(G.space == PDHG_SPACE_DG_P2_LF ? G.nkx * 9 * 2 * e : 0);
+    int64_t units = G.space == PDHG_SPACE_DG_P2_LF ? G.nx : G.S;
+    int64_t nblk = ((units + 255) / 256) * (G.nt + 1);
+    L.partials = take(nblk * 6 * sizeof(double));
+    L.scal = take(16 * sizeof(double));
+    L.fused = take(G.fused ? fused2d_workspace_bytes(G.nx, G.ny, G.nt) : 0);
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// host tables
+// ---------------------------------------------------------------------------
+typedef std::complex<double> cd;
+
+// theta with cosh(theta) = 1 + s/2, i.e. theta = 2 asinh(sqrt(s)/2), s = kappa h_t^2 >= 0
+double theta_of(double s) { return s <= 0 ? 0.0 : 2.0 * std::asinh(0.5 * std::sqrt(s)); }
+
+// L(theta_k) = (2 - 2 cos(2 pi k/n))/h^2 written as 4 sin^2(pi k/n)/h^2
+double symbol_L(int64_t k, int64_t n, double h) {
+    double s = std::sin(M_PI * (double)k / (double)n);
+    return 4.0 * s * s / (h * h);
+}
+
+// Cyclic Jacobi for a 3x3 Hermitian matrix: A = V diag(w) V^H.
+void jacobi_herm3(cd A[3][3], double w[3], cd V[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = std::abs(A[0][1]) + std::abs(A[0][2]) + std::abs(A[1][2]);
+        double dia = std::abs(A[0][0].real()) + std::abs(A[1][1].real()) + std::abs(A[2][2].real());
+        if (off <= 1e-300 || off <= 1e-17 * dia) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                double r = std::abs(A[p][q]);
+                if (r == 0.0) continue;
+                cd ph = A[p][q] / r;                      // A_pq = r e^{i phi}
+                double app = A[p][p].real(), aqq = A[q][q].real();
+                double tau = (aqq - app) / (2.0 * r);
+                double t = (tau >= 0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
+                double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+                // unitary G acting on columns p, q: col_p' = c col_p - s conj(ph) col_q, col_q' = s ph col_p + c col_q
+                cd gpp = c, gqp = -s * std::conj(ph), gpq = s * ph, gqq = c;
+                for (int k = 0; k < 3; ++k) {               // A <- A G
+                    cd akp = A[k][p], akq = A[k][q];
+                    A[k][p] = akp * gpp + akq * gqp;
+                    A[k][q] = akp * gpq + akq * gqq;
+                }
+                for (int k = 0; k < 3; ++k) {               // A <- G^H A
+                    cd apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = std::conj(gpp) * apk + std::conj(gqp) * aqk;
+                    A[q][k] = std::conj(gpq) * apk + std::conj(gqq) * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {               // V <- V G
+                    cd vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = vkp * gpp + vkq * gqp;
+                    V[k][q] = vkp * gpq + vkq * gqq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; ++i) w[i] = A[i][i].real();
+}
+
+// S(theta) of the DG P2 operator of c u_x with the upwind flux (Lax-Friedrichs
+// with a = |c|): D_m = -(2m+1)/h [vol_m - Fh_{j+1/2} + (-1)^m Fh_{j-1/2}],
+// vol_1 = 2 c U_0, vol_2 = 2 c U_1, Fh_{j+1/2} = cp uR_j + cm uL_{j+1}.
+void dg_symbol(double c, double h, double theta, cd S[3][3]) {
+    double cp = 0.5 * (c + std::fabs(c)), cm = 0.5 * (c - std::fabs(c));
+    cd em = std::exp(cd(0, -theta)), ep = std::exp(cd(0, theta));
+    for (int m = 0; m < 3; ++m) {
+        double sm = (m % 2) ? -1.0 : 1.0;
+        for (int n = 0; n < 3; ++n) {
+            double sn = (n % 2) ? -1.0 : 1.0;
+            double vol = (m == 1 && n == 0) ? 2 * c : (m == 2 && n == 1) ? 2 * c : 0.0;
+            double s0 = vol - cp + sm * cm * sn;       // from U_j
+            double sl = sm * cp;                        // from U_{j-1}
+            double sr = -cm * sn;                       // from U_{j+1}
+            double f = -(2 * m + 1) / h;
+            S[m][n] = f * (cd(s0) + cd(sl) * em + cd(sr) * ep);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct EvRec { int stage; cudaEvent_t a, b; };
+
+struct pdhg_handle {
+    Geom G;
+    Layout L;
+    char *ws;
+    cudaStream_t stream;
+    Params<float> pf;
+    Params<double> pd;
+    double ht, wx;
+    int64_t iters;
+    double res_init;
+    int64_t launches;
+    bool profiling;
+    std::vector<EvRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double stage_ms[PDHG_NUM_STAGES];
+    int64_t stage_n[PDHG_NUM_STAGES];
+    Fused2D fused;
+};
+
+template <typename T> static Params<T> &params_of(pdhg_handle *h);
+template <> Params<float> &params_of<float>(pdhg_handle *h) { return h->pf; }
+template <> Params<double> &params_of<double>(pdhg_handle *h) { return h->pd; }
+
+template <typename T> static T *F(pdhg_handle *h, size_t off) { return reinterpret_cast<T *>(h->ws + off); }
+
+static cudaEvent_t ev_get(pdhg_handle *h) {
+    if (!h->pool.empty()) { cudaEvent_t e = h->pool.back(); h->pool.pop_back(); return e; }
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// run one stage launch, bracketed by events when profiling
+template <typename Fn>
+static cudaError_t stage(pdhg_handle *h, int st, int nlaunch, Fn fn) {
+    EvRec r{st, nullptr, nullptr};
+    if (h->profiling) {
+        r.a = ev_get(h); r.b = ev_get(h);
+        if (r.a) cudaEventRecord(r.a, h->stream);
+    }
+    cudaError_t e = fn();
+    h->launches += nlaunch;
+    if (h->profiling && r.b) {
+        cudaEventRecord(r.b, h->stream);
+        h->recs.push_back(r);
+    }
+    return e;
+}
+
+template <typename T>
+static void fill_params(Params<T> &P, const Geom &G, const pdhg_problem *p, const pdhg_grid *g, double lf_a) {
+    memset(&P, 0, sizeof(P));
+    P.dims = G.dims; P.space = G.space; P.time = G.time; P.init = G.init;
+    P.nx = (int32_t)G.nx; P.ny = (int32_t)G.ny; P.nt = (int32_t)G.nt;
+    P.log2m = ilog2(G.nx / 2); P.log2ny = G.dims == 2 ? ilog2(G.ny) : 0;
+    P.S = G.S; P.nkx = (int32_t)G.nkx; P.lines = (int32_t)G.lines;
+    double ht = g->T / (double)g->nt, hx = g->lx / (double)g->nx;
+    double hy = G.dims == 2 ? g->ly / (double)g->ny : 1.0;
+    P.alpha = (T)p->alpha; P.beta = (T)p->beta; P.nu = (T)p->nu; P.lf_a = (T)lf_a;
+    P.ht = (T)ht; P.inv_ht = (T)(1.0 / ht); P.inv_hx = (T)(1.0 / hx); P.inv_hy = (T)(1.0 / hy);
+    P.tau_u = (T)p->tau_u; P.tau_u0 = (T)p->tau_u0; P.tau_phi = (T)p->tau_phi; P.tau_lambda = (T)p->tau_lambda;
+    P.dual_scale = (T)(p->tau_phi * ht * ht / ((double)(G.nx / 2) * (double)G.ny));
+    P.gamma_half = nullptr;
+}
+
+extern "C" pdhg_status pdhg_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                           const pdhg_scheme *scheme, size_t *bytes) {
+    Geom G;
+    pdhg_status st = validate(prob, grid, scheme, &G);
+    if (st != PDHG_OK) return st;
+    if (!bytes) return fail(PDHG_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = layout_of(G).total;
+    return PDHG_OK;
+}
+
+template <typename T>
+static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pdhg_grid *g, double lf_a) {
+    const Geom &G = h->G;
+    cudaStream_t s = h->stream;
+    std::vector<T> buf;
+    // u0 extended in t; phi = phit = 0; lambda = lambdat = 0 (Sec. 3.3)
+    buf.resize(G.S);
+    for (int64_t i = 0; i < G.S; ++i) buf[i] = (T)p->u0[i];
+    CK(cudaMemcpyAsync(F<T>(h, h->L.u0), buf.data(), G.S * sizeof(T), cudaMemcpyHostToDevice, s));
+    for (int64_t l = 0; l <= G.nt; ++l)
+        CK(cudaMemcpyAsync(F<T>(h, h->L.u) + l * G.S, F<T>(h, h->L.u0), G.S * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(F<T>(h, h->L.phi), 0, G.nt * G.S * sizeof(T), s));
+    CK(cudaMemsetAsync(F<T>(h, h->L.phit), 0, G.nt * G.S * sizeof(T), s));
+    CK(cudaMemsetAsync(F<T>(h, h->L.lam), 0, G.S * sizeof(T), s));
+    CK(cudaMemsetAsync(F<T>(h, h->L.lamt), 0, G.S * sizeof(T), s));
+    CK(cudaStreamSynchronize(s));
+    if (G.has_gamma) {
+        for (int64_t i = 0; i < G.S; ++i) buf[i] = (T)p->gamma_half[i];
+        CK(cudaMemcpy(F<T>(h, h->L.gamma), buf.data(), G.S * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    // twiddles W_N^k = exp(-2 pi i k/N)
+    std::vector<T> tw(2 * G.nkx);
+    for (int64_t k = 0; k < G.nkx; ++k) {
+        double a = 2.0 * M_PI * (double)k / (double)G.nx;
+        tw[2 * k] = (T)std::cos(a); tw[2 * k + 1] = (T)(-std::sin(a));
+    }
+    CK(cudaMemcpy(F<T>(h, h->L.twx), tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (G.dims == 2) {
+        std::vector<T> twy(2 * G.ny);
+        for (int64_t k = 0; k < G.ny; ++k) {
+            double a = 2.0 * M_PI * (double)k / (double)G.ny;
+            twy[2 * k] = (T)std::cos(a); twy[2 * k + 1] = (T)(-std::sin(a));
+        }
+        CK(cudaMemcpy(F<T>(h, h->L.twy), twy.data(), twy.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    // preconditioner: theta per Fourier mode (and the DG eigenvectors)
+    double ht = g->T / (double)g->nt, hx = g->lx / (double)g->nx;
+    double hy = G.dims == 2 ? g->ly / (double)g->ny : 1.0;
+    std::vector<T> th(G.modes);
+    if (G.space == PDHG_SPACE_DG_P2_LF) {
+        std::vector<T> V(G.nkx * 18);
+        for (int64_t k = 0; k < G.nkx; ++k) {
+            cd S[3][3], A[3][3], Vm[3][3];
+            double w[3];
+            dg_symbol(p->c, hx, 2.0 * M_PI * (double)k / (double)G.nx, S);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    cd acc = 0;
+                    for (int m = 0; m < 3; ++m) acc += std::conj(S[m][i]) * S[m][j];
+                    A[i][j] = acc;
+                }
+            jacobi_herm3(A, w, Vm);
+            for (int i = 0; i < 3; ++i) th[k * 3 + i] = (T)theta_of(std::max(w[i], 0.0) * ht * ht);
+            for (int m = 0; m < 3; ++m)
+                for (int i = 0; i < 3; ++i) {
+                    V[(k * 9 + m * 3 + i) * 2] = (T)Vm[m][i].real();
+                    V[(k * 9 + m * 3 + i) * 2 + 1] = (T)Vm[m][i].imag();
+                }
+        }
+        CK(cudaMemcpy(F<T>(h, h->L.V), V.data(), V.size() * sizeof(T), cudaMemcpyHostToDevice));
+    } else {
+        for (int64_t ky = 0; ky < G.lines; ++ky)
+            for (int64_t kx = 0; kx < G.nkx; ++kx) {
+                double L = symbol_L(kx, G.nx, hx) + (G.dims == 2 ? symbol_L(ky, G.ny, hy) : 0.0);
+                double kappa = p->c * p->c * L + p->gamma_hat * p->gamma_hat * L * L;
+                th[ky * G.nkx + kx] = (T)theta_of(kappa * ht * ht);
+            }
+    }
+    CK(cudaMemcpy(F<T>(h, h->L.theta), th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
+    Params<T> &P = params_of<T>(h);
+    fill_params(P, G, p, g, lf_a);
+    if (G.has_gamma) P.gamma_half = F<T>(h, h->L.gamma);
+    CK(init_plain_attributes<T>());
+    return PDHG_OK;
+}
+
+template <typename T>
+static cudaError_t enqueue_check(pdhg_handle *h) {
+    const Params<T> &P = params_of<T>(h);
+    return stage(h, PDHG_STAGE_CHECK, 2, [&] {
+        return launch_check<T>(P, F<T>(h, h->L.u), F<T>(h, h->L.phi), F<T>(h, h->L.lam), F<T>(h, h->L.u0),
+                               F<double>(h, h->L.partials), F<double>(h, h->L.scal), h->stream);
+    });
+}
+
+static pdhg_status read_res(pdhg_handle *h, double out[4]) {
+    double acc[6];
+    CK(cudaMemcpyAsync(acc, h->ws + h->L.scal, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double ht = h->ht, wx = h->wx;
+    double a2 = ht * wx * acc[0], b2 = ht * wx * acc[1], gap = ht * wx * acc[2], c2 = wx * acc[3];
+    if (h->G.init == PDHG_INIT_LAMBDA) {
+        a2 += c2;
+        b2 += wx * acc[4];
+        gap += wx * acc[5];
+    }
+    out[0] = std::sqrt(a2); out[1] = std::sqrt(b2); out[2] = std::sqrt(c2); out[3] = gap;
+    return PDHG_OK;
+}
+
+template <typename T>
+static pdhg_status compute_res(pdhg_handle *h, double out[4]) {
+    cudaError_t e = enqueue_check<T>(h);
+    if (e != cudaSuccess) return cuda_fail(e, "residual check");
+    return read_res(h, out);
+}
+
+extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                   void *workspace, size_t bytes, void *stream, pdhg_handle **out) {
+    Geom G;
+    pdhg_status st = validate(prob, grid, scheme, &G);
+    if (st != PDHG_OK) return st;
+    if (!out) return fail(PDHG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    Layout L = layout_of(G);
+    if (!workspace) return fail(PDHG_ERR_INVALID_ARG, "workspace is NULL");
+    if (((uintptr_t)workspace & 255) != 0) return fail(PDHG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (bytes < L.total) return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small: need " + std::to_string(L.total));
+    // LF constant: explicit, or max |f'(u0)| when 0
+    double lf_a = prob->lf_a;
+    for (int64_t i = 0; i < G.S; ++i)
+        if (!std::isfinite(prob->u0[i])) return fail(PDHG_ERR_INVALID_ARG, "u0 has a non-finite value");
+    if ((G.space == PDHG_SPACE_FD_LF || G.space == PDHG_SPACE_DG_P2_LF) && lf_a == 0.0) {
+        for (int64_t i = 0; i < G.S; ++i) lf_a = std::max(lf_a, std::fabs(2 * prob->alpha * prob->u0[i] + prob->beta));
+        if (lf_a == 0.0) lf_a = 1.0;
+    }
+    if (G.has_gamma)
+        for (int64_t i = 0; i < G.nx; ++i)
+            if (!std::isfinite(prob->gamma_half[i])) return fail(PDHG_ERR_INVALID_ARG, "gamma_half non-finite");
+    pdhg_handle *h = new pdhg_handle();
+    h->G = G; h->L = L; h->ws = (char *)workspace; h->stream = (cudaStream_t)stream;
+    h->ht = grid->T / (double)grid->nt;
+    double hx = grid->lx / (double)grid->nx;
+    h->wx = G.dims == 2 ? hx * (grid->ly / (double)grid->ny) : hx;
+    h->iters = 0; h->launches = 0; h->profiling = false;
+    memset(h->stage_ms, 0, sizeof(h->stage_ms));
+    memset(h->stage_n, 0, sizeof(h->stage_n));
+    st = (G.prec == PDHG_FP64) ? upload_tables<double>(h, prob, grid, lf_a) : upload_tables<float>(h, prob, grid, lf_a);
+    if (st == PDHG_OK && G.fused) {
+        cudaError_t e = fused2d_init(&h->fused, h->pf, h->ws + L.fused, F<float>(h, L.twx), F<float>(h, L.twy),
+                                     F<float>(h, L.theta));
+        if (e != cudaSuccess) st = cuda_fail(e, "fused2d_init");
+    }
+    double r[4];
+    if (st == PDHG_OK) st = (G.prec == PDHG_FP64) ? compute_res<double>(h, r) : compute_res<float>(h, r);
+    if (st != PDHG_OK) { delete h; return st; }
+    h->res_init = r[0];
+    h->launches = 0;
+    *out = h;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_destroy(pdhg_handle *h) {
+    if (!h) return PDHG_OK;
+    for (auto &r : h->recs) { h->pool.push_back(r.a); h->pool.push_back(r.b); }
+    for (auto e : h->pool) if (e) cudaEventDestroy(e);
+    delete h;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_set_stream(pdhg_handle *h, void *stream) {
+    if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
+    h->stream = (cudaStream_t)stream;
+    return PDHG_OK;
+}
+
+template <typename T>
+static cudaError_t enqueue_iteration(pdhg_handle *h) {
+    const Params<T> &P = params_of<T>(h);
+    cudaStream_t s = h->stream;
+    T *u = F<T>(h, h->L.u), *phi = F<T>(h, h->L.phi), *phit = F<T>(h, h->L.phit);
+    T *lam = F<T>(h, h->L.lam), *lamt = F<T>(h, h->L.lamt), *u0 = F<T>(h, h->L.u0);
+    void *spec = h->ws + h->L.spec;
+    const void *twx = h->ws + h->L.twx, *twy = h->ws + h->L.twy, *V = h->ws + h->L.V;
+    const T *theta = F<T>(h, h->L.theta);
+    cudaError_t e;
+    if (h->G.fused) {
+        if constexpr (sizeof(T) == 4) {
+            e = stage(h, PDHG_STAGE_FUSED_COLS, 1, [&] { return fused2d_cols(&h->fused, h->pf, s); });
+            if (e != cudaSuccess) return e;
+            return stage(h, PDHG_STAGE_FUSED_ROWS, 1, [&] {
+                return fused2d_rows(&h->fused, h->pf, u, phi, lam, lamt, u0, s);
+            });
+        }
+        return cudaErrorInvalidValue;
+    }
+    e = stage(h, PDHG_STAGE_PRIMAL, 1, [&] { return launch_primal<T>(P, u, phit, lam, lamt, u0, s); });
+    if (e != cudaSuccess) return e;
+    e = stage(h, PDHG_STAGE_RESIDUAL_FFT, 1, [&] { return launch_residual_rfft<T>(P, u, spec, twx, s); });
+    if (e != cudaSuccess) return e;
+    if (h->G.dims == 2) {
+        e = stage(h, PDHG_STAGE_FFT_Y, 1, [&] { return launch_fft_y<T>(P, spec, twy, 0, s); });
+        if (e != cudaSuccess) return e;
+    }
+    e = stage(h, PDHG_STAGE_TSOLVE, 1, [&] { return launch_tsolve<T>(P, spec, theta, V, s); });
+    if (e != cudaSuccess) return e;
+    if (h->G.dims == 2) {
+        e = stage(h, PDHG_STAGE_FFT_Y, 1, [&] { return launch_fft_y<T>(P, spec, twy, 1, s); });
+        if (e != cudaSuccess) return e;
+    }
+    return stage(h, PDHG_STAGE_DUAL, 1, [&] { return launch_dual_irfft<T>(P, spec, phi, phit, twx, s); });
+}
+
+template <typename T>
+static pdhg_status iterate_T(pdhg_handle *h, int64_t max_iters, double tol, int32_t check_every, int32_t relative,
+                             int64_t *done) {
+    int64_t n = 0;
+    double scale = relative ? h->res_init : 1.0;
+    for (; n < max_iters;) {
+        cudaError_t e = enqueue_iteration<T>(h);
+        if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
+        ++n;
+        ++h->iters;
+        if (check_every > 0 && (n % check_every == 0 || n == max_iters)) {
+            double r[4];
+            pdhg_status st = compute_res<T>(h, r);
+            if (st != PDHG_OK) { if (done) *done = n; return st; }
+            if (!std::isfinite(r[0]) || !std::isfinite(r[1])) {
+                if (done) *done = n;
+                return fail(PDHG_ERR_NONFINITE, "residual is not finite after " + std::to_string(h->iters) + " iterations");
+            }
+            if (r[0] > 1e10 * std::max(h->res_init, 1e-300)) {
+                if (done) *done = n;
+                return fail(PDHG_ERR_DIVERGED, "primal residual grew by more than 1e10");
+            }
+            if (r[0] <= tol * scale && r[1] <= tol * scale) break;
+        }
+    }
+    if (done) *done = n;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_iterate(pdhg_handle *h, int64_t max_iters, double tol, int32_t check_every,
+                                    int32_t relative, int64_t *iters_done) {
+    if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
+    if (max_iters < 0) return fail(PDHG_ERR_INVALID_ARG, "max_iters < 0");
+    if (iters_done) *iters_done = 0;
+    return h->G.prec == PDHG_FP64 ? iterate_T<double>(h, max_iters, tol, check_every, relative, iters_done)
+                                  : iterate_T<float>(h, max_iters, tol, check_every, relative, iters_done);
+}
+
+extern "C" pdhg_status pdhg_residual(pdhg_handle *h, double out[4]) {
+    if (!h || !out) return fail(PDHG_ERR_INVALID_ARG, "null handle or out");
+    return h->G.prec == PDHG_FP64 ? compute_res<double>(h, out) : compute_res<float>(h, out);
+}
+
+static pdhg_status field_of(pdhg_handle *h, int32_t field, size_t *off, size_t *count, bool for_set) {
+    const Geom &G = h->G;
+    switch (field) {
+    case PDHG_FIELD_U: *off = h->L.u; *count = (G.nt + 1) * G.S; break;
+    case PDHG_FIELD_U_TERMINAL:
+        if (for_set) return fail(PDHG_ERR_INVALID_ARG, "U_TERMINAL is read-only");
+        *off = h->L.u + G.nt * G.S * G.esz; *count = G.S; break;
+    case PDHG_FIELD_PHI: *off = h->L.phi; *count = G.nt * G.S; break;
+    case PDHG_FIELD_PHIT: *off = h->L.phit; *count = G.nt * G.S; break;
+    case PDHG_FIELD_LAMBDA: *off = h->L.lam; *count = G.S; break;
+    case PDHG_FIELD_LAMBDAT: *off = h->L.lamt; *count = G.S; break;
+    default: return fail(PDHG_ERR_INVALID_ARG, "unknown field");
+    }
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_get_field(pdhg_handle *h, int32_t field, void *dst, int32_t on_device) {
+    if (!h || !dst) return fail(PDHG_ERR_INVALID_ARG, "null handle or dst");
+    size_t off, count;
+    pdhg_status st = field_of(h, field, &off, &count, false);
+    if (st != PDHG_OK) return st;
+    CK(cudaMemcpyAsync(dst, h->ws + off, count * h->G.esz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_set_field(pdhg_handle *h, int32_t field, const void *src, int32_t on_device) {
+    if (!h || !src) return fail(PDHG_ERR_INVALID_ARG, "null handle or src");
+    size_t off, count;
+    pdhg_status st = field_of(h, field, &off, &count, true);
+    if (st != PDHG_OK) return st;
+    CK(cudaMemcpyAsync(h->ws + off, src, count * h->G.esz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_info(pdhg_handle *h, int64_t *ndof, int64_t *nt, int64_t *iterations, int32_t *precision,
+                                 int32_t *path) {
+    if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
+    if (ndof) *ndof = h->G.S;
+    if (nt) *nt = h->G.nt;
+    if (iterations) *iterations = h->iters;
+    if (precision) *precision = h->G.prec;
+    if (path) *path = h->G.fused ? PDHG_PATH_FUSED : PDHG_PATH_PLAIN;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_launch_count(pdhg_handle *h, int64_t *launches, int32_t reset) {
+    if (!h || !launches) return fail(PDHG_ERR_INVALID_ARG, "null handle or launches");
+    *launches = h->launches;
+    if (reset) h->launches = 0;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_set_profiling(pdhg_handle *h, int32_t enable) {
+    if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
+    h->profiling = enable != 0;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_stage_times(pdhg_handle *h, double ms[PDHG_NUM_STAGES], int64_t launches[PDHG_NUM_STAGES]) {
+    if (!h || !ms || !launches) return fail(PDHG_ERR_INVALID_ARG, "null argument");
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto &r : h->recs) {
+        float t = 0.f;
+        if (r.a && r.b && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            h->stage_ms[r.stage] += t;
+            h->stage_n[r.stage] += 1;
+        }
+        if (r.a) h->pool.push_back(r.a);
+        if (r.b) h->pool.push_back(r.b);
+    }
+    h->recs.clear();
+    for (int i = 0; i < PDHG_NUM_STAGES; ++i) {
+        ms[i] = h->stage_ms[i]; launches[i] = h->stage_n[i];
+        h->stage_ms[i] = 0; h->stage_n[i] = 0;
+    }
+    return PDHG_OK;
+}

@@ -1,0 +1,82 @@
+// fft_smem.cuh -- block-cooperative radix-2 FFTs in shared memory.
+//
+// The x-transform of a real line of length N uses a complex FFT of length
+// M = N/2 on the packed samples z_n = x_{2n} + i x_{2n+1} and the standard
+// even/odd split; the y-transform (2D) is a complex FFT of length ny.  Both
+// are unnormalised; the inverse scalings are folded into the dual step.
+// Twiddles W_N^k = exp(-2 pi i k / N) come from tables computed on the host
+// in double precision.
+#pragma once
+
+#include "common.cuh"
+
+namespace pdhg {
+
+__device__ __forceinline__ int bitrev(int i, int log2n) {
+    return log2n == 0 ? 0 : (int)(__brev((unsigned)i) >> (32 - log2n));
+}
+
+// In-place decimation-in-time radix-2 FFT of `batch` sequences of length
+// n = 2^log2n held in shared memory in bit-reversed order.  Element i of
+// sequence c lives at z[c*cs + i*is].  tw[j*tws] = W_n^j (j < n/2).
+// inverse: conjugate twiddles.  Ends with __syncthreads().
+template <typename C>
+__device__ void fft_radix2(C *z, int log2n, int batch, int cs, int is, const C *__restrict__ tw,
+                           int tws, bool inverse) {
+    const int n = 1 << log2n;
+    const int half = n >> 1;
+    const int total = half * batch;
+    for (int s = 0; s < log2n; ++s) {
+        const int hs = 1 << s;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int c = t / half;
+            int k = t - c * half;
+            int pos = k & (hs - 1);
+            int i0 = ((k >> s) << (s + 1)) + pos;
+            int i1 = i0 + hs;
+            C w = tw[(pos << (log2n - s - 1)) * tws];
+            if (inverse) w.y = -w.y;
+            C *a = z + c * cs + i0 * is;
+            C *b = z + c * cs + i1 * is;
+            C tb = cmul(w, *b);
+            C ta = *a;
+            *a = cadd(ta, tb);
+            *b = csub(ta, tb);
+        }
+        __syncthreads();
+    }
+}
+
+// Real-FFT split: given Z = FFT_M(z) (natural order, length M) produce
+// X_k = E_k + W_N^k O_k for k = 0..M, with E_k = (Z_k + conj Z_{M-k})/2 and
+// O_k = (Z_k - conj Z_{M-k})/(2i).  twN[k] = W_N^k, k = 0..M.
+template <typename C>
+__device__ __forceinline__ C rfft_split(const C *Z, int M, int k, const C *__restrict__ twN) {
+    C zk = Z[k == M ? 0 : k];
+    C zm = Z[k == 0 ? 0 : M - k];
+    C e, a, o;
+    e.x = 0.5f * (zk.x + zm.x);
+    e.y = 0.5f * (zk.y - zm.y);
+    a.x = zk.x - zm.x;
+    a.y = zk.y + zm.y;        // a = Z_k - conj(Z_{M-k})
+    o.x = 0.5f * a.y;         // a / (2i) = -i a / 2
+    o.y = -0.5f * a.x;
+    return cadd(e, cmul(twN[k], o));
+}
+
+// Inverse split: Z_k = E_k + i O_k for k = 0..M-1, E_k = (X_k + conj X_{M-k})/2,
+// O_k = (X_k - conj X_{M-k}) conj(W_N^k) / 2.
+template <typename C>
+__device__ __forceinline__ C irfft_merge(C xk, C xm, C w) {
+    C e, a, o, r;
+    e.x = 0.5f * (xk.x + xm.x);
+    e.y = 0.5f * (xk.y - xm.y);
+    a.x = 0.5f * (xk.x - xm.x);
+    a.y = 0.5f * (xk.y + xm.y);
+    o = cmulconj(a, w);
+    r.x = e.x - o.y;          // e + i o
+    r.y = e.y + o.x;
+    return r;
+}
+
+}  // namespace pdhg

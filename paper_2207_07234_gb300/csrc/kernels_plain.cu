@@ -1,0 +1,505 @@
+// kernels_plain.cu -- one kernel per stage of Algorithm 1 (Sec. 3.3), for every
+// scheme of the library, in float or double.  This is the general path (and
+// the float64 comparator): each stage streams the space-time fields through
+// HBM once.  The fused path for large 2D problems lives in kernels_fused2d.cu.
+//
+// Stages of one iteration n:
+//   k_primal        u^l <- u^l - tau_u (J(u)^T phit)^l, l >= 1; u^0 row and
+//                   lambda, lambdat (Algorithm 1 steps 1 and the lambda update)
+//   k_residual_rfft R^l(u^n) and its forward real FFT along x
+//   k_fft_y         2D: complex FFT along y (forward, and later inverse)
+//   k_tsolve        (T_t + kappa h_t^2) z = r per Fourier mode (Thomas, closed-form pivots)
+//   k_dual_irfft    inverse FFT along x, phi <- phi + tau_phi z, phit = 2 phi^n - phi^{n-1}
+// plus k_check / k_reduce for Res (Eq. 2.12).
+#include "plain.h"
+#include "fft_smem.cuh"
+
+namespace pdhg {
+
+// ---------------------------------------------------------------------------
+// time part of (J^T psi)^l = sum_m coef(m, l) psi^m  (summation by parts, Sec. 3.1)
+// psi points at the value of slice 0 for this dof; slice stride S.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T time_T(const Params<T> &P, const T *psi, int64_t S, int l) {
+    T t = T(0);
+    if (l >= 1) t += coef_new(P, l - 1) * psi[(int64_t)(l - 1) * S];
+    if (l <= P.nt - 1) t += coef_cur(P, l) * psi[(int64_t)l * S];
+    if (l + 1 <= P.nt - 1) t += coef_old(P, l + 1) * psi[(int64_t)(l + 1) * S];
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// primal step (Algorithm 1, step 1; linearised at u^{n-1} as in Eq. 2.11)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_primal(Params<T> P, T *__restrict__ u, const T *__restrict__ phit,
+                                                T *__restrict__ lam, T *__restrict__ lamt,
+                                                const T *__restrict__ u0) {
+    const int l = blockIdx.y;
+    const int64_t S = P.S;
+    if (P.space == DG_P2_LF) {
+        const int N = P.nx;
+        const int k = blockIdx.x * blockDim.x + threadIdx.x;
+        if (k >= N) return;
+        T c[3], g[3];
+        T *ul = u + (int64_t)l * S;
+        for (int m = 0; m < 3; ++m) {
+            c[m] = ul[m * N + k];
+            g[m] = time_T(P, phit + m * N + k, S, l);
+        }
+        if (l >= 1) {
+            const T *ps = phit + (int64_t)(l - 1) * S;
+            int km = wrapm(k, N), kp = wrapp(k, N);
+            T pl[3], pc[3], pr[3], d[3];
+            for (int m = 0; m < 3; ++m) {
+                pl[m] = ps[m * N + km]; pc[m] = ps[m * N + k]; pr[m] = ps[m * N + kp];
+            }
+            dg_DT(P, c, pl, pc, pr, d);
+            for (int m = 0; m < 3; ++m) ul[m * N + k] = c[m] - P.tau_u * (g[m] + d[m]);
+        } else if (P.init == INIT_LAMBDA) {
+            for (int m = 0; m < 3; ++m) {
+                int64_t i = m * N + k;
+                T un = c[m] - P.tau_u0 * (P.ht * g[m] + lamt[i]);
+                ul[i] = un;
+                T r0 = un - u0[i];
+                T ln = lam[i] + P.tau_lambda * r0;
+                lam[i] = ln;
+                lamt[i] = ln + P.tau_lambda * r0;
+            }
+        }
+        return;
+    }
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
+    T *ul = u + (int64_t)l * S;
+    T c = ul[i];
+    T g = time_T(P, phit + i, S, l);
+    if (l >= 1) {
+        g += fd_DT(P, c, phit + (int64_t)(l - 1) * S, y, x);
+        ul[i] = c - P.tau_u * g;
+    } else if (P.init == INIT_LAMBDA) {
+        T un = c - P.tau_u0 * (P.ht * g + lamt[i]);
+        ul[i] = un;
+        T r0 = un - u0[i];
+        T ln = lam[i] + P.tau_lambda * r0;
+        lam[i] = ln;
+        lamt[i] = ln + P.tau_lambda * r0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// residual R^l(u^n) and forward real FFT along x.  One block per (l, line);
+// DG: one block per l holding the three mode planes.
+// spec layout: [l][line][kx], kx = 0..nx/2 (complex).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T time_R(const Params<T> &P, const T *u, int64_t S, int l) {
+    // time part of R^l at this dof; u points at slice 0 of the dof
+    T r = coef_new(P, l) * u[(int64_t)(l + 1) * S] + coef_cur(P, l) * u[(int64_t)l * S];
+    if (l >= 1 && P.time == BDF2) r += coef_old(P, l) * u[(int64_t)(l - 1) * S];
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual_rfft(Params<T> P, const T *__restrict__ u,
+                                                       typename Cplx<T>::type *__restrict__ spec,
+                                                       const typename Cplx<T>::type *__restrict__ twx) {
+    typedef typename Cplx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *z = reinterpret_cast<C *>(smem_raw);
+    const int l = blockIdx.y;
+    const int line = blockIdx.x;          // row y (FD); 0 for DG
+    const int N = P.nx, M = N >> 1;
+    const int lg = P.log2m;
+    const int64_t S = P.S;
+    T *zr = reinterpret_cast<T *>(z);
+    if (P.space == DG_P2_LF) {
+        const T *un = u + (int64_t)(l + 1) * S;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            int jm = wrapm(j, N), jp = wrapp(j, N);
+            T c[3], lft[3], rgt[3], d[3];
+            for (int m = 0; m < 3; ++m) {
+                c[m] = un[m * N + j]; lft[m] = un[m * N + jm]; rgt[m] = un[m * N + jp];
+            }
+            dg_D(P, c, lft, rgt, d);
+            int pos = bitrev(j >> 1, lg) * 2 + (j & 1);
+            for (int m = 0; m < 3; ++m) zr[m * N + pos] = d[m] + time_R(P, u + m * N + j, S, l);
+        }
+        __syncthreads();
+        fft_radix2(z, lg, 3, M, 1, twx, 2, false);
+        for (int t = threadIdx.x; t < 3 * (M + 1); t += blockDim.x) {
+            int m = t / (M + 1), k = t - m * (M + 1);
+            spec[((int64_t)l * 3 + m) * P.nkx + k] = rfft_split(z + m * M, M, k, twx);
+        }
+        return;
+    }
+    const T *un = u + (int64_t)(l + 1) * S;
+    const int64_t row = (int64_t)line * N;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        T r = fd_D(P, un, line, x) + time_R(P, u + row + x, S, l);
+        zr[bitrev(x >> 1, lg) * 2 + (x & 1)] = r;
+    }
+    __syncthreads();
+    fft_radix2(z, lg, 1, M, 1, twx, 2, false);
+    C *out = spec + ((int64_t)l * P.lines + line) * P.nkx;
+    for (int k = threadIdx.x; k <= M; k += blockDim.x) out[k] = rfft_split(z, M, k, twx);
+}
+
+// ---------------------------------------------------------------------------
+// complex FFT along y (2D), in place on spec[l][y][kx], CB columns per block
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_y(Params<T> P, typename Cplx<T>::type *__restrict__ spec,
+                                               const typename Cplx<T>::type *__restrict__ twy, int CB,
+                                               int inverse) {
+    typedef typename Cplx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *z = reinterpret_cast<C *>(smem_raw);
+    const int l = blockIdx.y;
+    const int k0 = blockIdx.x * CB;
+    const int cb = min(CB, P.nkx - k0);
+    const int ny = P.ny, lg = P.log2ny;
+    C *base = spec + (int64_t)l * ny * P.nkx + k0;
+    for (int t = threadIdx.x; t < ny * cb; t += blockDim.x) {
+        int y = t / cb, c = t - y * cb;
+        z[bitrev(y, lg) * cb + c] = base[(int64_t)y * P.nkx + c];
+    }
+    __syncthreads();
+    fft_radix2(z, lg, cb, 1, cb, twy, 1, inverse != 0);
+    for (int t = threadIdx.x; t < ny * cb; t += blockDim.x) {
+        int y = t / cb, c = t - y * cb;
+        base[(int64_t)y * P.nkx + c] = z[y * cb + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tridiagonal solve in t per Fourier mode:  (T_t + s) z = r,  s = kappa h_t^2,
+// T_t = tridiag(-1; 1,2,...,2; -1).  With cosh(theta) = 1 + s/2 the LU pivots
+// are d_l = cosh((l+3/2) theta) / cosh((l+1/2) theta), so
+//   rho_l = 1/d_l = e^{-theta} (1 + w_l) / (1 + q w_l),  w_l = e^{-(2l+1) theta}, q = e^{-2 theta}.
+// Forward: y_0 = r_0, y_l = r_l + rho_{l-1} y_{l-1};  backward: z_{nt-1} = rho y,
+// z_l = rho_l (y_l + z_{l+1}).  The h_t^2 factor of the right-hand side is
+// applied in the dual step.  DG: per kx the 3x3 block K_x = V diag(lam) V^H is
+// diagonalised first (theta per eigenvalue), and transformed back at the end.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float expT(float x) { return expf(x); }
+__device__ __forceinline__ double expT(double x) { return exp(x); }
+
+template <typename T>
+__device__ __forceinline__ T rho_of(T theta, T emt, T q, int l) {
+    T w = expT(-(T)(2 * l + 1) * theta);
+    return emt * (T(1) + w) / (T(1) + q * w);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_tsolve(Params<T> P, typename Cplx<T>::type *__restrict__ spec,
+                                                const T *__restrict__ theta_tab,
+                                                const typename Cplx<T>::type *__restrict__ V) {
+    typedef typename Cplx<T>::type C;
+    const int nt = P.nt;
+    if (P.space == DG_P2_LF) {
+        const int k = blockIdx.x * blockDim.x + threadIdx.x;
+        if (k >= P.nkx) return;
+        const int64_t ls = 3 * (int64_t)P.nkx;       // slice stride
+        C v[9];
+        for (int i = 0; i < 9; ++i) v[i] = V[(int64_t)k * 9 + i];   // v[m*3+i] = V_{m,i}
+        T th[3], emt[3], q[3];
+        for (int i = 0; i < 3; ++i) {
+            th[i] = theta_tab[k * 3 + i]; emt[i] = expT(-th[i]); q[i] = emt[i] * emt[i];
+        }
+        C yv[3];
+        for (int l = 0; l < nt; ++l) {
+            C r[3], w[3];
+            for (int m = 0; m < 3; ++m) r[m] = spec[l * ls + m * P.nkx + k];
+            for (int i = 0; i < 3; ++i) {                 // w = V^H r
+                C acc = mk<C, T>(T(0), T(0));
+                for (int m = 0; m < 3; ++m) acc = cadd(acc, cmulconj(r[m], v[m * 3 + i]));
+                w[i] = acc;
+            }
+            for (int i = 0; i < 3; ++i) {
+                if (l > 0) w[i] = cadd(w[i], cscale(yv[i], rho_of(th[i], emt[i], q[i], l - 1)));
+                yv[i] = w[i];
+                spec[l * ls + i * P.nkx + k] = w[i];
+            }
+        }
+        C zv[3];
+        for (int l = nt - 1; l >= 0; --l) {
+            C zz[3];
+            for (int i = 0; i < 3; ++i) {
+                C yl = spec[l * ls + i * P.nkx + k];
+                if (l < nt - 1) yl = cadd(yl, zv[i]);
+                zv[i] = cscale(yl, rho_of(th[i], emt[i], q[i], l));
+            }
+            for (int m = 0; m < 3; ++m) {                 // z = V w
+                C acc = mk<C, T>(T(0), T(0));
+                for (int i = 0; i < 3; ++i) acc = cadd(acc, cmul(v[m * 3 + i], zv[i]));
+                zz[m] = acc;
+            }
+            for (int m = 0; m < 3; ++m) spec[l * ls + m * P.nkx + k] = zz[m];
+        }
+        return;
+    }
+    const int64_t modes = (int64_t)P.lines * P.nkx;
+    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= modes) return;
+    const T th = theta_tab[col];
+    const T emt = expT(-th), q = emt * emt;
+    C *s = spec + col;
+    C y = s[0];
+    for (int l = 1; l < nt; ++l) {
+        C r = s[(int64_t)l * modes];
+        y = cadd(r, cscale(y, rho_of(th, emt, q, l - 1)));
+        s[(int64_t)l * modes] = y;
+    }
+    C z = cscale(y, rho_of(th, emt, q, nt - 1));
+    s[(int64_t)(nt - 1) * modes] = z;
+    for (int l = nt - 2; l >= 0; --l) {
+        C yl = s[(int64_t)l * modes];
+        z = cscale(cadd(yl, z), rho_of(th, emt, q, l));
+        s[(int64_t)l * modes] = z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inverse real FFT along x + dual step + extrapolation:
+//   z = K_d^{-1} R,  phi^n = phi^{n-1} + tau_phi z,  phit = phi^n + tau_phi z
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_dual_irfft(Params<T> P, const typename Cplx<T>::type *__restrict__ spec,
+                                                    T *__restrict__ phi, T *__restrict__ phit,
+                                                    const typename Cplx<T>::type *__restrict__ twx) {
+    typedef typename Cplx<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *z = reinterpret_cast<C *>(smem_raw);
+    const int l = blockIdx.y;
+    const int N = P.nx, M = N >> 1, lg = P.log2m;
+    const int nl = (P.space == DG_P2_LF) ? 3 : 1;
+    const int line0 = (P.space == DG_P2_LF) ? 0 : blockIdx.x;
+    for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
+        int m = t / M, k = t - m * M;
+        const C *X = spec + ((int64_t)l * P.lines + line0 + m) * P.nkx;
+        z[m * M + bitrev(k, lg)] = irfft_merge(X[k], X[M - k], twx[k]);
+    }
+    __syncthreads();
+    fft_radix2(z, lg, nl, M, 1, twx, 2, true);
+    const T *zr = reinterpret_cast<const T *>(z);
+    const int64_t off = (int64_t)l * P.S + (int64_t)line0 * N;
+    for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
+        int m = t / N, x = t - m * N;
+        T dz = P.dual_scale * zr[m * N + x];
+        int64_t i = off + (int64_t)m * N + x;
+        T pn = phi[i] + dz;
+        phi[i] = pn;
+        phit[i] = pn + dz;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// residual norms (Eq. 2.12) in double: per-block partial sums, fixed order
+//   acc[0] = sum R^2, acc[1] = sum (J^T phi)^2 over l >= 1, acc[2] = sum phi R,
+//   acc[3] = sum (u^0 - u0)^2, acc[4] = sum (h_t (J^T phi)^0 + lambda)^2,
+//   acc[5] = sum lambda (u^0 - u0)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum6(double acc[6], double *out) {
+    __shared__ double red[32][6];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k) red[wid][k] = acc[k];
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < 6; ++k) {
+            double v = lane < nw ? red[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) out[k] = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_check(Params<T> P, const T *__restrict__ u, const T *__restrict__ phi,
+                                               const T *__restrict__ lam, const T *__restrict__ u0,
+                                               double *__restrict__ partials) {
+    const int l = blockIdx.y;
+    const int64_t S = P.S;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    if (P.space == DG_P2_LF) {
+        const int N = P.nx;
+        const int k = blockIdx.x * blockDim.x + threadIdx.x;
+        if (k < N) {
+            int km = wrapm(k, N), kp = wrapp(k, N);
+            if (l < P.nt) {
+                const T *un = u + (int64_t)(l + 1) * S;
+                T c[3], lf[3], rg[3], d[3];
+                for (int m = 0; m < 3; ++m) { c[m] = un[m * N + k]; lf[m] = un[m * N + km]; rg[m] = un[m * N + kp]; }
+                dg_D(P, c, lf, rg, d);
+                for (int m = 0; m < 3; ++m) {
+                    double r = (double)(d[m] + time_R(P, u + m * N + k, S, l));
+                    acc[0] += r * r;
+                    acc[2] += (double)phi[(int64_t)l * S + m * N + k] * r;
+                }
+            }
+            T c[3];
+            for (int m = 0; m < 3; ++m) c[m] = u[(int64_t)l * S + m * N + k];
+            if (l >= 1) {
+                const T *ps = phi + (int64_t)(l - 1) * S;
+                T pl[3], pc[3], pr[3], d[3];
+                for (int m = 0; m < 3; ++m) { pl[m] = ps[m * N + km]; pc[m] = ps[m * N + k]; pr[m] = ps[m * N + kp]; }
+                dg_DT(P, c, pl, pc, pr, d);
+                for (int m = 0; m < 3; ++m) {
+                    double g = (double)(d[m] + time_T(P, phi + m * N + k, S, l));
+                    acc[1] += g * g;
+                }
+            } else {
+                for (int m = 0; m < 3; ++m) {
+                    double r0 = (double)c[m] - (double)u0[m * N + k];
+                    acc[3] += r0 * r0;
+                    if (P.init == INIT_LAMBDA) {
+                        double g0 = (double)P.ht * (double)time_T(P, phi + m * N + k, S, 0) + (double)lam[m * N + k];
+                        acc[4] += g0 * g0;
+                        acc[5] += (double)lam[m * N + k] * r0;
+                    }
+                }
+            }
+        }
+    } else {
+        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < S) {
+            const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
+            if (l < P.nt) {
+                double r = (double)(fd_D(P, u + (int64_t)(l + 1) * S, y, x) + time_R(P, u + i, S, l));
+                acc[0] += r * r;
+                acc[2] += (double)phi[(int64_t)l * S + i] * r;
+            }
+            T c = u[(int64_t)l * S + i];
+            if (l >= 1) {
+                double g = (double)(fd_DT(P, c, phi + (int64_t)(l - 1) * S, y, x) + time_T(P, phi + i, S, l));
+                acc[1] += g * g;
+            } else {
+                double r0 = (double)c - (double)u0[i];
+                acc[3] += r0 * r0;
+                if (P.init == INIT_LAMBDA) {
+                    double g0 = (double)P.ht * (double)time_T(P, phi + i, S, 0) + (double)lam[i];
+                    acc[4] += g0 * g0;
+                    acc[5] += (double)lam[i] * r0;
+                }
+            }
+        }
+    }
+    block_sum6(acc, partials + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 6);
+}
+
+__global__ void __launch_bounds__(256) k_reduce6(const double *__restrict__ partials, int64_t nblocks,
+                                                 double *__restrict__ out) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int k = 0; k < 6; ++k) acc[k] += partials[b * 6 + k];
+    block_sum6(acc, out);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_primal(const Params<T> &P, T *u, const T *phit, T *lam, T *lamt, const T *u0, cudaStream_t s) {
+    int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
+    dim3 grid((unsigned)((units + 255) / 256), (unsigned)(P.nt + 1));
+    k_primal<T><<<grid, 256, 0, s>>>(P, u, phit, lam, lamt, u0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t smem_rows(const Params<T> &P) {
+    int nl = (P.space == DG_P2_LF) ? 3 : 1;
+    return (size_t)nl * (P.nx / 2) * sizeof(typename Cplx<T>::type);
+}
+
+template <typename T>
+cudaError_t launch_residual_rfft(const Params<T> &P, const T *u, void *spec, const void *twx, cudaStream_t s) {
+    typedef typename Cplx<T>::type C;
+    size_t sm = smem_rows(P);
+    int nlines = (P.space == DG_P2_LF) ? 1 : P.lines;
+    dim3 grid((unsigned)nlines, (unsigned)P.nt);
+    k_residual_rfft<T><<<grid, 256, sm, s>>>(P, u, (C *)spec, (const C *)twx);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int fft_y_cols(const Params<T> &P) {
+    return sizeof(T) == 4 ? 8 : 4;
+}
+
+template <typename T>
+cudaError_t launch_fft_y(const Params<T> &P, void *spec, const void *twy, int inverse, cudaStream_t s) {
+    typedef typename Cplx<T>::type C;
+    int CB = fft_y_cols(P);
+    size_t sm = (size_t)P.ny * CB * sizeof(C);
+    dim3 grid((unsigned)((P.nkx + CB - 1) / CB), (unsigned)P.nt);
+    k_fft_y<T><<<grid, 256, sm, s>>>(P, (C *)spec, (const C *)twy, CB, inverse);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tsolve(const Params<T> &P, void *spec, const T *theta, const void *V, cudaStream_t s) {
+    typedef typename Cplx<T>::type C;
+    int64_t cols = (P.space == DG_P2_LF) ? P.nkx : (int64_t)P.lines * P.nkx;
+    k_tsolve<T><<<(unsigned)((cols + 127) / 128), 128, 0, s>>>(P, (C *)spec, theta, (const C *)V);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *phit, const void *twx, cudaStream_t s) {
+    typedef typename Cplx<T>::type C;
+    size_t sm = smem_rows(P);
+    int nlines = (P.space == DG_P2_LF) ? 1 : P.lines;
+    dim3 grid((unsigned)nlines, (unsigned)P.nt);
+    k_dual_irfft<T><<<grid, 256, sm, s>>>(P, (const C *)spec, phi, phit, (const C *)twx);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int64_t check_blocks(const Params<T> &P) {
+    int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
+    return ((units + 255) / 256) * (int64_t)(P.nt + 1);
+}
+
+template <typename T>
+cudaError_t launch_check(const Params<T> &P, const T *u, const T *phi, const T *lam, const T *u0,
+                         double *partials, double *out, cudaStream_t s) {
+    int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
+    dim3 grid((unsigned)((units + 255) / 256), (unsigned)(P.nt + 1));
+    k_check<T><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce6<<<1, 256, 0, s>>>(partials, (int64_t)grid.x * grid.y, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t init_plain_attributes() {
+    const int mx = 200 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_residual_rfft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dual_irfft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+}
+
+#define PDHG_INSTANTIATE(T)                                                                                   \
+    template cudaError_t launch_primal<T>(const Params<T> &, T *, const T *, T *, T *, const T *, cudaStream_t); \
+    template cudaError_t launch_residual_rfft<T>(const Params<T> &, const T *, void *, const void *, cudaStream_t); \
+    template cudaError_t launch_fft_y<T>(const Params<T> &, void *, const void *, int, cudaStream_t);          \
+    template cudaError_t launch_tsolve<T>(const Params<T> &, void *, const T *, const void *, cudaStream_t);   \
+    template cudaError_t launch_dual_irfft<T>(const Params<T> &, const void *, T *, T *, const void *, cudaStream_t); \
+    template int64_t check_blocks<T>(const Params<T> &);                                                      \
+    template cudaError_t init_plain_attributes<T>();                                                      \
+    template cudaError_t launch_check<T>(const Params<T> &, const T *, const T *, const T *, const T *, double *, \
+                                         double *, cudaStream_t);
+
+PDHG_INSTANTIATE(float)
+PDHG_INSTANTIATE(double)
+
+}  // namespace pdhg

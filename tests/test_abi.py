@@ -1,0 +1,81 @@
+"""The C-ABI library loads on a machine without a GPU and exports every symbol
+that include/pdhg.h declares; host-side validation needs no GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import pdhg_workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_07234_gb300 import binding
+    return binding.load()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "pdhg.h")).read()
+    return sorted(set(re.findall(r"\b(pdhg_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2207_07234_gb300 import binding
+    names = declared_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding.EXPORTS) == names
+
+
+def _size(p, **kw):
+    from paper_2207_07234_gb300 import binding
+    return binding.workspace_size(p, **kw)
+
+
+def test_workspace_size_and_validation(lib):
+    from paper_2207_07234_gb300 import binding
+    p = W.burgers_2d(n=64, nt=8)
+    n32 = _size(p, precision="fp32", path="plain")
+    n64 = _size(p, precision="fp64", path="plain")
+    cells = 64 * 64 * 8
+    assert n32 >= 4 * cells * 4 and n64 >= 4 * cells * 8
+    with pytest.raises(binding.PdhgError) as e:
+        _size(W.advection_upwind_be(nx=96, nt=4))
+    assert e.value.status == -7                                   # UNSUPPORTED: nx not a power of two
+    with pytest.raises(binding.PdhgError) as e:
+        _size(W.advection_upwind_be(nx=64, nt=4).replace(tau_u=-1.0))
+    assert e.value.status == -1                                   # INVALID_ARG
+    with pytest.raises(binding.PdhgError) as e:
+        _size(W.burgers_dg_p2(ncell=64, nt=4).replace(nu=0.1))
+    assert e.value.status == -7
+    assert "power of two" in lib.pdhg_last_error().decode() or lib.pdhg_last_error()
+
+
+def test_create_rejects_without_device_work(lib):
+    """Argument errors are reported before any device work: NULL workspace,
+    misaligned workspace, too small a workspace."""
+    from paper_2207_07234_gb300 import binding
+    p = W.advection_upwind_be(nx=16, nt=4)
+    prob, grid, scheme, keep = binding.structs(p, "fp64", "plain")
+    h = ctypes.c_void_p()
+    st = lib.pdhg_create(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme), None, 0, None,
+                         ctypes.byref(h))
+    assert st == -1
+    st = lib.pdhg_create(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                         ctypes.c_void_p(256), 16, None, ctypes.byref(h))
+    assert st == -2
+    st = lib.pdhg_create(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                         ctypes.c_void_p(257), 1 << 30, None, ctypes.byref(h))
+    assert st == -1
+    bad = p.replace(u0=np.full_like(p.u0, np.nan))
+    prob, grid, scheme, keep = binding.structs(bad, "fp64", "plain")
+    st = lib.pdhg_create(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                         ctypes.c_void_p(256 * 1024), 1 << 30, None, ctypes.byref(h))
+    assert st == -1 and "non-finite" in lib.pdhg_last_error().decode()

@@ -1,0 +1,181 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+* fixed-count iterates: n iterations of Algorithm 1 on the GPU equal n
+  iterations of the oracle on the same seeded inputs, element by element
+  (float64: 1e-12 relative to the field's max; float32: 1e-4);
+* converged solutions equal the oracle's Newton time-stepper (the definition of
+  the discrete solution): float64 within 1e-11, float32 within 1e-5 relative L-inf;
+* edge cases: one time slice, the smallest grid, data that is already a solution,
+  determinism, field round trips, launch counts.
+"""
+import numpy as np
+import pytest
+
+import pdhg_workloads as W
+from oracle import newton, pdhg as opdhg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_07234_gb300 import binding
+    binding.load()
+    return binding
+
+
+def steps(p, tu, tp, tu0=0.1):
+    return p.replace(tau_u=tu, tau_phi=tp, tau_u0=tu0, tau_lambda=0.99)
+
+
+def auto_steps(p, fac=0.8):
+    """tau_u = tau_phi = sqrt(fac / nu_max) from the oracle's power estimate."""
+    t = float(np.sqrt(fac / opdhg.power_estimate(p, iters=60)))
+    return steps(p, t, t)
+
+
+def cases():
+    yield steps(W.advection_upwind_be(nx=512, nt=7), 0.6, 0.6)
+    yield steps(W.advection_upwind_be(nx=256, nt=9).replace(time="bdf2"), 0.4, 0.4)
+    yield W.heat_table1(128, 11)
+    yield steps(W.viscous_burgers(nx=512, nt=13, T=1.0, nu=0.01), 0.35, 0.35)
+    yield steps(W.viscous_burgers(nx=512, nt=13, T=1.0, nu=0.01).replace(init="pinned"), 0.35, 0.35)
+    yield steps(W.advection_upwind_be(nx=256, nt=5).replace(alpha=-1.0, beta=1.0,
+                u0=0.25 + 0.1 * np.sin(W.fd_nodes(256, 2 * np.pi))), 0.5, 0.5)
+    yield auto_steps(W.burgers_dg_p2(ncell=512, nt=6, T=0.5, time="be").replace(c=0.5))
+    yield auto_steps(W.burgers_dg_p2(ncell=512, nt=7, T=0.5).replace(c=0.5))
+    yield steps(W.burgers_2d(n=64, nt=5).replace(ny=32, u0=W.burgers_2d(n=64).u0[:32]).replace(ly=np.pi), 0.4, 0.4)
+    yield steps(W.burgers_2d(n=32, nt=3).replace(nu=0.01, time="bdf2"), 0.3, 0.3)
+
+
+def run_gpu(B, p, precision, n):
+    with B.Solver(p, precision=precision, path="plain") as s:
+        s.iterate(n)
+        return {k: s.get_host(k) for k in ("u", "phi", "phit", "lambda", "lambdat")}, s.residual()
+
+
+def run_oracle(p, n):
+    st = opdhg.initial_state(p)
+    for _ in range(n):
+        opdhg.step(p, st)
+    return st
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("p", list(cases()), ids=lambda p: f"{p.name}_{p.time}_{p.init}")
+def test_fixed_iterates_fp64(B, p):
+    n = 25
+    g, res = run_gpu(B, p, "fp64", n)
+    o = run_oracle(p, n)
+    assert rel(g["u"], o["u"]) <= 1e-12
+    assert rel(g["phi"], o["phi"]) <= 1e-11
+    assert rel(g["phit"], o["phit"]) <= 1e-11
+    if p.init == "lambda":
+        assert rel(g["lambda"], o["lam"]) <= 1e-11
+        assert rel(g["lambdat"], o["lamt"]) <= 1e-11
+    ores = opdhg.residual_norms(p, o)
+    assert np.allclose(res[:3], ores[:3], rtol=1e-10, atol=1e-300)
+    assert abs(res[3] - ores[3]) <= 1e-9 * max(abs(ores[3]), 1e-300)
+
+
+@pytest.mark.parametrize("p", list(cases())[::3], ids=lambda p: f"{p.name}_{p.time}_{p.init}")
+def test_fixed_iterates_fp32(B, p):
+    n = 10
+    g, _ = run_gpu(B, p, "fp32", n)
+    o = run_oracle(p, n)
+    assert rel(g["u"], o["u"]) <= 1e-4
+    assert rel(g["phi"], o["phi"]) <= 1e-3
+
+
+def converged_cases():
+    yield steps(W.advection_upwind_be(nx=16, nt=8), 0.6, 0.6)
+    yield steps(W.viscous_burgers(nx=16, nt=6, T=0.5, nu=0.05), 0.35, 0.35)
+    yield W.heat_table1(16, 8)
+    yield steps(W.burgers_2d(n=8, nt=3), 0.45, 0.45)
+    yield auto_steps(W.burgers_dg_p2(ncell=8, nt=4, T=0.4, time="be").replace(c=0.5), 1.0)
+
+
+@pytest.mark.parametrize("p", list(converged_cases()), ids=lambda p: f"{p.name}_{p.time}")
+def test_converged_matches_newton(B, p):
+    un = newton.solve(p)
+    scale = np.max(np.abs(un))
+    with B.Solver(p, precision="fp64", path="plain") as s:
+        it = s.iterate(60000, tol=1e-12, check_every=50)
+        r = s.residual()
+        u = s.get_host("u")
+    assert r[0] <= 1e-12 and r[1] <= 1e-12, (it, r)
+    assert np.max(np.abs(u - un)) <= 1e-11 * scale
+    with B.Solver(p, precision="fp32", path="plain") as s:
+        s.iterate(60000, tol=2e-6, check_every=50, relative=True)
+        u32 = s.get_host("u").astype(np.float64)
+    assert np.max(np.abs(u32 - un)) <= 1e-5 * scale
+
+
+def test_single_slice_and_smallest_grid(B):
+    for p in (steps(W.advection_upwind_be(nx=4, nt=1), 0.5, 0.5),
+              steps(W.burgers_2d(n=4, nt=1), 0.4, 0.4),
+              auto_steps(W.burgers_dg_p2(ncell=4, nt=1, time="bdf2").replace(c=0.5))):
+        g, _ = run_gpu(B, p, "fp64", 7)
+        o = run_oracle(p, 7)
+        assert rel(g["u"], o["u"]) <= 1e-12 and rel(g["phi"], o["phi"]) <= 1e-11
+
+
+def test_exact_solution_stays_fixed(B):
+    """A constant u0 solves every scheme (fluxes telescope, time differences vanish):
+    Res is 0 from the start and the iteration leaves the state unchanged."""
+    for p in (W.burgers_2d(n=16, nt=4), W.viscous_burgers(nx=32, nt=5),
+              W.burgers_dg_p2(ncell=16, nt=3)):
+        q = p.replace(u0=np.full_like(p.u0, 0.0) + (0.7 if p.space != "dg_p2_lf" else 0.0))
+        if p.space == "dg_p2_lf":
+            u0 = np.zeros_like(p.u0)
+            u0[0] = 0.7
+            q = p.replace(u0=u0)
+        with B.Solver(q, precision="fp64", path="plain") as s:
+            assert s.iterate(100, tol=1e-14, check_every=10) == 10
+            r = s.residual()
+            u = s.get_host("u")
+        assert r[0] <= 1e-13 and r[1] <= 1e-13
+        assert np.max(np.abs(u - q.u0[None])) <= 1e-13
+
+
+def test_determinism_roundtrip_and_launches(B):
+    import torch
+    p = steps(W.burgers_2d(n=64, nt=6), 0.4, 0.4)
+    outs = []
+    for _ in range(2):
+        with B.Solver(p, precision="fp32", path="plain") as s:
+            s.iterate(5)
+            outs.append(s.get_host("u"))
+            assert s.launches(reset=True) == 5 * 6
+            phi = s.get("phi")
+            s.set("phi", phi * 2)
+            assert torch.equal(s.get("phi"), phi * 2)
+            assert s.info()["iterations"] == 5
+    assert np.array_equal(outs[0], outs[1])
+    q = steps(W.advection_upwind_be(nx=64, nt=5), 0.5, 0.5)
+    with B.Solver(q, precision="fp64", path="plain") as s:
+        s.iterate(3)
+        assert s.launches() == 3 * 4
+
+
+def test_relative_stop_and_nonfinite(B):
+    p = steps(W.advection_upwind_be(nx=32, nt=8), 0.6, 0.6)
+    with B.Solver(p, precision="fp64", path="plain") as s:
+        it = s.iterate(100000, tol=1e-6, check_every=10, relative=True)
+        r = s.residual()
+    st = opdhg.initial_state(p)
+    r0 = opdhg.residual_norms(p, st)[0]
+    assert r[0] <= 1e-6 * r0 and it % 10 == 0
+    bad = p.replace(tau_u=50.0, tau_phi=50.0)
+    with B.Solver(bad, precision="fp64", path="plain") as s:
+        with pytest.raises(B.PdhgError) as e:
+            s.iterate(5000, tol=0.0, check_every=10)
+        assert e.value.status in (-4, -5)
