@@ -172,6 +172,32 @@ pdhg_status pdhg_stage_times(pdhg_handle *h, double ms[PDHG_NUM_STAGES],
 /* Message of the last error on the calling thread ("" if none). */
 const char *pdhg_last_error(void);
 
+/*
+ * Residual norms of a caller-held state, with no handle, no workspace and no
+ * device allocation.  (An addition of this library: the paper has no
+ * counterpart.)  For callers that cannot allocate device memory -- e.g. code
+ * that may only use buffers it was handed, or that runs where the allocator
+ * must not be entered -- and so cannot provide pdhg_create()'s workspace.
+ *
+ * Computes the same out[0..3] as pdhg_residual() for the state given by device
+ * pointers in the scheme's element type: u ((nt+1)*ndof), phi (nt*ndof), lambda
+ * (ndof; may be NULL with PDHG_INIT_PINNED), u0 (ndof) and gamma_half (nx, or
+ * NULL).  prob->u0 and prob->gamma_half are ignored; prob->lf_a must be > 0
+ * for the Lax-Friedrichs schemes.  Enqueued on `stream`, then synchronised.
+ *
+ * Scratch: a fixed 2 MiB array in device memory, part of the library image
+ * (held on every GPU that uses it until the process exits).  Problems with
+ * ceil(units/256)*(nt+1) > 43685 (units = ndof, or cells for DG) are rejected
+ * with PDHG_ERR_UNSUPPORTED.  All calls share the array: calls that overlap on
+ * the GPU race; calls ordered on one stream are safe.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make it before any stream capture.
+ */
+pdhg_status pdhg_residual_noalloc(const pdhg_problem *prob, const pdhg_grid *grid,
+                                  const pdhg_scheme *scheme, const void *u, const void *phi,
+                                  const void *lambda, const void *u0, const void *gamma_half,
+                                  double out[4], void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,7 @@ STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_r
 # every symbol include/pdhg.h declares
 EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_stream", "pdhg_iterate",
            "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_info", "pdhg_launch_count",
-           "pdhg_set_profiling", "pdhg_stage_times", "pdhg_last_error"]
+           "pdhg_set_profiling", "pdhg_stage_times", "pdhg_last_error", "pdhg_residual_noalloc"]
 
 
 class PdhgError(RuntimeError):

@@ -37,6 +37,9 @@ static pdhg_status cuda_fail(cudaError_t e, const char *where) {
 
 extern "C" const char *pdhg_last_error(void) { return g_last_error.c_str(); }
 
+// lets other translation units of the library report through pdhg_last_error()
+void pdhg::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 // ---------------------------------------------------------------------------
 // layout
 // ---------------------------------------------------------------------------

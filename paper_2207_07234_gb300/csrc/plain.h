@@ -1,9 +1,14 @@
 // plain.h -- launchers of the per-stage kernels (kernels_plain.cu).
 #pragma once
 
+#include <string>
+
 #include "common.cuh"
 
 namespace pdhg {
+
+// sets the message returned by pdhg_last_error() on the calling thread
+void set_last_error(const std::string &msg);
 
 template <typename T> cudaError_t init_plain_attributes();
 template <typename T>
