@@ -235,6 +235,7 @@ struct pdhg_handle {
     double stage_ms[PDHG_NUM_STAGES];
     int64_t stage_n[PDHG_NUM_STAGES];
     Fused2D fused;
+    size_t u_off;            // offset of the current u buffer (the fused path alternates two)
 };
 
 template <typename T> static Params<T> &params_of(pdhg_handle *h);
@@ -362,6 +363,26 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
             }
     }
     CK(cudaMemcpy(F<T>(h, h->L.theta), th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (G.fused) {
+        // fused 2D path: full twiddle tables W_M^j (M = nx/2), W_ny^j and theta in [kx][ky] order
+        Fused2D &f = h->fused;
+        fused2d_layout(&f, h->ws + h->L.fused, G.nx, G.ny, G.nt);
+        const int64_t M = G.nx / 2;
+        std::vector<float> tm(2 * M), ty(2 * G.ny), tt(G.nkx * G.ny);
+        for (int64_t j = 0; j < M; ++j) {
+            double a = 2.0 * M_PI * (double)j / (double)M;
+            tm[2 * j] = (float)std::cos(a); tm[2 * j + 1] = (float)(-std::sin(a));
+        }
+        for (int64_t j = 0; j < G.ny; ++j) {
+            double a = 2.0 * M_PI * (double)j / (double)G.ny;
+            ty[2 * j] = (float)std::cos(a); ty[2 * j + 1] = (float)(-std::sin(a));
+        }
+        for (int64_t ky = 0; ky < G.ny; ++ky)
+            for (int64_t kx = 0; kx < G.nkx; ++kx) tt[kx * G.ny + ky] = (float)th[ky * G.nkx + kx];
+        CK(cudaMemcpy(f.twM, tm.data(), tm.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(f.twY, ty.data(), ty.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(f.thetaT, tt.data(), tt.size() * 4, cudaMemcpyHostToDevice));
+    }
     Params<T> &P = params_of<T>(h);
     fill_params(P, G, p, g, lf_a);
     if (G.has_gamma) P.gamma_half = F<T>(h, h->L.gamma);
@@ -373,7 +394,7 @@ template <typename T>
 static cudaError_t enqueue_check(pdhg_handle *h) {
     const Params<T> &P = params_of<T>(h);
     return stage(h, PDHG_STAGE_CHECK, 2, [&] {
-        return launch_check<T>(P, F<T>(h, h->L.u), F<T>(h, h->L.phi), F<T>(h, h->L.lam), F<T>(h, h->L.u0),
+        return launch_check<T>(P, F<T>(h, h->u_off), F<T>(h, h->L.phi), F<T>(h, h->L.lam), F<T>(h, h->L.u0),
                                F<double>(h, h->L.partials), F<double>(h, h->L.scal), h->stream);
     });
 }
@@ -428,6 +449,7 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
     double hx = grid->lx / (double)grid->nx;
     h->wx = G.dims == 2 ? hx * (grid->ly / (double)grid->ny) : hx;
     h->iters = 0; h->launches = 0; h->profiling = false;
+    h->u_off = L.u;
     memset(h->stage_ms, 0, sizeof(h->stage_ms));
     memset(h->stage_n, 0, sizeof(h->stage_n));
     st = (G.prec == PDHG_FP64) ? upload_tables<double>(h, prob, grid, lf_a) : upload_tables<float>(h, prob, grid, lf_a);
@@ -463,7 +485,7 @@ template <typename T>
 static cudaError_t enqueue_iteration(pdhg_handle *h) {
     const Params<T> &P = params_of<T>(h);
     cudaStream_t s = h->stream;
-    T *u = F<T>(h, h->L.u), *phi = F<T>(h, h->L.phi), *phit = F<T>(h, h->L.phit);
+    T *u = F<T>(h, h->u_off), *phi = F<T>(h, h->L.phi), *phit = F<T>(h, h->L.phit);
     T *lam = F<T>(h, h->L.lam), *lamt = F<T>(h, h->L.lamt), *u0 = F<T>(h, h->L.u0);
     void *spec = h->ws + h->L.spec;
     const void *twx = h->ws + h->L.twx, *twy = h->ws + h->L.twy, *V = h->ws + h->L.V;
@@ -471,11 +493,18 @@ static cudaError_t enqueue_iteration(pdhg_handle *h) {
     cudaError_t e;
     if (h->G.fused) {
         if constexpr (sizeof(T) == 4) {
-            e = stage(h, PDHG_STAGE_FUSED_COLS, 1, [&] { return fused2d_cols(&h->fused, h->pf, s); });
-            if (e != cudaSuccess) return e;
-            return stage(h, PDHG_STAGE_FUSED_ROWS, 1, [&] {
-                return fused2d_rows(&h->fused, h->pf, u, phi, lam, lamt, u0, s);
+            Fused2D *f = &h->fused;
+            float *uin = F<float>(h, h->u_off);
+            float *uout = f->cur == 0 ? f->u2 : F<float>(h, h->L.u);
+            e = stage(h, PDHG_STAGE_FUSED_ROWS, 1, [&] {
+                return fused2d_rowsA(f, h->pf, uin, uout, phit, lam, lamt, u0, s);
             });
+            if (e != cudaSuccess) return e;
+            f->cur ^= 1;
+            h->u_off = (size_t)((char *)uout - h->ws);
+            e = stage(h, PDHG_STAGE_FUSED_COLS, 1, [&] { return fused2d_cols(f, h->pf, s); });
+            if (e != cudaSuccess) return e;
+            return stage(h, PDHG_STAGE_DUAL, 1, [&] { return fused2d_rowsC(f, h->pf, phi, phit, s); });
         }
         return cudaErrorInvalidValue;
     }
@@ -542,10 +571,10 @@ extern "C" pdhg_status pdhg_residual(pdhg_handle *h, double out[4]) {
 static pdhg_status field_of(pdhg_handle *h, int32_t field, size_t *off, size_t *count, bool for_set) {
     const Geom &G = h->G;
     switch (field) {
-    case PDHG_FIELD_U: *off = h->L.u; *count = (G.nt + 1) * G.S; break;
+    case PDHG_FIELD_U: *off = h->u_off; *count = (G.nt + 1) * G.S; break;
     case PDHG_FIELD_U_TERMINAL:
         if (for_set) return fail(PDHG_ERR_INVALID_ARG, "U_TERMINAL is read-only");
-        *off = h->L.u + G.nt * G.S * G.esz; *count = G.S; break;
+        *off = h->u_off + G.nt * G.S * G.esz; *count = G.S; break;
     case PDHG_FIELD_PHI: *off = h->L.phi; *count = G.nt * G.S; break;
     case PDHG_FIELD_PHIT: *off = h->L.phit; *count = G.nt * G.S; break;
     case PDHG_FIELD_LAMBDA: *off = h->L.lam; *count = G.S; break;

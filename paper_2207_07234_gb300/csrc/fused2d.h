@@ -1,4 +1,4 @@
-// fused2d.h -- the fused two-kernel iteration for 2D finite differences (FP32).
+// fused2d.h -- the fused three-kernel iteration for 2D finite differences (float32).
 #pragma once
 
 #include "common.cuh"
@@ -6,17 +6,24 @@
 namespace pdhg {
 
 struct Fused2D {
-    void *ws;            // fused-path scratch inside the caller's workspace
-    const float *twx, *twy, *theta;
-    bool pending;        // a dual update (spectrum in ws) is waiting to be applied
+    float *u2;               // second u buffer (rows-A reads one, writes the other)
+    float2 *spec;            // spectrum [l][kx][y]: X, then spill, then K_d^{-1} R, in place
+    float2 *twM;             // W_M^j, j < M = nx/2
+    float2 *twY;             // W_ny^j, j < ny
+    float *thetaT;           // theta per mode, [kx][ky]
+    const float2 *twN;       // W_nx^k, k <= nx/2 (the plain path's table)
+    int cur;                 // 0: current u is the main buffer, 1: u2
+    int tc;                  // time slices per rows-A block
 };
 
 bool fused2d_supported(int dims, int space, int time, int prec, int64_t nx, int64_t ny, int64_t nt, double nu);
 size_t fused2d_workspace_bytes(int64_t nx, int64_t ny, int64_t nt);
+void fused2d_layout(Fused2D *f, void *ws, int64_t nx, int64_t ny, int64_t nt);
 cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const float *twx, const float *twy,
                          const float *theta);
+cudaError_t fused2d_rowsA(Fused2D *f, const Params<float> &P, const float *uin, float *uout, const float *phit,
+                          float *lam, float *lamt, const float *u0, cudaStream_t s);
 cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s);
-cudaError_t fused2d_rows(Fused2D *f, const Params<float> &P, float *u, float *phi, float *lam, float *lamt,
-                         const float *u0, cudaStream_t s);
+cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float *phit, cudaStream_t s);
 
 }  // namespace pdhg

@@ -221,11 +221,11 @@ def burgers_dg_p2(ncell: int = 512, nt: int = 256, T: float = 2.0,
                    tau_lambda=tau[3], init=init, u0=u0)
 
 
-def burgers_2d(n: int = 1024, nt: int = 256, seed: int = 20722, cfl: float = 2.0,
+def burgers_2d(n: int = 1024, nt: int = 256, seed: int = 20722, cfl: float = 1.0,
                tau=(0.5, 0.5, 0.5, 0.99), init: str = "lambda") -> Problem:
     """2D Burgers u_t + (u^2/2)_x + (u^2/2)_y = 0 on periodic [0,2pi]^2, BE +
-    global Lax-Friedrichs FD, h_t = cfl*h_x, u0 = 8 random Fourier modes of
-    amplitude 0.5 (seeded); a = c = max|u0|."""
+    global Lax-Friedrichs FD, h_t = cfl*h_x (default h_t = h_x: T = pi/2 at
+    nt = n/4), u0 = 8 random Fourier modes of amplitude 0.5 (seeded); a = c = max|u0|."""
     lx = 2.0 * np.pi
     hx = lx / n
     u0 = random_fourier_2d(n, lx, seed)
