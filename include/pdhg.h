@@ -187,8 +187,9 @@ const char *pdhg_last_error(void);
  *
  * Scratch: a fixed 2 MiB array in device memory, part of the library image
  * (held on every GPU that uses it until the process exits).  Problems with
- * ceil(units/256)*(nt+1) > 43685 (units = ndof, or cells for DG) are rejected
- * with PDHG_ERR_UNSUPPORTED.  All calls share the array: calls that overlap on
+ * min(ceil(units/256), 32)*(nt+1) > 43685 partial blocks (units = ndof, or
+ * cells for DG; so nt <= 1364 always fits) are rejected with
+ * PDHG_ERR_UNSUPPORTED before any device work.  All calls share the array: calls that overlap on
  * the GPU race; calls ordered on one stream are safe.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make it before any stream capture.

@@ -106,7 +106,7 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
     if (s->path == PDHG_PATH_FUSED || s->path == PDHG_PATH_AUTO) {
         bool ok = fused2d_supported(g->dims, s->space, s->time, s->precision, g->nx, G->ny, g->nt, p->nu);
         if (s->path == PDHG_PATH_FUSED && !ok)
-            return fail(PDHG_ERR_UNSUPPORTED, "the fused path needs 2D FD, FP32, nx = ny in {256..1024}");
+            return fail(PDHG_ERR_UNSUPPORTED, "the fused path needs 2D FD, FP32, nx in [256, 2048], ny in [256, 1024] (powers of two), nt >= 2");
         G->fused = ok;
     }
     return PDHG_OK;
@@ -130,7 +130,7 @@ Layout layout_of(const Geom &G) {
     L.theta = take(G.modes * e);
     L.V = take(G.space == PDHG_SPACE_DG_P2_LF ? G.nkx * 9 * 2 * e : 0);
     int64_t units = G.space == PDHG_SPACE_DG_P2_LF ? G.nx : G.S;
-    int64_t nblk = ((units + 255) / 256) * (G.nt + 1);
+    int64_t nblk = std::min<int64_t>((units + 255) / 256, 32) * (G.nt + 1);    // k_check grid
     L.partials = take(nblk * 6 * sizeof(double));
     L.scal = take(16 * sizeof(double));
     L.fused = take(G.fused ? fused2d_workspace_bytes(G.nx, G.ny, G.nt) : 0);

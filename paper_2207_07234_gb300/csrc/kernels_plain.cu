@@ -11,6 +11,8 @@
 //   k_tsolve        (T_t + kappa h_t^2) z = r per Fourier mode (Thomas, closed-form pivots)
 //   k_dual_irfft    inverse FFT along x, phi <- phi + tau_phi z, phit = 2 phi^n - phi^{n-1}
 // plus k_check / k_reduce for Res (Eq. 2.12).
+#include <algorithm>
+
 #include "plain.h"
 #include "fft_smem.cuh"
 
@@ -320,76 +322,85 @@ __device__ __forceinline__ void block_sum6(double acc[6], double *out) {
     }
 }
 
+// One thread accumulates many units of one slice (grid-stride over units); the
+// products of a unit are added in T and folded into double accumulators every
+// unit, so float32 fields lose at most the rounding of a handful of terms.
+template <typename T>
+__device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restrict__ u, const T *__restrict__ phi,
+                                           const T *__restrict__ lam, const T *__restrict__ u0, int l, int64_t unit,
+                                           double acc[6]) {
+    const int64_t S = P.S;
+    if (P.space == DG_P2_LF) {
+        const int N = P.nx;
+        const int k = (int)unit;
+        const int km = wrapm(k, N), kp = wrapp(k, N);
+        if (l < P.nt) {
+            const T *un = u + (int64_t)(l + 1) * S;
+            T c[3], lf[3], rg[3], d[3];
+            for (int m = 0; m < 3; ++m) { c[m] = un[m * N + k]; lf[m] = un[m * N + km]; rg[m] = un[m * N + kp]; }
+            dg_D(P, c, lf, rg, d);
+            for (int m = 0; m < 3; ++m) {
+                double r = (double)(d[m] + time_R(P, u + m * N + k, S, l));
+                acc[0] += r * r;
+                acc[2] += (double)phi[(int64_t)l * S + m * N + k] * r;
+            }
+        }
+        T c[3];
+        for (int m = 0; m < 3; ++m) c[m] = u[(int64_t)l * S + m * N + k];
+        if (l >= 1) {
+            const T *ps = phi + (int64_t)(l - 1) * S;
+            T pl[3], pc[3], pr[3], d[3];
+            for (int m = 0; m < 3; ++m) { pl[m] = ps[m * N + km]; pc[m] = ps[m * N + k]; pr[m] = ps[m * N + kp]; }
+            dg_DT(P, c, pl, pc, pr, d);
+            for (int m = 0; m < 3; ++m) {
+                double g = (double)(d[m] + time_T(P, phi + m * N + k, S, l));
+                acc[1] += g * g;
+            }
+        } else {
+            for (int m = 0; m < 3; ++m) {
+                double r0 = (double)c[m] - (double)u0[m * N + k];
+                acc[3] += r0 * r0;
+                if (P.init == INIT_LAMBDA) {
+                    double g0 = (double)P.ht * (double)time_T(P, phi + m * N + k, S, 0) + (double)lam[m * N + k];
+                    acc[4] += g0 * g0;
+                    acc[5] += (double)lam[m * N + k] * r0;
+                }
+            }
+        }
+        return;
+    }
+    const int64_t i = unit;
+    const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
+    if (l < P.nt) {
+        const T r = fd_D(P, u + (int64_t)(l + 1) * S, y, x) + time_R(P, u + i, S, l);
+        acc[0] += (double)(r * r);
+        acc[2] += (double)(phi[(int64_t)l * S + i] * r);
+    }
+    const T c = u[(int64_t)l * S + i];
+    if (l >= 1) {
+        const T g = fd_DT(P, c, phi + (int64_t)(l - 1) * S, y, x) + time_T(P, phi + i, S, l);
+        acc[1] += (double)(g * g);
+    } else {
+        double r0 = (double)c - (double)u0[i];
+        acc[3] += r0 * r0;
+        if (P.init == INIT_LAMBDA) {
+            double g0 = (double)P.ht * (double)time_T(P, phi + i, S, 0) + (double)lam[i];
+            acc[4] += g0 * g0;
+            acc[5] += (double)lam[i] * r0;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_check(Params<T> P, const T *__restrict__ u, const T *__restrict__ phi,
                                                const T *__restrict__ lam, const T *__restrict__ u0,
                                                double *__restrict__ partials) {
     const int l = blockIdx.y;
-    const int64_t S = P.S;
+    const int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    if (P.space == DG_P2_LF) {
-        const int N = P.nx;
-        const int k = blockIdx.x * blockDim.x + threadIdx.x;
-        if (k < N) {
-            int km = wrapm(k, N), kp = wrapp(k, N);
-            if (l < P.nt) {
-                const T *un = u + (int64_t)(l + 1) * S;
-                T c[3], lf[3], rg[3], d[3];
-                for (int m = 0; m < 3; ++m) { c[m] = un[m * N + k]; lf[m] = un[m * N + km]; rg[m] = un[m * N + kp]; }
-                dg_D(P, c, lf, rg, d);
-                for (int m = 0; m < 3; ++m) {
-                    double r = (double)(d[m] + time_R(P, u + m * N + k, S, l));
-                    acc[0] += r * r;
-                    acc[2] += (double)phi[(int64_t)l * S + m * N + k] * r;
-                }
-            }
-            T c[3];
-            for (int m = 0; m < 3; ++m) c[m] = u[(int64_t)l * S + m * N + k];
-            if (l >= 1) {
-                const T *ps = phi + (int64_t)(l - 1) * S;
-                T pl[3], pc[3], pr[3], d[3];
-                for (int m = 0; m < 3; ++m) { pl[m] = ps[m * N + km]; pc[m] = ps[m * N + k]; pr[m] = ps[m * N + kp]; }
-                dg_DT(P, c, pl, pc, pr, d);
-                for (int m = 0; m < 3; ++m) {
-                    double g = (double)(d[m] + time_T(P, phi + m * N + k, S, l));
-                    acc[1] += g * g;
-                }
-            } else {
-                for (int m = 0; m < 3; ++m) {
-                    double r0 = (double)c[m] - (double)u0[m * N + k];
-                    acc[3] += r0 * r0;
-                    if (P.init == INIT_LAMBDA) {
-                        double g0 = (double)P.ht * (double)time_T(P, phi + m * N + k, S, 0) + (double)lam[m * N + k];
-                        acc[4] += g0 * g0;
-                        acc[5] += (double)lam[m * N + k] * r0;
-                    }
-                }
-            }
-        }
-    } else {
-        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        if (i < S) {
-            const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
-            if (l < P.nt) {
-                double r = (double)(fd_D(P, u + (int64_t)(l + 1) * S, y, x) + time_R(P, u + i, S, l));
-                acc[0] += r * r;
-                acc[2] += (double)phi[(int64_t)l * S + i] * r;
-            }
-            T c = u[(int64_t)l * S + i];
-            if (l >= 1) {
-                double g = (double)(fd_DT(P, c, phi + (int64_t)(l - 1) * S, y, x) + time_T(P, phi + i, S, l));
-                acc[1] += g * g;
-            } else {
-                double r0 = (double)c - (double)u0[i];
-                acc[3] += r0 * r0;
-                if (P.init == INIT_LAMBDA) {
-                    double g0 = (double)P.ht * (double)time_T(P, phi + i, S, 0) + (double)lam[i];
-                    acc[4] += g0 * g0;
-                    acc[5] += (double)lam[i] * r0;
-                }
-            }
-        }
-    }
+    for (int64_t unit = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; unit < units;
+         unit += (int64_t)gridDim.x * blockDim.x)
+        check_unit(P, u, phi, lam, u0, l, unit, acc);
     block_sum6(acc, partials + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 6);
 }
 
@@ -461,17 +472,22 @@ cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *p
     return cudaGetLastError();
 }
 
+// blocks per slice of the residual check: at most 32 (grid-stride beyond that)
+template <typename T>
+static int64_t check_grid_x(const Params<T> &P) {
+    int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
+    return std::min<int64_t>((units + 255) / 256, 32);
+}
+
 template <typename T>
 int64_t check_blocks(const Params<T> &P) {
-    int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
-    return ((units + 255) / 256) * (int64_t)(P.nt + 1);
+    return check_grid_x(P) * (int64_t)(P.nt + 1);
 }
 
 template <typename T>
 cudaError_t launch_check(const Params<T> &P, const T *u, const T *phi, const T *lam, const T *u0,
                          double *partials, double *out, cudaStream_t s) {
-    int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
-    dim3 grid((unsigned)((units + 255) / 256), (unsigned)(P.nt + 1));
+    dim3 grid((unsigned)check_grid_x(P), (unsigned)(P.nt + 1));
     k_check<T><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

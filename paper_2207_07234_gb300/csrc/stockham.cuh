@@ -8,16 +8,17 @@
 
 namespace pdhg {
 
+// tw may point to global or shared memory: plain (generic) load.
 template <bool INV>
-__device__ __forceinline__ float2 twid(const float2 *__restrict__ tw, int j) {
-    float2 w = __ldg(tw + j);
+__device__ __forceinline__ float2 twid(const float2 *tw, int j) {
+    float2 w = tw[j];
     if (INV) w.y = -w.y;
     return w;
 }
 
 // One radix-2 stage with span p (product of the radices of earlier stages).
 template <int LOG2N, bool INV>
-__device__ __forceinline__ void stage_r2(const float2 *a, float2 *b, int batch, int p, const float2 *__restrict__ tw) {
+__device__ __forceinline__ void stage_r2(const float2 *a, float2 *b, int batch, int p, const float2 *tw) {
     constexpr int N = 1 << LOG2N, Q = N >> 1;
     for (int idx = threadIdx.x; idx < batch * Q; idx += blockDim.x) {
         int s = idx >> (LOG2N - 1), i = idx & (Q - 1);
@@ -33,7 +34,7 @@ __device__ __forceinline__ void stage_r2(const float2 *a, float2 *b, int batch, 
 
 // One radix-4 stage with span p.
 template <int LOG2N, bool INV>
-__device__ __forceinline__ void stage_r4(const float2 *a, float2 *b, int batch, int p, const float2 *__restrict__ tw) {
+__device__ __forceinline__ void stage_r4(const float2 *a, float2 *b, int batch, int p, const float2 *tw) {
     constexpr int N = 1 << LOG2N, Q = N >> 2;
     for (int idx = threadIdx.x; idx < batch * Q; idx += blockDim.x) {
         int s = idx >> (LOG2N - 2), i = idx & (Q - 1);
@@ -64,7 +65,7 @@ __device__ __forceinline__ void stage_r4(const float2 *a, float2 *b, int batch, 
 // Full transform; data starts in a, b is scratch; returns the buffer holding
 // the result.  Ends with __syncthreads().
 template <int LOG2N, bool INV>
-__device__ float2 *stockham(float2 *a, float2 *b, int batch, const float2 *__restrict__ tw) {
+__device__ float2 *stockham(float2 *a, float2 *b, int batch, const float2 *tw) {
     int p = 1;
     if (LOG2N & 1) {
         stage_r2<LOG2N, INV>(a, b, batch, 1, tw);

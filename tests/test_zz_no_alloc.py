@@ -79,7 +79,7 @@ def test_noalloc_matches_handle_residual_twice(B, case):
 
 def test_noalloc_rejects_too_large(B):
     import torch
-    p = W.burgers_2d(n=1024, nt=64)
+    p = W.burgers_2d(n=1024, nt=2000)      # 32 * 2001 partial blocks > 43685: rejected before any launch
     prob, grid, scheme, keep = B.structs(p, "fp32", "plain")
     out = (ctypes.c_double * 4)()
     dummy = torch.zeros(4, device="cuda")
