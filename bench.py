@@ -50,6 +50,8 @@ def workload(name: str):
         return W.burgers_dg_p2(tau=(0.2, 0.1, 0.2, 0.99)).replace(c=0.5)
     if name == "advection":
         return W.advection_upwind_be(tau=(1.4, 0.1, 0.35, 0.99))
+    if name == "heat":                                # Table 1's finest mesh, Sec. 4.1
+        return W.heat_table1(1024, 256)
     raise ValueError(name)
 
 
@@ -360,7 +362,8 @@ def run_ours(args):
 
     ttr = None
     if args.ttr and rank == 0:
-        ttr = time_to_residual(binding, workload(args.ttr), device=dev, stream=stream)
+        ttr = [time_to_residual(binding, workload(w), device=dev, stream=stream)
+               for w in args.ttr.split(",") if w]
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -421,8 +424,8 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "plain", "fused"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ttr", default="advection",
-                    help="workload for the time-to-residual comparison ('' = skip)")
+    ap.add_argument("--ttr", default="advection,heat",
+                    help="comma-separated workloads for the time-to-residual comparison ('' = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -59,7 +59,6 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsA(Params<float> P, const float
     constexpr int NR = BDF2_ ? 3 : 2;            // u ring slots
     constexpr int RU = FH + 2;                   // u rows: block rows + one halo row each side
     constexpr int RP = FH + 4;                   // phit rows: two halo rows each side
-    constexpr int RPT = FH * NX / FTHREADS;      // residual values per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *ph = reinterpret_cast<float *>(smem_raw);            // [2][RP][NX]
     float *us = ph + 2 * RP * NX;                                // [NR][RU][NX]
@@ -80,42 +79,59 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsA(Params<float> P, const float
         load_rows<NX>(pc, phit + (int64_t)m * S, y0 - 2, RP, ny, m >= nt);
         load_rows<NX>(uc, u_in + (int64_t)m * S, y0 - 1, RU, ny, false);
         __syncthreads();
-        // (1) primal step on slice m, rows y0-1 .. y0+FH (in place in uc)
+        // (1) primal step on slice m, rows y0-1 .. y0+FH (in place in uc), four x per thread
         const bool own_write = (m >= l0) && (m < l1 || m == nt);
         const float cn = m >= 1 ? coef_new(P, m - 1) : 0.f;
         const float cc = m <= nt - 1 ? coef_cur(P, m) : 0.f;
         const float co = (BDF2_ && m + 1 <= nt - 1) ? coef_old(P, m + 1) : 0.f;
-        for (int idx = threadIdx.x; idx < RU * NX; idx += blockDim.x) {
-            const int r = idx / NX, x = idx - r * NX;
+        constexpr int V = NX / 4;
+        for (int gi = threadIdx.x; gi < RU * V; gi += blockDim.x) {
+            const int r = gi / V, x4 = gi - r * V;
             const bool own = (r >= 1 && r <= FH);
             if (m == 0 && !own) continue;                      // slice-0 halo is never read
             const int q = r + 1;                               // phit row of the same y
-            const float c = uc[idx];
-            // the phit^{m-1} slot is not loaded for m = 0: never read it there
-            float g = cc * pc[q * NX + x];
-            if (m >= 1) g += cn * pp[q * NX + x];
+            float4 c = reinterpret_cast<const float4 *>(uc + r * NX)[x4];
+            const float4 tc = reinterpret_cast<const float4 *>(pc + q * NX)[x4];
+            float g[4] = {cc * tc.x, cc * tc.y, cc * tc.z, cc * tc.w};
             if (BDF2_ && co != 0.f) {
                 int y = y0 - 1 + r;
                 y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-                g += co * __ldg(phit + (int64_t)(m + 1) * S + (int64_t)y * NX + x);
+                const float4 tn = __ldg(reinterpret_cast<const float4 *>(phit + (int64_t)(m + 1) * S + (int64_t)y * NX) + x4);
+                g[0] += co * tn.x; g[1] += co * tn.y; g[2] += co * tn.z; g[3] += co * tn.w;
             }
-            float un = c;
+            float cv[4] = {c.x, c.y, c.z, c.w};
+            float un[4] = {c.x, c.y, c.z, c.w};
             if (m >= 1) {
-                const int xm = x == 0 ? NX - 1 : x - 1, xp = x == NX - 1 ? 0 : x + 1;
                 const float *row = pp + q * NX;
-                g += fd_dir_T(P, c, row[xm], row[x], row[xp], P.inv_hx) +
-                     fd_dir_T(P, c, pp[(q - 1) * NX + x], row[x], pp[(q + 1) * NX + x], P.inv_hy);
-                un = c - P.tau_u * g;
+                const float4 pm = reinterpret_cast<const float4 *>(row)[x4];
+                const float4 pu = reinterpret_cast<const float4 *>(pp + (q - 1) * NX)[x4];
+                const float4 pd = reinterpret_cast<const float4 *>(pp + (q + 1) * NX)[x4];
+                const float lft = row[x4 == 0 ? NX - 1 : 4 * x4 - 1];
+                const float rgt = row[x4 == V - 1 ? 0 : 4 * x4 + 4];
+                const float pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
+                const float pv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float ge = g[e] + cn * pr[e + 1];
+                    ge += fd_dir_T(P, cv[e], pr[e], pr[e + 1], pr[e + 2], P.inv_hx) +
+                          fd_dir_T(P, cv[e], pv[e], pr[e + 1], dv[e], P.inv_hy);
+                    un[e] = cv[e] - P.tau_u * ge;
+                }
             } else if (P.init == INIT_LAMBDA) {
-                const int64_t i = (int64_t)(y0 - 1 + r) * NX + x;    // own rows only: no wrap
-                un = c - P.tau_u0 * (P.ht * g + lamt[i]);
-                const float r0 = un - u0[i];
-                const float ln = lam[i] + P.tau_lambda * r0;
-                lam[i] = ln;
-                lamt[i] = ln + P.tau_lambda * r0;
+                const int64_t i = (int64_t)(y0 - 1 + r) * NX + 4 * x4;     // own rows only: no wrap
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    un[e] = cv[e] - P.tau_u0 * (P.ht * g[e] + lamt[i + e]);
+                    const float r0 = un[e] - u0[i + e];
+                    const float ln = lam[i + e] + P.tau_lambda * r0;
+                    lam[i + e] = ln;
+                    lamt[i + e] = ln + P.tau_lambda * r0;
+                }
             }
-            uc[idx] = un;
-            if (own && own_write) u_out[(int64_t)m * S + (int64_t)(y0 - 1 + r) * NX + x] = un;
+            const float4 u4 = make_float4(un[0], un[1], un[2], un[3]);
+            reinterpret_cast<float4 *>(uc + r * NX)[x4] = u4;
+            if (own && own_write)
+                reinterpret_cast<float4 *>(u_out + (int64_t)m * S + (int64_t)(y0 - 1 + r) * NX)[x4] = u4;
         }
         __syncthreads();
         // (2) residual R^{m-1} on the block's rows, then its x-FFT
@@ -125,26 +141,45 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsA(Params<float> P, const float
             const float *ucur = us + ((m + NR - 1) % NR) * RU * NX;
             const float *uold = us + ((m + NR - 2) % NR) * RU * NX;
             const float kn = coef_new(P, lr), kc = coef_cur(P, lr), ko = coef_old(P, lr);
-            float R[RPT];
+            constexpr int GPT = FH * V / FTHREADS;              // float4 groups per thread
+            float4 R[GPT];
 #pragma unroll
-            for (int j = 0; j < RPT; ++j) {
-                const int idx = threadIdx.x + j * FTHREADS;
-                const int rr = idx / NX, x = idx - rr * NX;
+            for (int j = 0; j < GPT; ++j) {
+                const int gi = threadIdx.x + j * FTHREADS;
+                const int rr = gi / V, x4 = gi - rr * V;
                 const int r = rr + 1;
-                const int xm = x == 0 ? NX - 1 : x - 1, xp = x == NX - 1 ? 0 : x + 1;
-                const float v = un[r * NX + x];
-                float Rv = fd_dir(P, un[r * NX + xm], v, un[r * NX + xp], P.inv_hx) +
-                           fd_dir(P, un[(r - 1) * NX + x], v, un[(r + 1) * NX + x], P.inv_hy);
-                Rv += kn * v + kc * ucur[r * NX + x];
-                if (BDF2_ && lr >= 1) Rv += ko * uold[r * NX + x];
-                R[j] = Rv;
+                const float *row = un + r * NX;
+                const float4 v4 = reinterpret_cast<const float4 *>(row)[x4];
+                const float4 up = reinterpret_cast<const float4 *>(un + (r - 1) * NX)[x4];
+                const float4 dn = reinterpret_cast<const float4 *>(un + (r + 1) * NX)[x4];
+                const float4 cu = reinterpret_cast<const float4 *>(ucur + r * NX)[x4];
+                const float lft = row[x4 == 0 ? NX - 1 : 4 * x4 - 1];
+                const float rgt = row[x4 == V - 1 ? 0 : 4 * x4 + 4];
+                const float vr[6] = {lft, v4.x, v4.y, v4.z, v4.w, rgt};
+                const float uv[4] = {up.x, up.y, up.z, up.w}, dv[4] = {dn.x, dn.y, dn.z, dn.w};
+                const float cv[4] = {cu.x, cu.y, cu.z, cu.w};
+                float ov[4] = {0.f, 0.f, 0.f, 0.f};
+                if (BDF2_ && lr >= 1) {
+                    const float4 o4 = reinterpret_cast<const float4 *>(uold + r * NX)[x4];
+                    ov[0] = o4.x; ov[1] = o4.y; ov[2] = o4.z; ov[3] = o4.w;
+                }
+                float Rv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float v = vr[e + 1];
+                    Rv[e] = fd_dir(P, vr[e], v, vr[e + 2], P.inv_hx) + fd_dir(P, uv[e], v, dv[e], P.inv_hy) +
+                            kn * v + kc * cv[e];
+                    if (BDF2_ && lr >= 1) Rv[e] += ko * ov[e];
+                }
+                R[j] = make_float4(Rv[0], Rv[1], Rv[2], Rv[3]);
             }
             __syncthreads();
             // FFT input in the u slot the residual no longer needs (BE: u^{m-1}, BDF2: u^{m-2}),
             // FFT scratch in the phit slot of m-1
             float *fin = BDF2_ ? const_cast<float *>(uold) : const_cast<float *>(ucur);
 #pragma unroll
-            for (int j = 0; j < RPT; ++j) fin[threadIdx.x + j * FTHREADS] = R[j];   // z_n = R_{2n} + i R_{2n+1}
+            for (int j = 0; j < GPT; ++j)          // z_n = R_{2n} + i R_{2n+1}
+                reinterpret_cast<float4 *>(fin)[threadIdx.x + j * FTHREADS] = R[j];
             __syncthreads();
             const float2 *res = stockham<LOG2M, false>(reinterpret_cast<float2 *>(fin),
                                                        reinterpret_cast<float2 *>(pp), FH, twM);
@@ -171,79 +206,251 @@ template <int LOG2NY>
 __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__restrict__ spec,
                                                    const float2 *__restrict__ twY,
                                                    const float *__restrict__ thetaT) {
-    // CW kx columns per block: the transforms of both run as one batch, so every
-    // barrier covers twice the work and twice the loads are in flight.
+    // One kx column per block (all 513 blocks resident at 1024^2).  The y-FFTs of
+    // TB consecutive slices are independent, so they run as one batch; only the
+    // cheap recurrence over those slices is sequential.
     constexpr int NY = 1 << LOG2NY;
-    constexpr int CW = 2;
-    constexpr int NPT = CW * NY / FTHREADS > 0 ? CW * NY / FTHREADS : 1;
-    __shared__ __align__(16) float2 ba[CW * NY];
-    __shared__ __align__(16) float2 bb[CW * NY];
-    __shared__ __align__(16) float2 tw[NY];
-    const int kx0 = blockIdx.x * CW;
-    const int ncol = min(CW, P.nkx - kx0);
+    constexpr int TB = 2;
+    constexpr int NPT = NY / FTHREADS > 0 ? NY / FTHREADS : 1;     // modes per thread
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *ba = reinterpret_cast<float2 *>(smem_raw);              // [TB][NY]
+    float2 *bb = ba + TB * NY;                                      // [TB][NY]
+    float2 *tw = bb + TB * NY;                                      // [NY]
+    const int kx = blockIdx.x;
     const int nt = P.nt;
     const int64_t cs = (int64_t)P.nkx * NY;      // slice stride of the spectrum
-    float2 *base = spec + (int64_t)kx0 * NY;     // CW columns are contiguous: [kx][y]
+    float2 *col = spec + (int64_t)kx * NY;
     const int t = threadIdx.x;
     for (int j = t; j < NY; j += FTHREADS) tw[j] = twY[j];
     float th[NPT], emt[NPT], q[NPT];
-    float2 acc[NPT], pf[NPT];
-    bool act[NPT];
+    float2 acc[NPT], pf[TB][NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
-        const int e = t + j * FTHREADS;          // element of the batch: column e / NY, mode e % NY
-        act[j] = e < ncol * NY;
-        th[j] = act[j] ? thetaT[(int64_t)kx0 * NY + e] : 0.f;
+        const int k = t + j * FTHREADS;
+        th[j] = thetaT[(int64_t)kx * NY + k];
         emt[j] = expf(-th[j]);
         q[j] = emt[j] * emt[j];
         acc[j] = make_float2(0.f, 0.f);
-        pf[j] = act[j] ? base[e] : make_float2(0.f, 0.f);
     }
+    const int nb = (nt + TB - 1) / TB;           // slice batches
     // forward sweep: y_l = r_l + rho_{l-1} y_{l-1}
-    for (int l = 0; l < nt; ++l) {
 #pragma unroll
-        for (int j = 0; j < NPT; ++j) ba[t + j * FTHREADS] = pf[j];
-        __syncthreads();
-        if (l + 1 < nt) {
-#pragma unroll
-            for (int j = 0; j < NPT; ++j)
-                if (act[j]) pf[j] = base[(int64_t)(l + 1) * cs + t + j * FTHREADS];
-        }
-        const float2 *res = stockham<LOG2NY, false>(ba, bb, CW, tw);
-#pragma unroll
-        for (int j = 0; j < NPT; ++j) {
-            const int e = t + j * FTHREADS;
-            float2 v = res[e];
-            if (l > 0) v = cadd(v, cscale(acc[j], rho_f(th[j], emt[j], q[j], l - 1)));
-            acc[j] = v;
-            if (act[j]) base[(int64_t)l * cs + e] = v;
-        }
-        __syncthreads();
-    }
-    // backward sweep: z_{nt-1} = rho y, z_l = rho_l (y_l + z_{l+1}); then inverse y-FFT
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) pf[j] = act[j] ? base[(int64_t)(nt - 1) * cs + t + j * FTHREADS] : pf[j];
-    for (int l = nt - 1; l >= 0; --l) {
-#pragma unroll
-        for (int j = 0; j < NPT; ++j) {
-            float2 y = pf[j];
-            if (l < nt - 1) y = cadd(y, acc[j]);
-            acc[j] = cscale(y, rho_f(th[j], emt[j], q[j], l));
-            ba[t + j * FTHREADS] = acc[j];
-        }
-        __syncthreads();
-        if (l > 0) {
-#pragma unroll
-            for (int j = 0; j < NPT; ++j)
-                if (act[j]) pf[j] = base[(int64_t)(l - 1) * cs + t + j * FTHREADS];
-        }
-        const float2 *res = stockham<LOG2NY, true>(ba, bb, CW, tw);
+    for (int b = 0; b < TB; ++b)
 #pragma unroll
         for (int j = 0; j < NPT; ++j)
-            if (act[j]) base[(int64_t)l * cs + t + j * FTHREADS] = res[t + j * FTHREADS];
+            pf[b][j] = b < nt ? col[(int64_t)b * cs + t + j * FTHREADS] : make_float2(0.f, 0.f);
+    for (int g = 0; g < nb; ++g) {
+        const int lb = g * TB;
+#pragma unroll
+        for (int b = 0; b < TB; ++b)
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) ba[b * NY + t + j * FTHREADS] = pf[b][j];
+        __syncthreads();
+        if (g + 1 < nb) {
+#pragma unroll
+            for (int b = 0; b < TB; ++b) {
+                const int l = lb + TB + b;
+#pragma unroll
+                for (int j = 0; j < NPT; ++j)
+                    pf[b][j] = l < nt ? col[(int64_t)l * cs + t + j * FTHREADS] : make_float2(0.f, 0.f);
+            }
+        }
+        const float2 *res = stockham<LOG2NY, false>(ba, bb, TB, tw);
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {
+            const int l = lb + b;
+            if (l >= nt) break;
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) {
+                const int k = t + j * FTHREADS;
+                float2 v = res[b * NY + k];
+                if (l > 0) v = cadd(v, cscale(acc[j], rho_f(th[j], emt[j], q[j], l - 1)));
+                acc[j] = v;
+                col[(int64_t)l * cs + k] = v;
+            }
+        }
+        __syncthreads();
+    }
+    // backward sweep: z_{nt-1} = rho y, z_l = rho_l (y_l + z_{l+1}); then inverse y-FFT,
+    // batches taken from the top: slices hi-TB+1 .. hi
+    int hi = nt - 1;
+#pragma unroll
+    for (int b = 0; b < TB; ++b)
+#pragma unroll
+        for (int j = 0; j < NPT; ++j)
+            pf[b][j] = hi - b >= 0 ? col[(int64_t)(hi - b) * cs + t + j * FTHREADS] : make_float2(0.f, 0.f);
+    for (int g = 0; g < nb; ++g, hi -= TB) {
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {              // b-th slice from the top of this batch
+            const int l = hi - b;
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) {
+                float2 v = make_float2(0.f, 0.f);
+                if (l >= 0) {
+                    float2 y = pf[b][j];
+                    if (l < nt - 1) y = cadd(y, acc[j]);
+                    acc[j] = cscale(y, rho_f(th[j], emt[j], q[j], l));
+                    v = acc[j];
+                }
+                ba[b * NY + t + j * FTHREADS] = v;
+            }
+        }
+        __syncthreads();
+        if (g + 1 < nb) {
+#pragma unroll
+            for (int b = 0; b < TB; ++b) {
+                const int l = hi - TB - b;
+#pragma unroll
+                for (int j = 0; j < NPT; ++j)
+                    pf[b][j] = l >= 0 ? col[(int64_t)l * cs + t + j * FTHREADS] : make_float2(0.f, 0.f);
+            }
+        }
+        const float2 *res = stockham<LOG2NY, true>(ba, bb, TB, tw);
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {
+            const int l = hi - b;
+            if (l < 0) break;
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) col[(int64_t)l * cs + t + j * FTHREADS] = res[b * NY + t + j * FTHREADS];
+        }
         __syncthreads();
     }
 }
+
+// ny = 1024 with 256 threads: thread t owns modes t + 256 q (q = 0..3), which are
+// exactly the inputs of the first radix-4 stage (span 1) and the outputs of the
+// last (span 256).  Those two stages run in registers; only the three middle
+// stages (spans 4, 16, 64) go through shared memory.
+__global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *__restrict__ spec,
+                                                       const float2 *__restrict__ twY,
+                                                       const float *__restrict__ thetaT) {
+    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *ba = reinterpret_cast<float2 *>(smem_raw);              // [TB][NY]
+    float2 *bb = ba + TB * NY;                                      // [TB][NY]
+    float2 *tw = bb + TB * NY;                                      // [NY]
+    const int kx = blockIdx.x;
+    const int nt = P.nt;
+    const int64_t cs = (int64_t)P.nkx * NY;
+    float2 *col = spec + (int64_t)kx * NY;
+    const int t = threadIdx.x;
+    for (int j = t; j < NY; j += FTHREADS) tw[j] = twY[j];
+    float th[4], emt[4], q4[4];
+    float2 acc[4], pf[TB][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        th[q] = thetaT[(int64_t)kx * NY + t + q * Q];
+        emt[q] = expf(-th[q]);
+        q4[q] = emt[q] * emt[q];
+        acc[q] = make_float2(0.f, 0.f);
+    }
+    const int nb = (nt + TB - 1) / TB;
+    // ---- forward sweep ----
+#pragma unroll
+    for (int b = 0; b < TB; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pf[b][q] = b < nt ? col[(int64_t)b * cs + t + q * Q] : make_float2(0.f, 0.f);
+    __syncthreads();                                                // twiddles
+    for (int g = 0; g < nb; ++g) {
+        const int lb = g * TB;
+        // stage 1 (span 1) in registers: inputs t + 256 r, outputs 4 t + q
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {
+            float2 x0 = pf[b][0], x1 = pf[b][1], x2 = pf[b][2], x3 = pf[b][3];
+            dft4<false>(x0, x1, x2, x3);
+            float4 *d = reinterpret_cast<float4 *>(ba + b * NY + 4 * t);
+            d[0] = make_float4(x0.x, x0.y, x1.x, x1.y);
+            d[1] = make_float4(x2.x, x2.y, x3.x, x3.y);
+        }
+        __syncthreads();
+        if (g + 1 < nb) {
+#pragma unroll
+            for (int b = 0; b < TB; ++b) {
+                const int l = lb + TB + b;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pf[b][q] = l < nt ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
+            }
+        }
+        const float2 *res = stockham_r4_range<LOG2NY, false>(ba, bb, TB, tw, 4, 256);
+        // stage 5 (span 256) in registers: inputs t + 256 r with twiddles W^{r t}, outputs t + 256 q
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {
+            const int l = lb + b;
+            float2 x0 = res[b * NY + t];
+            float2 x1 = cmul(res[b * NY + t + Q], tw[t]);
+            float2 x2 = cmul(res[b * NY + t + 2 * Q], tw[2 * t]);
+            float2 x3 = cmul(res[b * NY + t + 3 * Q], tw[3 * t]);
+            dft4<false>(x0, x1, x2, x3);
+            if (l < nt) {
+                float2 y[4] = {x0, x1, x2, x3};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float2 v = y[q];
+                    if (l > 0) v = cadd(v, cscale(acc[q], rho_f(th[q], emt[q], q4[q], l - 1)));
+                    acc[q] = v;
+                    col[(int64_t)l * cs + t + q * Q] = v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---- backward sweep (batches from the top) ----
+    int hi = nt - 1;
+#pragma unroll
+    for (int b = 0; b < TB; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            pf[b][q] = hi - b >= 0 ? col[(int64_t)(hi - b) * cs + t + q * Q] : make_float2(0.f, 0.f);
+    for (int g = 0; g < nb; ++g, hi -= TB) {
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {
+            const int l = hi - b;
+            float2 z[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                z[q] = make_float2(0.f, 0.f);
+                if (l >= 0) {
+                    float2 y = pf[b][q];
+                    if (l < nt - 1) y = cadd(y, acc[q]);
+                    acc[q] = cscale(y, rho_f(th[q], emt[q], q4[q], l));
+                    z[q] = acc[q];
+                }
+            }
+            // inverse stage 1 (span 1) in registers
+            dft4<true>(z[0], z[1], z[2], z[3]);
+            float4 *d = reinterpret_cast<float4 *>(ba + b * NY + 4 * t);
+            d[0] = make_float4(z[0].x, z[0].y, z[1].x, z[1].y);
+            d[1] = make_float4(z[2].x, z[2].y, z[3].x, z[3].y);
+        }
+        __syncthreads();
+        if (g + 1 < nb) {
+#pragma unroll
+            for (int b = 0; b < TB; ++b) {
+                const int l = hi - TB - b;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pf[b][q] = l >= 0 ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
+            }
+        }
+        const float2 *res = stockham_r4_range<LOG2NY, true>(ba, bb, TB, tw, 4, 256);
+#pragma unroll
+        for (int b = 0; b < TB; ++b) {
+            const int l = hi - b;
+            float2 x0 = res[b * NY + t];
+            float2 x1 = cmulconj(res[b * NY + t + Q], tw[t]);
+            float2 x2 = cmulconj(res[b * NY + t + 2 * Q], tw[2 * t]);
+            float2 x3 = cmulconj(res[b * NY + t + 3 * Q], tw[3 * t]);
+            dft4<true>(x0, x1, x2, x3);
+            if (l >= 0) {
+                col[(int64_t)l * cs + t] = x0;
+                col[(int64_t)l * cs + t + Q] = x1;
+                col[(int64_t)l * cs + t + 2 * Q] = x2;
+                col[(int64_t)l * cs + t + 3 * Q] = x3;
+            }
+        }
+    }
+}
+
+static size_t smem_cols(int log2ny) { return (size_t)(2 * 2 + 1) * (1 << log2ny) * 8; }
 
 // ---------------------------------------------------------------------------
 // rows-C: inverse real FFT along x, dual step and extrapolation.  phi is read
@@ -352,6 +559,8 @@ template <int L> static cudaError_t attr_rows() {
 cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const float *twx, const float *twy,
                          const float *theta) {
     (void)twy; (void)theta;
+    cudaError_t ec = cudaFuncSetAttribute(k_cols1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols(10));
+    if (ec != cudaSuccess) return ec;
     fused2d_layout(f, ws, P.nx, P.ny, P.nt);
     f->twN = (const float2 *)twx;
     f->cur = 0;
@@ -397,11 +606,11 @@ cudaError_t fused2d_rowsA(Fused2D *f, const Params<float> &P, const float *uin, 
 }
 
 cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s) {
-    const unsigned grid = (unsigned)((P.nkx + 1) / 2);
+    const unsigned grid = (unsigned)P.nkx;
     switch (ilog2i(P.ny)) {
-    case 8: k_cols<8><<<grid, FTHREADS, 0, s>>>(P, f->spec, f->twY, f->thetaT); break;
-    case 9: k_cols<9><<<grid, FTHREADS, 0, s>>>(P, f->spec, f->twY, f->thetaT); break;
-    case 10: k_cols<10><<<grid, FTHREADS, 0, s>>>(P, f->spec, f->twY, f->thetaT); break;
+    case 8: k_cols<8><<<grid, FTHREADS, smem_cols(8), s>>>(P, f->spec, f->twY, f->thetaT); break;
+    case 9: k_cols<9><<<grid, FTHREADS, smem_cols(9), s>>>(P, f->spec, f->twY, f->thetaT); break;
+    case 10: k_cols1024<<<grid, FTHREADS, smem_cols(10), s>>>(P, f->spec, f->twY, f->thetaT); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

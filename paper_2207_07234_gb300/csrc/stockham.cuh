@@ -62,6 +62,29 @@ __device__ __forceinline__ void stage_r4(const float2 *a, float2 *b, int batch, 
     }
 }
 
+// Radix-4 stages with span p in [p_from, p_to) only (p_from a power of 4 times the
+// first span); returns the buffer holding the result.  Ends with __syncthreads().
+template <int LOG2N, bool INV>
+__device__ float2 *stockham_r4_range(float2 *a, float2 *b, int batch, const float2 *tw, int p_from, int p_to) {
+    for (int p = p_from; p < p_to; p <<= 2) {
+        stage_r4<LOG2N, INV>(a, b, batch, p, tw);
+        __syncthreads();
+        float2 *t = a; a = b; b = t;
+    }
+    return a;
+}
+
+// 4-point DFT of (x0, x1, x2, x3) in registers (forward: W_4 = -i).
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
+    const float2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = csub(x1, x3);
+    const float2 mi = make_float2(t3.y, -t3.x);
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = INV ? csub(t1, mi) : cadd(t1, mi);
+    x3 = INV ? cadd(t1, mi) : csub(t1, mi);
+}
+
 // Full transform; data starts in a, b is scratch; returns the buffer holding
 // the result.  Ends with __syncthreads().
 template <int LOG2N, bool INV>

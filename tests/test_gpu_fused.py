@@ -42,6 +42,7 @@ def small_cases():
     p = W.burgers_2d(n=512, nt=5).replace(**base)
     yield p.replace(ny=256, ly=np.pi, u0=np.ascontiguousarray(p.u0[:256]))   # nx != ny
     yield W.burgers_2d(n=256, nt=7).replace(space="fd_upwind", alpha=0.0, beta=1.0, **base)
+    yield W.burgers_2d(n=1024, nt=3).replace(**base)                         # the ny = 1024 column kernel
 
 
 @pytest.mark.parametrize("p", list(small_cases()), ids=lambda p: f"{p.name}_{p.time}_{p.init}_{p.ny}")
