@@ -387,26 +387,37 @@ def run_ours(args):
 
 def time_to_residual(binding, p, tol=1e-6, check_every=50, max_iters=20000, device=None, stream=None):
     """Wall time and iterations to relative Res <= tol for the float32 default path and
-    the plain float64 GPU path (the comparator named by the metric)."""
+    the plain float64 GPU path (the comparator named by the metric).  Iterates in chunks
+    of 20 checks; a residual that has not dropped by 5% over three chunks is reported as
+    the precision's floor instead of running to max_iters."""
     import torch
     out = {"workload": p.name, "tol": tol, "relative_to": "||A(u_init)||", "check_every": check_every}
+    chunk = 20 * check_every
     for label, prec, path in (("fp32", "fp32", "auto"), ("fp64_plain", "fp64", "plain")):
         s = binding.Solver(p, precision=prec, path=path, device=device, stream=stream)
+        r0 = float(s.residual()[0])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        status = "converged"
+        status, it, hist = "max_iters", 0, []
         try:
-            it = s.iterate(max_iters, tol=tol, check_every=check_every, relative=True)
+            while it < max_iters:
+                done = s.iterate(min(chunk, max_iters - it), tol=tol, check_every=check_every, relative=True)
+                it += done
+                r = s.residual()
+                hist.append(max(float(r[0]), float(r[1])) / r0)
+                if r[0] <= tol * r0 and r[1] <= tol * r0:
+                    status = "converged"
+                    break
+                if len(hist) >= 4 and hist[-1] > 0.95 * hist[-4]:
+                    status = "floor"
+                    break
         except binding.PdhgError as err:
-            it, status = s.info()["iterations"], f"stopped: {binding.STATUS.get(err.status)}"
+            status = f"stopped: {binding.STATUS.get(err.status)}"
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         r = s.residual()
-        rel = [float(r[0]), float(r[1])]
-        if it >= max_iters:
-            status = "max_iters"
         out[label] = {"seconds": dt, "iterations": it, "status": status, "path": s.info()["path"],
-                      "res_abs": rel}
+                      "rel_res": [float(r[0]) / r0, float(r[1]) / r0]}
         s.close()
         del s
         torch.cuda.empty_cache()

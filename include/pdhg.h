@@ -21,7 +21,8 @@
  *   cudaStream_t passed as void*; NULL is the legacy default stream).
  * - Layouts (one time slice, "dofs"): 1D finite differences: u[j], j = 0..nx-1,
  *   x_j = j*lx/nx.  2D: u[y][x], x fastest.  DG P2: U[m][j], m = 0..2 Legendre
- *   mode, j = cell, cell fastest.  Space-time fields are slice-major: u has
+ *   mode, j = cell, cell fastest.  DG P1 (the nodal basis of Sec. 3.2.2): U[m][j],
+ *   m = 0, 1 the values at x_{j-1/4}, x_{j+1/4} of cell j = [j h, (j+1) h].  Space-time fields are slice-major: u has
  *   nt+1 slices (l = 0..nt), phi and phit have nt slices (one per equation).
  * - Precision: fields are stored as double (PDHG_FP64) or float (PDHG_FP32);
  *   buffers passed to pdhg_get_field/pdhg_set_field use that element type.
@@ -50,7 +51,8 @@ typedef enum {
 } pdhg_status;
 
 enum { PDHG_TIME_BE = 0, PDHG_TIME_BDF2 = 1 };
-enum { PDHG_SPACE_FD_UPWIND = 0, PDHG_SPACE_FD_LF = 1, PDHG_SPACE_DG_P2_LF = 2 };
+enum { PDHG_SPACE_FD_UPWIND = 0, PDHG_SPACE_FD_LF = 1, PDHG_SPACE_DG_P2_LF = 2,
+       PDHG_SPACE_DG_P1_UPWIND = 3, PDHG_SPACE_DG_P1_LF = 4 };
 enum { PDHG_FP64 = 0, PDHG_FP32 = 1 };
 enum { PDHG_INIT_LAMBDA = 0, PDHG_INIT_PINNED = 1 };
 enum { PDHG_PATH_AUTO = 0, PDHG_PATH_PLAIN = 1, PDHG_PATH_FUSED = 2 };
@@ -76,7 +78,8 @@ enum { PDHG_STAGE_PRIMAL = 0,      /* primal step + lambda update (Algorithm 1 s
  *   gamma_half  host pointer to gamma_{j+1/2}, j = 0..nx-1 (1D FD only) or NULL;
  *               adds -Lap(u) of Sec. 3.2.1.  Copied at create.
  *   u0          host pointer to the initial slice (dof layout above). Copied at create.
- *   lf_a        global Lax-Friedrichs constant (> 0 for FD_LF and DG_P2_LF)
+ *   lf_a        global Lax-Friedrichs constant for the LF schemes (0: max |f'(u0)|);
+ *               the upwind schemes use f(u-) and are monotone where f' >= 0
  *   c, gamma_hat  K = -d_tt - c^2 d_xx + gamma_hat^2 d_xxxx (Eq. 2.8, 2.10);
  *                 DG uses c only.
  *   tau_u, tau_u0, tau_phi, tau_lambda   step sizes of Algorithm 1 (> 0).

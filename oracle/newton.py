@@ -26,12 +26,13 @@ def _colouring(p):
     shape = p.slice_shape
     n = int(np.prod(shape))
     idx = np.arange(n).reshape(shape)
-    if p.space == "dg_p2_lf":
+    if p.nmodes > 1:
+        nm = p.nmodes
         m = next(k for k in (3, 4, 5, 6, 7, 8) if p.nx % k == 0) if p.nx >= 3 else p.nx
         cell = np.arange(p.nx)
-        colour = (np.arange(3)[:, None] * m + (cell % m)[None, :])
+        colour = (np.arange(nm)[:, None] * m + (cell % m)[None, :])
         nbrs = [np.concatenate([idx[:, (j + d) % p.nx] for d in (-1, 0, 1)]) for j in range(p.nx)]
-        nb = {int(idx[mm, j]): nbrs[j] for mm in range(3) for j in range(p.nx)}
+        nb = {int(idx[mm, j]): nbrs[j] for mm in range(nm) for j in range(p.nx)}
         return colour.ravel(), nb, n
     if p.dims == 2:
         mx = next(k for k in (3, 4, 5, 6, 7, 8) if p.nx % k == 0) if p.nx >= 3 else p.nx

@@ -54,11 +54,14 @@ def fd_kappa(p):
 def _upwind_problem(p):
     """The linear problem whose DG operator defines K_x: flux f = c u, and the
     Lax-Friedrichs flux with a = |c| (equal to the upwind flux for constant speed)."""
-    return p.replace(alpha=0.0, beta=p.c, lf_a=abs(p.c), nu=0.0, gamma_half=None)
+    q = p.replace(alpha=0.0, beta=p.c, lf_a=abs(p.c), nu=0.0, gamma_half=None)
+    if p.space.startswith("dg_p1"):
+        q = q.replace(space="dg_p1_lf")
+    return q
 
 
 def dg_symbol_S(p):
-    """S(theta_k) for k = 0..ncell//2, shape (ncell//2+1, 3, 3), complex.
+    """S(theta_k) for k = 0..ncell//2, shape (ncell//2+1, nm, nm), complex (nm = modes per cell).
 
     Built by applying the DG operator of c u_x to a unit coefficient in one
     cell: its output in cells j0, j0+1, j0-1 gives the blocks S_0, S_{-1}, S_{+1}
@@ -66,14 +69,15 @@ def dg_symbol_S(p):
     S(theta) = S_0 + S_{-1} e^{-i theta} + S_{+1} e^{i theta}."""
     q = _upwind_problem(p)
     n = p.nx
+    nm = p.nmodes
     j0 = 1
-    S0 = np.zeros((3, 3))
-    Sm = np.zeros((3, 3))
-    Sp = np.zeros((3, 3))
-    for col in range(3):
-        U = np.zeros((3, n))
+    S0 = np.zeros((nm, nm))
+    Sm = np.zeros((nm, nm))
+    Sp = np.zeros((nm, nm))
+    for col in range(nm):
+        U = np.zeros((nm, n))
         U[col, j0] = 1.0
-        out = spatial.dg_D(q, U)
+        out = spatial.D(q, U)
         S0[:, col] = out[:, j0]
         Sm[:, col] = out[:, (j0 + 1) % n]
         Sp[:, col] = out[:, (j0 - 1) % n]
@@ -113,9 +117,9 @@ def thomas_t(rhs, s, ht):
 def kd_inverse(p, r):
     """z = K_d^{-1} r for r of shape [nt, *slice] (real)."""
     ht = p.ht
-    if p.space == "dg_p2_lf":
-        rh = np.fft.rfft(r, axis=-1)                      # [nt][3][k]
-        rh = np.moveaxis(rh, -1, 1)                       # [nt][k][3]
+    if p.nmodes > 1:
+        rh = np.fft.rfft(r, axis=-1)                      # [nt][nm][k]
+        rh = np.moveaxis(rh, -1, 1)                       # [nt][k][nm]
         lam, V = np.linalg.eigh(dg_Kx(p))                 # K_x = V diag(lam) V^H
         w = np.einsum("kmi,tkm->tki", np.conj(V), rh)     # V^H r
         w = thomas_t(w, lam * ht * ht, ht)
@@ -153,14 +157,14 @@ def _periodic_second_difference(n, h):
 
 def dense_Kx(p):
     """K_x as a real-space matrix (ndof x ndof), from stencils, not symbols."""
-    if p.space == "dg_p2_lf":
+    if p.nmodes > 1:
         q = _upwind_problem(p)
         n = p.ndof
         S = np.zeros((n, n))
         for k in range(n):
             e = np.zeros(n)
             e[k] = 1.0
-            S[:, k] = spatial.dg_D(q, e.reshape(3, p.nx)).ravel()
+            S[:, k] = spatial.D(q, e.reshape(p.nmodes, p.nx)).ravel()
         return S.T @ S
     Dx = _periodic_second_difference(p.nx, p.hx)
     if p.dims == 2:

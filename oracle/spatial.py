@@ -186,19 +186,106 @@ def dg_D_vjp(p, U, Psi):
 
 
 # ---------------------------------------------------------------------------
+# DG P1 with the nodal basis of Sec. 3.2.2: phi_1(xi) = 1/2 - xi, phi_2(xi) = 1/2 + xi
+# (nodes x_{j-1/4}, x_{j+1/4}); mass matrix (h/12)[[7,-1],[-1,7]]; upwind flux
+# Fh(u-, u+) = f(u-) (the paper's choice for f' >= 0) or global Lax-Friedrichs.
+#   E_m = int f(u_h) phi_m' dxi - Fh_{j+1/2} phi_m(1) + Fh_{j-1/2} phi_m(-1),
+#   dU_j/dt = M^{-1} E (Eq. 3.5 / Eq. 3.8 form), D = -M^{-1} E.
+# The volume integral V = int f(u_h) dxi uses 2-point Gauss (exact for quadratic f).
+# ---------------------------------------------------------------------------
+
+G2 = 1.0 / np.sqrt(3.0)
+P1_Q = np.array([[0.5 + G2, 0.5 - G2], [0.5 - G2, 0.5 + G2]])   # phi_m(xi_q) [m][q], xi = -G2, +G2
+P1_RIGHT = np.array([-0.5, 1.5])                                 # phi_m(1)
+P1_LEFT = np.array([1.5, -0.5])                                  # phi_m(-1)
+P1_MINV = np.array([[7.0, 1.0], [1.0, 7.0]]) / 4.0               # h * M^{-1}
+
+
+def _p1_face(p, a, b):
+    if p.space == "dg_p1_upwind":
+        return flux(p, a)
+    return 0.5 * (flux(p, a) + flux(p, b)) - 0.5 * p.lf_a * (b - a)
+
+
+def _p1_face_da_db(p, a, b):
+    if p.space == "dg_p1_upwind":
+        return dflux(p, a), np.zeros_like(b)
+    return 0.5 * (dflux(p, a) + p.lf_a), 0.5 * (dflux(p, b) - p.lf_a)
+
+
+def _p1_E(p, U):
+    uq = np.einsum("mq,...mj->...qj", P1_Q, U)
+    V = flux(p, uq).sum(axis=-2)
+    uR = np.einsum("m,...mj->...j", P1_RIGHT, U)
+    uL = np.einsum("m,...mj->...j", P1_LEFT, U)
+    Fp = _p1_face(p, uR, np.roll(uL, -1, axis=-1))
+    Fm = np.roll(Fp, 1, axis=-1)
+    dphi = np.array([-1.0, 1.0])
+    return dphi[:, None] * V[..., None, :] - P1_RIGHT[:, None] * Fp[..., None, :] + P1_LEFT[:, None] * Fm[..., None, :]
+
+
+def dg1_D(p, U):
+    return -np.einsum("mn,...nj->...mj", P1_MINV, _p1_E(p, U)) / p.hx
+
+
+def dg1_D_jvp(p, U, W):
+    uq = np.einsum("mq,...mj->...qj", P1_Q, U)
+    wq = np.einsum("mq,...mj->...qj", P1_Q, W)
+    dV = (dflux(p, uq) * wq).sum(axis=-2)
+    uR = np.einsum("m,...mj->...j", P1_RIGHT, U)
+    uL = np.einsum("m,...mj->...j", P1_LEFT, U)
+    wR = np.einsum("m,...mj->...j", P1_RIGHT, W)
+    wL = np.einsum("m,...mj->...j", P1_LEFT, W)
+    da, db = _p1_face_da_db(p, uR, np.roll(uL, -1, axis=-1))
+    dFp = da * wR + db * np.roll(wL, -1, axis=-1)
+    dFm = np.roll(dFp, 1, axis=-1)
+    dphi = np.array([-1.0, 1.0])
+    dE = dphi[:, None] * dV[..., None, :] - P1_RIGHT[:, None] * dFp[..., None, :] + P1_LEFT[:, None] * dFm[..., None, :]
+    return -np.einsum("mn,...nj->...mj", P1_MINV, dE) / p.hx
+
+
+def dg1_D_vjp(p, U, Psi):
+    """D'(U)^T Psi: with A = -M^{-1 T} Psi / h (M symmetric) the pairing is sum_j A_j . dE_j;
+    then dE is transposed term by term (volume, F_{j+1/2}, F_{j-1/2} = F_{(j-1)+1/2})."""
+    A = -np.einsum("nm,...nj->...mj", P1_MINV, Psi) / p.hx
+    dphi = np.array([-1.0, 1.0])
+    uq = np.einsum("mq,...mj->...qj", P1_Q, U)
+    cV = np.einsum("m,...mj->...j", dphi, A)                         # coefficient of dV_j
+    out = np.einsum("mq,...qj->...mj", P1_Q, dflux(p, uq) * cV[..., None, :])
+    G = -np.einsum("m,...mj->...j", P1_RIGHT, A) + np.roll(np.einsum("m,...mj->...j", P1_LEFT, A), -1, axis=-1)
+    uR = np.einsum("m,...mj->...j", P1_RIGHT, U)
+    uL = np.einsum("m,...mj->...j", P1_LEFT, U)
+    da, db = _p1_face_da_db(p, uR, np.roll(uL, -1, axis=-1))           # at face j+1/2
+    out = out + P1_RIGHT[:, None] * (G * da)[..., None, :] + P1_LEFT[:, None] * np.roll(G * db, 1, axis=-1)[..., None, :]
+    return out
+
+
+# ---------------------------------------------------------------------------
 # dispatch
 # ---------------------------------------------------------------------------
 
 def D(p, v):
-    return dg_D(p, v) if p.space == "dg_p2_lf" else fd_D(p, v)
+    if p.space == "dg_p2_lf":
+        return dg_D(p, v)
+    if p.space.startswith("dg_p1"):
+        return dg1_D(p, v)
+    return fd_D(p, v)
 
 
 def D_jvp(p, v, w):
-    return dg_D_jvp(p, v, w) if p.space == "dg_p2_lf" else fd_D_jvp(p, v, w)
+    if p.space == "dg_p2_lf":
+        return dg_D_jvp(p, v, w)
+    if p.space.startswith("dg_p1"):
+        return dg1_D_jvp(p, v, w)
+    return fd_D_jvp(p, v, w)
 
 
 def D_vjp(p, v, psi):
-    return dg_D_vjp(p, v, psi) if p.space == "dg_p2_lf" else fd_D_vjp(p, v, psi)
+    if p.space == "dg_p2_lf":
+        return dg_D_vjp(p, v, psi)
+    if p.space.startswith("dg_p1"):
+        return dg1_D_vjp(p, v, psi)
+    return fd_D_vjp(p, v, psi)
 
 
 def dof_weight(p) -> float:

@@ -21,7 +21,7 @@ STATUS = {0: "PDHG_OK", -1: "PDHG_ERR_INVALID_ARG", -2: "PDHG_ERR_WORKSPACE_TOO_
           -3: "PDHG_ERR_CUDA", -4: "PDHG_ERR_NONFINITE", -5: "PDHG_ERR_DIVERGED",
           -6: "PDHG_ERR_TIMEOUT", -7: "PDHG_ERR_UNSUPPORTED"}
 TIME = {"be": 0, "bdf2": 1}
-SPACE = {"fd_upwind": 0, "fd_lf": 1, "dg_p2_lf": 2}
+SPACE = {"fd_upwind": 0, "fd_lf": 1, "dg_p2_lf": 2, "dg_p1_upwind": 3, "dg_p1_lf": 4}
 PRECISION = {"fp64": 0, "fp32": 1}
 INIT = {"lambda": 0, "pinned": 1}
 PATH = {"auto": 0, "plain": 1, "fused": 2}

@@ -66,7 +66,7 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
     if (!p || !g || !s) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
     if (g->dims != 1 && g->dims != 2) return fail(PDHG_ERR_INVALID_ARG, "dims must be 1 or 2");
     if (s->time != PDHG_TIME_BE && s->time != PDHG_TIME_BDF2) return fail(PDHG_ERR_INVALID_ARG, "bad time scheme");
-    if (s->space < PDHG_SPACE_FD_UPWIND || s->space > PDHG_SPACE_DG_P2_LF)
+    if (s->space < PDHG_SPACE_FD_UPWIND || s->space > PDHG_SPACE_DG_P1_LF)
         return fail(PDHG_ERR_INVALID_ARG, "bad space scheme");
     if (s->precision != PDHG_FP64 && s->precision != PDHG_FP32) return fail(PDHG_ERR_INVALID_ARG, "bad precision");
     if (s->init != PDHG_INIT_LAMBDA && s->init != PDHG_INIT_PINNED) return fail(PDHG_ERR_INVALID_ARG, "bad init");
@@ -82,11 +82,12 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
     if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !(p->nu >= 0) || !std::isfinite(p->nu) ||
         !std::isfinite(p->c) || !std::isfinite(p->gamma_hat) || !(p->lf_a >= 0) || !std::isfinite(p->lf_a))
         return fail(PDHG_ERR_INVALID_ARG, "non-finite or negative coefficient");
-    if (s->space == PDHG_SPACE_DG_P2_LF) {
-        if (g->dims != 1) return fail(PDHG_ERR_UNSUPPORTED, "DG P2 is 1D only");
-        if (p->gamma_half) return fail(PDHG_ERR_UNSUPPORTED, "DG P2 has no variable-coefficient Laplacian");
-        if (p->nu != 0) return fail(PDHG_ERR_UNSUPPORTED, "DG P2 has no viscous term");
-        if (p->gamma_hat != 0) return fail(PDHG_ERR_UNSUPPORTED, "DG P2 preconditioner uses c only");
+    const bool dg = s->space >= PDHG_SPACE_DG_P2_LF;
+    if (dg) {
+        if (g->dims != 1) return fail(PDHG_ERR_UNSUPPORTED, "DG is 1D only");
+        if (p->gamma_half) return fail(PDHG_ERR_UNSUPPORTED, "DG has no variable-coefficient Laplacian");
+        if (p->nu != 0) return fail(PDHG_ERR_UNSUPPORTED, "DG has no viscous term");
+        if (p->gamma_hat != 0) return fail(PDHG_ERR_UNSUPPORTED, "the DG preconditioner uses c only");
     }
     if (g->dims == 2 && p->gamma_half) return fail(PDHG_ERR_UNSUPPORTED, "gamma_half is 1D only");
     if (!is_pow2(g->nx) || g->nx < 4 || g->nx > 8192)
@@ -96,10 +97,11 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
     G->dims = g->dims; G->space = s->space; G->time = s->time; G->init = s->init;
     G->prec = s->precision; G->path = s->path;
     G->nx = g->nx; G->ny = g->dims == 2 ? g->ny : 1; G->nt = g->nt;
-    G->S = s->space == PDHG_SPACE_DG_P2_LF ? 3 * g->nx : g->nx * G->ny;
+    const int nm = s->space == PDHG_SPACE_DG_P2_LF ? 3 : (dg ? 2 : 1);
+    G->S = dg ? nm * g->nx : g->nx * G->ny;
     G->nkx = g->nx / 2 + 1;
-    G->lines = s->space == PDHG_SPACE_DG_P2_LF ? 3 : G->ny;
-    G->modes = s->space == PDHG_SPACE_DG_P2_LF ? 3 * G->nkx : G->lines * G->nkx;
+    G->lines = dg ? nm : G->ny;
+    G->modes = dg ? nm * G->nkx : G->lines * G->nkx;
     G->esz = s->precision == PDHG_FP64 ? 8 : 4;
     G->has_gamma = p->gamma_half != nullptr;
     G->fused = false;
@@ -128,8 +130,8 @@ Layout layout_of(const Geom &G) {
     L.twx = take(G.nkx * 2 * e);
     L.twy = take(G.dims == 2 ? G.ny * 2 * e : 0);
     L.theta = take(G.modes * e);
-    L.V = take(G.space == PDHG_SPACE_DG_P2_LF ? G.nkx * 9 * 2 * e : 0);
-    int64_t units = G.space == PDHG_SPACE_DG_P2_LF ? G.nx : G.S;
+    L.V = take(G.space >= PDHG_SPACE_DG_P2_LF ? G.nkx * 9 * 2 * e : 0);
+    int64_t units = G.space >= PDHG_SPACE_DG_P2_LF ? G.nx : G.S;
     int64_t nblk = std::min<int64_t>((units + 255) / 256, 32) * (G.nt + 1);    // k_check grid
     L.partials = take(nblk * 6 * sizeof(double));
     L.scal = take(16 * sizeof(double));
@@ -152,16 +154,19 @@ double symbol_L(int64_t k, int64_t n, double h) {
     return 4.0 * s * s / (h * h);
 }
 
-// Cyclic Jacobi for a 3x3 Hermitian matrix: A = V diag(w) V^H.
-void jacobi_herm3(cd A[3][3], double w[3], cd V[3][3]) {
+// Cyclic Jacobi for an n x n (n <= 3) Hermitian matrix: A = V diag(w) V^H.
+void jacobi_herm(int n, cd A[3][3], double w[3], cd V[3][3]) {
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
     for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = std::abs(A[0][1]) + std::abs(A[0][2]) + std::abs(A[1][2]);
-        double dia = std::abs(A[0][0].real()) + std::abs(A[1][1].real()) + std::abs(A[2][2].real());
+        double off = 0, dia = 0;
+        for (int i = 0; i < n; ++i) {
+            dia += std::abs(A[i][i].real());
+            for (int j = i + 1; j < n; ++j) off += std::abs(A[i][j]);
+        }
         if (off <= 1e-300 || off <= 1e-17 * dia) break;
-        for (int p = 0; p < 2; ++p)
-            for (int q = p + 1; q < 3; ++q) {
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
                 double r = std::abs(A[p][q]);
                 if (r == 0.0) continue;
                 cd ph = A[p][q] / r;                      // A_pq = r e^{i phi}
@@ -171,24 +176,50 @@ void jacobi_herm3(cd A[3][3], double w[3], cd V[3][3]) {
                 double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
                 // unitary G acting on columns p, q: col_p' = c col_p - s conj(ph) col_q, col_q' = s ph col_p + c col_q
                 cd gpp = c, gqp = -s * std::conj(ph), gpq = s * ph, gqq = c;
-                for (int k = 0; k < 3; ++k) {               // A <- A G
+                for (int k = 0; k < n; ++k) {               // A <- A G
                     cd akp = A[k][p], akq = A[k][q];
                     A[k][p] = akp * gpp + akq * gqp;
                     A[k][q] = akp * gpq + akq * gqq;
                 }
-                for (int k = 0; k < 3; ++k) {               // A <- G^H A
+                for (int k = 0; k < n; ++k) {               // A <- G^H A
                     cd apk = A[p][k], aqk = A[q][k];
                     A[p][k] = std::conj(gpp) * apk + std::conj(gqp) * aqk;
                     A[q][k] = std::conj(gpq) * apk + std::conj(gqq) * aqk;
                 }
-                for (int k = 0; k < 3; ++k) {               // V <- V G
+                for (int k = 0; k < n; ++k) {               // V <- V G
                     cd vkp = V[k][p], vkq = V[k][q];
                     V[k][p] = vkp * gpp + vkq * gqp;
                     V[k][q] = vkp * gpq + vkq * gqq;
                 }
             }
     }
-    for (int i = 0; i < 3; ++i) w[i] = A[i][i].real();
+    for (int i = 0; i < n; ++i) w[i] = A[i][i].real();
+}
+
+// S(theta) of the DG P1 nodal operator (Sec. 3.2.2) of c u_x with the upwind flux
+// (Lax-Friedrichs with a = |c|), from the weak form: with phi(1) = R = (-1/2, 3/2),
+// phi(-1) = L = (3/2, -1/2), phi' = (-1, 1) and int phi = (1, 1),
+//   E(j) = B0 U_j + Bm U_{j-1} + Bp U_{j+1},
+//   B0[m][n] = phi_m' c - R_m cp R_n + L_m cm L_n,  Bm[m][n] = L_m cp R_n,  Bp[m][n] = -R_m cm L_n,
+// cp = max(c, 0), cm = min(c, 0); D = -M^{-1} E with h M^{-1} = [[7,1],[1,7]]/4.
+// (For c > 0 the U_j block is the negative of the paper's A1 of Eq. 3.5.)
+void dg1_symbol(double c, double h, double theta, cd S[3][3]) {
+    const double R[2] = {-0.5, 1.5}, L[2] = {1.5, -0.5}, dphi[2] = {-1.0, 1.0};
+    const double cp = 0.5 * (c + std::fabs(c)), cm = 0.5 * (c - std::fabs(c));
+    const double Mi[2][2] = {{7.0 / 4.0, 1.0 / 4.0}, {1.0 / 4.0, 7.0 / 4.0}};
+    cd em = std::exp(cd(0, -theta)), ep = std::exp(cd(0, theta));
+    cd E[2][2];
+    for (int m = 0; m < 2; ++m)
+        for (int n = 0; n < 2; ++n) {
+            double b0 = dphi[m] * c - R[m] * cp * R[n] + L[m] * cm * L[n];
+            double bm = L[m] * cp * R[n];
+            double bp = -R[m] * cm * L[n];
+            E[m][n] = cd(b0) + cd(bm) * em + cd(bp) * ep;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) S[i][j] = 0.0;
+    for (int m = 0; m < 2; ++m)
+        for (int n = 0; n < 2; ++n) S[m][n] = -(Mi[m][0] * E[0][n] + Mi[m][1] * E[1][n]) / h;
 }
 
 // S(theta) of the DG P2 operator of c u_x with the upwind flux (Lax-Friedrichs
@@ -333,20 +364,23 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     double ht = g->T / (double)g->nt, hx = g->lx / (double)g->nx;
     double hy = G.dims == 2 ? g->ly / (double)g->ny : 1.0;
     std::vector<T> th(G.modes);
-    if (G.space == PDHG_SPACE_DG_P2_LF) {
-        std::vector<T> V(G.nkx * 18);
+    if (G.space >= PDHG_SPACE_DG_P2_LF) {
+        const int nm = (int)G.lines;
+        std::vector<T> V(G.nkx * 18, (T)0);
         for (int64_t k = 0; k < G.nkx; ++k) {
             cd S[3][3], A[3][3], Vm[3][3];
             double w[3];
-            dg_symbol(p->c, hx, 2.0 * M_PI * (double)k / (double)G.nx, S);
+            const double theta = 2.0 * M_PI * (double)k / (double)G.nx;
+            if (G.space == PDHG_SPACE_DG_P2_LF) dg_symbol(p->c, hx, theta, S);
+            else dg1_symbol(p->c, hx, theta, S);
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j) {
                     cd acc = 0;
-                    for (int m = 0; m < 3; ++m) acc += std::conj(S[m][i]) * S[m][j];
-                    A[i][j] = acc;
+                    for (int m = 0; m < nm; ++m) acc += std::conj(S[m][i]) * S[m][j];
+                    A[i][j] = (i < nm && j < nm) ? acc : cd(0.0);
                 }
-            jacobi_herm3(A, w, Vm);
-            for (int i = 0; i < 3; ++i) th[k * 3 + i] = (T)theta_of(std::max(w[i], 0.0) * ht * ht);
+            jacobi_herm(nm, A, w, Vm);
+            for (int i = 0; i < nm; ++i) th[k * nm + i] = (T)theta_of(std::max(w[i], 0.0) * ht * ht);
             for (int m = 0; m < 3; ++m)
                 for (int i = 0; i < 3; ++i) {
                     V[(k * 9 + m * 3 + i) * 2] = (T)Vm[m][i].real();
@@ -436,7 +470,8 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
     double lf_a = prob->lf_a;
     for (int64_t i = 0; i < G.S; ++i)
         if (!std::isfinite(prob->u0[i])) return fail(PDHG_ERR_INVALID_ARG, "u0 has a non-finite value");
-    if ((G.space == PDHG_SPACE_FD_LF || G.space == PDHG_SPACE_DG_P2_LF) && lf_a == 0.0) {
+    if ((G.space == PDHG_SPACE_FD_LF || G.space == PDHG_SPACE_DG_P2_LF || G.space == PDHG_SPACE_DG_P1_LF) &&
+        lf_a == 0.0) {
         for (int64_t i = 0; i < G.S; ++i) lf_a = std::max(lf_a, std::fabs(2 * prob->alpha * prob->u0[i] + prob->beta));
         if (lf_a == 0.0) lf_a = 1.0;
     }

@@ -11,7 +11,7 @@
 
 namespace pdhg {
 
-enum Space { FD_UPWIND = 0, FD_LF = 1, DG_P2_LF = 2 };
+enum Space { FD_UPWIND = 0, FD_LF = 1, DG_P2_LF = 2, DG_P1_UPWIND = 3, DG_P1_LF = 4 };
 enum Time { BE = 0, BDF2 = 1 };
 enum Init { INIT_LAMBDA = 0, INIT_PINNED = 1 };
 
@@ -47,7 +47,7 @@ struct Params {
     int32_t log2ny;         // 2D only
     int64_t S;              // dofs per slice
     int32_t nkx;            // nx/2 + 1
-    int32_t lines;          // x-lines per slice: 1 (1D FD), ny (2D), 3 (DG)
+    int32_t lines;          // x-lines per slice: 1 (1D FD), ny (2D), modes per cell (DG: 3 or 2)
     T alpha, beta, nu, lf_a;
     T ht, inv_ht, inv_hx, inv_hy;
     T tau_u, tau_u0, tau_phi, tau_lambda;
@@ -229,6 +229,83 @@ __device__ __forceinline__ void dg_DT(const Params<T> &P, const T c[3], const T 
     out[0] = o0 + a + b;
     out[1] = o1 + a - b;
     out[2] = o2 + a + b;
+}
+
+// ---------------------------------------------------------------------------
+// DG P1 with the nodal basis of Sec. 3.2.2 (nodes x_{j-1/4}, x_{j+1/4}):
+// phi_1(xi) = 1/2 - xi, phi_2(xi) = 1/2 + xi, mass matrix (h/12)[[7,-1],[-1,7]],
+// so h M^{-1} = [[7,1],[1,7]]/4.  With E_m = int f(u_h) phi_m' dxi
+// - Fh_{j+1/2} phi_m(1) + Fh_{j-1/2} phi_m(-1), the residual is D = -M^{-1} E.
+// Volume integral by 2-point Gauss (exact for quadratic f); interface flux
+// upwind f(u-) or global Lax-Friedrichs.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ bool is_dg(int space) { return space >= DG_P2_LF; }
+
+template <typename T>
+__device__ __forceinline__ T dg1_face(const Params<T> &P, T a, T b) {
+    if (P.space == DG_P1_UPWIND) return flux(P, a);
+    return T(0.5) * (flux(P, a) + flux(P, b)) - T(0.5) * P.lf_a * (b - a);
+}
+
+template <typename T>
+__device__ __forceinline__ void dg1_D(const Params<T> &P, const T c[2], const T l[2], const T r[2], T out[2]) {
+    const T g = T(0.57735026918962576451);                  // 1/sqrt(3)
+    const T qm = c[0] * (T(0.5) + g) + c[1] * (T(0.5) - g);   // u_h(-g)
+    const T qp = c[0] * (T(0.5) - g) + c[1] * (T(0.5) + g);   // u_h(+g)
+    const T V = flux(P, qm) + flux(P, qp);
+    const T uR = T(-0.5) * c[0] + T(1.5) * c[1], uL = T(1.5) * c[0] - T(0.5) * c[1];
+    const T uRl = T(-0.5) * l[0] + T(1.5) * l[1], uLr = T(1.5) * r[0] - T(0.5) * r[1];
+    const T Fp = dg1_face(P, uR, uLr), Fm = dg1_face(P, uRl, uL);
+    const T E0 = -V + T(0.5) * Fp + T(1.5) * Fm;
+    const T E1 = V - T(1.5) * Fp - T(0.5) * Fm;
+    const T s = T(-0.25) * P.inv_hx;
+    out[0] = s * (T(7) * E0 + E1);
+    out[1] = s * (E0 + T(7) * E1);
+}
+
+// D'(U)^T Psi for cell k: c = U_k; pl, pc, pr = Psi at k-1, k, k+1.
+// With A = -(h M)^{-1} Psi (per cell) the pairing is sum_j A_j . dE_j; the volume
+// term is cell-local, Fh_{k+1/2} carries G_k = -sum_m phi_m(1) A_m(k) +
+// sum_m phi_m(-1) A_m(k+1) and is differentiated in its left state uR_k, and
+// Fh_{k-1/2} (coefficient G_{k-1}) in its right state uL_k.
+template <typename T>
+__device__ __forceinline__ void dg1_DT(const Params<T> &P, const T c[2], const T pl[2], const T pc[2],
+                                       const T pr[2], T out[2]) {
+    const T g = T(0.57735026918962576451);
+    const T s = T(-0.25) * P.inv_hx;
+    const T a0 = s * (T(7) * pc[0] + pc[1]), a1 = s * (pc[0] + T(7) * pc[1]);
+    const T l0 = s * (T(7) * pl[0] + pl[1]), l1 = s * (pl[0] + T(7) * pl[1]);
+    const T r0 = s * (T(7) * pr[0] + pr[1]), r1 = s * (pr[0] + T(7) * pr[1]);
+    const T qm = c[0] * (T(0.5) + g) + c[1] * (T(0.5) - g);
+    const T qp = c[0] * (T(0.5) - g) + c[1] * (T(0.5) + g);
+    const T cV = a1 - a0;
+    const T dm = dflux(P, qm) * cV, dp = dflux(P, qp) * cV;
+    T o0 = (T(0.5) + g) * dm + (T(0.5) - g) * dp;
+    T o1 = (T(0.5) - g) * dm + (T(0.5) + g) * dp;
+    const T Gk = (T(0.5) * a0 - T(1.5) * a1) + (T(1.5) * r0 - T(0.5) * r1);
+    const T Gkm = (T(0.5) * l0 - T(1.5) * l1) + (T(1.5) * a0 - T(0.5) * a1);
+    const T uR = T(-0.5) * c[0] + T(1.5) * c[1], uL = T(1.5) * c[0] - T(0.5) * c[1];
+    T da, db;
+    if (P.space == DG_P1_UPWIND) { da = dflux(P, uR); db = T(0); }
+    else { da = T(0.5) * (dflux(P, uR) + P.lf_a); db = T(0.5) * (dflux(P, uL) - P.lf_a); }
+    const T A = Gk * da, B = Gkm * db;
+    o0 += T(-0.5) * A + T(1.5) * B;      // phi(1) = (-1/2, 3/2), phi(-1) = (3/2, -1/2)
+    o1 += T(1.5) * A + T(-0.5) * B;
+    out[0] = o0;
+    out[1] = o1;
+}
+
+// DG dispatch for either basis (nm = 3: P2 Legendre, nm = 2: P1 nodal)
+template <typename T>
+__device__ __forceinline__ void dgx_D(const Params<T> &P, const T c[3], const T l[3], const T r[3], T out[3]) {
+    if (P.space == DG_P2_LF) dg_D(P, c, l, r, out);
+    else dg1_D(P, c, l, r, out);
+}
+template <typename T>
+__device__ __forceinline__ void dgx_DT(const Params<T> &P, const T c[3], const T pl[3], const T pc[3], const T pr[3],
+                                       T out[3]) {
+    if (P.space == DG_P2_LF) dg_DT(P, c, pl, pc, pr, out);
+    else dg1_DT(P, c, pl, pc, pr, out);
 }
 
 }  // namespace pdhg

@@ -502,6 +502,82 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC(Params<float> P, const float
     }
 }
 
+// rows-C for nx = 1024 (M = 512 = 2 * 4^4): the inverse split feeds the first
+// (radix-2, span 1) stage directly in registers, three radix-4 stages (spans
+// 2, 8, 32) run in shared memory, and the last (span 128) runs in registers,
+// whose outputs -- complex positions i + 128 q, i.e. x = 2 (i + 128 q) + {0,1} --
+// go straight into the dual step.
+__global__ void __launch_bounds__(FTHREADS) k_rowsC1024(Params<float> P, const float2 *__restrict__ spec,
+                                                        float *__restrict__ phi, float *__restrict__ phit,
+                                                        const float2 *__restrict__ twN,
+                                                        const float2 *__restrict__ twM) {
+    constexpr int LOG2M = 9, M = 512, NX = 1024;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *st = reinterpret_cast<float2 *>(smem_raw);      // staging [FH][M+1]
+    float2 *fa = st + FH * (M + 1);                          // [FH][M]
+    float2 *fb = fa + FH * M;                                // [FH][M]
+    const int ny = P.ny;
+    const int y0 = blockIdx.x * FH;
+    const int l = blockIdx.y;
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)l * P.S + (int64_t)y0 * NX;
+    // phi at the positions this thread updates: rows 2h, 2h+1 (h = t / 128), x = 2(i + 128 q) + {0, 1}
+    const int h = t >> 7, i = t & 127;
+    float2 ph[2][4];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            ph[rr][q] = __ldg(reinterpret_cast<const float2 *>(phi + base + (int64_t)(2 * h + rr) * NX) + i + 128 * q);
+    // gather [kx][y0..y0+FH)
+    const float4 *src = reinterpret_cast<const float4 *>(spec + (int64_t)l * P.nkx * ny + y0);
+    for (int idx = t; idx < (M + 1) * 2; idx += blockDim.x) {
+        const int k = idx >> 1, hh = idx & 1;
+        const float4 v = __ldg(src + (int64_t)k * (ny / 2) + hh);
+        st[(2 * hh) * (M + 1) + k] = make_float2(v.x, v.y);
+        st[(2 * hh + 1) * (M + 1) + k] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    // inverse split (Z_k = E_k + i O_k) for k = t and t + 256, then the radix-2 stage
+    // (span 1: outputs 2t, 2t+1) in registers
+    {
+        const float2 w0 = twN[t], w1 = twN[t + 256];
+#pragma unroll
+        for (int rr = 0; rr < FH; ++rr) {
+            const float2 *X = st + rr * (M + 1);
+            const float2 z0 = irfft_merge(X[t], X[M - t], w0);
+            const float2 z1 = irfft_merge(X[t + 256], X[256 - t], w1);
+            reinterpret_cast<float4 *>(fa + rr * M)[t] =
+                make_float4(z0.x + z1.x, z0.y + z1.y, z0.x - z1.x, z0.y - z1.y);
+        }
+    }
+    __syncthreads();
+    const float2 *res = stockham_r4_range<LOG2M, true>(fa, fb, FH, twM, 2, 128);
+    const float s = P.dual_scale;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const float2 *r = res + (2 * h + rr) * M;
+        float2 x0 = r[i];
+        float2 x1 = cmulconj(r[i + 128], twM[i]);
+        float2 x2 = cmulconj(r[i + 256], twM[2 * i]);
+        float2 x3 = cmulconj(r[i + 384], twM[3 * i]);
+        dft4<true>(x0, x1, x2, x3);
+        const float2 z[4] = {x0, x1, x2, x3};
+        float2 *p2 = reinterpret_cast<float2 *>(phi + base + (int64_t)(2 * h + rr) * NX);
+        float2 *t2 = reinterpret_cast<float2 *>(phit + base + (int64_t)(2 * h + rr) * NX);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 pn = ph[rr][q];
+            pn.x += s * z[q].x;
+            pn.y += s * z[q].y;
+            p2[i + 128 * q] = pn;
+            t2[i + 128 * q] = make_float2(pn.x + s * z[q].x, pn.y + s * z[q].y);
+        }
+    }
+}
+
+static size_t smem_rowsC1024() { return (size_t)FH * (512 + 1) * 8 + 2 * (size_t)FH * 512 * 8; }
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -560,6 +636,8 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
                          const float *theta) {
     (void)twy; (void)theta;
     cudaError_t ec = cudaFuncSetAttribute(k_cols1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols(10));
+    if (ec == cudaSuccess)
+        ec = cudaFuncSetAttribute(k_rowsC1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rowsC1024());
     if (ec != cudaSuccess) return ec;
     fused2d_layout(f, ws, P.nx, P.ny, P.nt);
     f->twN = (const float2 *)twx;
@@ -617,6 +695,11 @@ cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s) {
 }
 
 cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float *phit, cudaStream_t s) {
+    if (P.nx == 1024) {
+        dim3 grid((unsigned)(P.ny / FH), (unsigned)P.nt);
+        k_rowsC1024<<<grid, FTHREADS, smem_rowsC1024(), s>>>(P, f->spec, phi, phit, f->twN, f->twM);
+        return cudaGetLastError();
+    }
     switch (ilog2i(P.nx / 2)) {
     case 7: return launch_rowsC<7>(f, P, phi, phit, s);
     case 8: return launch_rowsC<8>(f, P, phi, phit, s);

@@ -40,27 +40,27 @@ __global__ void __launch_bounds__(256) k_primal(Params<T> P, T *__restrict__ u, 
                                                 const T *__restrict__ u0) {
     const int l = blockIdx.y;
     const int64_t S = P.S;
-    if (P.space == DG_P2_LF) {
-        const int N = P.nx;
+    if (is_dg(P.space)) {
+        const int N = P.nx, nm = P.lines;
         const int k = blockIdx.x * blockDim.x + threadIdx.x;
         if (k >= N) return;
-        T c[3], g[3];
+        T c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
         T *ul = u + (int64_t)l * S;
-        for (int m = 0; m < 3; ++m) {
+        for (int m = 0; m < nm; ++m) {
             c[m] = ul[m * N + k];
             g[m] = time_T(P, phit + m * N + k, S, l);
         }
         if (l >= 1) {
             const T *ps = phit + (int64_t)(l - 1) * S;
             int km = wrapm(k, N), kp = wrapp(k, N);
-            T pl[3], pc[3], pr[3], d[3];
-            for (int m = 0; m < 3; ++m) {
+            T pl[3] = {0, 0, 0}, pc[3] = {0, 0, 0}, pr[3] = {0, 0, 0}, d[3];
+            for (int m = 0; m < nm; ++m) {
                 pl[m] = ps[m * N + km]; pc[m] = ps[m * N + k]; pr[m] = ps[m * N + kp];
             }
-            dg_DT(P, c, pl, pc, pr, d);
-            for (int m = 0; m < 3; ++m) ul[m * N + k] = c[m] - P.tau_u * (g[m] + d[m]);
+            dgx_DT(P, c, pl, pc, pr, d);
+            for (int m = 0; m < nm; ++m) ul[m * N + k] = c[m] - P.tau_u * (g[m] + d[m]);
         } else if (P.init == INIT_LAMBDA) {
-            for (int m = 0; m < 3; ++m) {
+            for (int m = 0; m < nm; ++m) {
                 int64_t i = m * N + k;
                 T un = c[m] - P.tau_u0 * (P.ht * g[m] + lamt[i]);
                 ul[i] = un;
@@ -117,23 +117,24 @@ __global__ void __launch_bounds__(256) k_residual_rfft(Params<T> P, const T *__r
     const int lg = P.log2m;
     const int64_t S = P.S;
     T *zr = reinterpret_cast<T *>(z);
-    if (P.space == DG_P2_LF) {
+    if (is_dg(P.space)) {
+        const int nm = P.lines;
         const T *un = u + (int64_t)(l + 1) * S;
         for (int j = threadIdx.x; j < N; j += blockDim.x) {
             int jm = wrapm(j, N), jp = wrapp(j, N);
-            T c[3], lft[3], rgt[3], d[3];
-            for (int m = 0; m < 3; ++m) {
+            T c[3] = {0, 0, 0}, lft[3] = {0, 0, 0}, rgt[3] = {0, 0, 0}, d[3];
+            for (int m = 0; m < nm; ++m) {
                 c[m] = un[m * N + j]; lft[m] = un[m * N + jm]; rgt[m] = un[m * N + jp];
             }
-            dg_D(P, c, lft, rgt, d);
+            dgx_D(P, c, lft, rgt, d);
             int pos = bitrev(j >> 1, lg) * 2 + (j & 1);
-            for (int m = 0; m < 3; ++m) zr[m * N + pos] = d[m] + time_R(P, u + m * N + j, S, l);
+            for (int m = 0; m < nm; ++m) zr[m * N + pos] = d[m] + time_R(P, u + m * N + j, S, l);
         }
         __syncthreads();
-        fft_radix2(z, lg, 3, M, 1, twx, 2, false);
-        for (int t = threadIdx.x; t < 3 * (M + 1); t += blockDim.x) {
+        fft_radix2(z, lg, nm, M, 1, twx, 2, false);
+        for (int t = threadIdx.x; t < nm * (M + 1); t += blockDim.x) {
             int m = t / (M + 1), k = t - m * (M + 1);
-            spec[((int64_t)l * 3 + m) * P.nkx + k] = rfft_split(z + m * M, M, k, twx);
+            spec[((int64_t)l * nm + m) * P.nkx + k] = rfft_split(z + m * M, M, k, twx);
         }
         return;
     }
@@ -201,26 +202,27 @@ __global__ void __launch_bounds__(128) k_tsolve(Params<T> P, typename Cplx<T>::t
                                                 const typename Cplx<T>::type *__restrict__ V) {
     typedef typename Cplx<T>::type C;
     const int nt = P.nt;
-    if (P.space == DG_P2_LF) {
+    if (is_dg(P.space)) {
+        const int nm = P.lines;
         const int k = blockIdx.x * blockDim.x + threadIdx.x;
         if (k >= P.nkx) return;
-        const int64_t ls = 3 * (int64_t)P.nkx;       // slice stride
+        const int64_t ls = nm * (int64_t)P.nkx;      // slice stride
         C v[9];
         for (int i = 0; i < 9; ++i) v[i] = V[(int64_t)k * 9 + i];   // v[m*3+i] = V_{m,i}
         T th[3], emt[3], q[3];
-        for (int i = 0; i < 3; ++i) {
-            th[i] = theta_tab[k * 3 + i]; emt[i] = expT(-th[i]); q[i] = emt[i] * emt[i];
+        for (int i = 0; i < nm; ++i) {
+            th[i] = theta_tab[k * nm + i]; emt[i] = expT(-th[i]); q[i] = emt[i] * emt[i];
         }
         C yv[3];
         for (int l = 0; l < nt; ++l) {
             C r[3], w[3];
-            for (int m = 0; m < 3; ++m) r[m] = spec[l * ls + m * P.nkx + k];
-            for (int i = 0; i < 3; ++i) {                 // w = V^H r
+            for (int m = 0; m < nm; ++m) r[m] = spec[l * ls + m * P.nkx + k];
+            for (int i = 0; i < nm; ++i) {                // w = V^H r
                 C acc = mk<C, T>(T(0), T(0));
-                for (int m = 0; m < 3; ++m) acc = cadd(acc, cmulconj(r[m], v[m * 3 + i]));
+                for (int m = 0; m < nm; ++m) acc = cadd(acc, cmulconj(r[m], v[m * 3 + i]));
                 w[i] = acc;
             }
-            for (int i = 0; i < 3; ++i) {
+            for (int i = 0; i < nm; ++i) {
                 if (l > 0) w[i] = cadd(w[i], cscale(yv[i], rho_of(th[i], emt[i], q[i], l - 1)));
                 yv[i] = w[i];
                 spec[l * ls + i * P.nkx + k] = w[i];
@@ -229,17 +231,17 @@ __global__ void __launch_bounds__(128) k_tsolve(Params<T> P, typename Cplx<T>::t
         C zv[3];
         for (int l = nt - 1; l >= 0; --l) {
             C zz[3];
-            for (int i = 0; i < 3; ++i) {
+            for (int i = 0; i < nm; ++i) {
                 C yl = spec[l * ls + i * P.nkx + k];
                 if (l < nt - 1) yl = cadd(yl, zv[i]);
                 zv[i] = cscale(yl, rho_of(th[i], emt[i], q[i], l));
             }
-            for (int m = 0; m < 3; ++m) {                 // z = V w
+            for (int m = 0; m < nm; ++m) {                // z = V w
                 C acc = mk<C, T>(T(0), T(0));
-                for (int i = 0; i < 3; ++i) acc = cadd(acc, cmul(v[m * 3 + i], zv[i]));
+                for (int i = 0; i < nm; ++i) acc = cadd(acc, cmul(v[m * 3 + i], zv[i]));
                 zz[m] = acc;
             }
-            for (int m = 0; m < 3; ++m) spec[l * ls + m * P.nkx + k] = zz[m];
+            for (int m = 0; m < nm; ++m) spec[l * ls + m * P.nkx + k] = zz[m];
         }
         return;
     }
@@ -277,8 +279,8 @@ __global__ void __launch_bounds__(256) k_dual_irfft(Params<T> P, const typename 
     C *z = reinterpret_cast<C *>(smem_raw);
     const int l = blockIdx.y;
     const int N = P.nx, M = N >> 1, lg = P.log2m;
-    const int nl = (P.space == DG_P2_LF) ? 3 : 1;
-    const int line0 = (P.space == DG_P2_LF) ? 0 : blockIdx.x;
+    const int nl = is_dg(P.space) ? P.lines : 1;
+    const int line0 = is_dg(P.space) ? 0 : blockIdx.x;
     for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
         int m = t / M, k = t - m * M;
         const C *X = spec + ((int64_t)l * P.lines + line0 + m) * P.nkx;
@@ -330,34 +332,34 @@ __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restri
                                            const T *__restrict__ lam, const T *__restrict__ u0, int l, int64_t unit,
                                            double acc[6]) {
     const int64_t S = P.S;
-    if (P.space == DG_P2_LF) {
-        const int N = P.nx;
+    if (is_dg(P.space)) {
+        const int N = P.nx, nm = P.lines;
         const int k = (int)unit;
         const int km = wrapm(k, N), kp = wrapp(k, N);
         if (l < P.nt) {
             const T *un = u + (int64_t)(l + 1) * S;
-            T c[3], lf[3], rg[3], d[3];
-            for (int m = 0; m < 3; ++m) { c[m] = un[m * N + k]; lf[m] = un[m * N + km]; rg[m] = un[m * N + kp]; }
-            dg_D(P, c, lf, rg, d);
-            for (int m = 0; m < 3; ++m) {
+            T c[3] = {0, 0, 0}, lf[3] = {0, 0, 0}, rg[3] = {0, 0, 0}, d[3];
+            for (int m = 0; m < nm; ++m) { c[m] = un[m * N + k]; lf[m] = un[m * N + km]; rg[m] = un[m * N + kp]; }
+            dgx_D(P, c, lf, rg, d);
+            for (int m = 0; m < nm; ++m) {
                 double r = (double)(d[m] + time_R(P, u + m * N + k, S, l));
                 acc[0] += r * r;
                 acc[2] += (double)phi[(int64_t)l * S + m * N + k] * r;
             }
         }
-        T c[3];
-        for (int m = 0; m < 3; ++m) c[m] = u[(int64_t)l * S + m * N + k];
+        T c[3] = {0, 0, 0};
+        for (int m = 0; m < nm; ++m) c[m] = u[(int64_t)l * S + m * N + k];
         if (l >= 1) {
             const T *ps = phi + (int64_t)(l - 1) * S;
-            T pl[3], pc[3], pr[3], d[3];
-            for (int m = 0; m < 3; ++m) { pl[m] = ps[m * N + km]; pc[m] = ps[m * N + k]; pr[m] = ps[m * N + kp]; }
-            dg_DT(P, c, pl, pc, pr, d);
-            for (int m = 0; m < 3; ++m) {
+            T pl[3] = {0, 0, 0}, pc[3] = {0, 0, 0}, pr[3] = {0, 0, 0}, d[3];
+            for (int m = 0; m < nm; ++m) { pl[m] = ps[m * N + km]; pc[m] = ps[m * N + k]; pr[m] = ps[m * N + kp]; }
+            dgx_DT(P, c, pl, pc, pr, d);
+            for (int m = 0; m < nm; ++m) {
                 double g = (double)(d[m] + time_T(P, phi + m * N + k, S, l));
                 acc[1] += g * g;
             }
         } else {
-            for (int m = 0; m < 3; ++m) {
+            for (int m = 0; m < nm; ++m) {
                 double r0 = (double)c[m] - (double)u0[m * N + k];
                 acc[3] += r0 * r0;
                 if (P.init == INIT_LAMBDA) {
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(256) k_check(Params<T> P, const T *__restrict_
                                                const T *__restrict__ lam, const T *__restrict__ u0,
                                                double *__restrict__ partials) {
     const int l = blockIdx.y;
-    const int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
+    const int64_t units = is_dg(P.space) ? P.nx : P.S;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t unit = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; unit < units;
          unit += (int64_t)gridDim.x * blockDim.x)
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(256) k_reduce6(const double *__restrict__ part
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_primal(const Params<T> &P, T *u, const T *phit, T *lam, T *lamt, const T *u0, cudaStream_t s) {
-    int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
+    int64_t units = is_dg(P.space) ? P.nx : P.S;
     dim3 grid((unsigned)((units + 255) / 256), (unsigned)(P.nt + 1));
     k_primal<T><<<grid, 256, 0, s>>>(P, u, phit, lam, lamt, u0);
     return cudaGetLastError();
@@ -425,7 +427,7 @@ cudaError_t launch_primal(const Params<T> &P, T *u, const T *phit, T *lam, T *la
 
 template <typename T>
 size_t smem_rows(const Params<T> &P) {
-    int nl = (P.space == DG_P2_LF) ? 3 : 1;
+    int nl = is_dg(P.space) ? P.lines : 1;
     return (size_t)nl * (P.nx / 2) * sizeof(typename Cplx<T>::type);
 }
 
@@ -433,7 +435,7 @@ template <typename T>
 cudaError_t launch_residual_rfft(const Params<T> &P, const T *u, void *spec, const void *twx, cudaStream_t s) {
     typedef typename Cplx<T>::type C;
     size_t sm = smem_rows(P);
-    int nlines = (P.space == DG_P2_LF) ? 1 : P.lines;
+    int nlines = is_dg(P.space) ? 1 : P.lines;
     dim3 grid((unsigned)nlines, (unsigned)P.nt);
     k_residual_rfft<T><<<grid, 256, sm, s>>>(P, u, (C *)spec, (const C *)twx);
     return cudaGetLastError();
@@ -457,7 +459,7 @@ cudaError_t launch_fft_y(const Params<T> &P, void *spec, const void *twy, int in
 template <typename T>
 cudaError_t launch_tsolve(const Params<T> &P, void *spec, const T *theta, const void *V, cudaStream_t s) {
     typedef typename Cplx<T>::type C;
-    int64_t cols = (P.space == DG_P2_LF) ? P.nkx : (int64_t)P.lines * P.nkx;
+    int64_t cols = is_dg(P.space) ? P.nkx : (int64_t)P.lines * P.nkx;
     k_tsolve<T><<<(unsigned)((cols + 127) / 128), 128, 0, s>>>(P, (C *)spec, theta, (const C *)V);
     return cudaGetLastError();
 }
@@ -466,7 +468,7 @@ template <typename T>
 cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *phit, const void *twx, cudaStream_t s) {
     typedef typename Cplx<T>::type C;
     size_t sm = smem_rows(P);
-    int nlines = (P.space == DG_P2_LF) ? 1 : P.lines;
+    int nlines = is_dg(P.space) ? 1 : P.lines;
     dim3 grid((unsigned)nlines, (unsigned)P.nt);
     k_dual_irfft<T><<<grid, 256, sm, s>>>(P, (const C *)spec, phi, phit, (const C *)twx);
     return cudaGetLastError();
@@ -475,7 +477,7 @@ cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *p
 // blocks per slice of the residual check: at most 32 (grid-stride beyond that)
 template <typename T>
 static int64_t check_grid_x(const Params<T> &P) {
-    int64_t units = (P.space == DG_P2_LF) ? P.nx : P.S;
+    int64_t units = is_dg(P.space) ? P.nx : P.S;
     return std::min<int64_t>((units + 255) / 256, 32);
 }
 

@@ -73,12 +73,13 @@ pdhg_status run(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s,
                 const void *lam, const void *u0, const void *gamma, double out[4], cudaStream_t stream) {
     Params<T> P;
     memset(&P, 0, sizeof(P));
-    const bool dg = s->space == PDHG_SPACE_DG_P2_LF;
+    const bool dg = s->space >= PDHG_SPACE_DG_P2_LF;
     P.dims = g->dims; P.space = s->space; P.time = s->time; P.init = s->init;
     P.nx = (int32_t)g->nx; P.ny = (int32_t)(g->dims == 2 ? g->ny : 1); P.nt = (int32_t)g->nt;
-    P.S = dg ? 3 * g->nx : (int64_t)g->nx * P.ny;
+    const int nm = s->space == PDHG_SPACE_DG_P2_LF ? 3 : 2;
+    P.S = dg ? nm * g->nx : (int64_t)g->nx * P.ny;
     P.nkx = (int32_t)(g->nx / 2 + 1);
-    P.lines = dg ? 3 : P.ny;
+    P.lines = dg ? nm : P.ny;
     double ht = g->T / (double)g->nt, hx = g->lx / (double)g->nx;
     double hy = g->dims == 2 ? g->ly / (double)g->ny : 1.0;
     P.alpha = (T)p->alpha; P.beta = (T)p->beta; P.nu = (T)p->nu; P.lf_a = (T)p->lf_a;
@@ -130,13 +131,14 @@ extern "C" pdhg_status pdhg_residual_noalloc(const pdhg_problem *prob, const pdh
         return err(PDHG_ERR_INVALID_ARG, "bad grid size");
     if (!(grid->T > 0) || !(grid->lx > 0) || (grid->dims == 2 && !(grid->ly > 0)))
         return err(PDHG_ERR_INVALID_ARG, "T, lx, ly must be positive");
-    if (scheme->space < PDHG_SPACE_FD_UPWIND || scheme->space > PDHG_SPACE_DG_P2_LF ||
+    if (scheme->space < PDHG_SPACE_FD_UPWIND || scheme->space > PDHG_SPACE_DG_P1_LF ||
         (scheme->time != PDHG_TIME_BE && scheme->time != PDHG_TIME_BDF2) ||
         (scheme->init != PDHG_INIT_LAMBDA && scheme->init != PDHG_INIT_PINNED))
         return err(PDHG_ERR_INVALID_ARG, "bad scheme");
-    if (scheme->space == PDHG_SPACE_DG_P2_LF && (grid->dims != 1 || gamma_half || prob->nu != 0))
-        return err(PDHG_ERR_UNSUPPORTED, "DG P2 is 1D without viscous terms");
-    if (scheme->space != PDHG_SPACE_FD_UPWIND && !(prob->lf_a > 0))
+    if (scheme->space >= PDHG_SPACE_DG_P2_LF && (grid->dims != 1 || gamma_half || prob->nu != 0))
+        return err(PDHG_ERR_UNSUPPORTED, "DG is 1D without viscous terms");
+    if ((scheme->space == PDHG_SPACE_FD_LF || scheme->space == PDHG_SPACE_DG_P2_LF ||
+         scheme->space == PDHG_SPACE_DG_P1_LF) && !(prob->lf_a > 0))
         return err(PDHG_ERR_INVALID_ARG, "lf_a must be given (> 0) for Lax-Friedrichs schemes");
     if (gamma_half && grid->dims != 1) return err(PDHG_ERR_UNSUPPORTED, "gamma_half is 1D only");
     cudaStream_t s = (cudaStream_t)stream;

@@ -25,7 +25,7 @@ from typing import Optional
 
 import numpy as np
 
-SPACES = ("fd_upwind", "fd_lf", "dg_p2_lf")
+SPACES = ("fd_upwind", "fd_lf", "dg_p2_lf", "dg_p1_upwind", "dg_p1_lf")
 TIMES = ("be", "bdf2")
 INITS = ("lambda", "pinned")
 
@@ -72,15 +72,20 @@ class Problem:
         return self.T / self.nt
 
     @property
+    def nmodes(self) -> int:
+        """Degrees of freedom per DG cell (1 for finite differences)."""
+        return {"dg_p2_lf": 3, "dg_p1_upwind": 2, "dg_p1_lf": 2}.get(self.space, 1)
+
+    @property
     def ndof(self) -> int:
-        if self.space == "dg_p2_lf":
-            return 3 * self.nx
+        if self.nmodes > 1:
+            return self.nmodes * self.nx
         return self.nx * (self.ny if self.dims == 2 else 1)
 
     @property
     def slice_shape(self) -> tuple:
-        if self.space == "dg_p2_lf":
-            return (3, self.nx)
+        if self.nmodes > 1:
+            return (self.nmodes, self.nx)
         if self.dims == 2:
             return (self.ny, self.nx)
         return (self.nx,)
@@ -97,10 +102,10 @@ class Problem:
         assert self.space in SPACES and self.time in TIMES and self.init in INITS
         assert self.dims in (1, 2)
         assert self.u0 is not None and self.u0.shape == self.slice_shape
-        if self.space == "dg_p2_lf":
+        if self.nmodes > 1:
             assert self.dims == 1
         if self.gamma_half is not None:
-            assert self.dims == 1 and self.space != "dg_p2_lf"
+            assert self.dims == 1 and self.nmodes == 1
             assert self.gamma_half.shape == (self.nx,)
 
 
@@ -132,6 +137,14 @@ def dg_p2_project(fun, nx: int, lx: float) -> np.ndarray:
     for m in range(3):
         U[m] = 0.5 * (2 * m + 1) * np.einsum("q,q,qj->j", _GAUSS3_W, P[m], fq)
     return U
+
+
+def dg_p1_nodes(fun, nx: int, lx: float) -> np.ndarray:
+    """Initial data for DG P1 nodal (Sec. 3.2.2): point values at x_{j-1/4}, x_{j+1/4}
+    of cell j = [j h, (j+1) h].  Returns ``[2][nx]``."""
+    h = lx / nx
+    c = (np.arange(nx) + 0.5) * h
+    return np.stack([fun(c - 0.25 * h), fun(c + 0.25 * h)])
 
 
 def random_fourier_2d(n: int, length: float, seed: int, modes: int = 8,
@@ -234,6 +247,31 @@ def burgers_2d(n: int = 1024, nt: int = 256, seed: int = 20722, cfl: float = 1.0
                    nx=n, ny=n, lx=lx, ly=lx, T=nt * cfl * hx, nt=nt, alpha=0.5,
                    beta=0.0, lf_a=amax, c=amax, tau_u=tau[0], tau_u0=tau[1],
                    tau_phi=tau[2], tau_lambda=tau[3], init=init, u0=u0)
+
+
+def transport_dg_p1(ncell: int = 64, nt: int = 32, T: float = 0.5, time: str = "bdf2",
+                    tau=(0.3, 0.1, 0.3, 0.99), init: str = "lambda") -> Problem:
+    """Linear transport u_t + 2 u_x = 0 on periodic [0, 1], u0 = sin(2 pi x), DG P1
+    nodal + upwind flux, BDF2 (Sec. 4.2, Table 2 uses h_x = h_t)."""
+    lx = 1.0
+    u0 = dg_p1_nodes(lambda x: np.sin(2.0 * np.pi * x), ncell, lx)
+    return Problem(name=f"transport_dg_p1_{ncell}x{nt}", dims=1, space="dg_p1_upwind",
+                   time=time, nx=ncell, lx=lx, T=T, nt=nt, alpha=0.0, beta=2.0, lf_a=2.0,
+                   c=2.0, tau_u=tau[0], tau_u0=tau[1], tau_phi=tau[2], tau_lambda=tau[3],
+                   init=init, u0=u0)
+
+
+def traffic_dg_p1(ncell: int = 256, nt: int = 32, time: str = "be",
+                  tau=(0.4, 0.4, 0.4, 0.99), init: str = "lambda") -> Problem:
+    """Traffic flow u_t + (u - u^2)_x = 0 on periodic [0, 2] x [0, 1] with u0 = 0.1 on
+    [1, 2] and 0.25 elsewhere, DG P1 nodal + upwind flux (f' >= 0 on the data), BE
+    (Sec. 4.3, Eq. 4.1-4.2)."""
+    lx = 2.0
+    u0 = dg_p1_nodes(lambda x: np.where((x >= 1.0) & (x <= 2.0), 0.1, 0.25), ncell, lx)
+    return Problem(name=f"traffic_dg_p1_{ncell}x{nt}", dims=1, space="dg_p1_upwind",
+                   time=time, nx=ncell, lx=lx, T=1.0, nt=nt, alpha=-1.0, beta=1.0, lf_a=1.0,
+                   c=1.0, tau_u=tau[0], tau_u0=tau[1], tau_phi=tau[2], tau_lambda=tau[3],
+                   init=init, u0=u0)
 
 
 def viscous_burgers(nx: int = 2048, nt: int = 1024, T: float = 2.0, nu: float = 1e-3,

@@ -51,6 +51,8 @@ def cases():
     yield auto_steps(W.burgers_dg_p2(ncell=512, nt=7, T=0.5).replace(c=0.5))
     yield steps(W.burgers_2d(n=64, nt=5).replace(ny=32, u0=W.burgers_2d(n=64).u0[:32]).replace(ly=np.pi), 0.4, 0.4)
     yield steps(W.burgers_2d(n=32, nt=3).replace(nu=0.01, time="bdf2"), 0.3, 0.3)
+    yield auto_steps(W.transport_dg_p1(ncell=512, nt=9))
+    yield auto_steps(W.traffic_dg_p1(ncell=256, nt=7).replace(space="dg_p1_lf", lf_a=1.0))
 
 
 def run_gpu(B, p, precision, n):
@@ -72,15 +74,20 @@ def rel(a, b):
 
 @pytest.mark.parametrize("p", list(cases()), ids=lambda p: f"{p.name}_{p.time}_{p.init}")
 def test_fixed_iterates_fp64(B, p):
+    """25 iterations, element by element.  The bound is 1e-12 on u; for the DG P1 cases
+    it is 1e-11: there, perturbing the oracle's own u0 by 1e-16 grows 180-1200 times over
+    25 iterations (under 50 times for every other case), so rounding-order differences
+    between the two implementations reach a few 1e-12."""
     n = 25
     g, res = run_gpu(B, p, "fp64", n)
     o = run_oracle(p, n)
-    assert rel(g["u"], o["u"]) <= 1e-12
-    assert rel(g["phi"], o["phi"]) <= 1e-11
-    assert rel(g["phit"], o["phit"]) <= 1e-11
+    tu = 1e-11 if p.nmodes == 2 else 1e-12
+    assert rel(g["u"], o["u"]) <= tu
+    assert rel(g["phi"], o["phi"]) <= 10 * tu
+    assert rel(g["phit"], o["phit"]) <= 10 * tu
     if p.init == "lambda":
-        assert rel(g["lambda"], o["lam"]) <= 1e-11
-        assert rel(g["lambdat"], o["lamt"]) <= 1e-11
+        assert rel(g["lambda"], o["lam"]) <= 10 * tu
+        assert rel(g["lambdat"], o["lamt"]) <= 10 * tu
     ores = opdhg.residual_norms(p, o)
     assert np.allclose(res[:3], ores[:3], rtol=1e-10, atol=1e-300)
     assert abs(res[3] - ores[3]) <= 1e-9 * max(abs(ores[3]), 1e-300)
@@ -101,6 +108,7 @@ def converged_cases():
     yield W.heat_table1(16, 8)
     yield steps(W.burgers_2d(n=8, nt=3), 0.45, 0.45)
     yield auto_steps(W.burgers_dg_p2(ncell=8, nt=4, T=0.4, time="be").replace(c=0.5), 1.0)
+    yield auto_steps(W.transport_dg_p1(ncell=16, nt=8), 1.0)
 
 
 @pytest.mark.parametrize("p", list(converged_cases()), ids=lambda p: f"{p.name}_{p.time}")
@@ -179,3 +187,30 @@ def test_relative_stop_and_nonfinite(B):
         with pytest.raises(B.PdhgError) as e:
             s.iterate(5000, tol=0.0, check_every=10)
         assert e.value.status in (-4, -5)
+
+
+def test_table2_from_gpu_pdhg(B):
+    """Table 2 (DG P1 nodal + BDF2 linear transport) from the GPU's converged PDHG
+    iterates: the L2 errors round to the printed 0.1296, 0.0372, 0.0096."""
+    import test_oracle_solution as tos
+    rows = tos._table2()
+    sols = []
+    for k, _, _ in rows:
+        n = 2 ** k
+        p = auto_steps(W.transport_dg_p1(ncell=n, nt=n // 2, T=0.5), 1.0)
+        with B.Solver(p, precision="fp64", path="plain") as s:
+            s.iterate(200000, tol=1e-10, check_every=100)
+            sols.append((p, s.get_host("u")))
+    errs = tos.table2_errors(sols)
+    for (k, printed, _), e in zip(rows, errs):
+        assert abs(e - printed) <= 5e-5, (k, e, printed)
+
+
+def test_traffic_iterations_on_gpu(B):
+    """Sec. 4.3 traffic example on the GPU: iterations to Res <= 1e-3 within 10% of the
+    printed 4573, and equal to the float64 oracle's count up to the check granularity."""
+    p = W.traffic_dg_p1()
+    with B.Solver(p, precision="fp64", path="plain") as s:
+        it = s.iterate(20000, tol=1e-3, check_every=1)
+    assert abs(it - 4573) <= 0.1 * 4573
+    assert abs(it - 4715) <= 2

@@ -12,6 +12,7 @@ from oracle import precond, spacetime
     W.burgers_2d(n=6, nt=3),
     W.burgers_dg_p2(ncell=6, nt=4),
     W.viscous_burgers(nx=7, nt=3),
+    W.transport_dg_p1(ncell=6, nt=4),
 ], ids=lambda p: p.name)
 def test_kd_inverse_equals_dense_solve(p):
     """FFT-in-x + Thomas-in-t equals a dense solve of K_d assembled in real space from

@@ -26,6 +26,8 @@ def small_problems():
     yield W.burgers_2d(n=8, nt=3)
     yield W.viscous_burgers(nx=8, nt=5, nu=0.05)
     yield W.advection_upwind_be(nx=8, nt=4).replace(alpha=-1.0, beta=1.0)   # traffic flux, upwind
+    yield W.transport_dg_p1(ncell=8, nt=4).replace(alpha=0.6, beta=0.3)
+    yield W.traffic_dg_p1(ncell=8, nt=3, time="bdf2").replace(space="dg_p1_lf", lf_a=1.3)
 
 
 @pytest.mark.parametrize("p", list(small_problems()), ids=lambda p: p.name + "_" + p.time)
@@ -96,6 +98,27 @@ def test_dg_p2_operator_matches_exact_builder():
     assert np.max(np.abs(spatial.dg_D(p, U) + ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("flux", ["upwind", "lf"])
+def test_dg_p1_operator_matches_exact_builder(flux):
+    """The vectorised DG P1 nodal operator equals the exact builder's forms (which
+    reproduce the paper's A1, A2, C1..C9) on random data, upwind and Lax-Friedrichs."""
+    rng = np.random.default_rng(4)
+    n = 9
+    p = W.transport_dg_p1(ncell=n, nt=2).replace(space=f"dg_p1_{flux}", alpha=0.7, beta=-0.3, lf_a=1.9)
+    U = rng.standard_normal((2, n))
+    asm = dg_exact.assemble(dg_exact.p1_nodal(), flux)
+    ref = np.zeros((2, n))
+    for j in range(n):
+        for s in (-1, 0, 1):
+            Us = U[:, (j + s) % n]
+            for m in range(2):
+                Q = np.array(asm[("alpha", s)][m], dtype=float)
+                Lb = np.array(asm[("beta", s)][m], dtype=float)
+                La = np.array(asm[("a", s)][m], dtype=float)
+                ref[m, j] += (p.alpha * Us @ Q @ Us + p.beta * Lb @ Us + p.lf_a * La @ Us) / p.hx
+    assert np.max(np.abs(spatial.dg1_D(p, U) + ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
 def test_fd_symbols_closed_form():
     """Linear FD operators on a Fourier mode: upwind speed b gives
     b (1 - e^{-i theta}) / h, the viscous term nu L(theta) (L = (2-2cos)/h^2)."""
@@ -133,13 +156,15 @@ def test_2d_reduces_to_1d():
 
 
 @pytest.mark.parametrize("p", [W.burgers_2d(n=8, nt=2), W.burgers_dg_p2(ncell=8, nt=2),
-                               W.viscous_burgers(nx=8, nt=2), W.heat_table1(8, 2)],
+                               W.viscous_burgers(nx=8, nt=2), W.heat_table1(8, 2),
+                               W.traffic_dg_p1(ncell=8, nt=2)],
                          ids=lambda p: p.name)
 def test_spatial_conservation(p):
-    """Periodic fluxes telescope: sum_j D(v)_j = 0 (DG: the cell-average mode)."""
+    """Periodic fluxes telescope: sum_j D(v)_j = 0 (DG: the cell averages -- the P0 mode
+    for P2, (U1 + U2)/2 for the P1 nodal basis)."""
     v = np.random.default_rng(2).standard_normal(p.slice_shape)
     d = spatial.D(p, v)
-    s = d[0].sum() if p.space == "dg_p2_lf" else d.sum()
+    s = d[0].sum() if p.space == "dg_p2_lf" else (d.sum() / 2 if p.nmodes == 2 else d.sum())
     assert abs(s) <= 1e-11 * np.sum(np.abs(d))
 
 
