@@ -325,6 +325,26 @@ extern "C" pdhg_status pdhg_workspace_size(const pdhg_problem *prob, const pdhg_
     return PDHG_OK;
 }
 
+// Twiddles of a length-N Stockham transform grouped by stage: the radix-4 stage of
+// span p (p = P0, 4 P0, ... with P0 = 1 for even log2 N, 2 for odd) owns entries
+// (p - P0) + q p + k = W_N^{(q+1) k N/(4p)}, q = 0..2, k < p.  N complex entries
+// (interleaved re, im), unused ones zero.
+static std::vector<float> staged_twiddles(int64_t N) {
+    std::vector<float> t(2 * N, 0.f);
+    int lg = 0;
+    while ((int64_t(1) << lg) < N) ++lg;
+    const int64_t p0 = (lg & 1) ? 2 : 1;
+    for (int64_t p = p0; 4 * p <= N; p *= 4)
+        for (int64_t q = 0; q < 3; ++q)
+            for (int64_t k = 0; k < p; ++k) {
+                const int64_t e = (p - p0) + q * p + k;
+                const double a = 2.0 * M_PI * (double)((q + 1) * k * (N / (4 * p))) / (double)N;
+                t[2 * e] = (float)std::cos(a);
+                t[2 * e + 1] = (float)(-std::sin(a));
+            }
+    return t;
+}
+
 template <typename T>
 static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pdhg_grid *g, double lf_a) {
     const Geom &G = h->G;
@@ -398,19 +418,11 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     }
     CK(cudaMemcpy(F<T>(h, h->L.theta), th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
     if (G.fused) {
-        // fused 2D path: full twiddle tables W_M^j (M = nx/2), W_ny^j and theta in [kx][ky] order
+        // fused 2D path: staged twiddle tables for the Stockham transforms of length
+        // M = nx/2 (along x) and ny (along y), and theta in [kx][ky] order
         Fused2D &f = h->fused;
         fused2d_layout(&f, h->ws + h->L.fused, G.nx, G.ny, G.nt);
-        const int64_t M = G.nx / 2;
-        std::vector<float> tm(2 * M), ty(2 * G.ny), tt(G.nkx * G.ny);
-        for (int64_t j = 0; j < M; ++j) {
-            double a = 2.0 * M_PI * (double)j / (double)M;
-            tm[2 * j] = (float)std::cos(a); tm[2 * j + 1] = (float)(-std::sin(a));
-        }
-        for (int64_t j = 0; j < G.ny; ++j) {
-            double a = 2.0 * M_PI * (double)j / (double)G.ny;
-            ty[2 * j] = (float)std::cos(a); ty[2 * j + 1] = (float)(-std::sin(a));
-        }
+        std::vector<float> tm = staged_twiddles(G.nx / 2), ty = staged_twiddles(G.ny), tt(G.nkx * G.ny);
         for (int64_t ky = 0; ky < G.ny; ++ky)
             for (int64_t kx = 0; kx < G.nkx; ++kx) tt[kx * G.ny + ky] = (float)th[ky * G.nkx + kx];
         CK(cudaMemcpy(f.twM, tm.data(), tm.size() * 4, cudaMemcpyHostToDevice));

@@ -8,8 +8,8 @@ namespace pdhg {
 struct Fused2D {
     float *u2;               // second u buffer (rows-A reads one, writes the other)
     float2 *spec;            // spectrum [l][kx][y]: X, then spill, then K_d^{-1} R, in place
-    float2 *twM;             // W_M^j, j < M = nx/2
-    float2 *twY;             // W_ny^j, j < ny
+    float2 *twM;             // staged Stockham twiddles of length M = nx/2 (stockham.cuh)
+    float2 *twY;             // staged Stockham twiddles of length ny
     float *thetaT;           // theta per mode, [kx][ky]
     const float2 *twN;       // W_nx^k, k <= nx/2 (the plain path's table)
     int cur;                 // 0: current u is the main buffer, 1: u2

@@ -23,6 +23,7 @@ namespace pdhg {
 
 constexpr int FH = 4;          // rows per block in the row kernels
 constexpr int FTHREADS = 256;
+constexpr int ATHREADS = 256;  // rows-A block size
 
 // ---------------------------------------------------------------------------
 // rows-A
@@ -49,7 +50,7 @@ __device__ __forceinline__ void load_rows(float *dst, const float *__restrict__ 
 }
 
 template <int LOG2M, bool BDF2_>
-__global__ void __launch_bounds__(FTHREADS) k_rowsA(Params<float> P, const float *__restrict__ u_in,
+__global__ void __launch_bounds__(ATHREADS) k_rowsA(Params<float> P, const float *__restrict__ u_in,
                                                     float *__restrict__ u_out, const float *__restrict__ phit,
                                                     float *__restrict__ lam, float *__restrict__ lamt,
                                                     const float *__restrict__ u0, float2 *__restrict__ spec,
@@ -141,11 +142,12 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsA(Params<float> P, const float
             const float *ucur = us + ((m + NR - 1) % NR) * RU * NX;
             const float *uold = us + ((m + NR - 2) % NR) * RU * NX;
             const float kn = coef_new(P, lr), kc = coef_cur(P, lr), ko = coef_old(P, lr);
-            constexpr int GPT = FH * V / FTHREADS;              // float4 groups per thread
+            constexpr int GPT = FH * V / ATHREADS > 0 ? FH * V / ATHREADS : 1;   // float4 groups per thread
             float4 R[GPT];
 #pragma unroll
             for (int j = 0; j < GPT; ++j) {
-                const int gi = threadIdx.x + j * FTHREADS;
+                const int gi = threadIdx.x + j * ATHREADS;
+                if (gi >= FH * V) break;
                 const int rr = gi / V, x4 = gi - rr * V;
                 const int r = rr + 1;
                 const float *row = un + r * NX;
@@ -179,7 +181,8 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsA(Params<float> P, const float
             float *fin = BDF2_ ? const_cast<float *>(uold) : const_cast<float *>(ucur);
 #pragma unroll
             for (int j = 0; j < GPT; ++j)          // z_n = R_{2n} + i R_{2n+1}
-                reinterpret_cast<float4 *>(fin)[threadIdx.x + j * FTHREADS] = R[j];
+                if (threadIdx.x + j * ATHREADS < FH * V)
+                    reinterpret_cast<float4 *>(fin)[threadIdx.x + j * ATHREADS] = R[j];
             __syncthreads();
             const float2 *res = stockham<LOG2M, false>(reinterpret_cast<float2 *>(fin),
                                                        reinterpret_cast<float2 *>(pp), FH, twM);
@@ -324,11 +327,11 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
 __global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *__restrict__ spec,
                                                        const float2 *__restrict__ twY,
                                                        const float *__restrict__ thetaT) {
-    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2;
+    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2, PN = NY + NY / 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *ba = reinterpret_cast<float2 *>(smem_raw);              // [TB][NY]
-    float2 *bb = ba + TB * NY;                                      // [TB][NY]
-    float2 *tw = bb + TB * NY;                                      // [NY]
+    float2 *ba = reinterpret_cast<float2 *>(smem_raw);              // [TB][PN] (padded)
+    float2 *bb = ba + TB * PN;                                      // [TB][PN]
+    float2 *tw = bb + TB * PN;                                      // [NY]
     const int kx = blockIdx.x;
     const int nt = P.nt;
     const int64_t cs = (int64_t)P.nkx * NY;
@@ -358,7 +361,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *
         for (int b = 0; b < TB; ++b) {
             float2 x0 = pf[b][0], x1 = pf[b][1], x2 = pf[b][2], x3 = pf[b][3];
             dft4<false>(x0, x1, x2, x3);
-            float4 *d = reinterpret_cast<float4 *>(ba + b * NY + 4 * t);
+            float4 *d = reinterpret_cast<float4 *>(ba + b * PN + padx(4 * t));
             d[0] = make_float4(x0.x, x0.y, x1.x, x1.y);
             d[1] = make_float4(x2.x, x2.y, x3.x, x3.y);
         }
@@ -371,15 +374,16 @@ __global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *
                 for (int q = 0; q < 4; ++q) pf[b][q] = l < nt ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham_r4_range<LOG2NY, false>(ba, bb, TB, tw, 4, 256);
+        const float2 *res = stockham_r4_range_pad<LOG2NY, false>(ba, bb, TB, tw, 4, 256);
         // stage 5 (span 256) in registers: inputs t + 256 r with twiddles W^{r t}, outputs t + 256 q
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = lb + b;
-            float2 x0 = res[b * NY + t];
-            float2 x1 = cmul(res[b * NY + t + Q], tw[t]);
-            float2 x2 = cmul(res[b * NY + t + 2 * Q], tw[2 * t]);
-            float2 x3 = cmul(res[b * NY + t + 3 * Q], tw[3 * t]);
+            const float2 *rb = res + b * PN;
+            float2 x0 = rb[padx(t)];
+            float2 x1 = cmul(rb[padx(t + Q)], tw[255 + t]);             // staged block of span 256
+            float2 x2 = cmul(rb[padx(t + 2 * Q)], tw[255 + 256 + t]);
+            float2 x3 = cmul(rb[padx(t + 3 * Q)], tw[255 + 512 + t]);
             dft4<false>(x0, x1, x2, x3);
             if (l < nt) {
                 float2 y[4] = {x0, x1, x2, x3};
@@ -418,7 +422,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *
             }
             // inverse stage 1 (span 1) in registers
             dft4<true>(z[0], z[1], z[2], z[3]);
-            float4 *d = reinterpret_cast<float4 *>(ba + b * NY + 4 * t);
+            float4 *d = reinterpret_cast<float4 *>(ba + b * PN + padx(4 * t));
             d[0] = make_float4(z[0].x, z[0].y, z[1].x, z[1].y);
             d[1] = make_float4(z[2].x, z[2].y, z[3].x, z[3].y);
         }
@@ -431,14 +435,15 @@ __global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *
                 for (int q = 0; q < 4; ++q) pf[b][q] = l >= 0 ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham_r4_range<LOG2NY, true>(ba, bb, TB, tw, 4, 256);
+        const float2 *res = stockham_r4_range_pad<LOG2NY, true>(ba, bb, TB, tw, 4, 256);
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = hi - b;
-            float2 x0 = res[b * NY + t];
-            float2 x1 = cmulconj(res[b * NY + t + Q], tw[t]);
-            float2 x2 = cmulconj(res[b * NY + t + 2 * Q], tw[2 * t]);
-            float2 x3 = cmulconj(res[b * NY + t + 3 * Q], tw[3 * t]);
+            const float2 *rb = res + b * PN;
+            float2 x0 = rb[padx(t)];
+            float2 x1 = cmulconj(rb[padx(t + Q)], tw[255 + t]);
+            float2 x2 = cmulconj(rb[padx(t + 2 * Q)], tw[255 + 256 + t]);
+            float2 x3 = cmulconj(rb[padx(t + 3 * Q)], tw[255 + 512 + t]);
             dft4<true>(x0, x1, x2, x3);
             if (l >= 0) {
                 col[(int64_t)l * cs + t] = x0;
@@ -450,7 +455,10 @@ __global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *
     }
 }
 
-static size_t smem_cols(int log2ny) { return (size_t)(2 * 2 + 1) * (1 << log2ny) * 8; }
+static size_t smem_cols(int log2ny) {
+    const size_t n = (size_t)1 << log2ny;
+    return log2ny == 10 ? (4 * (n + n / 4) + n) * 8 : 5 * n * 8;    // ny = 1024: padded buffers
+}
 
 // ---------------------------------------------------------------------------
 // rows-C: inverse real FFT along x, dual step and extrapolation.  phi is read
@@ -558,9 +566,9 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC1024(Params<float> P, const f
     for (int rr = 0; rr < 2; ++rr) {
         const float2 *r = res + (2 * h + rr) * M;
         float2 x0 = r[i];
-        float2 x1 = cmulconj(r[i + 128], twM[i]);
-        float2 x2 = cmulconj(r[i + 256], twM[2 * i]);
-        float2 x3 = cmulconj(r[i + 384], twM[3 * i]);
+        float2 x1 = cmulconj(r[i + 128], twM[126 + i]);             // staged block of span 128
+        float2 x2 = cmulconj(r[i + 256], twM[126 + 128 + i]);
+        float2 x3 = cmulconj(r[i + 384], twM[126 + 256 + i]);
         dft4<true>(x0, x1, x2, x3);
         const float2 z[4] = {x0, x1, x2, x3};
         float2 *p2 = reinterpret_cast<float2 *>(phi + base + (int64_t)(2 * h + rr) * NX);
@@ -657,10 +665,10 @@ static cudaError_t launch_rowsA(const Fused2D *f, const Params<float> &P, const 
                                 const float *phit, float *lam, float *lamt, const float *u0, cudaStream_t s) {
     dim3 grid((unsigned)(P.ny / FH), (unsigned)((P.nt + f->tc - 1) / f->tc));
     if (P.time == BDF2)
-        k_rowsA<L, true><<<grid, FTHREADS, smem_rowsA(L, true), s>>>(P, uin, uout, phit, lam, lamt, u0, f->spec,
+        k_rowsA<L, true><<<grid, ATHREADS, smem_rowsA(L, true), s>>>(P, uin, uout, phit, lam, lamt, u0, f->spec,
                                                                      f->twN, f->twM, f->tc);
     else
-        k_rowsA<L, false><<<grid, FTHREADS, smem_rowsA(L, false), s>>>(P, uin, uout, phit, lam, lamt, u0, f->spec,
+        k_rowsA<L, false><<<grid, ATHREADS, smem_rowsA(L, false), s>>>(P, uin, uout, phit, lam, lamt, u0, f->spec,
                                                                        f->twN, f->twM, f->tc);
     return cudaGetLastError();
 }
