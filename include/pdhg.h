@@ -176,6 +176,59 @@ pdhg_status pdhg_stage_times(pdhg_handle *h, double ms[PDHG_NUM_STAGES],
 const char *pdhg_last_error(void);
 
 /*
+ * Algorithm 2 (Sec. 3.4): refinement of the time mesh.  Solves the problem on
+ * nt/2^(levels-1), nt/2^(levels-2), ..., nt slices of the same horizon T, each
+ * level started from the previous level's (u, phi, lambda) carried to the finer
+ * mesh: u and phi linearly in t (u^l sits at time l h_t, phi^l -- the multiplier
+ * of R^l -- at (l+1) h_t, constant below the first coarse time), lambda copied,
+ * and phit = phi, lamt = lambda.  The first level starts from [u0, 0, 0].
+ *
+ * levels in [1, 16]; grid->nt divisible by 2^(levels-1).  iters[k] (host,
+ * `levels` entries, coarsest first) bounds level k's iterations; a level stops
+ * early once Res <= tol when check_every > 0 (same rules as pdhg_iterate, with
+ * `relative` relative to that level's cold-start residual).  iters_done (host,
+ * `levels` entries, may be NULL) receives the counts.
+ *
+ * The workspace (device, caller-owned, 256-byte aligned, size from
+ * pdhg_refine_workspace_size) holds two alternating regions; the returned
+ * handle is the finest level, lives in the workspace, and is used and
+ * destroyed like one from pdhg_create.  Errors as pdhg_create/pdhg_iterate;
+ * on an error no handle is returned.
+ */
+pdhg_status pdhg_refine_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                       const pdhg_scheme *scheme, int32_t levels, size_t *bytes);
+pdhg_status pdhg_solve_refine(const pdhg_problem *prob, const pdhg_grid *grid,
+                              const pdhg_scheme *scheme, int32_t levels, const int64_t *iters,
+                              double tol, int32_t check_every, int32_t relative, void *workspace,
+                              size_t bytes, void *stream, pdhg_handle **out, int64_t *iters_done);
+
+/*
+ * Algorithm 3 (Sec. 3.5): one time step at a time.  For l = 0..nt-1, runs
+ * Algorithm 1 on the two-slice problem over [l h_t, (l+1) h_t] whose initial
+ * data is u*^l (u*^0 = u0), started from [u*^l, u*^l], 0, 0, until both
+ * entries of its Res are <= tol, checked every check_every iterations, or
+ * max_iters_per_step.  Res here is the L2 norm over the domain at one time
+ * (weight w_x, no h_t), as Sec. 3.5 defines it.  Every input of the full
+ * problem is kept (flux, c, step sizes, h_t, and the Lax-Friedrichs constant
+ * computed from the full problem's u0 when prob->lf_a is 0), so with tol -> 0
+ * the result is the full scheme's solution.  Backward Euler only
+ * (PDHG_ERR_UNSUPPORTED for BDF2: its steps need two past slices).
+ *
+ * u_out: device, (nt+1)*ndof values of the scheme's precision, written with
+ * u*^0..u*^nt.  iters_per_step (host, nt entries) and iters_total may be NULL.
+ * workspace: device, caller-owned, 256-byte aligned, size from
+ * pdhg_one_step_workspace_size (one handle with nt = 1).  Synchronises the
+ * stream before returning.  A step that fails (NONFINITE, DIVERGED, CUDA)
+ * returns its status; u_out then holds the steps completed so far.
+ */
+pdhg_status pdhg_one_step_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                         const pdhg_scheme *scheme, size_t *bytes);
+pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_grid *grid,
+                                const pdhg_scheme *scheme, double tol, int64_t max_iters_per_step,
+                                int32_t check_every, void *workspace, size_t bytes, void *stream,
+                                void *u_out, int64_t *iters_per_step, int64_t *iters_total);
+
+/*
  * Residual norms of a caller-held state, with no handle, no workspace and no
  * device allocation.  (An addition of this library: the paper has no
  * counterpart.)  For callers that cannot allocate device memory -- e.g. code

@@ -31,7 +31,9 @@ STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_r
 # every symbol include/pdhg.h declares
 EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_stream", "pdhg_iterate",
            "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_info", "pdhg_launch_count",
-           "pdhg_set_profiling", "pdhg_stage_times", "pdhg_last_error", "pdhg_residual_noalloc"]
+           "pdhg_set_profiling", "pdhg_stage_times", "pdhg_last_error", "pdhg_refine_workspace_size",
+           "pdhg_solve_refine", "pdhg_one_step_workspace_size", "pdhg_solve_one_step",
+           "pdhg_residual_noalloc"]
 
 
 class PdhgError(RuntimeError):
@@ -86,6 +88,12 @@ def load(path: str = LIB_PATH):
         "pdhg_launch_count": [vp, ctypes.POINTER(i64), i32],
         "pdhg_set_profiling": [vp, i32],
         "pdhg_stage_times": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
+        "pdhg_refine_workspace_size": [P, G, S, i32, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_solve_refine": [P, G, S, i32, ctypes.POINTER(i64), ctypes.c_double, i32, i32, vp, ctypes.c_size_t,
+                              vp, ctypes.POINTER(vp), ctypes.POINTER(i64)],
+        "pdhg_one_step_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_solve_one_step": [P, G, S, ctypes.c_double, i64, i32, vp, ctypes.c_size_t, vp, vp,
+                                ctypes.POINTER(i64), ctypes.POINTER(i64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -131,13 +139,18 @@ def workspace_size(p, precision="fp32", path="auto") -> int:
 class Solver:
     """One space-time problem on the GPU (a pdhg_handle plus its torch-owned workspace)."""
 
-    def __init__(self, p, precision="fp32", path="auto", device=None, stream=None):
+    def __init__(self, p, precision="fp32", path="auto", device=None, stream=None, _adopt=None):
         import torch
         self._torch = torch
         self.p = p
         self.precision = precision
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.device = torch.device(device if device is not None else "cuda")
+        self.ndof = p.ndof
+        self.nt = p.nt
+        if _adopt is not None:           # a handle made by another entry point, in `workspace`
+            self.h, self.workspace, self._stream = _adopt
+            return
         lib = load()
         prob, grid, scheme, keep = structs(p, precision, path)
         nbytes = ctypes.c_size_t(0)
@@ -151,8 +164,6 @@ class Solver:
                                ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
                                ctypes.c_void_p(s.cuda_stream), ctypes.byref(h)))
         self.h = h
-        self.ndof = p.ndof
-        self.nt = p.nt
 
     # ---- lifecycle ----
     def close(self):
@@ -236,3 +247,49 @@ def solve(p, precision="fp32", max_iters=10000, tol=1e-6, check_every=50, relati
     with Solver(p, precision=precision, path=path) as s:
         it = s.iterate(max_iters, tol=tol, check_every=check_every, relative=relative)
         return s.get_host("u"), it, s.residual()
+
+
+def solve_refine(p, levels, iters, tol=1e-3, check_every=1, relative=False, precision="fp64", path="auto",
+                 device=None, stream=None):
+    """Algorithm 2 (Sec. 3.4) on the final problem p: levels with p.nt >> (levels-1-k)
+    slices, iters[k] iterations at most on level k.  Returns (Solver of the finest
+    level, iterations per level)."""
+    import torch
+    lib = load()
+    prob, grid, scheme, keep = structs(p, precision, path)
+    nbytes = ctypes.c_size_t(0)
+    _check(lib.pdhg_refine_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                          int(levels), ctypes.byref(nbytes)))
+    dev = torch.device(device if device is not None else "cuda")
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    it_in = (ctypes.c_int64 * levels)(*[int(v) for v in iters])
+    it_out = (ctypes.c_int64 * levels)()
+    h = ctypes.c_void_p()
+    _check(lib.pdhg_solve_refine(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme), int(levels), it_in,
+                                 float(tol), int(check_every), int(bool(relative)), ctypes.c_void_p(ws.data_ptr()),
+                                 nbytes.value, ctypes.c_void_p(s.cuda_stream), ctypes.byref(h), it_out))
+    return Solver(p, precision=precision, device=dev, _adopt=(h, ws, s)), list(it_out)
+
+
+def solve_one_step(p, tol=1e-3, max_iters_per_step=100000, check_every=1, precision="fp64", device=None,
+                   stream=None):
+    """Algorithm 3 (Sec. 3.5): returns (u* as a device tensor [nt+1][...], iterations per step)."""
+    import torch
+    lib = load()
+    prob, grid, scheme, keep = structs(p, precision, "plain")
+    nbytes = ctypes.c_size_t(0)
+    _check(lib.pdhg_one_step_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                            ctypes.byref(nbytes)))
+    dev = torch.device(device if device is not None else "cuda")
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    u = torch.empty((p.nt + 1,) + tuple(p.slice_shape), dtype=dtype, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    per = (ctypes.c_int64 * p.nt)()
+    tot = ctypes.c_int64(0)
+    _check(lib.pdhg_solve_one_step(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme), float(tol),
+                                   int(max_iters_per_step), int(check_every), ctypes.c_void_p(ws.data_ptr()),
+                                   nbytes.value, ctypes.c_void_p(s.cuda_stream), ctypes.c_void_p(u.data_ptr()),
+                                   per, ctypes.byref(tot)))
+    return u, list(per)

@@ -13,6 +13,7 @@
 #include "../../include/pdhg.h"
 #include "fused2d.h"
 #include "plain.h"
+#include "variants.h"
 
 using namespace pdhg;
 
@@ -267,6 +268,7 @@ struct pdhg_handle {
     int64_t stage_n[PDHG_NUM_STAGES];
     Fused2D fused;
     size_t u_off;            // offset of the current u buffer (the fused path alternates two)
+    int res_norm;            // 0: space-time norms of Eq. 2.12; 1: per time slice (Sec. 3.5)
 };
 
 template <typename T> static Params<T> &params_of(pdhg_handle *h);
@@ -450,7 +452,10 @@ static pdhg_status read_res(pdhg_handle *h, double out[4]) {
     CK(cudaMemcpyAsync(acc, h->ws + h->L.scal, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     double ht = h->ht, wx = h->wx;
-    double a2 = ht * wx * acc[0], b2 = ht * wx * acc[1], gap = ht * wx * acc[2], c2 = wx * acc[3];
+    // space-time L2 (weight h_t w_x per equation value), or, for the one-step
+    // problems of Algorithm 3, L2 over the domain at one time (weight w_x)
+    const double we = h->res_norm == 1 ? wx : ht * wx;
+    double a2 = we * acc[0], b2 = we * acc[1], gap = we * acc[2], c2 = wx * acc[3];
     if (h->G.init == PDHG_INIT_LAMBDA) {
         a2 += c2;
         b2 += wx * acc[4];
@@ -467,6 +472,17 @@ static pdhg_status compute_res(pdhg_handle *h, double out[4]) {
     return read_res(h, out);
 }
 
+// Lax-Friedrichs constant: explicit, or max |f'(u0)| when 0 (1 if that is 0 too)
+static double lf_constant(const pdhg_problem *prob, const Geom &G) {
+    double lf_a = prob->lf_a;
+    if ((G.space == PDHG_SPACE_FD_LF || G.space == PDHG_SPACE_DG_P2_LF || G.space == PDHG_SPACE_DG_P1_LF) &&
+        lf_a == 0.0) {
+        for (int64_t i = 0; i < G.S; ++i) lf_a = std::max(lf_a, std::fabs(2 * prob->alpha * prob->u0[i] + prob->beta));
+        if (lf_a == 0.0) lf_a = 1.0;
+    }
+    return lf_a;
+}
+
 extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
                                    void *workspace, size_t bytes, void *stream, pdhg_handle **out) {
     Geom G;
@@ -478,15 +494,9 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
     if (!workspace) return fail(PDHG_ERR_INVALID_ARG, "workspace is NULL");
     if (((uintptr_t)workspace & 255) != 0) return fail(PDHG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (bytes < L.total) return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small: need " + std::to_string(L.total));
-    // LF constant: explicit, or max |f'(u0)| when 0
-    double lf_a = prob->lf_a;
     for (int64_t i = 0; i < G.S; ++i)
         if (!std::isfinite(prob->u0[i])) return fail(PDHG_ERR_INVALID_ARG, "u0 has a non-finite value");
-    if ((G.space == PDHG_SPACE_FD_LF || G.space == PDHG_SPACE_DG_P2_LF || G.space == PDHG_SPACE_DG_P1_LF) &&
-        lf_a == 0.0) {
-        for (int64_t i = 0; i < G.S; ++i) lf_a = std::max(lf_a, std::fabs(2 * prob->alpha * prob->u0[i] + prob->beta));
-        if (lf_a == 0.0) lf_a = 1.0;
-    }
+    const double lf_a = lf_constant(prob, G);
     if (G.has_gamma)
         for (int64_t i = 0; i < G.nx; ++i)
             if (!std::isfinite(prob->gamma_half[i])) return fail(PDHG_ERR_INVALID_ARG, "gamma_half non-finite");
@@ -496,6 +506,7 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
     double hx = grid->lx / (double)grid->nx;
     h->wx = G.dims == 2 ? hx * (grid->ly / (double)grid->ny) : hx;
     h->iters = 0; h->launches = 0; h->profiling = false;
+    h->res_norm = 0;
     h->u_off = L.u;
     memset(h->stage_ms, 0, sizeof(h->stage_ms));
     memset(h->stage_n, 0, sizeof(h->stage_n));
@@ -695,4 +706,174 @@ extern "C" pdhg_status pdhg_stage_times(pdhg_handle *h, double ms[PDHG_NUM_STAGE
         h->stage_ms[i] = 0; h->stage_n[i] = 0;
     }
     return PDHG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2 (Sec. 3.4): refinement of the time mesh.  Level k has nt >> (levels-1-k)
+// slices; consecutive levels live in two alternating regions of the workspace (region
+// A holds the final level), so a level is created before the previous one is freed.
+// ---------------------------------------------------------------------------
+static pdhg_grid level_grid(const pdhg_grid *g, int32_t levels, int32_t k) {
+    pdhg_grid c = *g;
+    c.nt = g->nt >> (levels - 1 - k);
+    return c;
+}
+
+static pdhg_status refine_regions(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                  int32_t levels, size_t *a, size_t *b) {
+    if (!grid) return fail(PDHG_ERR_INVALID_ARG, "null grid");
+    if (levels < 1 || levels > 16) return fail(PDHG_ERR_INVALID_ARG, "levels must be in [1, 16]");
+    if (grid->nt < 1 || (grid->nt % (int64_t(1) << (levels - 1))) != 0)
+        return fail(PDHG_ERR_INVALID_ARG, "nt must be divisible by 2^(levels-1)");
+    *a = *b = 0;
+    for (int32_t k = 0; k < levels; ++k) {
+        pdhg_grid gk = level_grid(grid, levels, k);
+        size_t n = 0;
+        pdhg_status st = pdhg_workspace_size(prob, &gk, scheme, &n);
+        if (st != PDHG_OK) return st;
+        size_t &r = ((levels - 1 - k) % 2 == 0) ? *a : *b;
+        r = std::max(r, n);
+    }
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_refine_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                                  const pdhg_scheme *scheme, int32_t levels, size_t *bytes) {
+    if (!bytes) return fail(PDHG_ERR_INVALID_ARG, "bytes is NULL");
+    size_t a, b;
+    pdhg_status st = refine_regions(prob, grid, scheme, levels, &a, &b);
+    if (st != PDHG_OK) return st;
+    *bytes = align256(a) + b;
+    return PDHG_OK;
+}
+
+template <typename T>
+static cudaError_t transfer_level(pdhg_handle *c, pdhg_handle *f) {
+    const int64_t S = c->G.S;
+    cudaError_t e = launch_interp_t<T>(F<T>(c, c->u_off), F<T>(c, c->L.phi), F<T>(f, f->u_off), F<T>(f, f->L.phi),
+                                       F<T>(f, f->L.phit), S, c->G.nt, f->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f->ws + f->L.lam, c->ws + c->L.lam, S * sizeof(T), cudaMemcpyDeviceToDevice, f->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f->ws + f->L.lamt, c->ws + c->L.lam, S * sizeof(T), cudaMemcpyDeviceToDevice, f->stream);
+    f->launches += 1;
+    return e;
+}
+
+extern "C" pdhg_status pdhg_solve_refine(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                         int32_t levels, const int64_t *iters, double tol, int32_t check_every,
+                                         int32_t relative, void *workspace, size_t bytes, void *stream,
+                                         pdhg_handle **out, int64_t *iters_done) {
+    if (!out || !iters) return fail(PDHG_ERR_INVALID_ARG, "out or iters is NULL");
+    *out = nullptr;
+    size_t a, b;
+    pdhg_status st = refine_regions(prob, grid, scheme, levels, &a, &b);
+    if (st != PDHG_OK) return st;
+    if (!workspace) return fail(PDHG_ERR_INVALID_ARG, "workspace is NULL");
+    if (bytes < align256(a) + b)
+        return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small: need " + std::to_string(align256(a) + b));
+    for (int32_t k = 0; k < levels; ++k)
+        if (iters[k] < 0) return fail(PDHG_ERR_INVALID_ARG, "iters[k] < 0");
+    char *ra = (char *)workspace, *rb = ra + align256(a);
+    pdhg_handle *prev = nullptr;
+    for (int32_t k = 0; k < levels; ++k) {
+        pdhg_grid gk = level_grid(grid, levels, k);
+        const bool in_a = (levels - 1 - k) % 2 == 0;
+        pdhg_handle *hk = nullptr;
+        st = pdhg_create(prob, &gk, scheme, in_a ? ra : rb, in_a ? a : b, stream, &hk);
+        if (st != PDHG_OK) { pdhg_destroy(prev); return st; }
+        if (prev) {
+            cudaError_t e = hk->G.prec == PDHG_FP64 ? transfer_level<double>(prev, hk) : transfer_level<float>(prev, hk);
+            pdhg_destroy(prev);
+            prev = nullptr;
+            if (e != cudaSuccess) { pdhg_destroy(hk); return cuda_fail(e, "time-mesh transfer"); }
+        }
+        int64_t done = 0;
+        st = pdhg_iterate(hk, iters[k], tol, check_every, relative, &done);
+        if (iters_done) iters_done[k] = done;
+        if (st != PDHG_OK) { pdhg_destroy(hk); return st; }
+        prev = hk;
+    }
+    *out = prev;
+    return PDHG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 3 (Sec. 3.5): one time step at a time.  One handle of nt = 1 on
+// [0, h_t] is reused for every step: its u0 becomes the previous end value, its
+// state restarts at [u0, u0], 0, 0, and its residual is the per-slice one.
+// ---------------------------------------------------------------------------
+static pdhg_status one_step_inputs(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                   pdhg_problem *p1, pdhg_grid *g1) {
+    if (!prob || !grid || !scheme) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
+    if (scheme->time != PDHG_TIME_BE)
+        return fail(PDHG_ERR_UNSUPPORTED, "the one-step variant is backward Euler only (a BDF2 step needs two past slices)");
+    Geom G;
+    pdhg_status st = validate(prob, grid, scheme, &G);
+    if (st != PDHG_OK) return st;
+    *g1 = *grid;
+    g1->nt = 1;
+    g1->T = grid->T / (double)grid->nt;
+    *p1 = *prob;
+    for (int64_t i = 0; i < G.S; ++i)
+        if (!std::isfinite(prob->u0[i])) return fail(PDHG_ERR_INVALID_ARG, "u0 has a non-finite value");
+    p1->lf_a = lf_constant(prob, G);          // the full problem's constant, for every step
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_one_step_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                                    const pdhg_scheme *scheme, size_t *bytes) {
+    if (!bytes) return fail(PDHG_ERR_INVALID_ARG, "bytes is NULL");
+    pdhg_problem p1;
+    pdhg_grid g1;
+    pdhg_status st = one_step_inputs(prob, grid, scheme, &p1, &g1);
+    if (st != PDHG_OK) return st;
+    return pdhg_workspace_size(&p1, &g1, scheme, bytes);
+}
+
+static cudaError_t restart_step(pdhg_handle *h, const char *u_start) {
+    const size_t sb = h->G.S * h->G.esz;
+    cudaError_t e = cudaMemcpyAsync(h->ws + h->L.u0, u_start, sb, cudaMemcpyDeviceToDevice, h->stream);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+        e = cudaMemcpyAsync(h->ws + h->u_off + s * sb, u_start, sb, cudaMemcpyDeviceToDevice, h->stream);
+    const size_t zero[4] = {h->L.phi, h->L.phit, h->L.lam, h->L.lamt};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMemsetAsync(h->ws + zero[i], 0, sb, h->stream);
+    return e;
+}
+
+extern "C" pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                           double tol, int64_t max_iters_per_step, int32_t check_every,
+                                           void *workspace, size_t bytes, void *stream, void *u_out,
+                                           int64_t *iters_per_step, int64_t *iters_total) {
+    pdhg_problem p1;
+    pdhg_grid g1;
+    pdhg_status st = one_step_inputs(prob, grid, scheme, &p1, &g1);
+    if (st != PDHG_OK) return st;
+    if (!u_out) return fail(PDHG_ERR_INVALID_ARG, "u_out is NULL");
+    if (max_iters_per_step < 1 || check_every < 1)
+        return fail(PDHG_ERR_INVALID_ARG, "max_iters_per_step and check_every must be >= 1");
+    if (iters_total) *iters_total = 0;
+    pdhg_handle *h = nullptr;
+    st = pdhg_create(&p1, &g1, scheme, workspace, bytes, stream, &h);
+    if (st != PDHG_OK) return st;
+    h->res_norm = 1;
+    const size_t sb = h->G.S * h->G.esz;
+    char *uo = (char *)u_out;
+    cudaError_t e = cudaMemcpyAsync(uo, h->ws + h->L.u0, sb, cudaMemcpyDeviceToDevice, h->stream);
+    int64_t total = 0;
+    for (int64_t l = 0; l < grid->nt && st == PDHG_OK; ++l) {
+        if (e == cudaSuccess && l > 0) e = restart_step(h, uo + l * sb);
+        if (e != cudaSuccess) { st = cuda_fail(e, "one-step restart"); break; }
+        int64_t done = 0;
+        st = pdhg_iterate(h, max_iters_per_step, tol, check_every, 0, &done);
+        total += done;
+        if (iters_per_step) iters_per_step[l] = done;
+        if (st != PDHG_OK) break;
+        e = cudaMemcpyAsync(uo + (l + 1) * sb, h->ws + h->u_off + sb, sb, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    if (st == PDHG_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (st == PDHG_OK && e != cudaSuccess) st = cuda_fail(e, "one-step copy");
+    if (iters_total) *iters_total = total;
+    pdhg_destroy(h);
+    return st;
 }

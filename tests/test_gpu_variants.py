@@ -1,0 +1,122 @@
+"""GPU parity of Algorithms 2 and 3 (Sec. 3.4, 3.5) through the C ABI against the
+oracle's drivers: iteration counts per level / per step, and the solutions."""
+import numpy as np
+import pytest
+
+import pdhg_workloads as W
+from oracle import newton, pdhg as opdhg, variants
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_07234_gb300 import binding
+    binding.load()
+    return binding
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def taus(p, fac, probs):
+    """tau_u = tau_u0 = tau_phi = sqrt(fac / nu_max), nu_max over the given problems."""
+    nu = max(opdhg.power_estimate(q, iters=60) for q in probs)
+    t = float(np.sqrt(fac / nu))
+    return p.replace(tau_u=t, tau_u0=t, tau_phi=t)
+
+
+def one_step_taus(p, fac=0.5):
+    return taus(p, fac, [p.replace(nt=1, T=p.ht)])
+
+
+def test_one_step_traffic_counts_and_solution(B):
+    """Table 3's one-timestep row on the GPU (float64): the per-step iteration counts
+    equal the oracle's (the stopping test may flip by one iteration where a residual
+    lands within rounding of the tolerance) and so do the end values."""
+    p = W.traffic_dg_p1()
+    uo, co = variants.one_timestep(p, 1e-3)
+    ug, cg = B.solve_one_step(p, tol=1e-3, precision="fp64")
+    ug = ug.cpu().numpy()
+    d = np.abs(np.array(cg) - np.array(co))
+    assert d.max() <= 1 and d.sum() <= 2, (cg, co)
+    tol = 1e-9 if d.sum() == 0 else 1e-3
+    assert rel(ug, uo) <= tol
+
+
+@pytest.mark.parametrize("p", [W.advection_upwind_be(nx=64, nt=8), W.traffic_dg_p1(ncell=64, nt=6),
+                               W.viscous_burgers(nx=128, nt=6, nu=0.05).replace(time="be")],
+                         ids=lambda p: p.name)
+def test_one_step_reaches_scheme_solution(B, p):
+    """Algorithm 3 on the GPU to Res <= 1e-12 equals the Newton time-stepper."""
+    p = one_step_taus(p)
+    ug, cg = B.solve_one_step(p, tol=1e-12, max_iters_per_step=20000, precision="fp64")
+    assert max(cg) < 20000
+    un = newton.solve(p)
+    assert rel(ug.cpu().numpy(), un) <= 1e-9
+
+
+def test_one_step_fp32_counts_near_fp64(B):
+    """float32 one-step on the traffic example stops within 5% of the float64 count."""
+    p = W.traffic_dg_p1()
+    _, c64 = B.solve_one_step(p, tol=1e-3, precision="fp64")
+    u32, c32 = B.solve_one_step(p, tol=1e-3, precision="fp32")
+    assert abs(sum(c32) - sum(c64)) <= 0.05 * sum(c64)
+    assert np.all(np.isfinite(u32.cpu().numpy()))
+
+
+def test_one_step_rejects_bdf2(B):
+    p = W.traffic_dg_p1(ncell=16, nt=4, time="bdf2")
+    with pytest.raises(B.PdhgError) as e:
+        B.solve_one_step(p, tol=1e-3)
+    assert e.value.status == -7
+
+
+def test_refine_traffic_counts_and_solution(B):
+    """Table 3's mesh-refinement row on the GPU (float64): 1000 + 1000 iterations on
+    256 x 8 and 256 x 16, then to Res <= 1e-3 on 256 x 32; counts and the final
+    state equal the oracle's driver."""
+    p = W.traffic_dg_p1()
+    sto, co = variants.refine_in_time(p, 3, [1000, 1000, 20000], 1e-3)
+    s, cg = B.solve_refine(p, 3, [1000, 1000, 20000], tol=1e-3, check_every=1, precision="fp64")
+    with s:
+        ug, phig = s.get_host("u"), s.get_host("phi")
+    assert cg[:2] == [1000, 1000] and abs(cg[2] - co[2]) <= 1, (cg, co)
+    if cg == co:
+        assert rel(ug, sto["u"]) <= 1e-9
+        assert rel(phig, sto["phi"]) <= 1e-7
+
+
+def test_refine_fixed_counts_match_oracle_elementwise(B):
+    """Fixed iteration counts (no residual checks) on three levels: the GPU's final
+    state equals the oracle's element by element, which pins the transfer of u, phi,
+    lambda between meshes."""
+    p = W.advection_upwind_be(nx=128, nt=8)
+    p = taus(p, 0.1, [p.replace(nt=n) for n in (2, 4, 8)])
+    sto, _ = variants.refine_in_time(p, 3, [7, 5, 6], 0.0)
+    s, cg = B.solve_refine(p, 3, [7, 5, 6], tol=0.0, check_every=0, precision="fp64", path="plain")
+    with s:
+        got = {k: s.get_host(k) for k in ("u", "phi", "phit", "lambda", "lambdat")}
+    assert cg == [7, 5, 6]
+    assert rel(got["u"], sto["u"]) <= 1e-12
+    assert rel(got["phi"], sto["phi"]) <= 1e-11
+    assert rel(got["phit"], sto["phit"]) <= 1e-11
+    assert rel(got["lambda"], sto["lam"]) <= 1e-11
+
+
+def test_refine_onto_fused_path(B):
+    """The finest level on the fused 2D float32 path, the transfer written into its
+    current u buffer: after fixed counts the state equals the oracle's (float32)."""
+    p = W.burgers_2d(n=256, nt=8).replace(tau_u=0.15, tau_u0=0.1, tau_phi=0.15)
+    sto, _ = variants.refine_in_time(p, 2, [4, 3], 0.0)
+    s, cg = B.solve_refine(p, 2, [4, 3], tol=0.0, check_every=0, precision="fp32", path="auto")
+    with s:
+        assert s.info()["path"] == "fused"
+        ug = s.get_host("u")
+    assert rel(ug, sto["u"]) <= 1e-4
