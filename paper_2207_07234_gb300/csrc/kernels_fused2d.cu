@@ -32,8 +32,8 @@ constexpr int ATHREADS = 256;  // rows-A block size
 //   us  [NR][FH+2][NX] u rows y0-1 .. y0+FH: raw u^m, then u^n in place (ring)
 // The FFT input aliases the u slot that the residual no longer needs and the
 // FFT scratch aliases the phit slot of m-1, so BE needs 2 x 112 KB at nx = 1024.
-// Each step loads its rows with independent float4 loads (one latency per
-// step) before computing.
+// The rows of step m+1 are fetched into registers while step m computes (their
+// ring slots are still in use), then stored at the top of step m+1.
 // ---------------------------------------------------------------------------
 template <int NX>
 __device__ __forceinline__ void load_rows(float *dst, const float *__restrict__ src_slice, int ybase, int nrows,
@@ -49,8 +49,38 @@ __device__ __forceinline__ void load_rows(float *dst, const float *__restrict__ 
     }
 }
 
+// nrows rows of a slice (y wrapped) into registers: float4 idx = threadIdx.x + j ATHREADS
+// of the [nrows][NX] block (zeros past the block, or everywhere when `zero`).
+template <int NX, int N>
+__device__ __forceinline__ void fetch_rows(float4 (&reg)[N], const float *__restrict__ src_slice, int ybase,
+                                           int nrows, int ny, bool zero) {
+    constexpr int V = NX / 4;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const int idx = threadIdx.x + j * ATHREADS;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!zero && idx < nrows * V) {
+            const int r = idx / V, c = idx - r * V;
+            int y = ybase + r;
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            v = __ldg(reinterpret_cast<const float4 *>(src_slice + (int64_t)y * NX) + c);
+        }
+        reg[j] = v;
+    }
+}
+
+template <int NX, int N>
+__device__ __forceinline__ void store_rows(float *dst, const float4 (&reg)[N], int nrows) {
+    constexpr int V = NX / 4;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const int idx = threadIdx.x + j * ATHREADS;
+        if (idx < nrows * V) reinterpret_cast<float4 *>(dst)[idx] = reg[j];
+    }
+}
+
 template <int LOG2M, bool BDF2_>
-__global__ void __launch_bounds__(ATHREADS) k_rowsA(Params<float> P, const float *__restrict__ u_in,
+__global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Params<float> P, const float *__restrict__ u_in,
                                                     float *__restrict__ u_out, const float *__restrict__ phit,
                                                     float *__restrict__ lam, float *__restrict__ lamt,
                                                     const float *__restrict__ u0, float2 *__restrict__ spec,
@@ -72,13 +102,22 @@ __global__ void __launch_bounds__(ATHREADS) k_rowsA(Params<float> P, const float
     const int mstart = (BDF2_ && l0 > 0) ? l0 - 1 : l0;
 
     if (mstart >= 1) load_rows<NX>(ph + ((mstart - 1) & 1) * RP * NX, phit + (int64_t)(mstart - 1) * S, y0 - 2, RP, ny, false);
+    constexpr int PPT = (RP * (NX / 4) + ATHREADS - 1) / ATHREADS;   // float4 per thread of one step's rows
+    constexpr int UPT = (RU * (NX / 4) + ATHREADS - 1) / ATHREADS;
+    float4 rp[PPT], ru[UPT];
+    fetch_rows<NX>(rp, phit + (int64_t)mstart * S, y0 - 2, RP, ny, mstart >= nt);
+    fetch_rows<NX>(ru, u_in + (int64_t)mstart * S, y0 - 1, RU, ny, false);
     for (int m = mstart; m <= l1; ++m) {
         float *pc = ph + (m & 1) * RP * NX;              // phit^m
         float *pp = ph + ((m + 1) & 1) * RP * NX;        // phit^{m-1}
         float *uc = us + (m % NR) * RU * NX;             // u^m -> u^n
-        // (0) rows of this step
-        load_rows<NX>(pc, phit + (int64_t)m * S, y0 - 2, RP, ny, m >= nt);
-        load_rows<NX>(uc, u_in + (int64_t)m * S, y0 - 1, RU, ny, false);
+        // (0) rows of this step (fetched during the previous one); start fetching the next
+        store_rows<NX>(pc, rp, RP);
+        store_rows<NX>(uc, ru, RU);
+        if (m + 1 <= l1) {
+            fetch_rows<NX>(rp, phit + (int64_t)(m + 1) * S, y0 - 2, RP, ny, m + 1 >= nt);
+            fetch_rows<NX>(ru, u_in + (int64_t)(m + 1) * S, y0 - 1, RU, ny, false);
+        }
         __syncthreads();
         // (1) primal step on slice m, rows y0-1 .. y0+FH (in place in uc), four x per thread
         const bool own_write = (m >= l0) && (m < l1 || m == nt);
