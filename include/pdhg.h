@@ -229,6 +229,40 @@ pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_grid *grid,
                                 void *u_out, int64_t *iters_per_step, int64_t *iters_total);
 
 /*
+ * Gradient of a terminal objective through the solve.  (An addition of this
+ * library: the paper solves forward problems only.)  With u the scheme's
+ * solution for the problem's u0 and nu,
+ *     Loss = w_x sum_j (u_j^nt - target_j)^2      (w_x = h_x, or h_x h_y in 2D),
+ * returns Loss, dLoss/du0_j (for every dof j) and dLoss/dnu.  Both come from the
+ * saddle form of Eq. 2.7 / 3.10 with Loss added as the primal objective: at its
+ * stationary point phi and lambda are the discrete adjoint, dLoss/du0 = -w_x lambda
+ * and dLoss/dnu = h_t w_x sum_l <phi^l, dR^l/dnu> = -h_t w_x sum_l <phi^l, Lap_h u^{l+1}>.
+ *
+ * Two runs of Algorithm 1 on one handle (plain path): the forward problem to
+ * Res <= tol (absolute, checked every check_every iterations, at most max_iters),
+ * then the same problem linearised at the forward solution u* (residual
+ * J(u*) v, transposes at u*) with the objective |u*^nt + v^nt - target|^2,
+ * whose last-slice update is the objective's proximal step; this linearised
+ * saddle problem is convex, so Algorithm 1 converges on it like on a linear
+ * problem.  Stops at Res <= adj_tol or adj_max_iters.
+ *
+ * Finite-difference schemes (1D or 2D, BE or BDF2, constant or zero nu, with or
+ * without gamma_half), PDHG_INIT_LAMBDA; PDHG_ERR_UNSUPPORTED otherwise (DG,
+ * PDHG_INIT_PINNED, PDHG_PATH_FUSED).  target: host, ndof float64 values.
+ * workspace: device, caller-owned, 256-byte aligned, size from
+ * pdhg_gradient_workspace_size.  loss, du0 (host, ndof), dnu, iters (host, 2:
+ * forward and adjoint iterations) may be NULL.  Synchronises the stream.
+ * Errors as pdhg_iterate (NONFINITE, DIVERGED, CUDA), for either solve.
+ */
+pdhg_status pdhg_gradient_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                         const pdhg_scheme *scheme, size_t *bytes);
+pdhg_status pdhg_solve_gradient(const pdhg_problem *prob, const pdhg_grid *grid,
+                                const pdhg_scheme *scheme, const double *target, double tol,
+                                int64_t max_iters, double adj_tol, int64_t adj_max_iters,
+                                int32_t check_every, void *workspace, size_t bytes, void *stream,
+                                double *loss, double *du0, double *dnu, int64_t *iters);
+
+/*
  * Residual norms of a caller-held state, with no handle, no workspace and no
  * device allocation.  (An addition of this library: the paper has no
  * counterpart.)  For callers that cannot allocate device memory -- e.g. code

@@ -35,18 +35,28 @@ def initial_state(p):
             "lam": np.zeros(p.u0.shape), "lamt": np.zeros(p.u0.shape), "iters": 0}
 
 
-def step(p, st, signs="standard"):
+def step(p, st, signs="standard", target=None):
     """One iteration of Algorithm 1, in place on the state dict ``st``.
 
     ``signs="paper"`` uses the signs as printed in Algorithm 1 (primal ascent along
     J^T phit, u^0 moved along -(phit^0 - lamt), dual descent); the tests record that
-    this choice does not converge (see test_oracle_pdhg)."""
+    this choice does not converge (see test_oracle_pdhg).
+
+    ``target`` (a slice) adds the terminal objective w_x |u^nt - target|^2 to the
+    Lagrangian (a primal objective in the saddle form of Eq. 2.7; its minimiser
+    over u is still the scheme's solution, and phi, lambda become the adjoint).
+    Scaled like the other rows of the primal step (by h_t w_x), the u^nt update
+    is the proximal step of |v - target|^2 / h_t: with y = u^nt - tau_u (J^T phit)^nt,
+    u^nt = (y + (2 tau_u / h_t) target) / (1 + 2 tau_u / h_t)."""
     ht = p.ht
     u, phit, lamt = st["u"], st["phit"], st["lamt"]
     g = spacetime.vjp(p, u, phit)
     un = u.copy()
     if signs == "standard":
         un[1:] = u[1:] - p.tau_u * g[1:]
+        if target is not None:
+            k = 2.0 * p.tau_u / ht
+            un[-1] = (un[-1] + k * target) / (1.0 + k)
         if p.init == "lambda":
             un[0] = u[0] - p.tau_u0 * (ht * g[0] + lamt)
     else:
@@ -69,7 +79,7 @@ def step(p, st, signs="standard"):
     return st
 
 
-def residual_norms(p, st):
+def residual_norms(p, st, target=None):
     """[||A(u)||, ||grad A(u)^T phi||, ||u^0 - u0||, <phi, R(u)>] (Eq. 2.12).
 
     Discrete L2 norms weighted by h_t w_x over equation slices and by w_x over the
@@ -83,6 +93,8 @@ def residual_norms(p, st):
     R = spacetime.residual(p, u)
     r0 = spacetime.initial_residual(p, u)
     g = spacetime.vjp(p, u, phi)
+    if target is not None:          # gradient of the terminal objective, scaled like J^T phi
+        g[-1] += 2.0 * (u[-1] - target) / ht
     a2 = ht * wx * np.sum(R * R)
     b2 = ht * wx * np.sum(g[1:] * g[1:])
     gap = ht * wx * np.sum(phi * R)
@@ -96,7 +108,7 @@ def residual_norms(p, st):
 
 
 def solve(p, max_iters=100000, tol=1e-10, check_every=1, relative=False,
-          signs="standard", history=False, state=None):
+          signs="standard", history=False, state=None, target=None):
     """Run Algorithm 1 until each entry of Res is <= tol (Sec. 3.3) or max_iters.
 
     relative=True scales both entries by ||A(u_init)|| (Res(u_init, 0) has a zero
@@ -105,13 +117,13 @@ def solve(p, max_iters=100000, tol=1e-10, check_every=1, relative=False,
     hist = []
     scale = 1.0
     if relative:
-        scale = residual_norms(p, st)[0]
+        scale = residual_norms(p, st, target)[0]
     it = 0
     while it < max_iters:
-        step(p, st, signs)
+        step(p, st, signs, target)
         it += 1
         if it % check_every == 0 or it == max_iters:
-            res = residual_norms(p, st)
+            res = residual_norms(p, st, target)
             if history:
                 hist.append((it, res))
             if not np.all(np.isfinite(res)) or res[0] > 1e30:

@@ -33,7 +33,7 @@ EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_strea
            "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_info", "pdhg_launch_count",
            "pdhg_set_profiling", "pdhg_stage_times", "pdhg_last_error", "pdhg_refine_workspace_size",
            "pdhg_solve_refine", "pdhg_one_step_workspace_size", "pdhg_solve_one_step",
-           "pdhg_residual_noalloc"]
+           "pdhg_gradient_workspace_size", "pdhg_solve_gradient", "pdhg_residual_noalloc"]
 
 
 class PdhgError(RuntimeError):
@@ -92,6 +92,10 @@ def load(path: str = LIB_PATH):
         "pdhg_solve_refine": [P, G, S, i32, ctypes.POINTER(i64), ctypes.c_double, i32, i32, vp, ctypes.c_size_t,
                               vp, ctypes.POINTER(vp), ctypes.POINTER(i64)],
         "pdhg_one_step_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_gradient_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_solve_gradient": [P, G, S, ctypes.POINTER(ctypes.c_double), ctypes.c_double, i64, ctypes.c_double, i64,
+                                i32, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
         "pdhg_solve_one_step": [P, G, S, ctypes.c_double, i64, i32, vp, ctypes.c_size_t, vp, vp,
                                 ctypes.POINTER(i64), ctypes.POINTER(i64)],
     }
@@ -293,3 +297,53 @@ def solve_one_step(p, tol=1e-3, max_iters_per_step=100000, check_every=1, precis
                                    nbytes.value, ctypes.c_void_p(s.cuda_stream), ctypes.c_void_p(u.data_ptr()),
                                    per, ctypes.byref(tot)))
     return u, list(per)
+
+
+def solve_gradient(p, target, tol=1e-10, max_iters=100000, adj_tol=1e-10, adj_max_iters=100000, check_every=10,
+                   precision="fp64", device=None, stream=None):
+    """Loss = w_x |u^nt - target|^2 of the scheme's solution and its gradient through
+    the solve: returns (loss, dLoss/du0 as numpy, dLoss/dnu, [forward, adjoint] iterations)."""
+    import torch
+    lib = load()
+    prob, grid, scheme, keep = structs(p, precision, "plain")
+    nbytes = ctypes.c_size_t(0)
+    _check(lib.pdhg_gradient_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                            ctypes.byref(nbytes)))
+    dev = torch.device(device if device is not None else "cuda")
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    tg = np.ascontiguousarray(target, dtype=np.float64).ravel()
+    assert tg.size == p.ndof
+    du0 = np.empty(p.ndof)
+    loss, dnu = ctypes.c_double(0), ctypes.c_double(0)
+    iters = (ctypes.c_int64 * 2)()
+    _check(lib.pdhg_solve_gradient(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                   tg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol), int(max_iters),
+                                   float(adj_tol), int(adj_max_iters), int(check_every),
+                                   ctypes.c_void_p(ws.data_ptr()), nbytes.value, ctypes.c_void_p(s.cuda_stream),
+                                   ctypes.byref(loss), du0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   ctypes.byref(dnu), iters))
+    return loss.value, du0.reshape(p.slice_shape), dnu.value, list(iters)
+
+
+def terminal_loss_fn():
+    """A torch.autograd.Function: loss = TerminalLoss.apply(u0, nu, problem, target, opts)
+    with u0 a float64 tensor of the slice shape and nu a 0-d float64 tensor; the
+    backward pass returns dLoss/du0 and dLoss/dnu computed by solve_gradient."""
+    import torch
+
+    class TerminalLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u0, nu, problem, target, opts=None):
+            q = problem.replace(u0=u0.detach().cpu().numpy().astype(np.float64), nu=float(nu))
+            loss, du0, dnu, _ = solve_gradient(q, target, **(opts or {}))
+            ctx.save_for_backward(torch.as_tensor(du0, dtype=u0.dtype, device=u0.device),
+                                  torch.as_tensor(dnu, dtype=nu.dtype, device=nu.device))
+            return torch.as_tensor(loss, dtype=u0.dtype, device=u0.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            du0, dnu = ctx.saved_tensors
+            return grad * du0, grad * dnu, None, None, None
+
+    return TerminalLoss

@@ -877,3 +877,124 @@ extern "C" pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_
     pdhg_destroy(h);
     return st;
 }
+
+// ---------------------------------------------------------------------------
+// Gradient of a terminal objective through the solve.  Forward: Algorithm 1 to
+// tol.  Adjoint: Algorithm 1 on the problem linearised at the solution u*, with
+// the objective |u*^nt + v^nt - target|^2 added (a convex saddle problem whose
+// multipliers phi, lambda are the discrete adjoint).  Workspace: the handle's
+// (plain path) followed by u* ((nt+1) S values) and target - u*^nt (S values).
+// ---------------------------------------------------------------------------
+static pdhg_status gradient_inputs(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                   pdhg_scheme *s1, size_t *handle_bytes, size_t *total) {
+    if (!prob || !grid || !scheme) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
+    if (scheme->space != PDHG_SPACE_FD_UPWIND && scheme->space != PDHG_SPACE_FD_LF)
+        return fail(PDHG_ERR_UNSUPPORTED, "gradients are implemented for the finite-difference schemes");
+    if (scheme->init != PDHG_INIT_LAMBDA) return fail(PDHG_ERR_UNSUPPORTED, "gradients need PDHG_INIT_LAMBDA");
+    if (scheme->path == PDHG_PATH_FUSED) return fail(PDHG_ERR_UNSUPPORTED, "gradients run on the plain path");
+    *s1 = *scheme;
+    s1->path = PDHG_PATH_PLAIN;
+    Geom G;
+    pdhg_status st = validate(prob, grid, s1, &G);
+    if (st != PDHG_OK) return st;
+    st = pdhg_workspace_size(prob, grid, s1, handle_bytes);
+    if (st != PDHG_OK) return st;
+    *total = align256(*handle_bytes) + align256((G.nt + 1) * G.S * G.esz) + align256(G.S * G.esz);
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_gradient_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                                    const pdhg_scheme *scheme, size_t *bytes) {
+    if (!bytes) return fail(PDHG_ERR_INVALID_ARG, "bytes is NULL");
+    pdhg_scheme s1;
+    size_t hb;
+    return gradient_inputs(prob, grid, scheme, &s1, &hb, bytes);
+}
+
+template <typename T>
+static pdhg_status gradient_T(pdhg_handle *h, const double *target, char *ustar, char *tshift, double tol,
+                              int64_t max_iters, double adj_tol, int64_t adj_max_iters, int32_t check_every,
+                              double *loss, double *du0, double *dnu, int64_t *iters) {
+    const Geom &G = h->G;
+    const int64_t S = G.S;
+    // forward solve
+    int64_t done = 0;
+    pdhg_status st = pdhg_iterate(h, max_iters, tol, check_every, 0, &done);
+    if (iters) iters[0] = done;
+    if (st != PDHG_OK) return st;
+    // u*, the objective and target - u*^nt
+    const size_t ub = (G.nt + 1) * S * sizeof(T);
+    CK(cudaMemcpyAsync(ustar, h->ws + h->u_off, ub, cudaMemcpyDeviceToDevice, h->stream));
+    std::vector<T> last(S), ts(S);
+    CK(cudaMemcpyAsync(last.data(), h->ws + h->u_off + G.nt * S * sizeof(T), S * sizeof(T), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double l2 = 0;
+    for (int64_t i = 0; i < S; ++i) {
+        if (!std::isfinite(target[i])) return fail(PDHG_ERR_INVALID_ARG, "target has a non-finite value");
+        const double d = (double)last[i] - target[i];
+        l2 += d * d;
+        ts[i] = (T)(target[i] - (double)last[i]);
+    }
+    if (loss) *loss = h->wx * l2;
+    CK(cudaMemcpyAsync(tshift, ts.data(), S * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    // adjoint mode: state v = 0, phi = lambda = 0, initial data 0
+    Params<T> &P = params_of<T>(h);
+    P.ulin = reinterpret_cast<const T *>(ustar);
+    P.tshift = reinterpret_cast<const T *>(tshift);
+    CK(cudaMemsetAsync(h->ws + h->u_off, 0, ub, h->stream));
+    const size_t zero[5] = {h->L.phi, h->L.phit, h->L.lam, h->L.lamt, h->L.u0};
+    const size_t zb[5] = {G.nt * S * sizeof(T), G.nt * S * sizeof(T), S * sizeof(T), S * sizeof(T), S * sizeof(T)};
+    for (int i = 0; i < 5; ++i) CK(cudaMemsetAsync(h->ws + zero[i], 0, zb[i], h->stream));
+    double r[4];
+    st = compute_res<T>(h, r);
+    if (st != PDHG_OK) return st;
+    h->res_init = r[0] > 0 ? r[0] : r[1];
+    st = pdhg_iterate(h, adj_max_iters, adj_tol, check_every, 0, &done);
+    if (iters) iters[1] = done;
+    if (st != PDHG_OK) return st;
+    // dLoss/du0 = -w_x lambda;  dLoss/dnu = -h_t w_x sum_l <phi^l, Lap_h u*^{l+1}>
+    std::vector<T> lam(S);
+    CK(cudaMemcpyAsync(lam.data(), h->ws + h->L.lam, S * sizeof(T), cudaMemcpyDeviceToHost, h->stream));
+    double *scal = F<double>(h, h->L.scal) + 8;
+    cudaError_t e = launch_phi_lap<T>(P, reinterpret_cast<const T *>(ustar), F<T>(h, h->L.phi),
+                                      F<double>(h, h->L.partials), scal, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "phi-Laplacian reduction");
+    h->launches += 2;
+    double pl = 0;
+    CK(cudaMemcpyAsync(&pl, scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (du0)
+        for (int64_t i = 0; i < S; ++i) du0[i] = -h->wx * (double)lam[i];
+    if (dnu) *dnu = -h->ht * h->wx * pl;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_solve_gradient(const pdhg_problem *prob, const pdhg_grid *grid,
+                                           const pdhg_scheme *scheme, const double *target, double tol,
+                                           int64_t max_iters, double adj_tol, int64_t adj_max_iters,
+                                           int32_t check_every, void *workspace, size_t bytes, void *stream,
+                                           double *loss, double *du0, double *dnu, int64_t *iters) {
+    pdhg_scheme s1;
+    size_t hb, total;
+    pdhg_status st = gradient_inputs(prob, grid, scheme, &s1, &hb, &total);
+    if (st != PDHG_OK) return st;
+    if (!target) return fail(PDHG_ERR_INVALID_ARG, "target is NULL");
+    if (!workspace) return fail(PDHG_ERR_INVALID_ARG, "workspace is NULL");
+    if (bytes < total) return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small: need " + std::to_string(total));
+    if (check_every < 1 || max_iters < 0 || adj_max_iters < 0)
+        return fail(PDHG_ERR_INVALID_ARG, "check_every must be >= 1 and iteration bounds >= 0");
+    char *ws = (char *)workspace;
+    pdhg_handle *h = nullptr;
+    st = pdhg_create(prob, grid, &s1, ws, hb, stream, &h);
+    if (st != PDHG_OK) return st;
+    const size_t ub = align256((grid->nt + 1) * h->G.S * h->G.esz);
+    char *ustar = ws + align256(hb), *tshift = ustar + ub;
+    st = h->G.prec == PDHG_FP64
+             ? gradient_T<double>(h, target, ustar, tshift, tol, max_iters, adj_tol, adj_max_iters, check_every, loss,
+                                  du0, dnu, iters)
+             : gradient_T<float>(h, target, ustar, tshift, tol, max_iters, adj_tol, adj_max_iters, check_every, loss,
+                                 du0, dnu, iters);
+    pdhg_destroy(h);
+    return st;
+}

@@ -53,6 +53,11 @@ struct Params {
     T tau_u, tau_u0, tau_phi, tau_lambda;
     T dual_scale;           // tau_phi * h_t^2 / (nx/2 * ny): folds FFT and Thomas scalings
     const T *gamma_half;    // 1D FD, nullable
+    // adjoint mode (FD, plain path): the state is a perturbation v of the solution
+    // u*, the residual is J(u*) v and the transposes are taken at u*; the last
+    // slice carries the objective |v - tshift|^2 (tshift = target - u*^nt).
+    const T *ulin = nullptr;     // u*, [nt+1][S]; nullptr: forward mode
+    const T *tshift = nullptr;   // [S]; nullptr: no terminal objective
 };
 
 template <typename T>
@@ -136,6 +141,39 @@ __device__ __forceinline__ T fd_D(const Params<T> &P, const T *__restrict__ v, i
         out += fd_dir(P, v[(int64_t)ym * nx + x], c, v[(int64_t)yp * nx + x], P.inv_hy);
     } else if (P.gamma_half) {
         out += fd_gamma(P, x, xm, vm, c, vp);
+    }
+    return out;
+}
+
+// derivative of one direction of D at u (values um, u, up) along w (wm, w, wp)
+template <typename T>
+__device__ __forceinline__ T fd_dir_jvp(const Params<T> &P, T um, T u, T up, T wm, T w, T wp, T inv_h) {
+    T fr, fl;                                   // derivatives of F_{j+1/2}, F_{j-1/2}
+    if (P.space == FD_UPWIND) {
+        fr = dflux(P, u) * w;
+        fl = dflux(P, um) * wm;
+    } else {
+        fr = T(0.5) * (dflux(P, u) * w + dflux(P, up) * wp) - T(0.5) * P.lf_a * (wp - w);
+        fl = T(0.5) * (dflux(P, um) * wm + dflux(P, u) * w) - T(0.5) * P.lf_a * (w - wm);
+    }
+    T out = (fr - fl) * inv_h;
+    if (P.nu != T(0)) out -= P.nu * (wp - T(2) * w + wm) * inv_h * inv_h;
+    return out;
+}
+
+// D'(u) w at point (y, x) of slices u, w
+template <typename T>
+__device__ __forceinline__ T fd_D_jvp(const Params<T> &P, const T *__restrict__ u, const T *__restrict__ w, int y,
+                                      int x) {
+    const int nx = P.nx;
+    const int64_t r = (int64_t)y * nx;
+    int xm = wrapm(x, nx), xp = wrapp(x, nx);
+    T out = fd_dir_jvp(P, u[r + xm], u[r + x], u[r + xp], w[r + xm], w[r + x], w[r + xp], P.inv_hx);
+    if (P.dims == 2) {
+        const int64_t rm = (int64_t)wrapm(y, P.ny) * nx, rp = (int64_t)wrapp(y, P.ny) * nx;
+        out += fd_dir_jvp(P, u[rm + x], u[r + x], u[rp + x], w[rm + x], w[r + x], w[rp + x], P.inv_hy);
+    } else if (P.gamma_half) {
+        out += fd_gamma(P, x, xm, w[r + xm], w[r + x], w[r + xp]);
     }
     return out;
 }

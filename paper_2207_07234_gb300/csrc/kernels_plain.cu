@@ -34,15 +34,16 @@ __device__ __forceinline__ T time_T(const Params<T> &P, const T *psi, int64_t S,
 // ---------------------------------------------------------------------------
 // primal step (Algorithm 1, step 1; linearised at u^{n-1} as in Eq. 2.11)
 // ---------------------------------------------------------------------------
+// Each kernel body below is a __device__ function of its block coordinates, so
+// that the batched path (kernels_batch.cu) runs the same code per instance.
 template <typename T>
-__global__ void __launch_bounds__(256) k_primal(Params<T> P, T *__restrict__ u, const T *__restrict__ phit,
-                                                T *__restrict__ lam, T *__restrict__ lamt,
-                                                const T *__restrict__ u0) {
-    const int l = blockIdx.y;
+__device__ __forceinline__ void primal_block(const Params<T> &P, T *__restrict__ u, const T *__restrict__ phit,
+                                             T *__restrict__ lam, T *__restrict__ lamt, const T *__restrict__ u0,
+                                             int bx, int l) {
     const int64_t S = P.S;
     if (is_dg(P.space)) {
         const int N = P.nx, nm = P.lines;
-        const int k = blockIdx.x * blockDim.x + threadIdx.x;
+        const int k = bx * blockDim.x + threadIdx.x;
         if (k >= N) return;
         T c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
         T *ul = u + (int64_t)l * S;
@@ -72,15 +73,21 @@ __global__ void __launch_bounds__(256) k_primal(Params<T> P, T *__restrict__ u, 
         }
         return;
     }
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
     if (i >= S) return;
     const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
     T *ul = u + (int64_t)l * S;
     T c = ul[i];
     T g = time_T(P, phit + i, S, l);
     if (l >= 1) {
-        g += fd_DT(P, c, phit + (int64_t)(l - 1) * S, y, x);
-        ul[i] = c - P.tau_u * g;
+        const T cl = P.ulin ? P.ulin[(int64_t)l * S + i] : c;     // linearisation point
+        g += fd_DT(P, cl, phit + (int64_t)(l - 1) * S, y, x);
+        T un = c - P.tau_u * g;
+        if (l == P.nt && P.tshift) {          // proximal step of |v - tshift|^2 / h_t
+            const T k = T(2) * P.tau_u * P.inv_ht;
+            un = (un + k * P.tshift[i]) / (T(1) + k);
+        }
+        ul[i] = un;
     } else if (P.init == INIT_LAMBDA) {
         T un = c - P.tau_u0 * (P.ht * g + lamt[i]);
         ul[i] = un;
@@ -89,6 +96,13 @@ __global__ void __launch_bounds__(256) k_primal(Params<T> P, T *__restrict__ u, 
         lam[i] = ln;
         lamt[i] = ln + P.tau_lambda * r0;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_primal(Params<T> P, T *__restrict__ u, const T *__restrict__ phit,
+                                                T *__restrict__ lam, T *__restrict__ lamt,
+                                                const T *__restrict__ u0) {
+    primal_block(P, u, phit, lam, lamt, u0, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -105,14 +119,12 @@ __device__ __forceinline__ T time_R(const Params<T> &P, const T *u, int64_t S, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_residual_rfft(Params<T> P, const T *__restrict__ u,
-                                                       typename Cplx<T>::type *__restrict__ spec,
-                                                       const typename Cplx<T>::type *__restrict__ twx) {
+__device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T *__restrict__ u,
+                                                    typename Cplx<T>::type *__restrict__ spec,
+                                                    const typename Cplx<T>::type *__restrict__ twx, int line, int l) {
     typedef typename Cplx<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *z = reinterpret_cast<C *>(smem_raw);
-    const int l = blockIdx.y;
-    const int line = blockIdx.x;          // row y (FD); 0 for DG
+    C *z = reinterpret_cast<C *>(smem_raw);      // line: row y (FD); 0 for DG
     const int N = P.nx, M = N >> 1;
     const int lg = P.log2m;
     const int64_t S = P.S;
@@ -141,13 +153,21 @@ __global__ void __launch_bounds__(256) k_residual_rfft(Params<T> P, const T *__r
     const T *un = u + (int64_t)(l + 1) * S;
     const int64_t row = (int64_t)line * N;
     for (int x = threadIdx.x; x < N; x += blockDim.x) {
-        T r = fd_D(P, un, line, x) + time_R(P, u + row + x, S, l);
+        T r = (P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 1) * S, un, line, x) : fd_D(P, un, line, x)) +
+              time_R(P, u + row + x, S, l);
         zr[bitrev(x >> 1, lg) * 2 + (x & 1)] = r;
     }
     __syncthreads();
     fft_radix2(z, lg, 1, M, 1, twx, 2, false);
     C *out = spec + ((int64_t)l * P.lines + line) * P.nkx;
     for (int k = threadIdx.x; k <= M; k += blockDim.x) out[k] = rfft_split(z, M, k, twx);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual_rfft(Params<T> P, const T *__restrict__ u,
+                                                       typename Cplx<T>::type *__restrict__ spec,
+                                                       const typename Cplx<T>::type *__restrict__ twx) {
+    residual_rfft_block(P, u, spec, twx, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -197,14 +217,14 @@ __device__ __forceinline__ T rho_of(T theta, T emt, T q, int l) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_tsolve(Params<T> P, typename Cplx<T>::type *__restrict__ spec,
-                                                const T *__restrict__ theta_tab,
-                                                const typename Cplx<T>::type *__restrict__ V) {
+__device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T>::type *__restrict__ spec,
+                                             const T *__restrict__ theta_tab,
+                                             const typename Cplx<T>::type *__restrict__ V, int bx) {
     typedef typename Cplx<T>::type C;
     const int nt = P.nt;
     if (is_dg(P.space)) {
         const int nm = P.lines;
-        const int k = blockIdx.x * blockDim.x + threadIdx.x;
+        const int k = bx * blockDim.x + threadIdx.x;
         if (k >= P.nkx) return;
         const int64_t ls = nm * (int64_t)P.nkx;      // slice stride
         C v[9];
@@ -246,7 +266,7 @@ __global__ void __launch_bounds__(128) k_tsolve(Params<T> P, typename Cplx<T>::t
         return;
     }
     const int64_t modes = (int64_t)P.lines * P.nkx;
-    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t col = (int64_t)bx * blockDim.x + threadIdx.x;
     if (col >= modes) return;
     const T th = theta_tab[col];
     const T emt = expT(-th), q = emt * emt;
@@ -266,21 +286,27 @@ __global__ void __launch_bounds__(128) k_tsolve(Params<T> P, typename Cplx<T>::t
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) k_tsolve(Params<T> P, typename Cplx<T>::type *__restrict__ spec,
+                                                const T *__restrict__ theta_tab,
+                                                const typename Cplx<T>::type *__restrict__ V) {
+    tsolve_block(P, spec, theta_tab, V, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // inverse real FFT along x + dual step + extrapolation:
 //   z = K_d^{-1} R,  phi^n = phi^{n-1} + tau_phi z,  phit = phi^n + tau_phi z
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_dual_irfft(Params<T> P, const typename Cplx<T>::type *__restrict__ spec,
-                                                    T *__restrict__ phi, T *__restrict__ phit,
-                                                    const typename Cplx<T>::type *__restrict__ twx) {
+__device__ __forceinline__ void dual_irfft_block(const Params<T> &P, const typename Cplx<T>::type *__restrict__ spec,
+                                                 T *__restrict__ phi, T *__restrict__ phit,
+                                                 const typename Cplx<T>::type *__restrict__ twx, int bx, int l) {
     typedef typename Cplx<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *z = reinterpret_cast<C *>(smem_raw);
-    const int l = blockIdx.y;
     const int N = P.nx, M = N >> 1, lg = P.log2m;
     const int nl = is_dg(P.space) ? P.lines : 1;
-    const int line0 = is_dg(P.space) ? 0 : blockIdx.x;
+    const int line0 = is_dg(P.space) ? 0 : bx;
     for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
         int m = t / M, k = t - m * M;
         const C *X = spec + ((int64_t)l * P.lines + line0 + m) * P.nkx;
@@ -298,6 +324,13 @@ __global__ void __launch_bounds__(256) k_dual_irfft(Params<T> P, const typename 
         phi[i] = pn;
         phit[i] = pn + dz;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dual_irfft(Params<T> P, const typename Cplx<T>::type *__restrict__ spec,
+                                                    T *__restrict__ phi, T *__restrict__ phit,
+                                                    const typename Cplx<T>::type *__restrict__ twx) {
+    dual_irfft_block(P, spec, phi, phit, twx, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -374,13 +407,17 @@ __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restri
     const int64_t i = unit;
     const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
     if (l < P.nt) {
-        const T r = fd_D(P, u + (int64_t)(l + 1) * S, y, x) + time_R(P, u + i, S, l);
+        const T *un = u + (int64_t)(l + 1) * S;
+        const T d = P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 1) * S, un, y, x) : fd_D(P, un, y, x);
+        const T r = d + time_R(P, u + i, S, l);
         acc[0] += (double)(r * r);
         acc[2] += (double)(phi[(int64_t)l * S + i] * r);
     }
     const T c = u[(int64_t)l * S + i];
     if (l >= 1) {
-        const T g = fd_DT(P, c, phi + (int64_t)(l - 1) * S, y, x) + time_T(P, phi + i, S, l);
+        const T cl = P.ulin ? P.ulin[(int64_t)l * S + i] : c;
+        T g = fd_DT(P, cl, phi + (int64_t)(l - 1) * S, y, x) + time_T(P, phi + i, S, l);
+        if (l == P.nt && P.tshift) g += T(2) * (c - P.tshift[i]) * P.inv_ht;
         acc[1] += (double)(g * g);
     } else {
         double r0 = (double)c - (double)u0[i];
@@ -393,17 +430,23 @@ __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restri
     }
 }
 
+// block bx of gx for slice row l; partial sums at partials[(l gx + bx) * 6]
+template <typename T>
+__device__ __forceinline__ void check_block(const Params<T> &P, const T *__restrict__ u, const T *__restrict__ phi,
+                                            const T *__restrict__ lam, const T *__restrict__ u0,
+                                            double *__restrict__ partials, int bx, int l, int gx) {
+    const int64_t units = is_dg(P.space) ? P.nx : P.S;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t unit = (int64_t)bx * blockDim.x + threadIdx.x; unit < units; unit += (int64_t)gx * blockDim.x)
+        check_unit(P, u, phi, lam, u0, l, unit, acc);
+    block_sum6(acc, partials + ((int64_t)l * gx + bx) * 6);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_check(Params<T> P, const T *__restrict__ u, const T *__restrict__ phi,
                                                const T *__restrict__ lam, const T *__restrict__ u0,
                                                double *__restrict__ partials) {
-    const int l = blockIdx.y;
-    const int64_t units = is_dg(P.space) ? P.nx : P.S;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t unit = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; unit < units;
-         unit += (int64_t)gridDim.x * blockDim.x)
-        check_unit(P, u, phi, lam, u0, l, unit, acc);
-    block_sum6(acc, partials + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 6);
+    check_block(P, u, phi, lam, u0, partials, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) k_reduce6(const double *__restrict__ partials, int64_t nblocks,
@@ -497,6 +540,39 @@ cudaError_t launch_check(const Params<T> &P, const T *u, const T *phi, const T *
     return cudaGetLastError();
 }
 
+// sum_l <phi^l, Lap_h u^{l+1}> in float64 (FD; 2D: both directions).  The viscous
+// term of D is -nu Lap_h u, so dR^l/dnu = -Lap_h u^{l+1}.
+template <typename T>
+__global__ void __launch_bounds__(256) k_phi_lap(Params<T> P, const T *__restrict__ u, const T *__restrict__ phi,
+                                                 double *__restrict__ partials) {
+    const int l = blockIdx.y;
+    const int64_t S = P.S;
+    const T *ul = u + (int64_t)(l + 1) * S;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
+        const int64_t r = (int64_t)y * P.nx;
+        const T c = ul[i];
+        T lap = (ul[r + wrapp(x, P.nx)] - T(2) * c + ul[r + wrapm(x, P.nx)]) * P.inv_hx * P.inv_hx;
+        if (P.dims == 2)
+            lap += (ul[(int64_t)wrapp(y, P.ny) * P.nx + x] - T(2) * c + ul[(int64_t)wrapm(y, P.ny) * P.nx + x]) *
+                   P.inv_hy * P.inv_hy;
+        acc[0] += (double)phi[(int64_t)l * S + i] * (double)lap;
+    }
+    block_sum6(acc, partials + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 6);
+}
+
+template <typename T>
+cudaError_t launch_phi_lap(const Params<T> &P, const T *u, const T *phi, double *partials, double *out,
+                           cudaStream_t s) {
+    dim3 grid((unsigned)check_grid_x(P), (unsigned)P.nt);
+    k_phi_lap<T><<<grid, 256, 0, s>>>(P, u, phi, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce6<<<1, 256, 0, s>>>(partials, (int64_t)grid.x * grid.y, out);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t init_plain_attributes() {
     const int mx = 200 * 1024;
@@ -515,7 +591,8 @@ cudaError_t init_plain_attributes() {
     template int64_t check_blocks<T>(const Params<T> &);                                                      \
     template cudaError_t init_plain_attributes<T>();                                                      \
     template cudaError_t launch_check<T>(const Params<T> &, const T *, const T *, const T *, const T *, double *, \
-                                         double *, cudaStream_t);
+                                         double *, cudaStream_t);                                             \
+    template cudaError_t launch_phi_lap<T>(const Params<T> &, const T *, const T *, double *, double *, cudaStream_t);
 
 PDHG_INSTANTIATE(float)
 PDHG_INSTANTIATE(double)
