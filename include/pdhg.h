@@ -263,6 +263,45 @@ pdhg_status pdhg_solve_gradient(const pdhg_problem *prob, const pdhg_grid *grid,
                                 double *loss, double *du0, double *dnu, int64_t *iters);
 
 /*
+ * Batches of independent 1D instances (an addition of this library: the paper
+ * solves one problem at a time).  Each instance is an ordinary problem (any 1D
+ * scheme of this library, its own nx, nt, flux, time scheme and step sizes;
+ * one precision for all) held as a handle on the plain path; every stage of
+ * Algorithm 1 is one launch over all active instances, whose blocks run the
+ * same per-block code as the single-instance launches, so a batched instance
+ * follows exactly the iterates it would follow alone.  Instances that reach
+ * the tolerance, or whose residual stops being finite or grows by 1e10, leave
+ * the launches at the next check.
+ *
+ * pdhg_batch_workspace_size / pdhg_batch_create: `count` structs each (host
+ * arrays); workspace device, caller-owned, 256-byte aligned.  Errors as
+ * pdhg_create, naming the failing instance; PDHG_ERR_UNSUPPORTED for 2D or
+ * PDHG_PATH_FUSED.
+ * pdhg_batch_iterate: up to max_iters iterations of every active instance,
+ * Res checked every check_every iterations (0: never) against tol (absolute,
+ * or relative to each instance's cold-start residual).  iters (host, count
+ * entries, may be NULL): iterations each instance ran in this call; state
+ * (host, count, may be NULL): 1 converged, 0 still active, -1 non-finite or
+ * diverged.  Returns PDHG_OK unless a launch fails.
+ * pdhg_batch_reset: makes every instance active again (their states are kept).
+ * pdhg_batch_instance: borrowed handle of instance i (fields, residual, info;
+ * owned and destroyed by the batch).
+ */
+typedef struct pdhg_batch pdhg_batch;
+pdhg_status pdhg_batch_workspace_size(int32_t count, const pdhg_problem *probs,
+                                      const pdhg_grid *grids, const pdhg_scheme *schemes,
+                                      size_t *bytes);
+pdhg_status pdhg_batch_create(int32_t count, const pdhg_problem *probs, const pdhg_grid *grids,
+                              const pdhg_scheme *schemes, void *workspace, size_t bytes,
+                              void *stream, pdhg_batch **out);
+pdhg_status pdhg_batch_destroy(pdhg_batch *b);
+pdhg_status pdhg_batch_iterate(pdhg_batch *b, int64_t max_iters, double tol, int32_t check_every,
+                               int32_t relative, int64_t *iters, int32_t *state);
+pdhg_status pdhg_batch_reset(pdhg_batch *b);
+pdhg_status pdhg_batch_instance(pdhg_batch *b, int32_t i, pdhg_handle **h);
+pdhg_status pdhg_batch_launch_count(pdhg_batch *b, int64_t *launches, int32_t reset);
+
+/*
  * Residual norms of a caller-held state, with no handle, no workspace and no
  * device allocation.  (An addition of this library: the paper has no
  * counterpart.)  For callers that cannot allocate device memory -- e.g. code

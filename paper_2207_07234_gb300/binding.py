@@ -33,7 +33,9 @@ EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_strea
            "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_info", "pdhg_launch_count",
            "pdhg_set_profiling", "pdhg_stage_times", "pdhg_last_error", "pdhg_refine_workspace_size",
            "pdhg_solve_refine", "pdhg_one_step_workspace_size", "pdhg_solve_one_step",
-           "pdhg_gradient_workspace_size", "pdhg_solve_gradient", "pdhg_residual_noalloc"]
+           "pdhg_gradient_workspace_size", "pdhg_solve_gradient", "pdhg_batch_workspace_size",
+           "pdhg_batch_create", "pdhg_batch_destroy", "pdhg_batch_iterate", "pdhg_batch_reset",
+           "pdhg_batch_instance", "pdhg_batch_launch_count", "pdhg_residual_noalloc"]
 
 
 class PdhgError(RuntimeError):
@@ -93,6 +95,13 @@ def load(path: str = LIB_PATH):
                               vp, ctypes.POINTER(vp), ctypes.POINTER(i64)],
         "pdhg_one_step_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
         "pdhg_gradient_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_batch_workspace_size": [i32, P, G, S, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_batch_create": [i32, P, G, S, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "pdhg_batch_destroy": [vp],
+        "pdhg_batch_iterate": [vp, i64, ctypes.c_double, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i32)],
+        "pdhg_batch_reset": [vp],
+        "pdhg_batch_instance": [vp, i32, ctypes.POINTER(vp)],
+        "pdhg_batch_launch_count": [vp, ctypes.POINTER(i64), i32],
         "pdhg_solve_gradient": [P, G, S, ctypes.POINTER(ctypes.c_double), ctypes.c_double, i64, ctypes.c_double, i64,
                                 i32, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
@@ -152,8 +161,10 @@ class Solver:
         self.device = torch.device(device if device is not None else "cuda")
         self.ndof = p.ndof
         self.nt = p.nt
+        self._owned = True
         if _adopt is not None:           # a handle made by another entry point, in `workspace`
-            self.h, self.workspace, self._stream = _adopt
+            self.h, self.workspace, self._stream = _adopt[:3]
+            self._owned = _adopt[3] if len(_adopt) > 3 else True
             return
         lib = load()
         prob, grid, scheme, keep = structs(p, precision, path)
@@ -172,7 +183,8 @@ class Solver:
     # ---- lifecycle ----
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
-            load().pdhg_destroy(self.h)
+            if getattr(self, "_owned", True):
+                load().pdhg_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -347,3 +359,70 @@ def terminal_loss_fn():
             return grad * du0, grad * dnu, None, None, None
 
     return TerminalLoss
+
+
+class Batch:
+    """Many independent 1D problems advanced by shared launches (pdhg_batch)."""
+
+    def __init__(self, problems, precision="fp32", device=None, stream=None):
+        import torch
+        lib = load()
+        self.problems = list(problems)
+        n = len(self.problems)
+        self.precision = precision
+        self.device = torch.device(device if device is not None else "cuda")
+        parts = [structs(p, precision, "plain") for p in self.problems]
+        self._keep = [k for part in parts for k in part[3]]
+        self._probs = (pdhg_problem * n)(*[part[0] for part in parts])
+        self._grids = (pdhg_grid * n)(*[part[1] for part in parts])
+        self._schemes = (pdhg_scheme * n)(*[part[2] for part in parts])
+        nbytes = ctypes.c_size_t(0)
+        _check(lib.pdhg_batch_workspace_size(n, self._probs, self._grids, self._schemes, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
+        self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        b = ctypes.c_void_p()
+        _check(lib.pdhg_batch_create(n, self._probs, self._grids, self._schemes,
+                                     ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                     ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(b)))
+        self.b = b
+        self.count = n
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            load().pdhg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def iterate(self, n, tol=0.0, check_every=0, relative=False):
+        """Returns (iterations per instance in this call, state per instance:
+        1 converged, 0 active, -1 non-finite or diverged)."""
+        it = (ctypes.c_int64 * self.count)()
+        st = (ctypes.c_int32 * self.count)()
+        _check(load().pdhg_batch_iterate(self.b, int(n), float(tol), int(check_every), int(bool(relative)), it, st))
+        return np.array(list(it)), np.array(list(st))
+
+    def reset(self):
+        _check(load().pdhg_batch_reset(self.b))
+
+    def instance(self, i):
+        """Borrowed view of instance i (a Solver that does not own its handle)."""
+        h = ctypes.c_void_p()
+        _check(load().pdhg_batch_instance(self.b, int(i), ctypes.byref(h)))
+        return Solver(self.problems[i], precision=self.precision, device=self.device,
+                      _adopt=(h, self.workspace, self._stream, False))
+
+    def launches(self, reset=False) -> int:
+        n = ctypes.c_int64()
+        _check(load().pdhg_batch_launch_count(self.b, ctypes.byref(n), int(bool(reset))))
+        return n.value

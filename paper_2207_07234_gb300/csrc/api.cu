@@ -998,3 +998,328 @@ extern "C" pdhg_status pdhg_solve_gradient(const pdhg_problem *prob, const pdhg_
     pdhg_destroy(h);
     return st;
 }
+
+// ---------------------------------------------------------------------------
+// Batches: many independent 1D instances advanced by shared launches (one
+// launch per stage for all active instances).  Each instance is an ordinary
+// handle (plain path) in its own part of the workspace; the batch adds the
+// instance descriptors, the block tables and the reduction buffers.
+// ---------------------------------------------------------------------------
+enum { TAB_PRIMAL = 0, TAB_ROWS = 1, TAB_TSOLVE = 2, TAB_CHECK = 3, TAB_N = 4 };
+
+struct pdhg_batch {
+    int32_t count;
+    int32_t prec;
+    cudaStream_t stream;
+    std::vector<pdhg_handle *> h;
+    char *insts;
+    BatchEntry *tab[TAB_N];
+    int64_t nblk[TAB_N];
+    int32_t *list;
+    int32_t nlist;
+    double *partials, *out;
+    std::vector<char> active;
+    std::vector<int32_t> order;          // instance ids, most cells first
+    size_t smem;
+    int64_t launches;
+};
+
+namespace {
+
+struct BatchLayout {
+    size_t insts, tab[TAB_N], list, partials, out, inst0, total;
+    int64_t cap[TAB_N];
+    std::vector<size_t> inst_off, inst_bytes;
+    std::vector<int64_t> part_off;
+    std::vector<Geom> G;
+};
+
+// blocks of each table for one instance (grids of the single-instance launchers)
+void batch_blocks(const Geom &G, int64_t out[TAB_N], int64_t *gx) {
+    const bool dg = G.space >= PDHG_SPACE_DG_P2_LF;
+    const int64_t units = dg ? G.nx : G.S;
+    const int64_t nlines = dg ? 1 : G.lines;
+    const int64_t cols = dg ? G.nkx : G.lines * G.nkx;
+    *gx = std::min<int64_t>((units + 255) / 256, 32);
+    out[TAB_PRIMAL] = ((units + 255) / 256) * (G.nt + 1);
+    out[TAB_ROWS] = nlines * G.nt;
+    out[TAB_TSOLVE] = (cols + 127) / 128;
+    out[TAB_CHECK] = *gx * (G.nt + 1);
+}
+
+pdhg_status batch_layout(int32_t count, const pdhg_problem *probs, const pdhg_grid *grids, const pdhg_scheme *schemes,
+                         BatchLayout *B) {
+    if (count < 1 || count > (1 << 20)) return fail(PDHG_ERR_INVALID_ARG, "count must be in [1, 2^20]");
+    if (!probs || !grids || !schemes) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme array");
+    B->G.resize(count);
+    B->inst_bytes.resize(count);
+    B->part_off.resize(count);
+    int64_t tabs[TAB_N] = {0, 0, 0, 0}, parts = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        pdhg_scheme s = schemes[i];
+        if (s.path == PDHG_PATH_FUSED) return fail(PDHG_ERR_UNSUPPORTED, "batched instances run on the plain path");
+        s.path = PDHG_PATH_PLAIN;
+        if (s.precision != schemes[0].precision) return fail(PDHG_ERR_INVALID_ARG, "all instances need one precision");
+        pdhg_status st = validate(&probs[i], &grids[i], &s, &B->G[i]);
+        if (st != PDHG_OK) return fail(st, "instance " + std::to_string(i) + ": " + g_last_error);
+        if (B->G[i].dims != 1) return fail(PDHG_ERR_UNSUPPORTED, "batched instances are 1D");
+        B->inst_bytes[i] = layout_of(B->G[i]).total;
+        int64_t nb[TAB_N], gx;
+        batch_blocks(B->G[i], nb, &gx);
+        for (int k = 0; k < TAB_N; ++k) tabs[k] += nb[k];
+        B->part_off[i] = parts;
+        parts += gx * (B->G[i].nt + 1);
+    }
+    const size_t isz = schemes[0].precision == PDHG_FP64 ? sizeof(BatchInst<double>) : sizeof(BatchInst<float>);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    B->insts = take(count * isz);
+    for (int k = 0; k < TAB_N; ++k) { B->cap[k] = tabs[k]; B->tab[k] = take(tabs[k] * sizeof(BatchEntry)); }
+    B->list = take(count * sizeof(int32_t));
+    B->partials = take(parts * 6 * sizeof(double));
+    B->out = take(count * 6 * sizeof(double));
+    B->inst_off.resize(count);
+    for (int32_t i = 0; i < count; ++i) B->inst_off[i] = take(B->inst_bytes[i]);
+    B->total = o;
+    return PDHG_OK;
+}
+
+}  // namespace
+
+extern "C" pdhg_status pdhg_batch_workspace_size(int32_t count, const pdhg_problem *probs, const pdhg_grid *grids,
+                                                 const pdhg_scheme *schemes, size_t *bytes) {
+    if (!bytes) return fail(PDHG_ERR_INVALID_ARG, "bytes is NULL");
+    BatchLayout B;
+    pdhg_status st = batch_layout(count, probs, grids, schemes, &B);
+    if (st != PDHG_OK) return st;
+    *bytes = B.total;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_batch_destroy(pdhg_batch *b) {
+    if (!b) return PDHG_OK;
+    for (auto *h : b->h) pdhg_destroy(h);
+    delete b;
+    return PDHG_OK;
+}
+
+template <typename T>
+static pdhg_status batch_upload_insts(pdhg_batch *b, const BatchLayout &B) {
+    std::vector<BatchInst<T>> I(b->count);
+    for (int32_t i = 0; i < b->count; ++i) {
+        pdhg_handle *h = b->h[i];
+        BatchInst<T> &d = I[i];
+        d.P = params_of<T>(h);
+        d.u = F<T>(h, h->u_off);
+        d.phi = F<T>(h, h->L.phi);
+        d.phit = F<T>(h, h->L.phit);
+        d.lam = F<T>(h, h->L.lam);
+        d.lamt = F<T>(h, h->L.lamt);
+        d.u0 = F<T>(h, h->L.u0);
+        d.spec = h->ws + h->L.spec;
+        d.twx = h->ws + h->L.twx;
+        d.V = h->ws + h->L.V;
+        d.theta = F<T>(h, h->L.theta);
+        d.part_off = B.part_off[i];
+        int64_t nb[TAB_N], gx;
+        batch_blocks(h->G, nb, &gx);
+        d.gx = (int32_t)gx;
+        b->smem = std::max(b->smem, (size_t)(h->G.space >= PDHG_SPACE_DG_P2_LF ? h->G.lines : 1) * (h->G.nx / 2) *
+                                        2 * sizeof(T));
+    }
+    CK(cudaMemcpyAsync(b->insts, I.data(), I.size() * sizeof(BatchInst<T>), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return PDHG_OK;
+}
+
+// tables of the active instances, most cells first
+static pdhg_status batch_tables(pdhg_batch *b) {
+    std::vector<BatchEntry> t[TAB_N];
+    std::vector<int32_t> list;
+    for (int32_t i : b->order) {
+        if (!b->active[i]) continue;
+        const Geom &G = b->h[i]->G;
+        int64_t nb[TAB_N], gx;
+        batch_blocks(G, nb, &gx);
+        const int64_t gxp = nb[TAB_PRIMAL] / (G.nt + 1), nlines = nb[TAB_ROWS] / G.nt;
+        for (int64_t l = 0; l <= G.nt; ++l)
+            for (int64_t x = 0; x < gxp; ++x) t[TAB_PRIMAL].push_back({i, (int32_t)x, (int32_t)l, 0});
+        for (int64_t l = 0; l < G.nt; ++l)
+            for (int64_t x = 0; x < nlines; ++x) t[TAB_ROWS].push_back({i, (int32_t)x, (int32_t)l, 0});
+        for (int64_t x = 0; x < nb[TAB_TSOLVE]; ++x) t[TAB_TSOLVE].push_back({i, (int32_t)x, 0, 0});
+        for (int64_t l = 0; l <= G.nt; ++l)
+            for (int64_t x = 0; x < gx; ++x) t[TAB_CHECK].push_back({i, (int32_t)x, (int32_t)l, 0});
+        list.push_back(i);
+    }
+    for (int k = 0; k < TAB_N; ++k) {
+        b->nblk[k] = (int64_t)t[k].size();
+        if (!t[k].empty())
+            CK(cudaMemcpyAsync(b->tab[k], t[k].data(), t[k].size() * sizeof(BatchEntry), cudaMemcpyHostToDevice,
+                               b->stream));
+    }
+    b->nlist = (int32_t)list.size();
+    if (!list.empty())
+        CK(cudaMemcpyAsync(b->list, list.data(), list.size() * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));        // the host vectors go out of scope
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_batch_create(int32_t count, const pdhg_problem *probs, const pdhg_grid *grids,
+                                         const pdhg_scheme *schemes, void *workspace, size_t bytes, void *stream,
+                                         pdhg_batch **out) {
+    if (!out) return fail(PDHG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    BatchLayout B;
+    pdhg_status st = batch_layout(count, probs, grids, schemes, &B);
+    if (st != PDHG_OK) return st;
+    if (!workspace) return fail(PDHG_ERR_INVALID_ARG, "workspace is NULL");
+    if (((uintptr_t)workspace & 255) != 0) return fail(PDHG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (bytes < B.total) return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small: need " + std::to_string(B.total));
+    char *ws = (char *)workspace;
+    pdhg_batch *b = new pdhg_batch();
+    b->count = count;
+    b->prec = schemes[0].precision;
+    b->stream = (cudaStream_t)stream;
+    b->insts = ws + B.insts;
+    for (int k = 0; k < TAB_N; ++k) { b->tab[k] = (BatchEntry *)(ws + B.tab[k]); b->nblk[k] = 0; }
+    b->list = (int32_t *)(ws + B.list);
+    b->partials = (double *)(ws + B.partials);
+    b->out = (double *)(ws + B.out);
+    b->smem = 0;
+    b->launches = 0;
+    b->active.assign(count, 1);
+    for (int32_t i = 0; i < count; ++i) {
+        pdhg_scheme s = schemes[i];
+        s.path = PDHG_PATH_PLAIN;
+        pdhg_handle *h = nullptr;
+        st = pdhg_create(&probs[i], &grids[i], &s, ws + B.inst_off[i], B.inst_bytes[i], stream, &h);
+        if (st != PDHG_OK) { pdhg_batch_destroy(b); return fail(st, "instance " + std::to_string(i) + ": " + g_last_error); }
+        b->h.push_back(h);
+    }
+    b->order.resize(count);
+    for (int32_t i = 0; i < count; ++i) b->order[i] = i;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int32_t x, int32_t y) {
+        return B.G[x].S * (B.G[x].nt + 1) > B.G[y].S * (B.G[y].nt + 1);
+    });
+    st = b->prec == PDHG_FP64 ? batch_upload_insts<double>(b, B) : batch_upload_insts<float>(b, B);
+    if (st == PDHG_OK) st = batch_tables(b);
+    if (st != PDHG_OK) { pdhg_batch_destroy(b); return st; }
+    *out = b;
+    return PDHG_OK;
+}
+
+template <typename T>
+static cudaError_t batch_iteration(pdhg_batch *b) {
+    const BatchInst<T> *I = (const BatchInst<T> *)b->insts;
+    cudaError_t e = launch_batch<T>(BATCH_PRIMAL, I, b->tab[TAB_PRIMAL], b->nblk[TAB_PRIMAL], 0, nullptr, nullptr,
+                                    nullptr, b->stream);
+    if (e == cudaSuccess)
+        e = launch_batch<T>(BATCH_RESIDUAL, I, b->tab[TAB_ROWS], b->nblk[TAB_ROWS], b->smem, nullptr, nullptr, nullptr,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = launch_batch<T>(BATCH_TSOLVE, I, b->tab[TAB_TSOLVE], b->nblk[TAB_TSOLVE], 0, nullptr, nullptr, nullptr,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = launch_batch<T>(BATCH_DUAL, I, b->tab[TAB_ROWS], b->nblk[TAB_ROWS], b->smem, nullptr, nullptr, nullptr,
+                            b->stream);
+    b->launches += 4;
+    return e;
+}
+
+template <typename T>
+static pdhg_status batch_check(pdhg_batch *b, std::vector<double> &acc) {
+    const BatchInst<T> *I = (const BatchInst<T> *)b->insts;
+    cudaError_t e = launch_batch<T>(BATCH_CHECK, I, b->tab[TAB_CHECK], b->nblk[TAB_CHECK], 0, nullptr, b->partials,
+                                    nullptr, b->stream);
+    if (e == cudaSuccess)
+        e = launch_batch<T>(BATCH_REDUCE, I, nullptr, b->nlist, 0, b->list, b->partials, b->out, b->stream);
+    b->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(e, "batched residual check");
+    acc.resize((size_t)b->count * 6);
+    CK(cudaMemcpyAsync(acc.data(), b->out, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return PDHG_OK;
+}
+
+// Res of one instance from its six sums (as read_res)
+static void res_from_sums(const pdhg_handle *h, const double *acc, double out[4]) {
+    const double ht = h->ht, wx = h->wx;
+    const double we = h->res_norm == 1 ? wx : ht * wx;
+    double a2 = we * acc[0], b2 = we * acc[1], gap = we * acc[2], c2 = wx * acc[3];
+    if (h->G.init == PDHG_INIT_LAMBDA) {
+        a2 += c2;
+        b2 += wx * acc[4];
+        gap += wx * acc[5];
+    }
+    out[0] = std::sqrt(a2); out[1] = std::sqrt(b2); out[2] = std::sqrt(c2); out[3] = gap;
+}
+
+template <typename T>
+static pdhg_status batch_iterate_T(pdhg_batch *b, int64_t max_iters, double tol, int32_t check_every, int32_t relative,
+                                   int64_t *iters, int32_t *state) {
+    std::vector<int64_t> it(b->count, 0);
+    std::vector<int32_t> stt(b->count, 0);
+    for (int32_t i = 0; i < b->count; ++i)
+        if (!b->active[i]) stt[i] = 1;
+    std::vector<double> acc;
+    pdhg_status st = PDHG_OK;
+    for (int64_t n = 0; n < max_iters && b->nlist > 0;) {
+        cudaError_t e = batch_iteration<T>(b);
+        if (e != cudaSuccess) { st = cuda_fail(e, "batched iteration"); break; }
+        ++n;
+        for (int32_t i = 0; i < b->count; ++i)
+            if (b->active[i]) { ++it[i]; ++b->h[i]->iters; }
+        if (check_every > 0 && (n % check_every == 0 || n == max_iters)) {
+            st = batch_check<T>(b, acc);
+            if (st != PDHG_OK) break;
+            bool changed = false;
+            for (int32_t i = 0; i < b->count; ++i) {
+                if (!b->active[i]) continue;
+                double r[4];
+                res_from_sums(b->h[i], &acc[(size_t)i * 6], r);
+                const double scale = relative ? b->h[i]->res_init : 1.0;
+                if (!std::isfinite(r[0]) || !std::isfinite(r[1]) ||
+                    r[0] > 1e10 * std::max(b->h[i]->res_init, 1e-300)) {
+                    stt[i] = -1; b->active[i] = 0; changed = true;
+                } else if (r[0] <= tol * scale && r[1] <= tol * scale) {
+                    stt[i] = 1; b->active[i] = 0; changed = true;
+                }
+            }
+            if (changed) {
+                st = batch_tables(b);
+                if (st != PDHG_OK) break;
+            }
+        }
+    }
+    if (iters) std::copy(it.begin(), it.end(), iters);
+    if (state) std::copy(stt.begin(), stt.end(), state);
+    return st;
+}
+
+extern "C" pdhg_status pdhg_batch_iterate(pdhg_batch *b, int64_t max_iters, double tol, int32_t check_every,
+                                          int32_t relative, int64_t *iters, int32_t *state) {
+    if (!b) return fail(PDHG_ERR_INVALID_ARG, "null batch");
+    if (max_iters < 0) return fail(PDHG_ERR_INVALID_ARG, "max_iters < 0");
+    return b->prec == PDHG_FP64 ? batch_iterate_T<double>(b, max_iters, tol, check_every, relative, iters, state)
+                                : batch_iterate_T<float>(b, max_iters, tol, check_every, relative, iters, state);
+}
+
+extern "C" pdhg_status pdhg_batch_reset(pdhg_batch *b) {
+    if (!b) return fail(PDHG_ERR_INVALID_ARG, "null batch");
+    b->active.assign(b->count, 1);
+    return batch_tables(b);
+}
+
+extern "C" pdhg_status pdhg_batch_instance(pdhg_batch *b, int32_t i, pdhg_handle **h) {
+    if (!b || !h) return fail(PDHG_ERR_INVALID_ARG, "null batch or out");
+    if (i < 0 || i >= b->count) return fail(PDHG_ERR_INVALID_ARG, "instance index out of range");
+    *h = b->h[i];
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_batch_launch_count(pdhg_batch *b, int64_t *launches, int32_t reset) {
+    if (!b || !launches) return fail(PDHG_ERR_INVALID_ARG, "null batch or out");
+    *launches = b->launches;
+    if (reset) b->launches = 0;
+    return PDHG_OK;
+}

@@ -573,12 +573,92 @@ cudaError_t launch_phi_lap(const Params<T> &P, const T *u, const T *phi, double 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Batched launches: many 1D instances per launch.  Every block looks up its
+// (instance, block coordinates) in a table and runs the same block function as
+// the single-instance kernels above; tables list active instances only,
+// largest first.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_primal(const BatchInst<T> *__restrict__ I, const BatchEntry *__restrict__ tab) {
+    const BatchEntry e = tab[blockIdx.x];
+    const BatchInst<T> &b = I[e.inst];
+    primal_block(b.P, b.u, b.phit, b.lam, b.lamt, b.u0, e.bx, e.l);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_residual_rfft(const BatchInst<T> *__restrict__ I,
+                                                         const BatchEntry *__restrict__ tab) {
+    typedef typename Cplx<T>::type C;
+    const BatchEntry e = tab[blockIdx.x];
+    const BatchInst<T> &b = I[e.inst];
+    residual_rfft_block(b.P, b.u, (C *)b.spec, (const C *)b.twx, e.bx, e.l);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_b_tsolve(const BatchInst<T> *__restrict__ I, const BatchEntry *__restrict__ tab) {
+    typedef typename Cplx<T>::type C;
+    const BatchEntry e = tab[blockIdx.x];
+    const BatchInst<T> &b = I[e.inst];
+    tsolve_block(b.P, (C *)b.spec, b.theta, (const C *)b.V, e.bx);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_dual_irfft(const BatchInst<T> *__restrict__ I,
+                                                      const BatchEntry *__restrict__ tab) {
+    typedef typename Cplx<T>::type C;
+    const BatchEntry e = tab[blockIdx.x];
+    const BatchInst<T> &b = I[e.inst];
+    dual_irfft_block(b.P, (const C *)b.spec, b.phi, b.phit, (const C *)b.twx, e.bx, e.l);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_check(const BatchInst<T> *__restrict__ I, const BatchEntry *__restrict__ tab,
+                                                 double *__restrict__ partials) {
+    const BatchEntry e = tab[blockIdx.x];
+    const BatchInst<T> &b = I[e.inst];
+    check_block(b.P, b.u, b.phi, b.lam, b.u0, partials + b.part_off * 6, e.bx, e.l, b.gx);
+}
+
+// one block per listed instance: the sum of its (nt+1) * gx partial records
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_reduce(const BatchInst<T> *__restrict__ I, const int32_t *__restrict__ list,
+                                                  const double *__restrict__ partials, double *__restrict__ out) {
+    const int inst = list[blockIdx.x];
+    const BatchInst<T> &b = I[inst];
+    const int64_t n = (int64_t)(b.P.nt + 1) * b.gx;
+    const double *p = partials + b.part_off * 6;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x)
+        for (int j = 0; j < 6; ++j) acc[j] += p[k * 6 + j];
+    block_sum6(acc, out + (int64_t)inst * 6);
+}
+
+template <typename T>
+cudaError_t launch_batch(int kind, const BatchInst<T> *I, const BatchEntry *tab, int64_t nblocks, size_t smem,
+                         const int32_t *list, double *partials, double *out, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)nblocks;
+    switch (kind) {
+    case BATCH_PRIMAL: k_b_primal<T><<<g, 256, 0, s>>>(I, tab); break;
+    case BATCH_RESIDUAL: k_b_residual_rfft<T><<<g, 256, smem, s>>>(I, tab); break;
+    case BATCH_TSOLVE: k_b_tsolve<T><<<g, 128, 0, s>>>(I, tab); break;
+    case BATCH_DUAL: k_b_dual_irfft<T><<<g, 256, smem, s>>>(I, tab); break;
+    case BATCH_CHECK: k_b_check<T><<<g, 256, 0, s>>>(I, tab, partials); break;
+    case BATCH_REDUCE: k_b_reduce<T><<<g, 256, 0, s>>>(I, list, partials, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t init_plain_attributes() {
     const int mx = 200 * 1024;
     cudaError_t e = cudaFuncSetAttribute(k_residual_rfft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dual_irfft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_residual_rfft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_b_dual_irfft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return e;
 }
 
@@ -592,7 +672,9 @@ cudaError_t init_plain_attributes() {
     template cudaError_t init_plain_attributes<T>();                                                      \
     template cudaError_t launch_check<T>(const Params<T> &, const T *, const T *, const T *, const T *, double *, \
                                          double *, cudaStream_t);                                             \
-    template cudaError_t launch_phi_lap<T>(const Params<T> &, const T *, const T *, double *, double *, cudaStream_t);
+    template cudaError_t launch_phi_lap<T>(const Params<T> &, const T *, const T *, double *, double *, cudaStream_t); \
+    template cudaError_t launch_batch<T>(int, const BatchInst<T> *, const BatchEntry *, int64_t, size_t,        \
+                                         const int32_t *, double *, double *, cudaStream_t);
 
 PDHG_INSTANTIATE(float)
 PDHG_INSTANTIATE(double)

@@ -29,4 +29,27 @@ template <typename T>
 cudaError_t launch_check(const Params<T> &P, const T *u, const T *phi, const T *lam, const T *u0, double *partials,
                          double *out, cudaStream_t s);
 
+// ---- batched launches (many 1D instances per launch) ----
+// One instance: its parameters and device arrays (those of an ordinary handle).
+template <typename T>
+struct BatchInst {
+    Params<T> P;
+    T *u, *phi, *phit, *lam, *lamt;
+    const T *u0;
+    void *spec;               // Cplx<T> spectrum of the plain path
+    const void *twx, *V;      // twiddles, DG eigenvectors
+    const T *theta;
+    int64_t part_off;         // first 6-double partial record of this instance
+    int32_t gx;               // residual-check blocks per slice row
+};
+// one block of a batched launch: instance and the block's coordinates in that
+// instance's own grid (bx = blockIdx.x, l = blockIdx.y of the single launch)
+struct BatchEntry { int32_t inst, bx, l, pad; };
+enum { BATCH_PRIMAL, BATCH_RESIDUAL, BATCH_TSOLVE, BATCH_DUAL, BATCH_CHECK, BATCH_REDUCE };
+// kind: one of BATCH_*; nblocks table entries (BATCH_REDUCE: entries of `list`,
+// instance ids, each summing its partial records into out[inst * 6 ..]).
+template <typename T>
+cudaError_t launch_batch(int kind, const BatchInst<T> *I, const BatchEntry *tab, int64_t nblocks, size_t smem,
+                         const int32_t *list, double *partials, double *out, cudaStream_t s);
+
 }  // namespace pdhg

@@ -284,3 +284,42 @@ def viscous_burgers(nx: int = 2048, nt: int = 1024, T: float = 2.0, nu: float = 
                    time="bdf2", nx=nx, lx=lx, T=T, nt=nt, alpha=0.5, beta=0.0,
                    nu=nu, lf_a=1.5, c=1.5, tau_u=tau[0], tau_u0=tau[1],
                    tau_phi=tau[2], tau_lambda=tau[3], init=init, u0=u0)
+
+
+def batch_instances(count: int = 256, seed: int = 20723, nx_range=(256, 4096), nt_range=(64, 1024),
+                    cfl_range=(1.0, 8.0), tau=(0.5, 0.1, 0.5, 0.99)) -> list:
+    """A batch of independent 1D problems of mixed kind, size and scheme, drawn
+    per instance from default_rng(seed):
+
+    * kind: linear advection u_t + u_x = 0 (upwind FD) or Burgers u_t + (u^2/2)_x = 0
+      (global Lax-Friedrichs FD), probability 1/2 each;
+    * nx: a power of two with log2 nx uniform over the range (the preconditioner's
+      FFT along x needs power-of-two lengths in this library);
+    * nt uniform in nt_range; CFL = c h_t / h_x uniform in cfl_range; BE or BDF2;
+    * u0 = sum_{k=1..8} (0.5/k) N(0,1) sin(k x + theta_k) on [0, 2 pi] (plus 0.5 for
+      Burgers), c = a = max |f'(u0)| (1 for advection)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = int(np.log2(nx_range[0])), int(np.log2(nx_range[1]))
+    out = []
+    for i in range(count):
+        burgers = bool(rng.random() < 0.5)
+        nx = 1 << int(rng.integers(lo, hi + 1))
+        nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+        cfl = float(rng.uniform(*cfl_range))
+        time = "bdf2" if rng.random() < 0.5 else "be"
+        useed = int(rng.integers(0, 2 ** 31 - 1))
+        lx = 2.0 * np.pi
+        u0 = random_fourier_1d(nx, lx, useed)
+        if burgers:
+            u0 = u0 + 0.5
+            c = float(np.max(np.abs(u0)))
+            alpha, beta, space = 0.5, 0.0, "fd_lf"
+        else:
+            c, alpha, beta, space = 1.0, 0.0, 1.0, "fd_upwind"
+        hx = lx / nx
+        T = nt * cfl * hx / c
+        out.append(Problem(name=f"batch{i}_{'burgers' if burgers else 'advection'}_{nx}x{nt}", dims=1,
+                           space=space, time=time, nx=nx, lx=lx, T=T, nt=nt, alpha=alpha, beta=beta,
+                           lf_a=c, c=c, tau_u=tau[0], tau_u0=tau[1], tau_phi=tau[2],
+                           tau_lambda=tau[3], u0=u0))
+    return out

@@ -79,3 +79,29 @@ def test_create_rejects_without_device_work(lib):
     st = lib.pdhg_create(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
                          ctypes.c_void_p(256 * 1024), 1 << 30, None, ctypes.byref(h))
     assert st == -1 and "non-finite" in lib.pdhg_last_error().decode()
+
+
+def test_batch_validation_without_device_work(lib):
+    """Batch sizes add up the instances; 2D, mixed precision and the fused path are
+    rejected before any device work."""
+    from paper_2207_07234_gb300 import binding
+    probs = [W.advection_upwind_be(nx=64, nt=8), W.traffic_dg_p1(ncell=32, nt=4)]
+
+    def arrays(ps, precisions, paths):
+        parts = [binding.structs(p, pr, pa) for p, pr, pa in zip(ps, precisions, paths)]
+        n = len(ps)
+        return (n, (binding.pdhg_problem * n)(*[x[0] for x in parts]), (binding.pdhg_grid * n)(*[x[1] for x in parts]),
+                (binding.pdhg_scheme * n)(*[x[2] for x in parts]), parts)
+
+    n, P, G, S, keep = arrays(probs, ["fp32", "fp32"], ["auto", "auto"])
+    total = ctypes.c_size_t(0)
+    assert lib.pdhg_batch_workspace_size(n, P, G, S, ctypes.byref(total)) == 0
+    parts = sum(binding.workspace_size(p, "fp32", "plain") for p in probs)
+    assert total.value > parts
+    for bad in ([probs[0], W.burgers_2d(n=16, nt=4)], ):
+        n, P, G, S, keep = arrays(bad, ["fp32", "fp32"], ["auto", "auto"])
+        assert lib.pdhg_batch_workspace_size(n, P, G, S, ctypes.byref(total)) == -7
+    n, P, G, S, keep = arrays(probs, ["fp32", "fp64"], ["auto", "auto"])
+    assert lib.pdhg_batch_workspace_size(n, P, G, S, ctypes.byref(total)) == -1
+    n, P, G, S, keep = arrays(probs, ["fp32", "fp32"], ["auto", "fused"])
+    assert lib.pdhg_batch_workspace_size(n, P, G, S, ctypes.byref(total)) == -7

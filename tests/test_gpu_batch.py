@@ -1,0 +1,113 @@
+"""GPU batches (pdhg_batch): many 1D instances per launch.
+
+A batched instance runs the same per-block code as a lone handle, so its
+iterates equal the lone instance's bit for bit; against the oracle the
+batched iterates meet the same bounds as single-instance parity; instances
+leave the launches when they converge, after as many iterations as alone."""
+import numpy as np
+import pytest
+
+import pdhg_workloads as W
+from oracle import pdhg as opdhg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_07234_gb300 import binding
+    binding.load()
+    return binding
+
+
+def steps(p, t, t0=0.1):
+    return p.replace(tau_u=t, tau_phi=t, tau_u0=t0, tau_lambda=0.99)
+
+
+def mixed():
+    return [
+        steps(W.advection_upwind_be(nx=256, nt=9), 0.6),
+        steps(W.advection_upwind_be(nx=64, nt=5).replace(time="bdf2"), 0.4),
+        steps(W.viscous_burgers(nx=512, nt=13, T=1.0, nu=0.01), 0.35),
+        W.heat_table1(128, 11),
+        W.burgers_dg_p2(ncell=128, nt=6, T=0.5, time="be").replace(c=0.5, tau_u=0.05, tau_u0=0.05, tau_phi=0.05),
+        W.traffic_dg_p1(ncell=64, nt=7),
+        steps(W.advection_upwind_be(nx=1024, nt=3).replace(alpha=-1.0, beta=1.0,
+              u0=0.25 + 0.1 * np.sin(W.fd_nodes(1024, 2 * np.pi)), space="fd_lf", lf_a=0.5), 0.5),
+    ]
+
+
+FIELDS = ("u", "phi", "phit", "lambda", "lambdat")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_equals_lone_instances_bitwise(B, precision):
+    probs = mixed()
+    with B.Batch(probs, precision=precision) as bt:
+        its, st = bt.iterate(20)
+        assert list(its) == [20] * len(probs) and list(st) == [0] * len(probs)
+        got = [{f: bt.instance(i).get_host(f) for f in FIELDS} for i in range(len(probs))]
+    for p, g in zip(probs, got):
+        with B.Solver(p, precision=precision, path="plain") as s:
+            s.iterate(20)
+            for f in FIELDS:
+                assert np.array_equal(s.get_host(f), g[f]), (p.name, f)
+
+
+def test_batch_fixed_iterates_vs_oracle(B):
+    probs = mixed()
+    with B.Batch(probs, precision="fp64") as bt:
+        bt.iterate(25)
+        got = [(bt.instance(i).get_host("u"), bt.instance(i).get_host("phi")) for i in range(len(probs))]
+    for p, (u, phi) in zip(probs, got):
+        st = opdhg.initial_state(p)
+        for _ in range(25):
+            opdhg.step(p, st)
+        tu = 1e-11 if p.nmodes == 2 else 1e-12
+        assert np.max(np.abs(u - st["u"])) <= tu * np.max(np.abs(st["u"])), p.name
+        assert np.max(np.abs(phi - st["phi"])) <= 10 * tu * np.max(np.abs(st["phi"])), p.name
+
+
+def test_batch_convergence_masks_match_lone_counts(B):
+    """Each instance stops at the check where it alone would stop; the others go on."""
+    probs = [W.advection_upwind_be(nx=128, nt=64, tau=(1.4, 0.1, 0.35, 0.99)), W.heat_table1(64, 16),
+             W.advection_upwind_be(nx=64, nt=16, cfl=1.0, tau=(0.5, 0.1, 0.5, 0.99)),
+             W.traffic_dg_p1(ncell=32, nt=8)]
+    with B.Batch(probs, precision="fp64") as bt:
+        its, st = bt.iterate(20000, tol=1e-8, check_every=10)
+    assert list(st) == [1] * len(probs)
+    for p, n in zip(probs, its):
+        with B.Solver(p, precision="fp64", path="plain") as s:
+            assert s.iterate(20000, tol=1e-8, check_every=10) == n, p.name
+    assert len(set(its)) > 1
+
+
+def test_batch_isolates_a_diverging_instance(B):
+    good = W.advection_upwind_be(nx=128, nt=16, tau=(0.5, 0.1, 0.5, 0.99))
+    bad = good.replace(tau_u=40.0, tau_phi=40.0, tau_u0=40.0)
+    with B.Batch([good, bad, good], precision="fp64") as bt:
+        its, st = bt.iterate(20000, tol=1e-8, check_every=10)
+        assert list(st) == [1, -1, 1]
+        assert its[1] < its[0]
+        assert np.all(np.isfinite(bt.instance(0).get_host("u")))
+
+
+def test_batch_of_256_sampled(B):
+    """The 256-instance workload (float32): a few iterations, then three instances
+    (largest, smallest, median) against lone runs, bit for bit."""
+    probs = W.batch_instances()
+    with B.Batch(probs, precision="fp32") as bt:
+        bt.iterate(5)
+        cells = np.array([p.ndof * p.nt for p in probs])
+        pick = [int(np.argmax(cells)), int(np.argmin(cells)), int(np.argsort(cells)[len(cells) // 2])]
+        got = {i: bt.instance(i).get_host("u") for i in pick}
+        assert bt.launches() >= 4 * 5
+    for i in pick:
+        with B.Solver(probs[i], precision="fp32", path="plain") as s:
+            s.iterate(5)
+            assert np.array_equal(s.get_host("u"), got[i]), probs[i].name
