@@ -223,8 +223,8 @@ __global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Param
                 if (threadIdx.x + j * ATHREADS < FH * V)
                     reinterpret_cast<float4 *>(fin)[threadIdx.x + j * ATHREADS] = R[j];
             __syncthreads();
-            const float2 *res = stockham<LOG2M, false>(reinterpret_cast<float2 *>(fin),
-                                                       reinterpret_cast<float2 *>(pp), FH, twM);
+            const float2 *res = stockham<LOG2M, false, FH, ATHREADS>(reinterpret_cast<float2 *>(fin),
+                                                                     reinterpret_cast<float2 *>(pp), twM);
             float2 *dst = spec + (int64_t)lr * P.nkx * ny + y0;
             for (int idx = threadIdx.x; idx < (M + 1) * FH; idx += blockDim.x) {
                 const int k = idx / FH, rr = idx - k * FH;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
                     pf[b][j] = l < nt ? col[(int64_t)l * cs + t + j * FTHREADS] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham<LOG2NY, false>(ba, bb, TB, tw);
+        const float2 *res = stockham<LOG2NY, false, TB, FTHREADS>(ba, bb, tw);
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = lb + b;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
                     pf[b][j] = l >= 0 ? col[(int64_t)l * cs + t + j * FTHREADS] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham<LOG2NY, true>(ba, bb, TB, tw);
+        const float2 *res = stockham<LOG2NY, true, TB, FTHREADS>(ba, bb, tw);
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = hi - b;
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
 // exactly the inputs of the first radix-4 stage (span 1) and the outputs of the
 // last (span 256).  Those two stages run in registers; only the three middle
 // stages (spans 4, 16, 64) go through shared memory.
-__global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *__restrict__ spec,
+__global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float2 *__restrict__ spec,
                                                        const float2 *__restrict__ twY,
                                                        const float *__restrict__ thetaT) {
     constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2, PN = NY + NY / 4;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *
                 for (int q = 0; q < 4; ++q) pf[b][q] = l < nt ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham_r4_range_pad<LOG2NY, false>(ba, bb, TB, tw, 4, 256);
+        const float2 *res = stockham_r4_range<LOG2NY, false, 4, 256, TB, FTHREADS, true>(ba, bb, tw);
         // stage 5 (span 256) in registers: inputs t + 256 r with twiddles W^{r t}, outputs t + 256 q
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols1024(Params<float> P, float2 *
                 for (int q = 0; q < 4; ++q) pf[b][q] = l >= 0 ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham_r4_range_pad<LOG2NY, true>(ba, bb, TB, tw, 4, 256);
+        const float2 *res = stockham_r4_range<LOG2NY, true, 4, 256, TB, FTHREADS, true>(ba, bb, tw);
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = hi - b;
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC(Params<float> P, const float
         fa[rr * M + k] = irfft_merge(fb[rr * (M + 1) + k], fb[rr * (M + 1) + M - k], twN[k]);
     }
     __syncthreads();
-    const float2 *res = stockham<LOG2M, true>(fa, fb, FH, twM);
+    const float2 *res = stockham<LOG2M, true, FH, FTHREADS>(fa, fb, twM);
     const float4 *z4 = reinterpret_cast<const float4 *>(res);
     float4 *p4 = reinterpret_cast<float4 *>(phi + base);
     float4 *t4 = reinterpret_cast<float4 *>(phit + base);
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC1024(Params<float> P, const f
         }
     }
     __syncthreads();
-    const float2 *res = stockham_r4_range<LOG2M, true>(fa, fb, FH, twM, 2, 128);
+    const float2 *res = stockham_r4_range<LOG2M, true, 2, 128, FH, FTHREADS, false>(fa, fb, twM);
     const float s = P.dual_scale;
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
