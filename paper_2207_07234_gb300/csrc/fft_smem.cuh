@@ -51,9 +51,7 @@ __device__ void fft_radix2(C *z, int log2n, int batch, int cs, int is, const C *
 // X_k = E_k + W_N^k O_k for k = 0..M, with E_k = (Z_k + conj Z_{M-k})/2 and
 // O_k = (Z_k - conj Z_{M-k})/(2i).  twN[k] = W_N^k, k = 0..M.
 template <typename C>
-__device__ __forceinline__ C rfft_split(const C *Z, int M, int k, const C *__restrict__ twN) {
-    C zk = Z[k == M ? 0 : k];
-    C zm = Z[k == 0 ? 0 : M - k];
+__device__ __forceinline__ C rfft_split_vals(C zk, C zm, int k, const C *__restrict__ twN) {
     C e, a, o;
     e.x = 0.5f * (zk.x + zm.x);
     e.y = 0.5f * (zk.y - zm.y);
@@ -62,6 +60,11 @@ __device__ __forceinline__ C rfft_split(const C *Z, int M, int k, const C *__res
     o.x = 0.5f * a.y;         // a / (2i) = -i a / 2
     o.y = -0.5f * a.x;
     return cadd(e, cmul(twN[k], o));
+}
+
+template <typename C>
+__device__ __forceinline__ C rfft_split(const C *Z, int M, int k, const C *__restrict__ twN) {
+    return rfft_split_vals(Z[k == M ? 0 : k], Z[k == 0 ? 0 : M - k], k, twN);
 }
 
 // Inverse split: Z_k = E_k + i O_k for k = 0..M-1, E_k = (X_k + conj X_{M-k})/2,

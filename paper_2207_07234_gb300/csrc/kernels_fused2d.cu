@@ -204,13 +204,31 @@ __global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Param
                     const float4 o4 = reinterpret_cast<const float4 *>(uold + r * NX)[x4];
                     ov[0] = o4.x; ov[1] = o4.y; ov[2] = o4.z; ov[3] = o4.w;
                 }
+                // D in flux-difference form with each f(v) evaluated once per value:
+                //   LF: (F_{j+1/2} - F_{j-1/2}) = (f_{j+1} - f_{j-1})/2 - a (v_{j+1} - 2 v_j + v_{j-1})/2
+                //   upwind: f_j - f_{j-1};  viscous: -nu (v_{j+1} - 2 v_j + v_{j-1}) / h^2
+                float fx[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) fx[k] = flux(P, vr[k]);
+                const bool lf = P.space != FD_UPWIND;
                 float Rv[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const float v = vr[e + 1];
-                    Rv[e] = fd_dir(P, vr[e], v, vr[e + 2], P.inv_hx) + fd_dir(P, uv[e], v, dv[e], P.inv_hy) +
-                            kn * v + kc * cv[e];
-                    if (BDF2_ && lr >= 1) Rv[e] += ko * ov[e];
+                    const float fu = flux(P, uv[e]), fdn = flux(P, dv[e]);
+                    const float lx = vr[e] - 2.f * v + vr[e + 2], ly = uv[e] - 2.f * v + dv[e];
+                    float dx, dy;
+                    if (lf) {
+                        dx = 0.5f * (fx[e + 2] - fx[e]) - 0.5f * P.lf_a * lx;
+                        dy = 0.5f * (fdn - fu) - 0.5f * P.lf_a * ly;
+                    } else {
+                        dx = fx[e + 1] - fx[e];
+                        dy = fx[e + 1] - fu;
+                    }
+                    float r = dx * P.inv_hx + dy * P.inv_hy + kn * v + kc * cv[e];
+                    if (P.nu != 0.f) r -= P.nu * (lx * P.inv_hx * P.inv_hx + ly * P.inv_hy * P.inv_hy);
+                    if (BDF2_ && lr >= 1) r += ko * ov[e];
+                    Rv[e] = r;
                 }
                 R[j] = make_float4(Rv[0], Rv[1], Rv[2], Rv[3]);
             }
@@ -218,17 +236,25 @@ __global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Param
             // FFT input in the u slot the residual no longer needs (BE: u^{m-1}, BDF2: u^{m-2}),
             // FFT scratch in the phit slot of m-1
             float *fin = BDF2_ ? const_cast<float *>(uold) : const_cast<float *>(ucur);
+            // rows of the padded layout of stockham.cuh (sequence stride PN, 4 per 16)
+            constexpr int PN = SeqLayout<LOG2M, 2>::PN;
+            float2 *fin2 = reinterpret_cast<float2 *>(fin);
 #pragma unroll
-            for (int j = 0; j < GPT; ++j)          // z_n = R_{2n} + i R_{2n+1}
-                if (threadIdx.x + j * ATHREADS < FH * V)
-                    reinterpret_cast<float4 *>(fin)[threadIdx.x + j * ATHREADS] = R[j];
+            for (int j = 0; j < GPT; ++j) {        // z_n = R_{2n} + i R_{2n+1}
+                const int gi = threadIdx.x + j * ATHREADS;
+                if (gi < FH * V) {
+                    const int rr = gi / V, x4 = gi - rr * V;
+                    *reinterpret_cast<float4 *>(fin2 + rr * PN + padx(2 * x4)) = R[j];
+                }
+            }
             __syncthreads();
-            const float2 *res = stockham<LOG2M, false, FH, ATHREADS>(reinterpret_cast<float2 *>(fin),
-                                                                     reinterpret_cast<float2 *>(pp), twM);
+            const float2 *res = stockham<LOG2M, false, FH, ATHREADS, 2>(fin2, reinterpret_cast<float2 *>(pp), twM);
             float2 *dst = spec + (int64_t)lr * P.nkx * ny + y0;
             for (int idx = threadIdx.x; idx < (M + 1) * FH; idx += blockDim.x) {
                 const int k = idx / FH, rr = idx - k * FH;
-                dst[(int64_t)k * ny + rr] = rfft_split(res + rr * M, M, k, twN);
+                const float2 *row = res + rr * PN;
+                dst[(int64_t)k * ny + rr] =
+                    rfft_split_vals(row[padx(k == M ? 0 : k)], row[padx(k == 0 ? 0 : M - k)], k, twN);
             }
         }
         __syncthreads();
@@ -297,7 +323,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
                     pf[b][j] = l < nt ? col[(int64_t)l * cs + t + j * FTHREADS] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham<LOG2NY, false, TB, FTHREADS>(ba, bb, tw);
+        const float2 *res = stockham<LOG2NY, false, TB, FTHREADS, 0>(ba, bb, tw);
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = lb + b;
@@ -347,7 +373,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
                     pf[b][j] = l >= 0 ? col[(int64_t)l * cs + t + j * FTHREADS] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham<LOG2NY, true, TB, FTHREADS>(ba, bb, tw);
+        const float2 *res = stockham<LOG2NY, true, TB, FTHREADS, 0>(ba, bb, tw);
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = hi - b;
@@ -366,7 +392,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
 __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float2 *__restrict__ spec,
                                                        const float2 *__restrict__ twY,
                                                        const float *__restrict__ thetaT) {
-    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2, PN = NY + NY / 4;
+    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2, PN = SeqLayout<LOG2NY, 1>::PN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *ba = reinterpret_cast<float2 *>(smem_raw);              // [TB][PN] (padded)
     float2 *bb = ba + TB * PN;                                      // [TB][PN]
@@ -413,7 +439,7 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
                 for (int q = 0; q < 4; ++q) pf[b][q] = l < nt ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham_r4_range<LOG2NY, false, 4, 256, TB, FTHREADS, true>(ba, bb, tw);
+        const float2 *res = stockham_r4_range<LOG2NY, false, 4, 256, TB, FTHREADS, 1>(ba, bb, tw);
         // stage 5 (span 256) in registers: inputs t + 256 r with twiddles W^{r t}, outputs t + 256 q
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
@@ -474,7 +500,7 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
                 for (int q = 0; q < 4; ++q) pf[b][q] = l >= 0 ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham_r4_range<LOG2NY, true, 4, 256, TB, FTHREADS, true>(ba, bb, tw);
+        const float2 *res = stockham_r4_range<LOG2NY, true, 4, 256, TB, FTHREADS, 1>(ba, bb, tw);
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = hi - b;
@@ -496,7 +522,7 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
 
 static size_t smem_cols(int log2ny) {
     const size_t n = (size_t)1 << log2ny;
-    return log2ny == 10 ? (4 * (n + n / 4) + n) * 8 : 5 * n * 8;    // ny = 1024: padded buffers
+    return log2ny == 10 ? (4 * (size_t)SeqLayout<10, 1>::PN + n) * 8 : 5 * n * 8;    // ny = 1024: padded
 }
 
 // ---------------------------------------------------------------------------
@@ -510,8 +536,9 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC(Params<float> P, const float
     constexpr int M = 1 << LOG2M, NX = 2 * M;
     constexpr int VPT = FH * NX / 4 / FTHREADS;              // float4 of phi per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *fa = reinterpret_cast<float2 *>(smem_raw);      // [FH][M]
-    float2 *fb = fa + FH * (M + 1);                          // staging [FH][M+1], then scratch
+    constexpr int PN = SeqLayout<LOG2M, 2>::PN;           // padded rows (stockham.cuh)
+    float2 *fa = reinterpret_cast<float2 *>(smem_raw);      // [FH][PN]
+    float2 *fb = fa + FH * PN;                               // staging [FH][M+1], then scratch [FH][PN]
     const int ny = P.ny;
     const int y0 = blockIdx.x * FH;
     const int l = blockIdx.y;
@@ -530,18 +557,19 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC(Params<float> P, const float
     __syncthreads();
     for (int idx = threadIdx.x; idx < FH * M; idx += blockDim.x) {
         const int rr = idx / M, k = idx - rr * M;
-        fa[rr * M + k] = irfft_merge(fb[rr * (M + 1) + k], fb[rr * (M + 1) + M - k], twN[k]);
+        fa[rr * PN + padx(k)] = irfft_merge(fb[rr * (M + 1) + k], fb[rr * (M + 1) + M - k], twN[k]);
     }
     __syncthreads();
-    const float2 *res = stockham<LOG2M, true, FH, FTHREADS>(fa, fb, twM);
-    const float4 *z4 = reinterpret_cast<const float4 *>(res);
+    const float2 *res = stockham<LOG2M, true, FH, FTHREADS, 2>(fa, fb, twM);
     float4 *p4 = reinterpret_cast<float4 *>(phi + base);
     float4 *t4 = reinterpret_cast<float4 *>(phit + base);
     const float s = P.dual_scale;
+    constexpr int V = NX / 4;
 #pragma unroll
     for (int j = 0; j < VPT; ++j) {
         const int idx = threadIdx.x + j * FTHREADS;
-        const float4 z = z4[idx];
+        const int rr = idx / V, x4 = idx - rr * V;
+        const float4 z = *reinterpret_cast<const float4 *>(res + rr * PN + padx(2 * x4));
         float4 pn = ph[j];
         pn.x += s * z.x; pn.y += s * z.y; pn.z += s * z.z; pn.w += s * z.w;
         p4[idx] = pn;
@@ -561,8 +589,9 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC1024(Params<float> P, const f
     constexpr int LOG2M = 9, M = 512, NX = 1024;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *st = reinterpret_cast<float2 *>(smem_raw);      // staging [FH][M+1]
-    float2 *fa = st + FH * (M + 1);                          // [FH][M]
-    float2 *fb = fa + FH * M;                                // [FH][M]
+    constexpr int PN = SeqLayout<LOG2M, 2>::PN;           // padded rows (stockham.cuh)
+    float2 *fa = st + FH * (M + 1);                          // [FH][PN]
+    float2 *fb = fa + FH * PN;                               // [FH][PN]
     const int ny = P.ny;
     const int y0 = blockIdx.x * FH;
     const int l = blockIdx.y;
@@ -594,20 +623,20 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC1024(Params<float> P, const f
             const float2 *X = st + rr * (M + 1);
             const float2 z0 = irfft_merge(X[t], X[M - t], w0);
             const float2 z1 = irfft_merge(X[t + 256], X[256 - t], w1);
-            reinterpret_cast<float4 *>(fa + rr * M)[t] =
+            *reinterpret_cast<float4 *>(fa + rr * PN + padx(2 * t)) =
                 make_float4(z0.x + z1.x, z0.y + z1.y, z0.x - z1.x, z0.y - z1.y);
         }
     }
     __syncthreads();
-    const float2 *res = stockham_r4_range<LOG2M, true, 2, 128, FH, FTHREADS, false>(fa, fb, twM);
+    const float2 *res = stockham_r4_range<LOG2M, true, 2, 128, FH, FTHREADS, 2>(fa, fb, twM);
     const float s = P.dual_scale;
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-        const float2 *r = res + (2 * h + rr) * M;
-        float2 x0 = r[i];
-        float2 x1 = cmulconj(r[i + 128], twM[126 + i]);             // staged block of span 128
-        float2 x2 = cmulconj(r[i + 256], twM[126 + 128 + i]);
-        float2 x3 = cmulconj(r[i + 384], twM[126 + 256 + i]);
+        const float2 *r = res + (2 * h + rr) * PN;
+        float2 x0 = r[padx(i)];
+        float2 x1 = cmulconj(r[padx(i + 128)], twM[126 + i]);       // staged block of span 128
+        float2 x2 = cmulconj(r[padx(i + 256)], twM[126 + 128 + i]);
+        float2 x3 = cmulconj(r[padx(i + 384)], twM[126 + 256 + i]);
         dft4<true>(x0, x1, x2, x3);
         const float2 z[4] = {x0, x1, x2, x3};
         float2 *p2 = reinterpret_cast<float2 *>(phi + base + (int64_t)(2 * h + rr) * NX);
@@ -623,7 +652,9 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC1024(Params<float> P, const f
     }
 }
 
-static size_t smem_rowsC1024() { return (size_t)FH * (512 + 1) * 8 + 2 * (size_t)FH * 512 * 8; }
+static size_t smem_rowsC1024() {
+    return (size_t)FH * (512 + 1) * 8 + 2 * (size_t)FH * SeqLayout<9, 2>::PN * 8;
+}
 
 // ---------------------------------------------------------------------------
 // host side
@@ -665,8 +696,8 @@ static size_t smem_rowsA(int log2m, bool bdf2) {
     return (size_t)2 * (FH + 4) * NX * 4 + (size_t)(bdf2 ? 3 : 2) * (FH + 2) * NX * 4;
 }
 static size_t smem_rowsC(int log2m) {
-    const int M = 1 << log2m;
-    return (size_t)FH * (M + 1) * 8 * 2;
+    const int M = 1 << log2m, PN = M + M / 4 + 4;                // SeqLayout<log2m, 2>::PN
+    return (size_t)FH * PN * 8 * 2;
 }
 
 template <int L> static cudaError_t attr_rows() {

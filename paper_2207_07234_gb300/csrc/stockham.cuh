@@ -32,31 +32,42 @@ __device__ __forceinline__ float2 twmul(float2 x, float2 w) { return INV ? cmulc
 // conflicts (the span-4 writes, 64 bytes apart per lane, otherwise hit 4 ways).
 __device__ __forceinline__ int padx(int j) { return j + 4 * (j >> 4); }
 
-template <bool PAD>
+// Layouts (PAD): 0 plain, sequence stride N; 1 padded within a sequence (padx),
+// stride N + N/4; 2 as 1 with stride N + N/4 + 4 -- the extra 4 puts the same
+// index of consecutive sequences 4 banks apart, so lanes that read one index of
+// 4 sequences (the real-FFT split of 4 rows) do not collide.
+template <int PAD>
 __device__ __forceinline__ int sidx(int j) { return PAD ? padx(j) : j; }
 
+template <int LOG2N, int PAD>
+struct SeqLayout {
+    static constexpr int N = 1 << LOG2N;
+    static constexpr int PN = PAD == 0 ? N : (PAD == 1 ? N + N / 4 : N + N / 4 + 4);
+};
+
 // The radix-2 stage, always first (span 1, so no twiddles): outputs 2i, 2i+1.
-template <int LOG2N, int BATCH, int NTHR>
+template <int LOG2N, int BATCH, int NTHR, int PAD>
 __device__ __forceinline__ void stage_r2_first(const float2 *a, float2 *b) {
     constexpr int N = 1 << LOG2N, Q = N >> 1, W = BATCH * Q, ITERS = (W + NTHR - 1) / NTHR;
+    constexpr int PN = SeqLayout<LOG2N, PAD>::PN;
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
         const int idx = threadIdx.x + it * NTHR;
         if (W % NTHR != 0 && idx >= W) break;
         const int s = idx >> (LOG2N - 1), i = idx & (Q - 1);
-        const float2 *src = a + s * N;
-        float2 *dst = b + s * N;
-        const float2 x0 = src[i], x1 = src[i + Q];
-        dst[2 * i] = cadd(x0, x1);
-        dst[2 * i + 1] = csub(x0, x1);
+        const float2 *src = a + s * PN;
+        float2 *dst = b + s * PN;
+        const float2 x0 = src[sidx<PAD>(i)], x1 = src[sidx<PAD>(i + Q)];
+        dst[sidx<PAD>(2 * i)] = cadd(x0, x1);
+        dst[sidx<PAD>(2 * i + 1)] = csub(x0, x1);
     }
 }
 
 // One radix-4 stage with span P (the product of the radices of earlier stages).
-template <int LOG2N, bool INV, int P, int BATCH, int NTHR, bool PAD>
+template <int LOG2N, bool INV, int P, int BATCH, int NTHR, int PAD>
 __device__ __forceinline__ void stage_r4(const float2 *a, float2 *b, const float2 *tw) {
     constexpr int N = 1 << LOG2N, Q = N >> 2, W = BATCH * Q, ITERS = (W + NTHR - 1) / NTHR;
-    constexpr int PN = PAD ? N + N / 4 : N;
+    constexpr int PN = SeqLayout<LOG2N, PAD>::PN;
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
         const int idx = threadIdx.x + it * NTHR;
@@ -88,7 +99,7 @@ __device__ __forceinline__ void stage_r4(const float2 *a, float2 *b, const float
 
 // Radix-4 stages with spans PFROM, 4 PFROM, ... below PTO; returns the buffer
 // holding the result.  Ends with __syncthreads() (when it runs any stage).
-template <int LOG2N, bool INV, int PFROM, int PTO, int BATCH, int NTHR, bool PAD>
+template <int LOG2N, bool INV, int PFROM, int PTO, int BATCH, int NTHR, int PAD>
 __device__ __forceinline__ float2 *stockham_r4_range(float2 *a, float2 *b, const float2 *tw) {
     if constexpr (PFROM >= PTO) {
         return a;
@@ -112,14 +123,14 @@ __device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 
 
 // Full transform of BATCH sequences by NTHR threads; data starts in a, b is
 // scratch; returns the buffer holding the result.  Ends with __syncthreads().
-template <int LOG2N, bool INV, int BATCH, int NTHR>
+template <int LOG2N, bool INV, int BATCH, int NTHR, int PAD = 0>
 __device__ __forceinline__ float2 *stockham(float2 *a, float2 *b, const float2 *tw) {
     if constexpr (LOG2N & 1) {
-        stage_r2_first<LOG2N, BATCH, NTHR>(a, b);
+        stage_r2_first<LOG2N, BATCH, NTHR, PAD>(a, b);
         __syncthreads();
-        return stockham_r4_range<LOG2N, INV, 2, (1 << LOG2N), BATCH, NTHR, false>(b, a, tw);
+        return stockham_r4_range<LOG2N, INV, 2, (1 << LOG2N), BATCH, NTHR, PAD>(b, a, tw);
     } else {
-        return stockham_r4_range<LOG2N, INV, 1, (1 << LOG2N), BATCH, NTHR, false>(a, b, tw);
+        return stockham_r4_range<LOG2N, INV, 1, (1 << LOG2N), BATCH, NTHR, PAD>(a, b, tw);
     }
 }
 
