@@ -269,7 +269,19 @@ struct pdhg_handle {
     Fused2D fused;
     size_t u_off;            // offset of the current u buffer (the fused path alternates two)
     int res_norm;            // 0: space-time norms of Eq. 2.12; 1: per time slice (Sec. 3.5)
+    // CUDA graph of `gchunk` iterations plus the residual check (plain path)
+    bool graphs;
+    cudaGraphExec_t gexec;
+    cudaStream_t gstream;
+    int32_t gchunk;
+    int64_t glaunches;       // kernel launches per replay
 };
+
+static void graph_drop(pdhg_handle *h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->gchunk = 0;
+}
 
 template <typename T> static Params<T> &params_of(pdhg_handle *h);
 template <> Params<float> &params_of<float>(pdhg_handle *h) { return h->pf; }
@@ -507,6 +519,8 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
     h->wx = G.dims == 2 ? hx * (grid->ly / (double)grid->ny) : hx;
     h->iters = 0; h->launches = 0; h->profiling = false;
     h->res_norm = 0;
+    h->graphs = !G.fused;
+    h->gexec = nullptr; h->gstream = nullptr; h->gchunk = 0; h->glaunches = 0;
     h->u_off = L.u;
     memset(h->stage_ms, 0, sizeof(h->stage_ms));
     memset(h->stage_n, 0, sizeof(h->stage_n));
@@ -527,6 +541,8 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
 
 extern "C" pdhg_status pdhg_destroy(pdhg_handle *h) {
     if (!h) return PDHG_OK;
+    graph_drop(h);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     for (auto &r : h->recs) { h->pool.push_back(r.a); h->pool.push_back(r.b); }
     for (auto e : h->pool) if (e) cudaEventDestroy(e);
     delete h;
@@ -583,19 +599,65 @@ static cudaError_t enqueue_iteration(pdhg_handle *h) {
     return stage(h, PDHG_STAGE_DUAL, 1, [&] { return launch_dual_irfft<T>(P, spec, phi, phit, twx, s); });
 }
 
+// Capture m iterations and the residual check as one graph (on a private stream;
+// replayed on the handle's stream).  Returns an error if capture is not possible;
+// the caller then launches kernel by kernel.
+template <typename T>
+static cudaError_t graph_build(pdhg_handle *h, int32_t m) {
+    graph_drop(h);
+    cudaError_t e = cudaSuccess;
+    if (!h->gstream) e = cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaStream_t user = h->stream;
+    const int64_t l0 = h->launches;
+    h->stream = h->gstream;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int32_t i = 0; i < m && e == cudaSuccess; ++i) e = enqueue_iteration<T>(h);
+        if (e == cudaSuccess) e = enqueue_check<T>(h);
+        cudaError_t e2 = cudaStreamEndCapture(h->gstream, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    h->stream = user;
+    h->glaunches = h->launches - l0;
+    h->launches = l0;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) h->gchunk = m;
+    else graph_drop(h);
+    return e;
+}
+
 template <typename T>
 static pdhg_status iterate_T(pdhg_handle *h, int64_t max_iters, double tol, int32_t check_every, int32_t relative,
                              int64_t *done) {
     int64_t n = 0;
     double scale = relative ? h->res_init : 1.0;
     for (; n < max_iters;) {
-        cudaError_t e = enqueue_iteration<T>(h);
-        if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
-        ++n;
-        ++h->iters;
-        if (check_every > 0 && (n % check_every == 0 || n == max_iters)) {
-            double r[4];
-            pdhg_status st = compute_res<T>(h, r);
+        double r[4];
+        pdhg_status st;
+        const bool chunk = h->graphs && !h->profiling && check_every > 0 && max_iters - n >= check_every;
+        if (chunk && h->gchunk != check_every && graph_build<T>(h, check_every) != cudaSuccess) {
+            cudaGetLastError();                          // capture refused: launch kernel by kernel
+            h->graphs = false;
+        }
+        if (chunk && h->gchunk == check_every) {
+            cudaError_t e = cudaGraphLaunch(h->gexec, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+            n += check_every;
+            h->iters += check_every;
+            h->launches += h->glaunches;
+            st = read_res(h, r);
+        } else {
+            cudaError_t e = enqueue_iteration<T>(h);
+            if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
+            ++n;
+            ++h->iters;
+            if (!(check_every > 0 && (n % check_every == 0 || n == max_iters))) continue;
+            st = compute_res<T>(h, r);
+        }
+        {
             if (st != PDHG_OK) { if (done) *done = n; return st; }
             if (!std::isfinite(r[0]) || !std::isfinite(r[1])) {
                 if (done) *done = n;
@@ -942,6 +1004,7 @@ static pdhg_status gradient_T(pdhg_handle *h, const double *target, char *ustar,
     Params<T> &P = params_of<T>(h);
     P.ulin = reinterpret_cast<const T *>(ustar);
     P.tshift = reinterpret_cast<const T *>(tshift);
+    graph_drop(h);                                   // the captured launches hold the old parameters
     CK(cudaMemsetAsync(h->ws + h->u_off, 0, ub, h->stream));
     const size_t zero[5] = {h->L.phi, h->L.phit, h->L.lam, h->L.lamt, h->L.u0};
     const size_t zb[5] = {G.nt * S * sizeof(T), G.nt * S * sizeof(T), S * sizeof(T), S * sizeof(T), S * sizeof(T)};
@@ -1321,5 +1384,12 @@ extern "C" pdhg_status pdhg_batch_launch_count(pdhg_batch *b, int64_t *launches,
     if (!b || !launches) return fail(PDHG_ERR_INVALID_ARG, "null batch or out");
     *launches = b->launches;
     if (reset) b->launches = 0;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_set_graphs(pdhg_handle *h, int32_t enable) {
+    if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
+    graph_drop(h);
+    h->graphs = enable != 0 && !h->G.fused;
     return PDHG_OK;
 }
