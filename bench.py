@@ -46,12 +46,18 @@ def workload(name: str):
         return W.burgers_2d(n=256, nt=64, tau=(0.15, 0.1, 0.15, 0.99))
     if name == "burgers2d_nt32":                      # profiling case: 134 MB per field (> L2)
         return W.burgers_2d(n=1024, nt=32, tau=(0.15, 0.1, 0.15, 0.99))
+    if name == "burgers2d_nt64":                      # profiling case with the full run's t-chunking
+        return W.burgers_2d(n=1024, nt=64, tau=(0.15, 0.1, 0.15, 0.99))
     if name == "dg_p2":
         return W.burgers_dg_p2(tau=(0.2, 0.1, 0.2, 0.99)).replace(c=0.5)
     if name == "advection":
         return W.advection_upwind_be(tau=(1.4, 0.1, 0.35, 0.99))
     if name == "heat":                                # Table 1's finest mesh, Sec. 4.1
         return W.heat_table1(1024, 256)
+    if name == "transport2d":                         # 2D linear transport: the fused path converges
+        return W.burgers_2d(n=1024, nt=64).replace(name="transport2d_1024x1024x64", alpha=0.0, beta=1.0,
+                                                    space="fd_upwind", lf_a=1.0, c=1.0, tau_u=0.5,
+                                                    tau_phi=0.5, tau_u0=0.1)
     raise ValueError(name)
 
 
@@ -474,7 +480,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch leg")
-    ap.add_argument("--ttr", default="advection,heat",
+    ap.add_argument("--ttr", default="advection,heat,transport2d",
                     help="comma-separated workloads for the time-to-residual comparison ('' = skip)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -47,7 +47,7 @@ typedef enum {
     PDHG_ERR_NONFINITE = -4,            /* a residual norm became NaN or Inf */
     PDHG_ERR_DIVERGED = -5,             /* the primal residual grew by more than 1e10 */
     PDHG_ERR_TIMEOUT = -6,              /* a bounded device wait gave up */
-    PDHG_ERR_UNSUPPORTED = -7           /* valid but not implemented (e.g. nx not a power of two) */
+    PDHG_ERR_UNSUPPORTED = -7           /* valid but not implemented (e.g. a 2D nx not a power of two) */
 } pdhg_status;
 
 enum { PDHG_TIME_BE = 0, PDHG_TIME_BDF2 = 1 };
@@ -95,7 +95,11 @@ typedef struct {
 } pdhg_problem;
 
 /* Uniform space-time grid (Sec. 3.1, 3.2): h_x = lx/nx, h_y = ly/ny, h_t = T/nt.
- * dims = 1 or 2; ny = 1 in 1D; for DG, nx is the number of cells. */
+ * dims = 1 or 2; ny = 1 in 1D; for DG, nx is the number of cells.  nx and ny are
+ * powers of two in [4, 8192] (ny <= 2048), 1 <= nt <= 65534; 1D finite differences
+ * also take any nx in [4, 4096] (the preconditioner's x-DFT then runs as a
+ * Bluestein chirp convolution through power-of-two FFTs).  Others:
+ * PDHG_ERR_UNSUPPORTED. */
 typedef struct {
     int32_t dims;
     int64_t nx, ny;

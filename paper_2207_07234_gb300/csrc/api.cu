@@ -48,6 +48,7 @@ namespace {
 
 struct Layout {
     size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, partials, scal, fused;
+    size_t blu_tw, blu_c, blu_b;
     size_t total;
 };
 
@@ -61,6 +62,7 @@ struct Geom {
     size_t esz;      // element size
     bool has_gamma;
     bool fused;
+    int blu_log2L;   // > 0: Bluestein x-transform (1D FD, nx not a power of two)
 };
 
 pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s, Geom *G) {
@@ -91,8 +93,15 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
         if (p->gamma_hat != 0) return fail(PDHG_ERR_UNSUPPORTED, "the DG preconditioner uses c only");
     }
     if (g->dims == 2 && p->gamma_half) return fail(PDHG_ERR_UNSUPPORTED, "gamma_half is 1D only");
-    if (!is_pow2(g->nx) || g->nx < 4 || g->nx > 8192)
+    G->blu_log2L = 0;
+    if (!is_pow2(g->nx)) {
+        if (g->dims != 1 || dg || g->nx < 4 || g->nx > 4096)
+            return fail(PDHG_ERR_UNSUPPORTED, "nx must be a power of two in [4, 8192] (1D finite differences: any "
+                                              "nx in [4, 4096])");
+        G->blu_log2L = ilog2(2 * g->nx - 1);
+    } else if (g->nx < 4 || g->nx > 8192) {
         return fail(PDHG_ERR_UNSUPPORTED, "nx must be a power of two in [4, 8192]");
+    }
     if (g->dims == 2 && (!is_pow2(g->ny) || g->ny < 4 || g->ny > 2048))
         return fail(PDHG_ERR_UNSUPPORTED, "ny must be a power of two in [4, 2048]");
     G->dims = g->dims; G->space = s->space; G->time = s->time; G->init = s->init;
@@ -137,6 +146,10 @@ Layout layout_of(const Geom &G) {
     L.partials = take(nblk * 6 * sizeof(double));
     L.scal = take(16 * sizeof(double));
     L.fused = take(G.fused ? fused2d_workspace_bytes(G.nx, G.ny, G.nt) : 0);
+    const size_t lb = G.blu_log2L ? ((size_t)1 << G.blu_log2L) : 0;
+    L.blu_tw = take(lb * 2 * e);
+    L.blu_c = take(G.blu_log2L ? G.nx * 2 * e : 0);
+    L.blu_b = take(lb * 2 * e);
     L.total = o;
     return L;
 }
@@ -327,6 +340,59 @@ static void fill_params(Params<T> &P, const Geom &G, const pdhg_problem *p, cons
     P.tau_u = (T)p->tau_u; P.tau_u0 = (T)p->tau_u0; P.tau_phi = (T)p->tau_phi; P.tau_lambda = (T)p->tau_lambda;
     P.dual_scale = (T)(p->tau_phi * ht * ht / ((double)(G.nx / 2) * (double)G.ny));
     P.gamma_half = nullptr;
+    P.blu_log2L = G.blu_log2L;
+    P.blu_scale = (T)(p->tau_phi * ht * ht);
+}
+
+// In-place iterative radix-2 FFT (forward, unnormalised) of n = 2^k values, host, double.
+static void host_fft(std::vector<std::complex<double>> &a) {
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = -2.0 * M_PI / (double)len;
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const std::complex<double> w(std::cos(ang * (double)k), std::sin(ang * (double)k));
+                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+// Bluestein tables for a length-N DFT through length-L FFTs: stage-grouped W_L, the
+// chirp c_n = exp(i pi n^2 / N) (n^2 reduced mod 2N before scaling), FFT_L(b).
+template <typename T>
+static void bluestein_tables(int64_t N, int log2L, std::vector<T> &tw, std::vector<T> &c, std::vector<T> &bh) {
+    const int64_t L = int64_t(1) << log2L;
+    tw.assign(2 * L, (T)0);                   // stage s: entries (2^s - 1) + pos, pos < 2^s
+    for (int s = 0; s < log2L; ++s) {
+        const int64_t hs = int64_t(1) << s;
+        for (int64_t pos = 0; pos < hs; ++pos) {
+            const double a = -2.0 * M_PI * (double)(pos * (L / (2 * hs))) / (double)L;
+            tw[2 * (hs - 1 + pos)] = (T)std::cos(a);
+            tw[2 * (hs - 1 + pos) + 1] = (T)std::sin(a);
+        }
+    }
+    std::vector<std::complex<double>> cd(N), b(L, 0.0);
+    for (int64_t n = 0; n < N; ++n) {
+        const int64_t q = (n * n) % (2 * N);
+        cd[n] = std::polar(1.0, M_PI * (double)q / (double)N);
+    }
+    for (int64_t m = 0; m < N; ++m) {
+        b[m] = cd[m];
+        if (m > 0) b[L - m] = cd[m];
+    }
+    host_fft(b);
+    c.resize(2 * N);
+    for (int64_t n = 0; n < N; ++n) { c[2 * n] = (T)cd[n].real(); c[2 * n + 1] = (T)cd[n].imag(); }
+    bh.resize(2 * L);
+    for (int64_t m = 0; m < L; ++m) { bh[2 * m] = (T)b[m].real(); bh[2 * m + 1] = (T)b[m].imag(); }
 }
 
 extern "C" pdhg_status pdhg_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
@@ -431,6 +497,13 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
             }
     }
     CK(cudaMemcpy(F<T>(h, h->L.theta), th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (G.blu_log2L) {
+        std::vector<T> btw, bc, bb;
+        bluestein_tables<T>(G.nx, G.blu_log2L, btw, bc, bb);
+        CK(cudaMemcpy(h->ws + h->L.blu_tw, btw.data(), btw.size() * sizeof(T), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->ws + h->L.blu_c, bc.data(), bc.size() * sizeof(T), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->ws + h->L.blu_b, bb.data(), bb.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
     if (G.fused) {
         // fused 2D path: staged twiddle tables for the Stockham transforms of length
         // M = nx/2 (along x) and ny (along y), and theta in [kx][ky] order
@@ -446,6 +519,11 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     Params<T> &P = params_of<T>(h);
     fill_params(P, G, p, g, lf_a);
     if (G.has_gamma) P.gamma_half = F<T>(h, h->L.gamma);
+    if (G.blu_log2L) {
+        P.blu_tw = h->ws + h->L.blu_tw;
+        P.blu_c = h->ws + h->L.blu_c;
+        P.blu_b = h->ws + h->L.blu_b;
+    }
     CK(init_plain_attributes<T>());
     return PDHG_OK;
 }
@@ -1187,8 +1265,9 @@ static pdhg_status batch_upload_insts(pdhg_batch *b, const BatchLayout &B) {
         int64_t nb[TAB_N], gx;
         batch_blocks(h->G, nb, &gx);
         d.gx = (int32_t)gx;
-        b->smem = std::max(b->smem, (size_t)(h->G.space >= PDHG_SPACE_DG_P2_LF ? h->G.lines : 1) * (h->G.nx / 2) *
-                                        2 * sizeof(T));
+        const size_t rows = h->G.blu_log2L ? ((size_t)1 << h->G.blu_log2L)
+                                           : (size_t)(h->G.space >= PDHG_SPACE_DG_P2_LF ? h->G.lines : 1) * (h->G.nx / 2);
+        b->smem = std::max(b->smem, rows * 2 * sizeof(T));
     }
     CK(cudaMemcpyAsync(b->insts, I.data(), I.size() * sizeof(BatchInst<T>), cudaMemcpyHostToDevice, b->stream));
     CK(cudaStreamSynchronize(b->stream));

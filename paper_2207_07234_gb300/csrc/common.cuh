@@ -53,6 +53,13 @@ struct Params {
     T tau_u, tau_u0, tau_phi, tau_lambda;
     T dual_scale;           // tau_phi * h_t^2 / (nx/2 * ny): folds FFT and Thomas scalings
     const T *gamma_half;    // 1D FD, nullable
+    // Bluestein x-transform (1D FD, nx not a power of two): DFT of length nx as a
+    // chirp convolution through radix-2 FFTs of length L = 2^blu_log2L >= 2 nx - 1
+    int32_t blu_log2L = 0;      // 0: the packed power-of-two transform
+    T blu_scale = T(0);         // tau_phi h_t^2 (the Bluestein inverse is normalised)
+    const void *blu_tw = nullptr;   // stage-grouped W_L: entry (2^s - 1) + pos = W_L^{pos L / 2^{s+1}}
+    const void *blu_c = nullptr;    // chirp c_n = exp(i pi n^2 / nx), n < nx
+    const void *blu_b = nullptr;    // FFT_L of b: b_m = c_|m| for |m| < nx (indices mod L), else 0
     // adjoint mode (FD, plain path): the state is a perturbation v of the solution
     // u*, the residual is J(u*) v and the transposes are taken at u*; the last
     // slice carries the objective |v - tshift|^2 (tshift = target - u*^nt).

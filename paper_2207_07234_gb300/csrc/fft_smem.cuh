@@ -47,6 +47,28 @@ __device__ void fft_radix2(C *z, int log2n, int batch, int cs, int is, const C *
     }
 }
 
+// The same in-place DIT transform for one sequence of length n = 2^log2n with
+// twiddles grouped by stage: stage s (half-span hs = 2^s) reads tw[(hs - 1) + pos]
+// = W_n^{pos n / (2 hs)}, so a warp's lanes read consecutive entries.
+template <typename C>
+__device__ void fft_radix2_staged(C *z, int log2n, const C *__restrict__ tw, bool inverse) {
+    const int half = 1 << (log2n - 1);
+    for (int s = 0; s < log2n; ++s) {
+        const int hs = 1 << s;
+        for (int k = threadIdx.x; k < half; k += blockDim.x) {
+            const int pos = k & (hs - 1);
+            const int i0 = ((k >> s) << (s + 1)) + pos;
+            C w = tw[(hs - 1) + pos];
+            if (inverse) w.y = -w.y;
+            const C tb = cmul(w, z[i0 + hs]);
+            const C ta = z[i0];
+            z[i0] = cadd(ta, tb);
+            z[i0 + hs] = csub(ta, tb);
+        }
+        __syncthreads();
+    }
+}
+
 // Real-FFT split: given Z = FFT_M(z) (natural order, length M) produce
 // X_k = E_k + W_N^k O_k for k = 0..M, with E_k = (Z_k + conj Z_{M-k})/2 and
 // O_k = (Z_k - conj Z_{M-k})/(2i).  twN[k] = W_N^k, k = 0..M.

@@ -118,6 +118,26 @@ __device__ __forceinline__ T time_R(const Params<T> &P, const T *u, int64_t S, i
     return r;
 }
 
+// Bluestein core on z (length L, shared memory): on entry z[bitrev(n)] = a_n; on
+// exit z_k = L conj((a * b)_k), the circular convolution with the chirp filter b,
+// via FFT(a), the product with FFT(b), and a second forward FFT of its conjugate.
+template <typename T>
+__device__ __forceinline__ void bluestein_core(const Params<T> &P, typename Cplx<T>::type *z) {
+    typedef typename Cplx<T>::type C;
+    const int lgL = P.blu_log2L, L = 1 << lgL;
+    const C *tw = (const C *)P.blu_tw, *bh = (const C *)P.blu_b;
+    fft_radix2_staged(z, lgL, tw, false);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {       // Y = conj(A B^), bit-reversed in place
+        const int j = bitrev(i, lgL);
+        if (i > j) continue;
+        const C a = cconj(cmul(z[i], bh[i])), b = cconj(cmul(z[j], bh[j]));
+        z[j] = a;
+        z[i] = b;
+    }
+    __syncthreads();
+    fft_radix2_staged(z, lgL, tw, false);
+}
+
 template <typename T>
 __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T *__restrict__ u,
                                                     typename Cplx<T>::type *__restrict__ spec,
@@ -152,6 +172,26 @@ __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T 
     }
     const T *un = u + (int64_t)(l + 1) * S;
     const int64_t row = (int64_t)line * N;
+    if (P.blu_log2L) {           // DFT_k = conj(c_k) (a * b)_k with a_n = R_n conj(c_n)
+        const int lgL = P.blu_log2L, L = 1 << lgL;
+        const C *cc = (const C *)P.blu_c;
+        for (int x = threadIdx.x; x < L; x += blockDim.x) {
+            C v = mk<C, T>(T(0), T(0));
+            if (x < N) {
+                const T r = (P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 1) * S, un, line, x) : fd_D(P, un, line, x)) +
+                            time_R(P, u + row + x, S, l);
+                v = mk<C, T>(r * cc[x].x, -r * cc[x].y);
+            }
+            z[bitrev(x, lgL)] = v;
+        }
+        __syncthreads();
+        bluestein_core(P, z);
+        C *out = spec + ((int64_t)l * P.lines + line) * P.nkx;
+        const T invL = T(1) / T(L);
+        for (int k = threadIdx.x; k < P.nkx; k += blockDim.x)
+            out[k] = cconj(cscale(cmul(cc[k], z[k]), invL));           // conj(c_k) conj(z_k) / L
+        return;
+    }
     for (int x = threadIdx.x; x < N; x += blockDim.x) {
         T r = (P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 1) * S, un, line, x) : fd_D(P, un, line, x)) +
               time_R(P, u + row + x, S, l);
@@ -307,6 +347,33 @@ __device__ __forceinline__ void dual_irfft_block(const Params<T> &P, const typen
     const int N = P.nx, M = N >> 1, lg = P.log2m;
     const int nl = is_dg(P.space) ? P.lines : 1;
     const int line0 = is_dg(P.space) ? 0 : bx;
+    if (P.blu_log2L) {
+        // x = Re IDFT(Z) with Z the Hermitian extension of X_k (k <= nx/2):
+        // x_n = Re(c_n z_n) / (L nx) after the core on a_k = conj(Z_k c_k)
+        const int lgL = P.blu_log2L, L = 1 << lgL;
+        const C *cc = (const C *)P.blu_c;
+        const C *X = spec + ((int64_t)l * P.lines + line0) * P.nkx;
+        for (int k = threadIdx.x; k < L; k += blockDim.x) {
+            C v = mk<C, T>(T(0), T(0));
+            if (k < N) {
+                const C Zk = k < P.nkx ? X[k] : cconj(X[N - k]);
+                v = cconj(cmul(Zk, cc[k]));
+            }
+            z[bitrev(k, lgL)] = v;
+        }
+        __syncthreads();
+        bluestein_core(P, z);
+        const T sc = P.blu_scale / (T(L) * T(N));
+        const int64_t off = (int64_t)l * P.S + (int64_t)line0 * N;
+        for (int x = threadIdx.x; x < N; x += blockDim.x) {
+            const T dz = sc * (cc[x].x * z[x].x - cc[x].y * z[x].y);
+            const int64_t i = off + x;
+            const T pn = phi[i] + dz;
+            phi[i] = pn;
+            phit[i] = pn + dz;
+        }
+        return;
+    }
     for (int t = threadIdx.x; t < nl * M; t += blockDim.x) {
         int m = t / M, k = t - m * M;
         const C *X = spec + ((int64_t)l * P.lines + line0 + m) * P.nkx;
@@ -470,6 +537,7 @@ cudaError_t launch_primal(const Params<T> &P, T *u, const T *phit, T *lam, T *la
 
 template <typename T>
 size_t smem_rows(const Params<T> &P) {
+    if (P.blu_log2L) return ((size_t)1 << P.blu_log2L) * sizeof(typename Cplx<T>::type);
     int nl = is_dg(P.space) ? P.lines : 1;
     return (size_t)nl * (P.nx / 2) * sizeof(typename Cplx<T>::type);
 }

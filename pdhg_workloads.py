@@ -287,14 +287,14 @@ def viscous_burgers(nx: int = 2048, nt: int = 1024, T: float = 2.0, nu: float = 
 
 
 def batch_instances(count: int = 256, seed: int = 20723, nx_range=(256, 4096), nt_range=(64, 1024),
-                    cfl_range=(1.0, 8.0), tau=(0.5, 0.1, 0.5, 0.99)) -> list:
+                    cfl_range=(1.0, 8.0), tau=(0.5, 0.1, 0.5, 0.99), pow2: bool = False) -> list:
     """A batch of independent 1D problems of mixed kind, size and scheme, drawn
     per instance from default_rng(seed):
 
     * kind: linear advection u_t + u_x = 0 (upwind FD) or Burgers u_t + (u^2/2)_x = 0
       (global Lax-Friedrichs FD), probability 1/2 each;
-    * nx: a power of two with log2 nx uniform over the range (the preconditioner's
-      FFT along x needs power-of-two lengths in this library);
+    * nx uniform over the integers of the range (pow2=True: a power of two with
+      log2 nx uniform over the range);
     * nt uniform in nt_range; CFL = c h_t / h_x uniform in cfl_range; BE or BDF2;
     * u0 = sum_{k=1..8} (0.5/k) N(0,1) sin(k x + theta_k) on [0, 2 pi] (plus 0.5 for
       Burgers), c = a = max |f'(u0)| (1 for advection)."""
@@ -303,7 +303,7 @@ def batch_instances(count: int = 256, seed: int = 20723, nx_range=(256, 4096), n
     out = []
     for i in range(count):
         burgers = bool(rng.random() < 0.5)
-        nx = 1 << int(rng.integers(lo, hi + 1))
+        nx = (1 << int(rng.integers(lo, hi + 1))) if pow2 else int(rng.integers(nx_range[0], nx_range[1] + 1))
         nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
         cfl = float(rng.uniform(*cfl_range))
         time = "bdf2" if rng.random() < 0.5 else "be"

@@ -47,8 +47,8 @@ def test_workspace_size_and_validation(lib):
     cells = 64 * 64 * 8
     assert n32 >= 4 * cells * 4 and n64 >= 4 * cells * 8
     with pytest.raises(binding.PdhgError) as e:
-        _size(W.advection_upwind_be(nx=96, nt=4))
-    assert e.value.status == -7                                   # UNSUPPORTED: nx not a power of two
+        _size(W.burgers_dg_p2(ncell=96, nt=4))
+    assert e.value.status == -7                                   # UNSUPPORTED: DG nx not a power of two
     with pytest.raises(binding.PdhgError) as e:
         _size(W.advection_upwind_be(nx=64, nt=4).replace(tau_u=-1.0))
     assert e.value.status == -1                                   # INVALID_ARG
@@ -105,3 +105,16 @@ def test_batch_validation_without_device_work(lib):
     assert lib.pdhg_batch_workspace_size(n, P, G, S, ctypes.byref(total)) == -1
     n, P, G, S, keep = arrays(probs, ["fp32", "fp32"], ["auto", "fused"])
     assert lib.pdhg_batch_workspace_size(n, P, G, S, ctypes.byref(total)) == -7
+
+
+def test_non_power_of_two_nx_accepted_only_for_1d_fd(lib):
+    """nx outside the powers of two: 1D finite differences up to 4096 (Bluestein
+    x-transform); DG, 2D and longer 1D lines are rejected before any device work."""
+    from paper_2207_07234_gb300 import binding
+    assert binding.workspace_size(W.advection_upwind_be(nx=1000, nt=8), "fp64") > 0
+    assert binding.workspace_size(W.advection_upwind_be(nx=257, nt=8), "fp32") > 0
+    for bad in (W.advection_upwind_be(nx=4097, nt=4), W.traffic_dg_p1(ncell=100, nt=4),
+                W.burgers_2d(n=16, nt=4).replace(nx=24, u0=np.zeros((16, 24)))):
+        with pytest.raises(binding.PdhgError) as e:
+            binding.workspace_size(bad, "fp64")
+        assert e.value.status == -7

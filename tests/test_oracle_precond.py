@@ -13,6 +13,8 @@ from oracle import precond, spacetime
     W.burgers_dg_p2(ncell=6, nt=4),
     W.viscous_burgers(nx=7, nt=3),
     W.transport_dg_p1(ncell=6, nt=4),
+    W.advection_upwind_be(nx=7, nt=4).replace(nu=0.1),         # odd nx (the Bluestein path's lengths)
+    W.viscous_burgers(nx=10, nt=3),
 ], ids=lambda p: p.name)
 def test_kd_inverse_equals_dense_solve(p):
     """FFT-in-x + Thomas-in-t equals a dense solve of K_d assembled in real space from
