@@ -172,24 +172,45 @@ __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T 
     }
     const T *un = u + (int64_t)(l + 1) * S;
     const int64_t row = (int64_t)line * N;
-    if (P.blu_log2L) {           // DFT_k = conj(c_k) (a * b)_k with a_n = R_n conj(c_n)
+    if (P.blu_log2L) {
+        // Two real rows per complex transform: the block of an even slice l takes
+        // w_n = R^l_n + i R^{l+1}_n (R^{l+1} = 0 past the last slice); the block of an
+        // odd slice has nothing to do.  DFT(w)_k = conj(c_k) (a * b)_k with
+        // a_n = w_n conj(c_n); then X_k = (W_k + conj W_{N-k}) / 2 and
+        // Y_k = (W_k - conj W_{N-k}) / (2i) are the spectra of the two rows.
+        if (l & 1) return;
+        const bool two = l + 1 < P.nt;
         const int lgL = P.blu_log2L, L = 1 << lgL;
         const C *cc = (const C *)P.blu_c;
+        const T *un2 = u + (int64_t)(l + 2) * S;
         for (int x = threadIdx.x; x < L; x += blockDim.x) {
             C v = mk<C, T>(T(0), T(0));
             if (x < N) {
                 const T r = (P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 1) * S, un, line, x) : fd_D(P, un, line, x)) +
                             time_R(P, u + row + x, S, l);
-                v = mk<C, T>(r * cc[x].x, -r * cc[x].y);
+                T r2 = T(0);
+                if (two)
+                    r2 = (P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 2) * S, un2, line, x) : fd_D(P, un2, line, x)) +
+                         time_R(P, u + row + x, S, l + 1);
+                v = cmulconj(mk<C, T>(r, r2), cc[x]);
             }
             z[bitrev(x, lgL)] = v;
         }
         __syncthreads();
         bluestein_core(P, z);
+        // z_k = L conj((a * b)_k): W_k = conj(c_k z_k) / L
         C *out = spec + ((int64_t)l * P.lines + line) * P.nkx;
-        const T invL = T(1) / T(L);
-        for (int k = threadIdx.x; k < P.nkx; k += blockDim.x)
-            out[k] = cconj(cscale(cmul(cc[k], z[k]), invL));           // conj(c_k) conj(z_k) / L
+        C *out2 = spec + ((int64_t)(l + 1) * P.lines + line) * P.nkx;
+        const T h = T(0.5) / T(L);
+        for (int k = threadIdx.x; k < P.nkx; k += blockDim.x) {
+            const int km = k == 0 ? 0 : N - k;
+            const C wk = cconj(cmul(cc[k], z[k])), wm = cmul(cc[km], z[km]);     // W_k L, conj(W_{N-k}) L
+            out[k] = cscale(cadd(wk, wm), h);
+            if (two) {
+                const C d = csub(wk, wm);                                      // (W_k - conj W_{N-k}) L
+                out2[k] = cscale(mk<C, T>(d.y, -d.x), h);                     // / (2i)
+            }
+        }
         return;
     }
     for (int x = threadIdx.x; x < N; x += blockDim.x) {
@@ -348,16 +369,25 @@ __device__ __forceinline__ void dual_irfft_block(const Params<T> &P, const typen
     const int nl = is_dg(P.space) ? P.lines : 1;
     const int line0 = is_dg(P.space) ? 0 : bx;
     if (P.blu_log2L) {
-        // x = Re IDFT(Z) with Z the Hermitian extension of X_k (k <= nx/2):
-        // x_n = Re(c_n z_n) / (L nx) after the core on a_k = conj(Z_k c_k)
+        // Two rows per transform (even slice l with l+1): W = Z^l + i Z^{l+1}, the
+        // Hermitian extensions of the two half spectra; IDFT(W) = x^l + i x^{l+1}, and
+        // IDFT(W)_n = c_n z_n / (L nx) after the core on a_k = conj(W_k c_k).
+        if (l & 1) return;
+        const bool two = l + 1 < P.nt;
         const int lgL = P.blu_log2L, L = 1 << lgL;
         const C *cc = (const C *)P.blu_c;
         const C *X = spec + ((int64_t)l * P.lines + line0) * P.nkx;
+        const C *Y = spec + ((int64_t)(l + 1) * P.lines + line0) * P.nkx;
         for (int k = threadIdx.x; k < L; k += blockDim.x) {
             C v = mk<C, T>(T(0), T(0));
             if (k < N) {
                 const C Zk = k < P.nkx ? X[k] : cconj(X[N - k]);
-                v = cconj(cmul(Zk, cc[k]));
+                C Wk = Zk;
+                if (two) {
+                    const C Vk = k < P.nkx ? Y[k] : cconj(Y[N - k]);
+                    Wk = mk<C, T>(Zk.x - Vk.y, Zk.y + Vk.x);                      // Z + i V
+                }
+                v = cconj(cmul(Wk, cc[k]));
             }
             z[bitrev(k, lgL)] = v;
         }
@@ -366,11 +396,19 @@ __device__ __forceinline__ void dual_irfft_block(const Params<T> &P, const typen
         const T sc = P.blu_scale / (T(L) * T(N));
         const int64_t off = (int64_t)l * P.S + (int64_t)line0 * N;
         for (int x = threadIdx.x; x < N; x += blockDim.x) {
-            const T dz = sc * (cc[x].x * z[x].x - cc[x].y * z[x].y);
+            const C w = cmul(cc[x], z[x]);
+            const T dz = sc * w.x;
             const int64_t i = off + x;
             const T pn = phi[i] + dz;
             phi[i] = pn;
             phit[i] = pn + dz;
+            if (two) {
+                const T dz2 = sc * w.y;
+                const int64_t i2 = i + P.S;
+                const T pn2 = phi[i2] + dz2;
+                phi[i2] = pn2;
+                phit[i2] = pn2 + dz2;
+            }
         }
         return;
     }

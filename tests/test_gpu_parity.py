@@ -54,7 +54,7 @@ def cases():
     yield auto_steps(W.transport_dg_p1(ncell=512, nt=9))
     yield auto_steps(W.traffic_dg_p1(ncell=256, nt=7).replace(space="dg_p1_lf", lf_a=1.0))
     # nx not a power of two: the Bluestein x-transform (even, odd, and the largest length)
-    yield steps(W.advection_upwind_be(nx=100, nt=7), 0.6, 0.6)
+    yield steps(W.advection_upwind_be(nx=100, nt=8), 0.6, 0.6)
     yield steps(W.viscous_burgers(nx=257, nt=9, T=1.0, nu=0.01), 0.35, 0.35)
     yield steps(W.advection_upwind_be(nx=4095, nt=5).replace(time="bdf2"), 0.4, 0.4)
 
