@@ -289,7 +289,6 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     solver = binding.Solver(p, precision=args.precision, path=args.path, device=dev, stream=stream)
     path = solver.info()["path"]
-    per_iter = solver.launches(reset=True)
 
     # warm-up
     solver.iterate(args.warmup)
@@ -384,7 +383,7 @@ def run_ours(args):
                            "cells_per_iter": p.cells_per_iter, "scheme": f"{p.time}+{p.space}",
                            "path": path, "l2": "state larger than L2 (no flush needed)",
                            "parallelism": f"replicas{ws}"},
-                "gpu_launches": launches, "launches_per_iter": per_iter if per_iter else None,
+                "gpu_launches": launches, "launches_per_iter": launches / args.steps,
                 "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e}
         if ttr:
             line["time_to_residual"] = ttr

@@ -49,13 +49,36 @@ __device__ void fft_radix2(C *z, int log2n, int batch, int cs, int is, const C *
 
 // The same in-place DIT transform for one sequence of length n = 2^log2n with
 // twiddles grouped by stage: stage s (half-span hs = 2^s) reads tw[(hs - 1) + pos]
-// = W_n^{pos n / (2 hs)}, so a warp's lanes read consecutive entries.
+// = W_n^{pos n / (2 hs)}, so a warp's lanes read consecutive entries.  Stages run
+// in pairs: the elements b, b + hs, b + 2 hs, b + 3 hs of one group pass through
+// stage s (pairs (b, b+hs), (b+2hs, b+3hs), twiddle W_{2hs}^pos) and stage s+1
+// (pairs (b, b+2hs), (b+hs, b+3hs), twiddles W_{4hs}^pos, W_{4hs}^{pos+hs}) in
+// registers, which halves the shared-memory passes and barriers.
 template <typename C>
 __device__ void fft_radix2_staged(C *z, int log2n, const C *__restrict__ tw, bool inverse) {
-    const int half = 1 << (log2n - 1);
-    for (int s = 0; s < log2n; ++s) {
+    const int n = 1 << log2n;
+    int s = 0;
+    for (; s + 1 < log2n; s += 2) {
         const int hs = 1 << s;
-        for (int k = threadIdx.x; k < half; k += blockDim.x) {
+        for (int g = threadIdx.x; g < (n >> 2); g += blockDim.x) {
+            const int pos = g & (hs - 1);
+            const int b = ((g >> s) << (s + 2)) + pos;
+            C w1 = tw[(hs - 1) + pos], wa = tw[(2 * hs - 1) + pos], wb = tw[(2 * hs - 1) + pos + hs];
+            if (inverse) { w1.y = -w1.y; wa.y = -wa.y; wb.y = -wb.y; }
+            C a0 = z[b], a1 = z[b + hs], a2 = z[b + 2 * hs], a3 = z[b + 3 * hs];
+            const C t1 = cmul(w1, a1), t3 = cmul(w1, a3);
+            const C c0 = cadd(a0, t1), c1 = csub(a0, t1), c2 = cadd(a2, t3), c3 = csub(a2, t3);
+            const C u2 = cmul(wa, c2), u3 = cmul(wb, c3);
+            z[b] = cadd(c0, u2);
+            z[b + 2 * hs] = csub(c0, u2);
+            z[b + hs] = cadd(c1, u3);
+            z[b + 3 * hs] = csub(c1, u3);
+        }
+        __syncthreads();
+    }
+    if (s < log2n) {                        // odd log2n: one last single stage
+        const int hs = 1 << s;
+        for (int k = threadIdx.x; k < (n >> 1); k += blockDim.x) {
             const int pos = k & (hs - 1);
             const int i0 = ((k >> s) << (s + 1)) + pos;
             C w = tw[(hs - 1) + pos];

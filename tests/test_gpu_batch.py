@@ -99,8 +99,7 @@ def test_batch_isolates_a_diverging_instance(B):
 
 def test_batch_of_256_sampled(B):
     """The 256-instance workload (float32): a few iterations, then four instances
-    (largest, smallest, median, smallest advection) against lone runs, bit for bit,
-    and one against the oracle."""
+    (largest, smallest, median, smallest advection) against lone runs, bit for bit."""
     probs = W.batch_instances()
     with B.Batch(probs, precision="fp32") as bt:
         bt.iterate(5)
@@ -114,11 +113,28 @@ def test_batch_of_256_sampled(B):
         with B.Solver(probs[i], precision="fp32", path="plain") as s:
             s.iterate(5)
             assert np.array_equal(s.get_host("u"), got[i]), probs[i].name
-    # the smallest linear-advection instance against the oracle (float32 bound; some
-    # Burgers instances' iterates grow under the batch's fixed step sizes, which makes
-    # float32 and float64 drift apart without saying anything about the kernels)
-    i = small_adv
-    st = opdhg.initial_state(probs[i])
-    for _ in range(5):
-        opdhg.step(probs[i], st)
-    assert np.max(np.abs(got[i] - st["u"])) <= 1e-4 * np.max(np.abs(st["u"])), probs[i].name
+
+
+def test_batch_instances_fp64_vs_oracle(B):
+    """Instances drawn from the 256-instance distribution (the smallest advection and
+    the smallest Burgers one, both with Bluestein lengths), batched in float64: 5
+    iterations equal the oracle's within 1e-9.  These long-horizon instances (T up to
+    ~12, CFL up to 8) lose digits to cancellation in J^T phit, whose low-frequency part
+    the preconditioner makes large: in the oracle itself a 1e-15 relative change of u0
+    moves u by 3e-11 relative after 5 iterations (advection 369 x 107), so rounding
+    order alone accounts for differences of that size; in float32 the same cancellation
+    costs about three digits, which is why the oracle comparison is made in float64 (the
+    float32 batch is checked bit for bit against lone float32 runs above)."""
+    probs = W.batch_instances()
+    cells = np.array([p.ndof * p.nt for p in probs])
+    pick = [min((i for i, p in enumerate(probs) if p.space == sp), key=lambda i: cells[i])
+            for sp in ("fd_upwind", "fd_lf")]
+    sub = [probs[i] for i in pick]
+    with B.Batch(sub, precision="fp64") as bt:
+        bt.iterate(5)
+        got = [bt.instance(i).get_host("u") for i in range(len(sub))]
+    for p, u in zip(sub, got):
+        st = opdhg.initial_state(p)
+        for _ in range(5):
+            opdhg.step(p, st)
+        assert np.max(np.abs(u - st["u"])) <= 1e-9 * np.max(np.abs(st["u"])), p.name
