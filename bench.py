@@ -300,7 +300,7 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk_path = os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+    clk_path = args.clock_log
     with ClockSampler(gpu_index(local), clk_path) as clk:
         start.record(stream)
         solver.iterate(args.steps)
@@ -479,6 +479,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch leg")
+    ap.add_argument("--clock-log", default=None, help="also write the raw nvidia-smi clock samples to this CSV")
     ap.add_argument("--ttr", default="advection,heat,transport2d",
                     help="comma-separated workloads for the time-to-residual comparison ('' = skip)")
     args = ap.parse_args()
