@@ -20,8 +20,15 @@ Modules (each function cites the passage of the paper it follows):
 * ``newton``    -- the definition of the discrete solution: the implicit scheme
                    solved time step by time step with Newton's method.
 * ``dg_exact``  -- exact-rational DG assembly (Sec. 3.2.2, 3.2.3, Appendix A).
+* ``variants``  -- Algorithm 2 (refinement of the time mesh, Sec. 3.4) and
+                   Algorithm 3 (one time step at a time, Sec. 3.5).
+* ``adjoint``   -- gradients of a terminal objective through the scheme: the
+                   sequential discrete adjoint and Algorithm 1 on the problem
+                   linearised at the solution.
 
 Pins (the tests that tie this oracle to something other than itself) live in
-``tests/test_oracle_*.py``.  Parity unpinned: the nonlinear iteration counts of
-Sec. 4.3 (only the converged u is pinned there, through ``newton``).
+``tests/test_oracle_*.py``: printed matrices (Eq. 3.5, A.1), Table 1, Table 2's
+errors, the iteration counts of Sec. 4.3 and Table 3 (within 10%, 15% and 5%: counts
+depend on step-size readings, so these pins are approximate), closed forms, the
+proposition of Sec. 2.3, dense solves, finite differences of Newton solves.
 """
