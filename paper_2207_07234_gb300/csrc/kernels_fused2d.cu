@@ -150,11 +150,25 @@ __global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Param
                 const float rgt = row[x4 == V - 1 ? 0 : 4 * x4 + 4];
                 const float pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
                 const float pv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
+                // transposed stencil per direction (multipliers m, p, q at j-1, j, j+1):
+                //   LF: (f'(u) (m - q) + a (2p - m - q)) / 2h;  upwind: f'(u) (p - q) / h;
+                //   viscous: -nu (q - 2p + m) / h^2
+                const bool lf = P.space != FD_UPWIND;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    float ge = g[e] + cn * pr[e + 1];
-                    ge += fd_dir_T(P, cv[e], pr[e], pr[e + 1], pr[e + 2], P.inv_hx) +
-                          fd_dir_T(P, cv[e], pv[e], pr[e + 1], dv[e], P.inv_hy);
+                    const float p0 = pr[e + 1], df = dflux(P, cv[e]);
+                    const float mx = pr[e], qx = pr[e + 2], my = pv[e], qy = dv[e];
+                    float tx, ty;
+                    if (lf) {
+                        tx = 0.5f * (df * (mx - qx) + P.lf_a * (2.f * p0 - mx - qx));
+                        ty = 0.5f * (df * (my - qy) + P.lf_a * (2.f * p0 - my - qy));
+                    } else {
+                        tx = df * (p0 - qx);
+                        ty = df * (p0 - qy);
+                    }
+                    float ge = g[e] + cn * p0 + tx * P.inv_hx + ty * P.inv_hy;
+                    if (P.nu != 0.f)
+                        ge -= P.nu * ((qx - 2.f * p0 + mx) * P.inv_hx * P.inv_hx + (qy - 2.f * p0 + my) * P.inv_hy * P.inv_hy);
                     un[e] = cv[e] - P.tau_u * ge;
                 }
             } else if (P.init == INIT_LAMBDA) {
