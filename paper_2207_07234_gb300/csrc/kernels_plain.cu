@@ -462,13 +462,15 @@ __device__ __forceinline__ void block_sum6(double acc[6], double *out) {
     }
 }
 
-// One thread accumulates many units of one slice (grid-stride over units); the
-// products of a unit are added in T and folded into double accumulators every
-// unit, so float32 fields lose at most the rounding of a handful of terms.
-template <typename T>
+// One thread accumulates many units of one slice (grid-stride over units) into
+// acc (type A).  check_block folds float32 partial sums of at most 16 units into
+// float64 accumulators (GB300's float64 adds would otherwise bound this kernel), so
+// each partial carries a relative rounding error below 16 x 2^-24 ~ 1e-6; float64
+// fields accumulate in float64 throughout.
+template <typename T, typename A>
 __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restrict__ u, const T *__restrict__ phi,
                                            const T *__restrict__ lam, const T *__restrict__ u0, int l, int64_t unit,
-                                           double acc[6]) {
+                                           A acc[6]) {
     const int64_t S = P.S;
     if (is_dg(P.space)) {
         const int N = P.nx, nm = P.lines;
@@ -481,8 +483,8 @@ __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restri
             dgx_D(P, c, lf, rg, d);
             for (int m = 0; m < nm; ++m) {
                 double r = (double)(d[m] + time_R(P, u + m * N + k, S, l));
-                acc[0] += r * r;
-                acc[2] += (double)phi[(int64_t)l * S + m * N + k] * r;
+                acc[0] += (A)(r * r);
+                acc[2] += (A)((double)phi[(int64_t)l * S + m * N + k] * r);
             }
         }
         T c[3] = {0, 0, 0};
@@ -494,16 +496,16 @@ __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restri
             dgx_DT(P, c, pl, pc, pr, d);
             for (int m = 0; m < nm; ++m) {
                 double g = (double)(d[m] + time_T(P, phi + m * N + k, S, l));
-                acc[1] += g * g;
+                acc[1] += (A)(g * g);
             }
         } else {
             for (int m = 0; m < nm; ++m) {
-                double r0 = (double)c[m] - (double)u0[m * N + k];
-                acc[3] += r0 * r0;
+                const double r0 = (double)c[m] - (double)u0[m * N + k];
+                acc[3] += (A)(r0 * r0);
                 if (P.init == INIT_LAMBDA) {
-                    double g0 = (double)P.ht * (double)time_T(P, phi + m * N + k, S, 0) + (double)lam[m * N + k];
-                    acc[4] += g0 * g0;
-                    acc[5] += (double)lam[m * N + k] * r0;
+                    const double g0 = (double)P.ht * (double)time_T(P, phi + m * N + k, S, 0) + (double)lam[m * N + k];
+                    acc[4] += (A)(g0 * g0);
+                    acc[5] += (A)((double)lam[m * N + k] * r0);
                 }
             }
         }
@@ -515,22 +517,22 @@ __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restri
         const T *un = u + (int64_t)(l + 1) * S;
         const T d = P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 1) * S, un, y, x) : fd_D(P, un, y, x);
         const T r = d + time_R(P, u + i, S, l);
-        acc[0] += (double)(r * r);
-        acc[2] += (double)(phi[(int64_t)l * S + i] * r);
+        acc[0] += (A)(r * r);
+        acc[2] += (A)(phi[(int64_t)l * S + i] * r);
     }
     const T c = u[(int64_t)l * S + i];
     if (l >= 1) {
         const T cl = P.ulin ? P.ulin[(int64_t)l * S + i] : c;
         T g = fd_DT(P, cl, phi + (int64_t)(l - 1) * S, y, x) + time_T(P, phi + i, S, l);
         if (l == P.nt && P.tshift) g += T(2) * (c - P.tshift[i]) * P.inv_ht;
-        acc[1] += (double)(g * g);
+        acc[1] += (A)(g * g);
     } else {
-        double r0 = (double)c - (double)u0[i];
-        acc[3] += r0 * r0;
+        const double r0 = (double)c - (double)u0[i];
+        acc[3] += (A)(r0 * r0);
         if (P.init == INIT_LAMBDA) {
-            double g0 = (double)P.ht * (double)time_T(P, phi + i, S, 0) + (double)lam[i];
-            acc[4] += g0 * g0;
-            acc[5] += (double)lam[i] * r0;
+            const double g0 = (double)P.ht * (double)time_T(P, phi + i, S, 0) + (double)lam[i];
+            acc[4] += (A)(g0 * g0);
+            acc[5] += (A)((double)lam[i] * r0);
         }
     }
 }
@@ -542,8 +544,21 @@ __device__ __forceinline__ void check_block(const Params<T> &P, const T *__restr
                                             double *__restrict__ partials, int bx, int l, int gx) {
     const int64_t units = is_dg(P.space) ? P.nx : P.S;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t unit = (int64_t)bx * blockDim.x + threadIdx.x; unit < units; unit += (int64_t)gx * blockDim.x)
-        check_unit(P, u, phi, lam, u0, l, unit, acc);
+    if constexpr (sizeof(T) == 4) {
+        float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int cnt = 0;
+        for (int64_t unit = (int64_t)bx * blockDim.x + threadIdx.x; unit < units; unit += (int64_t)gx * blockDim.x) {
+            check_unit<T, float>(P, u, phi, lam, u0, l, unit, part);
+            if (++cnt == 16) {
+                for (int k = 0; k < 6; ++k) { acc[k] += (double)part[k]; part[k] = 0.f; }
+                cnt = 0;
+            }
+        }
+        for (int k = 0; k < 6; ++k) acc[k] += (double)part[k];
+    } else {
+        for (int64_t unit = (int64_t)bx * blockDim.x + threadIdx.x; unit < units; unit += (int64_t)gx * blockDim.x)
+            check_unit<T, double>(P, u, phi, lam, u0, l, unit, acc);
+    }
     block_sum6(acc, partials + ((int64_t)l * gx + bx) * 6);
 }
 
