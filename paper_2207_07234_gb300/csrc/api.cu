@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <complex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pdhg.h"
@@ -425,6 +426,24 @@ static std::vector<float> staged_twiddles(int64_t N) {
     return t;
 }
 
+// Run fn(r0, r1) over [0, nrows) in contiguous chunks on up to 16 host threads when
+// the work (total elements) is large; inline otherwise.  Results do not depend on
+// the split: every element is computed the same way.
+template <typename Fn>
+static void parallel_rows(int64_t nrows, int64_t total, Fn fn) {
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::min<unsigned>(nt == 0 ? 1 : nt, 16);
+    if (total < (int64_t(1) << 16) || nt <= 1 || nrows < 2) { fn(0, nrows); return; }
+    nt = (unsigned)std::min<int64_t>(nt, nrows);
+    std::vector<std::thread> pool;
+    const int64_t chunk = (nrows + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; ++t) {
+        const int64_t r0 = t * chunk, r1 = std::min<int64_t>(nrows, r0 + chunk);
+        if (r0 < r1) pool.emplace_back(fn, r0, r1);
+    }
+    for (auto &th : pool) th.join();
+}
+
 template <typename T>
 static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pdhg_grid *g, double lf_a) {
     const Geom &G = h->G;
@@ -489,12 +508,21 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
         }
         CK(cudaMemcpy(F<T>(h, h->L.V), V.data(), V.size() * sizeof(T), cudaMemcpyHostToDevice));
     } else {
-        for (int64_t ky = 0; ky < G.lines; ++ky)
-            for (int64_t kx = 0; kx < G.nkx; ++kx) {
-                double L = symbol_L(kx, G.nx, hx) + (G.dims == 2 ? symbol_L(ky, G.ny, hy) : 0.0);
-                double kappa = p->c * p->c * L + p->gamma_hat * p->gamma_hat * L * L;
-                th[ky * G.nkx + kx] = (T)theta_of(kappa * ht * ht);
-            }
+        // L = L_x(kx) + L_y(ky) is separable: tabulate both, then one sqrt and asinh per
+        // mode, rows of ky spread over host threads (2D grids have up to 1M modes)
+        std::vector<double> Lx(G.nkx), Ly(G.lines, 0.0);
+        for (int64_t kx = 0; kx < G.nkx; ++kx) Lx[kx] = symbol_L(kx, G.nx, hx);
+        if (G.dims == 2)
+            for (int64_t ky = 0; ky < G.lines; ++ky) Ly[ky] = symbol_L(ky, G.ny, hy);
+        const double c2 = p->c * p->c, g2 = p->gamma_hat * p->gamma_hat;
+        auto rows = [&](int64_t y0, int64_t y1) {
+            for (int64_t ky = y0; ky < y1; ++ky)
+                for (int64_t kx = 0; kx < G.nkx; ++kx) {
+                    const double L = Lx[kx] + Ly[ky];
+                    th[ky * G.nkx + kx] = (T)theta_of((c2 * L + g2 * L * L) * ht * ht);
+                }
+        };
+        parallel_rows(G.lines, G.lines * G.nkx, rows);
     }
     CK(cudaMemcpy(F<T>(h, h->L.theta), th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
     if (G.blu_log2L) {
@@ -510,8 +538,10 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
         Fused2D &f = h->fused;
         fused2d_layout(&f, h->ws + h->L.fused, G.nx, G.ny, G.nt);
         std::vector<float> tm = staged_twiddles(G.nx / 2), ty = staged_twiddles(G.ny), tt(G.nkx * G.ny);
-        for (int64_t ky = 0; ky < G.ny; ++ky)
-            for (int64_t kx = 0; kx < G.nkx; ++kx) tt[kx * G.ny + ky] = (float)th[ky * G.nkx + kx];
+        parallel_rows(G.nkx, G.nkx * G.ny, [&](int64_t x0, int64_t x1) {
+            for (int64_t kx = x0; kx < x1; ++kx)
+                for (int64_t ky = 0; ky < G.ny; ++ky) tt[kx * G.ny + ky] = (float)th[ky * G.nkx + kx];
+        });
         CK(cudaMemcpy(f.twM, tm.data(), tm.size() * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(f.twY, ty.data(), ty.size() * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(f.thetaT, tt.data(), tt.size() * 4, cudaMemcpyHostToDevice));
@@ -573,6 +603,19 @@ static double lf_constant(const pdhg_problem *prob, const Geom &G) {
     return lf_a;
 }
 
+template <typename T>
+static pdhg_status initial_res_sum(pdhg_handle *h, double *a0) {
+    const Params<T> &P = params_of<T>(h);
+    cudaError_t e = launch_check<T>(P, F<T>(h, h->u_off), F<T>(h, h->L.phi), F<T>(h, h->L.lam), F<T>(h, h->L.u0),
+                                    F<double>(h, h->L.partials), F<double>(h, h->L.scal), h->stream, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "initial residual");
+    double acc[6];
+    CK(cudaMemcpyAsync(acc, h->ws + h->L.scal, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *a0 = acc[0];
+    return PDHG_OK;
+}
+
 extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
                                    void *workspace, size_t bytes, void *stream, pdhg_handle **out) {
     Geom G;
@@ -608,10 +651,13 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
                                      F<float>(h, L.theta));
         if (e != cudaSuccess) st = cuda_fail(e, "fused2d_init");
     }
-    double r[4];
-    if (st == PDHG_OK) st = (G.prec == PDHG_FP64) ? compute_res<double>(h, r) : compute_res<float>(h, r);
+    // ||A(u_init)||: at [u0, 0, 0] every slice's residual is D(u0) (the time differences
+    // vanish) and the initial row and the phi, lambda terms are zero, so slice 0's sum
+    // times nt gives it without a pass over all slices
+    double a0 = 0.0;
+    if (st == PDHG_OK) st = (G.prec == PDHG_FP64) ? initial_res_sum<double>(h, &a0) : initial_res_sum<float>(h, &a0);
     if (st != PDHG_OK) { delete h; return st; }
-    h->res_init = r[0];
+    h->res_init = std::sqrt(h->ht * h->wx * (double)G.nt * a0);
     h->launches = 0;
     *out = h;
     return PDHG_OK;

@@ -652,8 +652,8 @@ int64_t check_blocks(const Params<T> &P) {
 
 template <typename T>
 cudaError_t launch_check(const Params<T> &P, const T *u, const T *phi, const T *lam, const T *u0,
-                         double *partials, double *out, cudaStream_t s) {
-    dim3 grid((unsigned)check_grid_x(P), (unsigned)(P.nt + 1));
+                         double *partials, double *out, cudaStream_t s, int slices) {
+    dim3 grid((unsigned)check_grid_x(P), (unsigned)(slices > 0 ? slices : P.nt + 1));
     k_check<T><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -792,7 +792,7 @@ cudaError_t init_plain_attributes() {
     template int64_t check_blocks<T>(const Params<T> &);                                                      \
     template cudaError_t init_plain_attributes<T>();                                                      \
     template cudaError_t launch_check<T>(const Params<T> &, const T *, const T *, const T *, const T *, double *, \
-                                         double *, cudaStream_t);                                             \
+                                         double *, cudaStream_t, int);                                        \
     template cudaError_t launch_phi_lap<T>(const Params<T> &, const T *, const T *, double *, double *, cudaStream_t); \
     template cudaError_t launch_batch<T>(int, const BatchInst<T> *, const BatchEntry *, int64_t, size_t,        \
                                          const int32_t *, double *, double *, cudaStream_t);

@@ -26,8 +26,10 @@ template <typename T> int64_t check_blocks(const Params<T> &P);
 template <typename T>
 cudaError_t launch_phi_lap(const Params<T> &P, const T *u, const T *phi, double *partials, double *out, cudaStream_t s);
 template <typename T>
+// Residual sums (Eq. 2.12) into out[0..5]: slice rows 0..nt (slices = 0), or only
+// the first `slices` rows.
 cudaError_t launch_check(const Params<T> &P, const T *u, const T *phi, const T *lam, const T *u0, double *partials,
-                         double *out, cudaStream_t s);
+                         double *out, cudaStream_t s, int slices = 0);
 
 // ---- batched launches (many 1D instances per launch) ----
 // One instance: its parameters and device arrays (those of an ordinary handle).

@@ -198,6 +198,22 @@ def test_relative_stop_and_nonfinite(B):
         assert e.value.status in (-4, -5)
 
 
+@pytest.mark.parametrize("p", [steps(W.advection_upwind_be(nx=64, nt=8).replace(time="bdf2"), 0.4, 0.4),
+                               W.heat_table1(64, 16), W.traffic_dg_p1(ncell=32, nt=6)],
+                         ids=lambda p: p.name)
+def test_relative_scale_matches_full_initial_residual(B, p):
+    """The relative stopping scale ||A(u_init)|| is taken at create from one slice
+    (at [u0, 0, 0] every slice's residual is D(u0)); iterating to a relative tolerance
+    stops at the same check as the oracle, whose scale is the full residual."""
+    with B.Solver(p, precision="fp64", path="plain") as s:
+        r_full = s.residual()[0]                       # full check at the initial state
+        it = s.iterate(20000, tol=1e-6, check_every=10, relative=True)
+    r0 = opdhg.residual_norms(p, opdhg.initial_state(p))[0]
+    assert abs(r_full - r0) <= 1e-12 * r0
+    st, it_o, _ = opdhg.solve(p, max_iters=20000, tol=1e-6, check_every=10, relative=True)
+    assert it == it_o, (it, it_o)
+
+
 def test_table2_from_gpu_pdhg(B):
     """Table 2 (DG P1 nodal + BDF2 linear transport) from the GPU's converged PDHG
     iterates: the L2 errors round to the printed 0.1296, 0.0372, 0.0096."""
