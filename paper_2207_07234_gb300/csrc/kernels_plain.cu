@@ -75,7 +75,7 @@ __device__ __forceinline__ void primal_block(const Params<T> &P, T *__restrict__
     }
     const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
     if (i >= S) return;
-    const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
+    const int ii = (int)i, y = ii / P.nx, x = ii - y * P.nx;     // one slice < 2^31 dofs: 32-bit division
     T *ul = u + (int64_t)l * S;
     T c = ul[i];
     T g = time_T(P, phit + i, S, l);
@@ -512,7 +512,7 @@ __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restri
         return;
     }
     const int64_t i = unit;
-    const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
+    const int ii = (int)i, y = ii / P.nx, x = ii - y * P.nx;     // one slice < 2^31 dofs: 32-bit division
     if (l < P.nt) {
         const T *un = u + (int64_t)(l + 1) * S;
         const T d = P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 1) * S, un, y, x) : fd_D(P, un, y, x);
@@ -547,6 +547,7 @@ __device__ __forceinline__ void check_block(const Params<T> &P, const T *__restr
     if constexpr (sizeof(T) == 4) {
         float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
+#pragma unroll 4
         for (int64_t unit = (int64_t)bx * blockDim.x + threadIdx.x; unit < units; unit += (int64_t)gx * blockDim.x) {
             check_unit<T, float>(P, u, phi, lam, u0, l, unit, part);
             if (++cnt == 16) {
@@ -556,6 +557,7 @@ __device__ __forceinline__ void check_block(const Params<T> &P, const T *__restr
         }
         for (int k = 0; k < 6; ++k) acc[k] += (double)part[k];
     } else {
+#pragma unroll 4
         for (int64_t unit = (int64_t)bx * blockDim.x + threadIdx.x; unit < units; unit += (int64_t)gx * blockDim.x)
             check_unit<T, double>(P, u, phi, lam, u0, l, unit, acc);
     }
@@ -653,7 +655,12 @@ int64_t check_blocks(const Params<T> &P) {
 template <typename T>
 cudaError_t launch_check(const Params<T> &P, const T *u, const T *phi, const T *lam, const T *u0,
                          double *partials, double *out, cudaStream_t s, int slices) {
-    dim3 grid((unsigned)check_grid_x(P), (unsigned)(slices > 0 ? slices : P.nt + 1));
+    // blocks per slice row: the usual check_grid_x; a launch over fewer rows may use
+    // the blocks (and partial records) of the rows it skips
+    const int rows = slices > 0 ? slices : P.nt + 1;
+    const int64_t units = is_dg(P.space) ? P.nx : P.S;
+    const int64_t gx = std::min<int64_t>(check_grid_x(P) * (int64_t)(P.nt + 1) / rows, (units + 255) / 256);
+    dim3 grid((unsigned)std::max<int64_t>(gx, check_grid_x(P)), (unsigned)rows);
     k_check<T><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -671,7 +678,7 @@ __global__ void __launch_bounds__(256) k_phi_lap(Params<T> P, const T *__restric
     const T *ul = u + (int64_t)(l + 1) * S;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / P.nx), x = (int)(i - (int64_t)y * P.nx);
+        const int ii = (int)i, y = ii / P.nx, x = ii - y * P.nx;     // one slice < 2^31 dofs: 32-bit division
         const int64_t r = (int64_t)y * P.nx;
         const T c = ul[i];
         T lap = (ul[r + wrapp(x, P.nx)] - T(2) * c + ul[r + wrapm(x, P.nx)]) * P.inv_hx * P.inv_hx;
