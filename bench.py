@@ -432,13 +432,15 @@ def time_to_residual(binding, p, tol=1e-6, check_every=50, max_iters=20000, devi
     """Wall time and iterations to relative Res <= tol for the float32 default path and
     the plain float64 GPU path (the comparator named by the metric).  Iterates in chunks
     of 20 checks; a residual that has not dropped by 5% over three chunks is reported as
-    the precision's floor instead of running to max_iters."""
+    the precision's floor instead of running to max_iters.  A third leg times the
+    mixed-precision solve (float32, then float64 from the widened state)."""
     import torch
     out = {"workload": p.name, "tol": tol, "relative_to": "||A(u_init)||", "check_every": check_every}
     chunk = 20 * check_every
     for label, prec, path in (("fp32", "fp32", "auto"), ("fp64_plain", "fp64", "plain")):
         s = binding.Solver(p, precision=prec, path=path, device=device, stream=stream)
         r0 = float(s.residual()[0])
+        scale0 = r0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         status, it, hist = "max_iters", 0, []
@@ -464,6 +466,24 @@ def time_to_residual(binding, p, tol=1e-6, check_every=50, max_iters=20000, devi
         s.close()
         del s
         torch.cuda.empty_cache()
+    # float32 until the tolerance or its floor, then float64 (pdhg_solve_mixed); the
+    # creation of both handles is inside the timed call
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    try:
+        s, its = binding.solve_mixed(p, tol=tol, relative=True, check_every=check_every, max_iters=max_iters,
+                                     device=device, stream=stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        r = s.residual()
+        r0 = scale0
+        status = "converged" if r[0] <= tol * r0 and r[1] <= tol * r0 else "max_iters"
+        out["mixed"] = {"seconds": dt, "iterations": its, "status": status, "path": "float32 then float64 plain",
+                        "rel_res": [float(r[0]) / r0, float(r[1]) / r0]}
+        s.close()
+    except binding.PdhgError as err:
+        out["mixed"] = {"status": f"stopped: {binding.STATUS.get(err.status)}"}
+    torch.cuda.empty_cache()
     return out
 
 

@@ -276,6 +276,31 @@ pdhg_status pdhg_solve_gradient(const pdhg_problem *prob, const pdhg_grid *grid,
                                 double *loss, double *du0, double *dnu, int64_t *iters);
 
 /*
+ * Mixed-precision solve (an addition of this library: the paper states no
+ * precision).  Algorithm 1 runs in float32 -- on the fused path where
+ * pdhg_create would choose it, scheme->path as given -- until both entries of
+ * Res are <= tol (absolute, or relative to ||A(u_init)||), checked every
+ * check_every iterations, or until the larger entry has not fallen by 5% over
+ * the last three checks (float32's rounding floor); then the state (u, phi,
+ * phit, lambda, lamt) is widened to float64 on the device and Algorithm 1 goes
+ * on in float64 on the plain path to tol, within max_iters iterations in all.
+ * scheme->precision is ignored.
+ *
+ * workspace: device, caller-owned, 256-byte aligned, size from
+ * pdhg_mixed_workspace_size (a float32 and a float64 handle's regions).  The
+ * returned handle is the float64 one, in the workspace; use and destroy it like
+ * one from pdhg_create.  iters (host, 2 entries, may be NULL): float32 and
+ * float64 iterations.  Errors as pdhg_create / pdhg_iterate; on an error no
+ * handle is returned.
+ */
+pdhg_status pdhg_mixed_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                      const pdhg_scheme *scheme, size_t *bytes);
+pdhg_status pdhg_solve_mixed(const pdhg_problem *prob, const pdhg_grid *grid,
+                             const pdhg_scheme *scheme, double tol, int32_t relative,
+                             int32_t check_every, int64_t max_iters, void *workspace, size_t bytes,
+                             void *stream, pdhg_handle **out, int64_t iters[2]);
+
+/*
  * Batches of independent 1D instances (an addition of this library: the paper
  * solves one problem at a time).  Each instance is an ordinary problem (any 1D
  * scheme of this library, its own nx, nt, flux, time scheme and step sizes;

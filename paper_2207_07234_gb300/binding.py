@@ -34,7 +34,8 @@ EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_strea
            "pdhg_set_profiling", "pdhg_stage_times", "pdhg_set_graphs", "pdhg_last_error",
            "pdhg_refine_workspace_size",
            "pdhg_solve_refine", "pdhg_one_step_workspace_size", "pdhg_solve_one_step",
-           "pdhg_gradient_workspace_size", "pdhg_solve_gradient", "pdhg_batch_workspace_size",
+           "pdhg_gradient_workspace_size", "pdhg_solve_gradient", "pdhg_mixed_workspace_size",
+           "pdhg_solve_mixed", "pdhg_batch_workspace_size",
            "pdhg_batch_create", "pdhg_batch_destroy", "pdhg_batch_iterate", "pdhg_batch_reset",
            "pdhg_batch_instance", "pdhg_batch_launch_count", "pdhg_residual_noalloc"]
 
@@ -97,6 +98,9 @@ def load(path: str = LIB_PATH):
                               vp, ctypes.POINTER(vp), ctypes.POINTER(i64)],
         "pdhg_one_step_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
         "pdhg_gradient_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_mixed_workspace_size": [P, G, S, ctypes.POINTER(ctypes.c_size_t)],
+        "pdhg_solve_mixed": [P, G, S, ctypes.c_double, i32, i32, i64, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp),
+                             ctypes.POINTER(i64)],
         "pdhg_batch_workspace_size": [i32, P, G, S, ctypes.POINTER(ctypes.c_size_t)],
         "pdhg_batch_create": [i32, P, G, S, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "pdhg_batch_destroy": [vp],
@@ -364,6 +368,27 @@ def terminal_loss_fn():
             return grad * du0, grad * dnu, None, None, None
 
     return TerminalLoss
+
+
+def solve_mixed(p, tol=1e-6, relative=True, check_every=50, max_iters=100000, path="auto", device=None,
+                stream=None):
+    """float32 until tol or float32's floor, then float64 to tol (pdhg_solve_mixed).
+    Returns (float64 Solver holding the result, [float32, float64] iterations)."""
+    import torch
+    lib = load()
+    prob, grid, scheme, keep = structs(p, "fp64", path)
+    nbytes = ctypes.c_size_t(0)
+    _check(lib.pdhg_mixed_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                         ctypes.byref(nbytes)))
+    dev = torch.device(device if device is not None else "cuda")
+    ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    h = ctypes.c_void_p()
+    its = (ctypes.c_int64 * 2)()
+    _check(lib.pdhg_solve_mixed(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme), float(tol),
+                                int(bool(relative)), int(check_every), int(max_iters), ctypes.c_void_p(ws.data_ptr()),
+                                nbytes.value, ctypes.c_void_p(s.cuda_stream), ctypes.byref(h), its))
+    return Solver(p, precision="fp64", device=dev, _adopt=(h, ws, s)), list(its)
 
 
 class Batch:

@@ -274,6 +274,7 @@ struct pdhg_handle {
     double ht, wx;
     int64_t iters;
     double res_init;
+    double last_res[4];      // Res at the last check of pdhg_iterate
     int64_t launches;
     bool profiling;
     std::vector<EvRec> recs;
@@ -640,6 +641,7 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
     h->wx = G.dims == 2 ? hx * (grid->ly / (double)grid->ny) : hx;
     h->iters = 0; h->launches = 0; h->profiling = false;
     h->res_norm = 0;
+    for (int k = 0; k < 4; ++k) h->last_res[k] = NAN;
     h->graphs = !G.fused;
     h->gexec = nullptr; h->gstream = nullptr; h->gchunk = 0; h->glaunches = 0;
     h->u_off = L.u;
@@ -791,6 +793,7 @@ static pdhg_status iterate_T(pdhg_handle *h, int64_t max_iters, double tol, int3
                 if (done) *done = n;
                 return fail(PDHG_ERR_DIVERGED, "primal residual grew by more than 1e10");
             }
+            for (int k = 0; k < 4; ++k) h->last_res[k] = r[k];
             if (r[0] <= tol * scale && r[1] <= tol * scale) break;
         }
     }
@@ -1516,5 +1519,96 @@ extern "C" pdhg_status pdhg_set_graphs(pdhg_handle *h, int32_t enable) {
     if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
     graph_drop(h);
     h->graphs = enable != 0 && !h->G.fused;
+    return PDHG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision solve: Algorithm 1 in float32 (the fused path where it applies)
+// until Res reaches tol or stops falling (float32 rounding floor), then the state
+// widened to float64 and the iteration finished on the float64 plain path.  The
+// workspace holds the float32 handle's region, then the float64 one's.
+// ---------------------------------------------------------------------------
+static pdhg_status mixed_schemes(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                 pdhg_scheme *s32, pdhg_scheme *s64, size_t *b32, size_t *b64) {
+    if (!scheme) return fail(PDHG_ERR_INVALID_ARG, "null scheme");
+    *s32 = *scheme;
+    s32->precision = PDHG_FP32;
+    *s64 = *scheme;
+    s64->precision = PDHG_FP64;
+    s64->path = PDHG_PATH_PLAIN;
+    pdhg_status st = pdhg_workspace_size(prob, grid, s32, b32);
+    if (st == PDHG_OK) st = pdhg_workspace_size(prob, grid, s64, b64);
+    return st;
+}
+
+extern "C" pdhg_status pdhg_mixed_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
+                                                 const pdhg_scheme *scheme, size_t *bytes) {
+    if (!bytes) return fail(PDHG_ERR_INVALID_ARG, "bytes is NULL");
+    pdhg_scheme s32, s64;
+    size_t b32, b64;
+    pdhg_status st = mixed_schemes(prob, grid, scheme, &s32, &s64, &b32, &b64);
+    if (st != PDHG_OK) return st;
+    *bytes = align256(b32) + b64;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_solve_mixed(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                        double tol, int32_t relative, int32_t check_every, int64_t max_iters,
+                                        void *workspace, size_t bytes, void *stream, pdhg_handle **out,
+                                        int64_t iters[2]) {
+    if (!out) return fail(PDHG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (iters) iters[0] = iters[1] = 0;
+    pdhg_scheme s32, s64;
+    size_t b32, b64;
+    pdhg_status st = mixed_schemes(prob, grid, scheme, &s32, &s64, &b32, &b64);
+    if (st != PDHG_OK) return st;
+    if (!workspace) return fail(PDHG_ERR_INVALID_ARG, "workspace is NULL");
+    if (bytes < align256(b32) + b64)
+        return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small: need " + std::to_string(align256(b32) + b64));
+    if (check_every < 1 || max_iters < 0 || !(tol >= 0))
+        return fail(PDHG_ERR_INVALID_ARG, "check_every must be >= 1, max_iters >= 0 and tol >= 0");
+    char *ws = (char *)workspace;
+    pdhg_handle *h32 = nullptr, *h64 = nullptr;
+    st = pdhg_create(prob, grid, &s32, ws, b32, stream, &h32);
+    if (st != PDHG_OK) return st;
+    // float32 phase: chunks of check_every iterations; stop at tol, or when the worse
+    // entry of Res has not fallen by 5% over the last three checks (the float32 floor)
+    const double scale = relative ? h32->res_init : 1.0;
+    std::vector<double> hist;
+    int64_t n32 = 0;
+    while (n32 < max_iters) {
+        int64_t done = 0;
+        st = pdhg_iterate(h32, std::min<int64_t>(check_every, max_iters - n32), tol, check_every, relative, &done);
+        n32 += done;
+        if (st != PDHG_OK) break;
+        const double r = std::max(h32->last_res[0], h32->last_res[1]);
+        if (h32->last_res[0] <= tol * scale && h32->last_res[1] <= tol * scale) break;
+        hist.push_back(r);
+        if (hist.size() >= 4 && hist.back() > 0.95 * hist[hist.size() - 4]) break;
+    }
+    if (iters) iters[0] = n32;
+    if (st != PDHG_OK) { pdhg_destroy(h32); return st; }
+    // float64 phase from the widened state
+    st = pdhg_create(prob, grid, &s64, ws + align256(b32), b64, stream, &h64);
+    if (st != PDHG_OK) { pdhg_destroy(h32); return st; }
+    const Geom &G = h32->G;
+    const int64_t S = G.S;
+    struct { size_t src, dst; int64_t n; } parts[5] = {
+        {h32->u_off, h64->u_off, (G.nt + 1) * S}, {h32->L.phi, h64->L.phi, G.nt * S},
+        {h32->L.phit, h64->L.phit, G.nt * S}, {h32->L.lam, h64->L.lam, S}, {h32->L.lamt, h64->L.lamt, S}};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+        e = launch_widen((const float *)(h32->ws + parts[i].src), (double *)(h64->ws + parts[i].dst), parts[i].n,
+                         h64->stream);
+    h64->launches += 5;
+    pdhg_destroy(h32);
+    if (e != cudaSuccess) { pdhg_destroy(h64); return cuda_fail(e, "float32 -> float64 hand-over"); }
+    int64_t n64 = 0;
+    if (max_iters - n32 > 0)
+        st = pdhg_iterate(h64, max_iters - n32, tol, check_every, relative, &n64);
+    if (iters) iters[1] = n64;
+    if (st != PDHG_OK) { pdhg_destroy(h64); return st; }
+    *out = h64;
     return PDHG_OK;
 }

@@ -35,6 +35,18 @@ cudaError_t launch_interp_t(const T *uc, const T *phic, T *uf, T *phif, T *phitf
     return cudaGetLastError();
 }
 
+__global__ void k_widen(const float *__restrict__ src, double *__restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+cudaError_t launch_widen(const float *src, double *dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_widen<<<(unsigned)blocks, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_interp_t<float>(const float *, const float *, float *, float *, float *, int64_t, int64_t,
                                             cudaStream_t);
 template cudaError_t launch_interp_t<double>(const double *, const double *, double *, double *, double *, int64_t,

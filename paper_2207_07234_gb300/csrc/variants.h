@@ -1,4 +1,5 @@
-// variants.h -- device helpers of the drivers of Algorithms 2 and 3 (Sec. 3.4, 3.5).
+// variants.h -- device helpers of the drivers of Algorithms 2 and 3 (Sec. 3.4, 3.5)
+// and of the mixed-precision solve.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -13,5 +14,8 @@ namespace pdhg {
 template <typename T>
 cudaError_t launch_interp_t(const T *uc, const T *phic, T *uf, T *phif, T *phitf, int64_t S, int64_t ntc,
                             cudaStream_t s);
+
+// dst[i] = (double)src[i], i < n (the float32 -> float64 hand-over of a mixed solve)
+cudaError_t launch_widen(const float *src, double *dst, int64_t n, cudaStream_t s);
 
 }  // namespace pdhg
