@@ -1604,9 +1604,10 @@ extern "C" pdhg_status pdhg_solve_mixed(const pdhg_problem *prob, const pdhg_gri
     h64->launches += 5;
     pdhg_destroy(h32);
     if (e != cudaSuccess) { pdhg_destroy(h64); return cuda_fail(e, "float32 -> float64 hand-over"); }
+    // from the float32 state the float64 phase is short: check five times as often
     int64_t n64 = 0;
     if (max_iters - n32 > 0)
-        st = pdhg_iterate(h64, max_iters - n32, tol, check_every, relative, &n64);
+        st = pdhg_iterate(h64, max_iters - n32, tol, std::max<int32_t>(1, check_every / 5), relative, &n64);
     if (iters) iters[1] = n64;
     if (st != PDHG_OK) { pdhg_destroy(h64); return st; }
     *out = h64;
