@@ -178,7 +178,7 @@ def stage_bytes(p, esz: int):
         "fft_y": 2 * spec,                                  # read + write spectrum
         "tsolve": 4 * spec,                                 # forward sweep r/w, backward r/w
         "dual": spec + f + 2 * f,                           # read spectrum, phi; write phi, phit
-        "fused_rows": u + f + u + spec,                     # rows-A: read u, phit; write u; write X
+        "fused_rows": u + spec,                             # rows-R: read u; write X
         "fused_cols": spec + spec + 2 * spec,               # read X, write Zx, spill w/r
     }
 
@@ -187,9 +187,11 @@ KERNEL_SOURCES = {"primal": "kernels_plain.cu", "residual_fft": "kernels_plain.c
                   "fft_y": "kernels_plain.cu", "tsolve": "kernels_plain.cu",
                   "dual": "kernels_plain.cu", "fused_rows": "kernels_fused2d.cu",
                   "fused_cols": "kernels_fused2d.cu"}
+# the fused 2D path runs its own primal and dual kernels
+FUSED_SOURCES = dict(KERNEL_SOURCES, primal="kernels_fused2d.cu", dual="kernels_fused2d.cu")
 
 
-def traffic_for(stage: str, workload_name: str):
+def traffic_for(stage: str, workload_name: str, fused: bool = False):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -200,7 +202,7 @@ def traffic_for(stage: str, workload_name: str):
         ent = db.get(workload_name, {}).get(stage)
         if not ent:
             return None
-        src = os.path.join(ROOT, "paper_2207_07234_gb300", "csrc", KERNEL_SOURCES[stage])
+        src = os.path.join(ROOT, "paper_2207_07234_gb300", "csrc", (FUSED_SOURCES if fused else KERNEL_SOURCES)[stage])
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if ent.get("src_sha") != sha:
             return None
@@ -323,7 +325,7 @@ def run_ours(args):
         ms, n = stages[dom]
         achieved = sb[dom] / (ms / n * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_for(dom, p.name),
+                "frac": achieved / peak, "traffic": traffic_for(dom, p.name, path == "fused"),
                 "algorithmic_bytes_per_launch": sb[dom], "avg_launch_ms": ms / n,
                 "peak_source": peak_kind,
                 "stage_ms_share": {k: round(v[0] / sum(x[0] for x in stages.values()), 4)

@@ -66,7 +66,8 @@ enum { PDHG_STAGE_PRIMAL = 0,      /* primal step + lambda update (Algorithm 1 s
        PDHG_STAGE_TSOLVE = 3,      /* tridiagonal solve in t per Fourier mode */
        PDHG_STAGE_DUAL = 4,        /* inverse x-transform, dual step and extrapolation */
        PDHG_STAGE_CHECK = 5,       /* residual norms (every check_every iterations) */
-       PDHG_STAGE_FUSED_ROWS = 6,  /* fused 2D path: primal + residual + x-FFT (its dual step is STAGE_DUAL) */
+       PDHG_STAGE_FUSED_ROWS = 6,  /* fused 2D path: residual + x-FFT, spectrum stored transposed
+                                      (its primal step is STAGE_PRIMAL, its dual step STAGE_DUAL) */
        PDHG_STAGE_FUSED_COLS = 7,  /* fused 2D path: y-FFT + t-solve + inverse y-FFT */
        PDHG_NUM_STAGES = 8 };
 

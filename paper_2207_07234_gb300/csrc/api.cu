@@ -282,7 +282,7 @@ struct pdhg_handle {
     double stage_ms[PDHG_NUM_STAGES];
     int64_t stage_n[PDHG_NUM_STAGES];
     Fused2D fused;
-    size_t u_off;            // offset of the current u buffer (the fused path alternates two)
+    size_t u_off;            // offset of the current u buffer
     int res_norm;            // 0: space-time norms of Eq. 2.12; 1: per time slice (Sec. 3.5)
     // CUDA graph of `gchunk` iterations plus the residual check (plain path)
     bool graphs;
@@ -694,14 +694,13 @@ static cudaError_t enqueue_iteration(pdhg_handle *h) {
     if (h->G.fused) {
         if constexpr (sizeof(T) == 4) {
             Fused2D *f = &h->fused;
-            float *uin = F<float>(h, h->u_off);
-            float *uout = f->cur == 0 ? f->u2 : F<float>(h, h->L.u);
-            e = stage(h, PDHG_STAGE_FUSED_ROWS, 1, [&] {
-                return fused2d_rowsA(f, h->pf, uin, uout, phit, lam, lamt, u0, s);
+            float *uf = F<float>(h, h->u_off);
+            e = stage(h, PDHG_STAGE_PRIMAL, 1, [&] {
+                return fused2d_primal(h->pf, uf, phit, lam, lamt, u0, s);
             });
             if (e != cudaSuccess) return e;
-            f->cur ^= 1;
-            h->u_off = (size_t)((char *)uout - h->ws);
+            e = stage(h, PDHG_STAGE_FUSED_ROWS, 1, [&] { return fused2d_rowsR(f, h->pf, uf, s); });
+            if (e != cudaSuccess) return e;
             e = stage(h, PDHG_STAGE_FUSED_COLS, 1, [&] { return fused2d_cols(f, h->pf, s); });
             if (e != cudaSuccess) return e;
             return stage(h, PDHG_STAGE_DUAL, 1, [&] { return fused2d_rowsC(f, h->pf, phi, phit, s); });

@@ -1,4 +1,4 @@
-// fused2d.h -- the fused three-kernel iteration for 2D finite differences (float32).
+// fused2d.h -- the fused four-kernel iteration for 2D finite differences (float32).
 #pragma once
 
 #include "common.cuh"
@@ -6,14 +6,12 @@
 namespace pdhg {
 
 struct Fused2D {
-    float *u2;               // second u buffer (rows-A reads one, writes the other)
     float2 *spec;            // spectrum [l][kx][y]: X, then spill, then K_d^{-1} R, in place
     float2 *twM;             // staged Stockham twiddles of length M = nx/2 (stockham.cuh)
     float2 *twY;             // staged Stockham twiddles of length ny
     float *thetaT;           // theta per mode, [kx][ky]
     const float2 *twN;       // W_nx^k, k <= nx/2 (the plain path's table)
-    int cur;                 // 0: current u is the main buffer, 1: u2
-    int tc;                  // time slices per rows-A block
+    int tc;                  // time slices per rows-R block
 };
 
 bool fused2d_supported(int dims, int space, int time, int prec, int64_t nx, int64_t ny, int64_t nt, double nu);
@@ -21,8 +19,9 @@ size_t fused2d_workspace_bytes(int64_t nx, int64_t ny, int64_t nt);
 void fused2d_layout(Fused2D *f, void *ws, int64_t nx, int64_t ny, int64_t nt);
 cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const float *twx, const float *twy,
                          const float *theta);
-cudaError_t fused2d_rowsA(Fused2D *f, const Params<float> &P, const float *uin, float *uout, const float *phit,
-                          float *lam, float *lamt, const float *u0, cudaStream_t s);
+cudaError_t fused2d_primal(const Params<float> &P, float *u, const float *phit, float *lam, float *lamt,
+                           const float *u0, cudaStream_t s);
+cudaError_t fused2d_rowsR(Fused2D *f, const Params<float> &P, const float *u, cudaStream_t s);
 cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s);
 cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float *phit, cudaStream_t s);
 

@@ -1,20 +1,17 @@
 // kernels_fused2d.cu -- the fused iteration of Algorithm 1 (Sec. 3.3) for 2D
-// finite differences in float32: three kernels per iteration.
+// finite differences in float32: four kernels per iteration.
 //
-//   rows-A  (row blocks of H rows x a chunk of time slices, marching in t)
-//           primal step u^n = u^{n-1} - tau_u J(u^{n-1})^T phit^{n-1} on the
-//           block's rows plus one halo row on each side, residual R^{l}(u^n)
-//           on the block's rows, real FFT along x of each residual row, and a
-//           transposed store of the spectrum (layout [l][kx][y]).
+//   primal  (every slice at once, in place) u^n = u^{n-1} - tau_u J(u^{n-1})^T phit^{n-1},
+//           and the u^0 / lambda row.
+//   rows-R  (row blocks of H rows x a chunk of time slices, marching in t)
+//           residual R^{l}(u^n) on the block's rows, real FFT along x of each
+//           residual row, and a transposed store of the spectrum (layout [l][kx][y]).
 //   cols    (one kx column per block, marching in t forward then backward)
 //           complex FFT along y, forward elimination of (T_t + kappa h_t^2)
 //           per mode with the spill written in place, back substitution, and
 //           inverse FFT along y, written in place: the x-spectrum of z.
 //   rows-C  (H rows x one slice per block) inverse real FFT along x, dual
 //           step phi^n = phi^{n-1} + tau_phi z and extrapolation phit = phi^n + tau_phi z.
-//
-// u is double-buffered (rows-A reads u^{n-1} from one buffer and writes u^n
-// to the other) because a block recomputes its neighbours' halo rows.
 #include "fused2d.h"
 #include "fft_smem.cuh"
 #include "stockham.cuh"
@@ -23,43 +20,130 @@ namespace pdhg {
 
 constexpr int FH = 4;          // rows per block in the row kernels
 constexpr int FTHREADS = 256;
-constexpr int ATHREADS = 256;  // rows-A block size
+constexpr int ATHREADS = 256;  // rows-R block size
 
 // ---------------------------------------------------------------------------
-// rows-A
-// Shared memory per block (x fastest):
-//   ph  [2][FH+4][NX]  phit^{m-1}, phit^m rows y0-2 .. y0+FH+1 (a ring over m)
-//   us  [NR][FH+2][NX] u rows y0-1 .. y0+FH: raw u^m, then u^n in place (ring)
-// The FFT input aliases the u slot that the residual no longer needs and the
-// FFT scratch aliases the phit slot of m-1, so BE needs 2 x 112 KB at nx = 1024.
-// The rows of step m+1 are fetched into registers while step m computes (their
-// ring slots are still in use), then stored at the top of step m+1.
+// primal (every slice at once): u^n = u^{n-1} - tau_u J(u^{n-1})^T phit^{n-1}.
+// J^T phit at (m, y, x) needs u only at that point (f'(u) multiplies the
+// transposed stencil of phit^{m-1}), so the update is in place.  A thread owns
+// one float4 of x and RY consecutive rows of one slice and slides a three-row
+// window of phit^{m-1} down them, so each phit^{m-1} value is loaded once per
+// thread column (plus one halo row above and below).
 // ---------------------------------------------------------------------------
+constexpr int PRY = 4;          // rows per thread in the primal kernel
+
 template <int NX>
-__device__ __forceinline__ void load_rows(float *dst, const float *__restrict__ src_slice, int ybase, int nrows,
-                                          int ny, bool zero) {
-    constexpr int V = NX / 4;
-    float4 *d4 = reinterpret_cast<float4 *>(dst);
-    for (int idx = threadIdx.x; idx < nrows * V; idx += blockDim.x) {
-        const int r = idx / V, c = idx - r * V;
-        int y = ybase + r;
+__global__ void __launch_bounds__(256) k_primal2d(Params<float> P, float *__restrict__ u,
+                                                  const float *__restrict__ phit, float *__restrict__ lam,
+                                                  float *__restrict__ lamt, const float *__restrict__ u0) {
+    constexpr int V = NX / 4;                        // blockDim = (min(V, 256), max(256 / V, 1))
+    const int x4 = threadIdx.x + (V > 256 ? blockIdx.z * 256 : 0);
+    const int ya = (blockIdx.x * blockDim.y + threadIdx.y) * PRY;
+    const int m = blockIdx.y;
+    const int ny = P.ny, nt = P.nt;
+    const int64_t S = P.S;
+    float *um = u + (int64_t)m * S;
+    const float cc = m <= nt - 1 ? coef_cur(P, m) : 0.f;
+    const float co = (P.time == BDF2 && m + 1 <= nt - 1) ? coef_old(P, m + 1) : 0.f;
+    if (m == 0) {
+        if (P.init != INIT_LAMBDA) return;              // u^0 pinned to u0
+        // u^0 -= tau_u0 (h_t (J^T phit)^0 + lamt); lambda ascent and extrapolation
+#pragma unroll
+        for (int r = 0; r < PRY; ++r) {
+            const int64_t i = (int64_t)(ya + r) * NX + 4 * x4;
+            const float4 c = *reinterpret_cast<const float4 *>(um + i);
+            const float4 tc = __ldg(reinterpret_cast<const float4 *>(phit + i));
+            float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (co != 0.f) tn = __ldg(reinterpret_cast<const float4 *>(phit + S + i));
+            const float cv[4] = {c.x, c.y, c.z, c.w};
+            const float gv[4] = {cc * tc.x + co * tn.x, cc * tc.y + co * tn.y, cc * tc.z + co * tn.z,
+                                 cc * tc.w + co * tn.w};
+            float un[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                un[e] = cv[e] - P.tau_u0 * (P.ht * gv[e] + lamt[i + e]);
+                const float r0 = un[e] - u0[i + e];
+                const float ln = lam[i + e] + P.tau_lambda * r0;
+                lam[i + e] = ln;
+                lamt[i + e] = ln + P.tau_lambda * r0;
+            }
+            *reinterpret_cast<float4 *>(um + i) = make_float4(un[0], un[1], un[2], un[3]);
+        }
+        return;
+    }
+    const float cn = coef_new(P, m - 1);
+    const float *pp = phit + (int64_t)(m - 1) * S;        // phit^{m-1}: transposed stencil
+    const float *pc = phit + (int64_t)m * S;              // phit^m: pointwise (m <= nt-1)
+    const bool lf = P.space != FD_UPWIND;
+    auto prow = [&](int y) {
         y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-        d4[idx] = zero ? make_float4(0.f, 0.f, 0.f, 0.f)
-                       : __ldg(reinterpret_cast<const float4 *>(src_slice + (int64_t)y * NX) + c);
+        return pp + (int64_t)y * NX;
+    };
+    float4 pu = __ldg(reinterpret_cast<const float4 *>(prow(ya - 1)) + x4);
+    float4 pm = __ldg(reinterpret_cast<const float4 *>(prow(ya)) + x4);
+#pragma unroll
+    for (int r = 0; r < PRY; ++r) {
+        const int y = ya + r;
+        const float *row = pp + (int64_t)y * NX;
+        const float4 pd = __ldg(reinterpret_cast<const float4 *>(prow(y + 1)) + x4);
+        const float lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
+        const float rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
+        const int64_t i = (int64_t)y * NX + 4 * x4;
+        const float4 c = *reinterpret_cast<const float4 *>(um + i);
+        float4 tc = make_float4(0.f, 0.f, 0.f, 0.f), tn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (cc != 0.f) tc = __ldg(reinterpret_cast<const float4 *>(pc + i));
+        if (co != 0.f) tn = __ldg(reinterpret_cast<const float4 *>(pc + S + i));
+        const float pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
+        const float uv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
+        const float cv[4] = {c.x, c.y, c.z, c.w};
+        const float gv[4] = {cc * tc.x + co * tn.x, cc * tc.y + co * tn.y, cc * tc.z + co * tn.z,
+                             cc * tc.w + co * tn.w};
+        float un[4];
+        // transposed stencil per direction (multipliers m, p, q at j-1, j, j+1):
+        //   LF: (f'(u) (m - q) + a (2p - m - q)) / 2h;  upwind: f'(u) (p - q) / h;
+        //   viscous: -nu (q - 2p + m) / h^2
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float p0 = pr[e + 1], df = dflux(P, cv[e]);
+            const float mx = pr[e], qx = pr[e + 2], my = uv[e], qy = dv[e];
+            float tx, ty;
+            if (lf) {
+                tx = 0.5f * (df * (mx - qx) + P.lf_a * (2.f * p0 - mx - qx));
+                ty = 0.5f * (df * (my - qy) + P.lf_a * (2.f * p0 - my - qy));
+            } else {
+                tx = df * (p0 - qx);
+                ty = df * (p0 - qy);
+            }
+            float ge = gv[e] + cn * p0 + tx * P.inv_hx + ty * P.inv_hy;
+            if (P.nu != 0.f)
+                ge -= P.nu * ((qx - 2.f * p0 + mx) * P.inv_hx * P.inv_hx + (qy - 2.f * p0 + my) * P.inv_hy * P.inv_hy);
+            un[e] = cv[e] - P.tau_u * ge;
+        }
+        *reinterpret_cast<float4 *>(um + i) = make_float4(un[0], un[1], un[2], un[3]);
+        pu = pm;
+        pm = pd;
     }
 }
 
-// nrows rows of a slice (y wrapped) into registers: float4 idx = threadIdx.x + j ATHREADS
-// of the [nrows][NX] block (zeros past the block, or everywhere when `zero`).
+// ---------------------------------------------------------------------------
+// rows-R: residual R^l(u^n) and its real FFT along x, spectrum stored
+// transposed ([l][kx][y]).  A block owns FH rows and a chunk of time slices and
+// marches in t over a ring of u rows y0-1 .. y0+FH (the y-stencil needs one
+// halo row each side); the rows of step m+1 are fetched into registers while
+// step m computes.  Shared memory (x fastest):
+//   us  [NR][FH+2][NX]  u^m, u^{m-1} (and u^{m-2} for BDF2)
+//   scr [FH][PN]        FFT scratch
+// The FFT input aliases the u slot that the residual no longer needs, so BE
+// takes 69 KB at nx = 1024: three blocks per SM.
+// ---------------------------------------------------------------------------
 template <int NX, int N>
-__device__ __forceinline__ void fetch_rows(float4 (&reg)[N], const float *__restrict__ src_slice, int ybase,
-                                           int nrows, int ny, bool zero) {
+__device__ __forceinline__ void fetch_rows(float4 (&reg)[N], const float *__restrict__ src_slice, int ybase, int ny) {
     constexpr int V = NX / 4;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const int idx = threadIdx.x + j * ATHREADS;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!zero && idx < nrows * V) {
+        if (idx < (FH + 2) * V) {
             const int r = idx / V, c = idx - r * V;
             int y = ybase + r;
             y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
@@ -70,29 +154,26 @@ __device__ __forceinline__ void fetch_rows(float4 (&reg)[N], const float *__rest
 }
 
 template <int NX, int N>
-__device__ __forceinline__ void store_rows(float *dst, const float4 (&reg)[N], int nrows) {
+__device__ __forceinline__ void store_rows(float *dst, const float4 (&reg)[N]) {
     constexpr int V = NX / 4;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const int idx = threadIdx.x + j * ATHREADS;
-        if (idx < nrows * V) reinterpret_cast<float4 *>(dst)[idx] = reg[j];
+        if (idx < (FH + 2) * V) reinterpret_cast<float4 *>(dst)[idx] = reg[j];
     }
 }
 
 template <int LOG2M, bool BDF2_>
-__global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Params<float> P, const float *__restrict__ u_in,
-                                                    float *__restrict__ u_out, const float *__restrict__ phit,
-                                                    float *__restrict__ lam, float *__restrict__ lamt,
-                                                    const float *__restrict__ u0, float2 *__restrict__ spec,
-                                                    const float2 *__restrict__ twN, const float2 *__restrict__ twM,
-                                                    int Tc) {
+__global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : (BDF2_ ? 2 : 3)))
+k_rowsR(Params<float> P, const float *__restrict__ u, float2 *__restrict__ spec,
+        const float2 *__restrict__ twN, const float2 *__restrict__ twM, int Tc) {
     constexpr int M = 1 << LOG2M, NX = 2 * M;
     constexpr int NR = BDF2_ ? 3 : 2;            // u ring slots
     constexpr int RU = FH + 2;                   // u rows: block rows + one halo row each side
-    constexpr int RP = FH + 4;                   // phit rows: two halo rows each side
+    constexpr int PN = SeqLayout<LOG2M, 2>::PN;  // padded FFT rows (stockham.cuh)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *ph = reinterpret_cast<float *>(smem_raw);            // [2][RP][NX]
-    float *us = ph + 2 * RP * NX;                                // [NR][RU][NX]
+    float *us = reinterpret_cast<float *>(smem_raw);                  // [NR][RU][NX]
+    float2 *scr = reinterpret_cast<float2 *>(us + NR * RU * NX);     // [FH][PN]
 
     const int ny = P.ny, nt = P.nt;
     const int64_t S = P.S;
@@ -100,101 +181,21 @@ __global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Param
     const int l0 = blockIdx.y * Tc;
     const int l1 = min(l0 + Tc, nt);              // residual slices [l0, l1)
     const int mstart = (BDF2_ && l0 > 0) ? l0 - 1 : l0;
-
-    if (mstart >= 1) load_rows<NX>(ph + ((mstart - 1) & 1) * RP * NX, phit + (int64_t)(mstart - 1) * S, y0 - 2, RP, ny, false);
-    constexpr int PPT = (RP * (NX / 4) + ATHREADS - 1) / ATHREADS;   // float4 per thread of one step's rows
     constexpr int UPT = (RU * (NX / 4) + ATHREADS - 1) / ATHREADS;
-    float4 rp[PPT], ru[UPT];
-    fetch_rows<NX>(rp, phit + (int64_t)mstart * S, y0 - 2, RP, ny, mstart >= nt);
-    fetch_rows<NX>(ru, u_in + (int64_t)mstart * S, y0 - 1, RU, ny, false);
+    float4 ru[UPT];
+    fetch_rows<NX>(ru, u + (int64_t)mstart * S, y0 - 1, ny);
     for (int m = mstart; m <= l1; ++m) {
-        float *pc = ph + (m & 1) * RP * NX;              // phit^m
-        float *pp = ph + ((m + 1) & 1) * RP * NX;        // phit^{m-1}
-        float *uc = us + (m % NR) * RU * NX;             // u^m -> u^n
-        // (0) rows of this step (fetched during the previous one); start fetching the next
-        store_rows<NX>(pc, rp, RP);
-        store_rows<NX>(uc, ru, RU);
-        if (m + 1 <= l1) {
-            fetch_rows<NX>(rp, phit + (int64_t)(m + 1) * S, y0 - 2, RP, ny, m + 1 >= nt);
-            fetch_rows<NX>(ru, u_in + (int64_t)(m + 1) * S, y0 - 1, RU, ny, false);
-        }
+        float *uc = us + (m % NR) * RU * NX;             // u^m
+        store_rows<NX>(uc, ru);
+        if (m + 1 <= l1) fetch_rows<NX>(ru, u + (int64_t)(m + 1) * S, y0 - 1, ny);
         __syncthreads();
-        // (1) primal step on slice m, rows y0-1 .. y0+FH (in place in uc), four x per thread
-        const bool own_write = (m >= l0) && (m < l1 || m == nt);
-        const float cn = m >= 1 ? coef_new(P, m - 1) : 0.f;
-        const float cc = m <= nt - 1 ? coef_cur(P, m) : 0.f;
-        const float co = (BDF2_ && m + 1 <= nt - 1) ? coef_old(P, m + 1) : 0.f;
-        constexpr int V = NX / 4;
-        for (int gi = threadIdx.x; gi < RU * V; gi += blockDim.x) {
-            const int r = gi / V, x4 = gi - r * V;
-            const bool own = (r >= 1 && r <= FH);
-            if (m == 0 && !own) continue;                      // slice-0 halo is never read
-            const int q = r + 1;                               // phit row of the same y
-            float4 c = reinterpret_cast<const float4 *>(uc + r * NX)[x4];
-            const float4 tc = reinterpret_cast<const float4 *>(pc + q * NX)[x4];
-            float g[4] = {cc * tc.x, cc * tc.y, cc * tc.z, cc * tc.w};
-            if (BDF2_ && co != 0.f) {
-                int y = y0 - 1 + r;
-                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-                const float4 tn = __ldg(reinterpret_cast<const float4 *>(phit + (int64_t)(m + 1) * S + (int64_t)y * NX) + x4);
-                g[0] += co * tn.x; g[1] += co * tn.y; g[2] += co * tn.z; g[3] += co * tn.w;
-            }
-            float cv[4] = {c.x, c.y, c.z, c.w};
-            float un[4] = {c.x, c.y, c.z, c.w};
-            if (m >= 1) {
-                const float *row = pp + q * NX;
-                const float4 pm = reinterpret_cast<const float4 *>(row)[x4];
-                const float4 pu = reinterpret_cast<const float4 *>(pp + (q - 1) * NX)[x4];
-                const float4 pd = reinterpret_cast<const float4 *>(pp + (q + 1) * NX)[x4];
-                const float lft = row[x4 == 0 ? NX - 1 : 4 * x4 - 1];
-                const float rgt = row[x4 == V - 1 ? 0 : 4 * x4 + 4];
-                const float pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
-                const float pv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
-                // transposed stencil per direction (multipliers m, p, q at j-1, j, j+1):
-                //   LF: (f'(u) (m - q) + a (2p - m - q)) / 2h;  upwind: f'(u) (p - q) / h;
-                //   viscous: -nu (q - 2p + m) / h^2
-                const bool lf = P.space != FD_UPWIND;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float p0 = pr[e + 1], df = dflux(P, cv[e]);
-                    const float mx = pr[e], qx = pr[e + 2], my = pv[e], qy = dv[e];
-                    float tx, ty;
-                    if (lf) {
-                        tx = 0.5f * (df * (mx - qx) + P.lf_a * (2.f * p0 - mx - qx));
-                        ty = 0.5f * (df * (my - qy) + P.lf_a * (2.f * p0 - my - qy));
-                    } else {
-                        tx = df * (p0 - qx);
-                        ty = df * (p0 - qy);
-                    }
-                    float ge = g[e] + cn * p0 + tx * P.inv_hx + ty * P.inv_hy;
-                    if (P.nu != 0.f)
-                        ge -= P.nu * ((qx - 2.f * p0 + mx) * P.inv_hx * P.inv_hx + (qy - 2.f * p0 + my) * P.inv_hy * P.inv_hy);
-                    un[e] = cv[e] - P.tau_u * ge;
-                }
-            } else if (P.init == INIT_LAMBDA) {
-                const int64_t i = (int64_t)(y0 - 1 + r) * NX + 4 * x4;     // own rows only: no wrap
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    un[e] = cv[e] - P.tau_u0 * (P.ht * g[e] + lamt[i + e]);
-                    const float r0 = un[e] - u0[i + e];
-                    const float ln = lam[i + e] + P.tau_lambda * r0;
-                    lam[i + e] = ln;
-                    lamt[i + e] = ln + P.tau_lambda * r0;
-                }
-            }
-            const float4 u4 = make_float4(un[0], un[1], un[2], un[3]);
-            reinterpret_cast<float4 *>(uc + r * NX)[x4] = u4;
-            if (own && own_write)
-                reinterpret_cast<float4 *>(u_out + (int64_t)m * S + (int64_t)(y0 - 1 + r) * NX)[x4] = u4;
-        }
-        __syncthreads();
-        // (2) residual R^{m-1} on the block's rows, then its x-FFT
         const int lr = m - 1;
         if (lr >= l0 && lr < l1) {
             const float *un = uc;
             const float *ucur = us + ((m + NR - 1) % NR) * RU * NX;
             const float *uold = us + ((m + NR - 2) % NR) * RU * NX;
             const float kn = coef_new(P, lr), kc = coef_cur(P, lr), ko = coef_old(P, lr);
+            constexpr int V = NX / 4;
             constexpr int GPT = FH * V / ATHREADS > 0 ? FH * V / ATHREADS : 1;   // float4 groups per thread
             float4 R[GPT];
 #pragma unroll
@@ -247,12 +248,8 @@ __global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Param
                 R[j] = make_float4(Rv[0], Rv[1], Rv[2], Rv[3]);
             }
             __syncthreads();
-            // FFT input in the u slot the residual no longer needs (BE: u^{m-1}, BDF2: u^{m-2}),
-            // FFT scratch in the phit slot of m-1
-            float *fin = BDF2_ ? const_cast<float *>(uold) : const_cast<float *>(ucur);
-            // rows of the padded layout of stockham.cuh (sequence stride PN, 4 per 16)
-            constexpr int PN = SeqLayout<LOG2M, 2>::PN;
-            float2 *fin2 = reinterpret_cast<float2 *>(fin);
+            // FFT input in the u slot the residual no longer needs (BE: u^{m-1}, BDF2: u^{m-2})
+            float2 *fin2 = reinterpret_cast<float2 *>(const_cast<float *>(BDF2_ ? uold : ucur));
 #pragma unroll
             for (int j = 0; j < GPT; ++j) {        // z_n = R_{2n} + i R_{2n+1}
                 const int gi = threadIdx.x + j * ATHREADS;
@@ -262,7 +259,7 @@ __global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : 2)) k_rowsA(Param
                 }
             }
             __syncthreads();
-            const float2 *res = stockham<LOG2M, false, FH, ATHREADS, 2>(fin2, reinterpret_cast<float2 *>(pp), twM);
+            const float2 *res = stockham<LOG2M, false, FH, ATHREADS, 2>(fin2, scr, twM);
             float2 *dst = spec + (int64_t)lr * P.nkx * ny + y0;
             for (int idx = threadIdx.x; idx < (M + 1) * FH; idx += blockDim.x) {
                 const int k = idx / FH, rr = idx - k * FH;
@@ -691,26 +688,24 @@ bool fused2d_supported(int dims, int space, int time, int prec, int64_t nx, int6
 static size_t al(size_t v) { return (v + 255) & ~size_t(255); }
 
 size_t fused2d_workspace_bytes(int64_t nx, int64_t ny, int64_t nt) {
-    const int64_t S = nx * ny, nkx = nx / 2 + 1;
-    return al((nt + 1) * S * 4) +              // second u buffer
-           al(nt * nkx * ny * 8) +             // spectrum [l][kx][y]
+    const int64_t nkx = nx / 2 + 1;
+    return al(nt * nkx * ny * 8) +             // spectrum [l][kx][y]
            al(nx / 2 * 8) + al(ny * 8) +       // twiddles W_M, W_ny
            al(nkx * ny * 4);                   // theta [kx][ky]
 }
 
 void fused2d_layout(Fused2D *f, void *ws, int64_t nx, int64_t ny, int64_t nt) {
-    const int64_t S = nx * ny, nkx = nx / 2 + 1;
+    const int64_t nkx = nx / 2 + 1;
     char *p = (char *)ws;
-    f->u2 = (float *)p; p += al((nt + 1) * S * 4);
     f->spec = (float2 *)p; p += al(nt * nkx * ny * 8);
     f->twM = (float2 *)p; p += al(nx / 2 * 8);
     f->twY = (float2 *)p; p += al(ny * 8);
     f->thetaT = (float *)p;
 }
 
-static size_t smem_rowsA(int log2m, bool bdf2) {
-    const int M = 1 << log2m, NX = 2 * M;
-    return (size_t)2 * (FH + 4) * NX * 4 + (size_t)(bdf2 ? 3 : 2) * (FH + 2) * NX * 4;
+static size_t smem_rowsR(int log2m, bool bdf2) {
+    const int M = 1 << log2m, NX = 2 * M, PN = M + M / 4 + 4;     // SeqLayout<log2m, 2>::PN
+    return (size_t)(bdf2 ? 3 : 2) * (FH + 2) * NX * 4 + (size_t)FH * PN * 8;
 }
 static size_t smem_rowsC(int log2m) {
     const int M = 1 << log2m, PN = M + M / 4 + 4;                // SeqLayout<log2m, 2>::PN
@@ -718,10 +713,10 @@ static size_t smem_rowsC(int log2m) {
 }
 
 template <int L> static cudaError_t attr_rows() {
-    cudaError_t e = cudaFuncSetAttribute(k_rowsA<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_rowsA(L, false));
+    cudaError_t e = cudaFuncSetAttribute(k_rowsR<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_rowsR(L, false));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_rowsA<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rowsA(L, true));
+        e = cudaFuncSetAttribute(k_rowsR<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rowsR(L, true));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_rowsC<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rowsC(L));
     return e;
@@ -736,7 +731,6 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
     if (ec != cudaSuccess) return ec;
     fused2d_layout(f, ws, P.nx, P.ny, P.nt);
     f->twN = (const float2 *)twx;
-    f->cur = 0;
     f->tc = P.nt >= 64 ? 32 : (P.nt >= 8 ? 8 : 2);
     switch (ilog2i(P.nx / 2)) {
     case 7: return attr_rows<7>();
@@ -748,15 +742,22 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
 }
 
 template <int L>
-static cudaError_t launch_rowsA(const Fused2D *f, const Params<float> &P, const float *uin, float *uout,
-                                const float *phit, float *lam, float *lamt, const float *u0, cudaStream_t s) {
+static cudaError_t launch_rowsR(const Fused2D *f, const Params<float> &P, const float *u, cudaStream_t s) {
     dim3 grid((unsigned)(P.ny / FH), (unsigned)((P.nt + f->tc - 1) / f->tc));
     if (P.time == BDF2)
-        k_rowsA<L, true><<<grid, ATHREADS, smem_rowsA(L, true), s>>>(P, uin, uout, phit, lam, lamt, u0, f->spec,
-                                                                     f->twN, f->twM, f->tc);
+        k_rowsR<L, true><<<grid, ATHREADS, smem_rowsR(L, true), s>>>(P, u, f->spec, f->twN, f->twM, f->tc);
     else
-        k_rowsA<L, false><<<grid, ATHREADS, smem_rowsA(L, false), s>>>(P, uin, uout, phit, lam, lamt, u0, f->spec,
-                                                                       f->twN, f->twM, f->tc);
+        k_rowsR<L, false><<<grid, ATHREADS, smem_rowsR(L, false), s>>>(P, u, f->spec, f->twN, f->twM, f->tc);
+    return cudaGetLastError();
+}
+
+template <int NX>
+static cudaError_t launch_primal2d(const Params<float> &P, float *u, const float *phit, float *lam, float *lamt,
+                                   const float *u0, cudaStream_t s) {
+    constexpr int V = NX / 4;
+    const dim3 block(V < 256 ? V : 256, V < 256 ? 256 / V : 1);
+    const dim3 grid((unsigned)(P.ny / (PRY * (int)block.y)), (unsigned)(P.nt + 1), V > 256 ? V / 256 : 1);
+    k_primal2d<NX><<<grid, block, 0, s>>>(P, u, phit, lam, lamt, u0);
     return cudaGetLastError();
 }
 
@@ -767,13 +768,23 @@ static cudaError_t launch_rowsC(const Fused2D *f, const Params<float> &P, float 
     return cudaGetLastError();
 }
 
-cudaError_t fused2d_rowsA(Fused2D *f, const Params<float> &P, const float *uin, float *uout, const float *phit,
-                          float *lam, float *lamt, const float *u0, cudaStream_t s) {
+cudaError_t fused2d_primal(const Params<float> &P, float *u, const float *phit, float *lam, float *lamt,
+                           const float *u0, cudaStream_t s) {
+    switch (P.nx) {
+    case 256: return launch_primal2d<256>(P, u, phit, lam, lamt, u0, s);
+    case 512: return launch_primal2d<512>(P, u, phit, lam, lamt, u0, s);
+    case 1024: return launch_primal2d<1024>(P, u, phit, lam, lamt, u0, s);
+    case 2048: return launch_primal2d<2048>(P, u, phit, lam, lamt, u0, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t fused2d_rowsR(Fused2D *f, const Params<float> &P, const float *u, cudaStream_t s) {
     switch (ilog2i(P.nx / 2)) {
-    case 7: return launch_rowsA<7>(f, P, uin, uout, phit, lam, lamt, u0, s);
-    case 8: return launch_rowsA<8>(f, P, uin, uout, phit, lam, lamt, u0, s);
-    case 9: return launch_rowsA<9>(f, P, uin, uout, phit, lam, lamt, u0, s);
-    case 10: return launch_rowsA<10>(f, P, uin, uout, phit, lam, lamt, u0, s);
+    case 7: return launch_rowsR<7>(f, P, u, s);
+    case 8: return launch_rowsR<8>(f, P, u, s);
+    case 9: return launch_rowsR<9>(f, P, u, s);
+    case 10: return launch_rowsR<10>(f, P, u, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -51,7 +51,7 @@ def test_fused_matches_oracle_and_plain(B, p):
     with B.Solver(p, precision="fp32", path="fused") as s:
         assert s.info()["path"] == "fused"
         s.iterate(n)
-        assert s.launches() == 3 * n
+        assert s.launches() == 4 * n
         g = {k: s.get_host(k) for k in ("u", "phi", "phit", "lambda")}
         rg = s.residual()
     with B.Solver(p, precision="fp32", path="plain") as s:
