@@ -107,6 +107,24 @@ __device__ __forceinline__ C rfft_split_vals(C zk, C zm, int k, const C *__restr
     return cadd(e, cmul(twN[k], o));
 }
 
+// Both outputs of the pair (k, M-k) from the same two inputs: with t = W_N^k O_k,
+// X_k = E_k + t and X_{M-k} = conj(E_k - t) (E_{M-k} = conj E_k, O_{M-k} = conj O_k and
+// W_N^{M-k} = -conj W_N^k).  k = 0 gives X_0 and X_M.
+template <typename C>
+__device__ __forceinline__ void rfft_split_pair(C zk, C zm, C w, C &xk, C &xm) {
+    C e, a, o;
+    e.x = 0.5f * (zk.x + zm.x);
+    e.y = 0.5f * (zk.y - zm.y);
+    a.x = zk.x - zm.x;
+    a.y = zk.y + zm.y;
+    o.x = 0.5f * a.y;
+    o.y = -0.5f * a.x;
+    const C t = cmul(w, o);
+    xk = cadd(e, t);
+    xm.x = e.x - t.x;
+    xm.y = t.y - e.y;
+}
+
 template <typename C>
 __device__ __forceinline__ C rfft_split(const C *Z, int M, int k, const C *__restrict__ twN) {
     return rfft_split_vals(Z[k == M ? 0 : k], Z[k == 0 ? 0 : M - k], k, twN);

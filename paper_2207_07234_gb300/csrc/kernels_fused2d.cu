@@ -195,77 +195,92 @@ k_rowsR(Params<float> P, const float *__restrict__ u, float2 *__restrict__ spec,
             const float *ucur = us + ((m + NR - 1) % NR) * RU * NX;
             const float *uold = us + ((m + NR - 2) % NR) * RU * NX;
             const float kn = coef_new(P, lr), kc = coef_cur(P, lr), ko = coef_old(P, lr);
+            // thread -> CPT float4 columns x RPT consecutive rows (a sliding window over
+            // the rows, so each value's flux is evaluated once per thread column)
             constexpr int V = NX / 4;
-            constexpr int GPT = FH * V / ATHREADS > 0 ? FH * V / ATHREADS : 1;   // float4 groups per thread
-            float4 R[GPT];
+            constexpr int TX = V < ATHREADS ? V : ATHREADS;       // threads across a row
+            constexpr int RPT = FH * TX / ATHREADS;                // rows per thread
+            constexpr int CPT = V / TX;                            // columns per thread
+            const int xb = threadIdx.x % TX, rb = (threadIdx.x / TX) * RPT;
+            const bool lf = P.space != FD_UPWIND;
+            float4 R[CPT][RPT];
 #pragma unroll
-            for (int j = 0; j < GPT; ++j) {
-                const int gi = threadIdx.x + j * ATHREADS;
-                if (gi >= FH * V) break;
-                const int rr = gi / V, x4 = gi - rr * V;
-                const int r = rr + 1;
-                const float *row = un + r * NX;
-                const float4 v4 = reinterpret_cast<const float4 *>(row)[x4];
-                const float4 up = reinterpret_cast<const float4 *>(un + (r - 1) * NX)[x4];
-                const float4 dn = reinterpret_cast<const float4 *>(un + (r + 1) * NX)[x4];
-                const float4 cu = reinterpret_cast<const float4 *>(ucur + r * NX)[x4];
-                const float lft = row[x4 == 0 ? NX - 1 : 4 * x4 - 1];
-                const float rgt = row[x4 == V - 1 ? 0 : 4 * x4 + 4];
-                const float vr[6] = {lft, v4.x, v4.y, v4.z, v4.w, rgt};
-                const float uv[4] = {up.x, up.y, up.z, up.w}, dv[4] = {dn.x, dn.y, dn.z, dn.w};
-                const float cv[4] = {cu.x, cu.y, cu.z, cu.w};
-                float ov[4] = {0.f, 0.f, 0.f, 0.f};
-                if (BDF2_ && lr >= 1) {
-                    const float4 o4 = reinterpret_cast<const float4 *>(uold + r * NX)[x4];
-                    ov[0] = o4.x; ov[1] = o4.y; ov[2] = o4.z; ov[3] = o4.w;
-                }
-                // D in flux-difference form with each f(v) evaluated once per value:
-                //   LF: (F_{j+1/2} - F_{j-1/2}) = (f_{j+1} - f_{j-1})/2 - a (v_{j+1} - 2 v_j + v_{j-1})/2
-                //   upwind: f_j - f_{j-1};  viscous: -nu (v_{j+1} - 2 v_j + v_{j-1}) / h^2
-                float fx[6];
+            for (int c = 0; c < CPT; ++c) {
+                const int x4 = xb + c * TX;
+                float4 up = reinterpret_cast<const float4 *>(un + rb * NX)[x4];
+                float fu[4] = {flux(P, up.x), flux(P, up.y), flux(P, up.z), flux(P, up.w)};
+                float4 v4 = reinterpret_cast<const float4 *>(un + (rb + 1) * NX)[x4];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) fx[k] = flux(P, vr[k]);
-                const bool lf = P.space != FD_UPWIND;
-                float Rv[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float v = vr[e + 1];
-                    const float fu = flux(P, uv[e]), fdn = flux(P, dv[e]);
-                    const float lx = vr[e] - 2.f * v + vr[e + 2], ly = uv[e] - 2.f * v + dv[e];
-                    float dx, dy;
-                    if (lf) {
-                        dx = 0.5f * (fx[e + 2] - fx[e]) - 0.5f * P.lf_a * lx;
-                        dy = 0.5f * (fdn - fu) - 0.5f * P.lf_a * ly;
-                    } else {
-                        dx = fx[e + 1] - fx[e];
-                        dy = fx[e + 1] - fu;
+                for (int q = 0; q < RPT; ++q) {
+                    const int r = rb + q + 1;                      // ring row of the residual row
+                    const float *row = un + r * NX;
+                    const float4 dn = reinterpret_cast<const float4 *>(un + (r + 1) * NX)[x4];
+                    const float4 cu = reinterpret_cast<const float4 *>(ucur + r * NX)[x4];
+                    const float lft = row[x4 == 0 ? NX - 1 : 4 * x4 - 1];
+                    const float rgt = row[x4 == V - 1 ? 0 : 4 * x4 + 4];
+                    const float vr[6] = {lft, v4.x, v4.y, v4.z, v4.w, rgt};
+                    const float uv[4] = {up.x, up.y, up.z, up.w}, dv[4] = {dn.x, dn.y, dn.z, dn.w};
+                    const float cv[4] = {cu.x, cu.y, cu.z, cu.w};
+                    float ov[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (BDF2_ && lr >= 1) {
+                        const float4 o4 = reinterpret_cast<const float4 *>(uold + r * NX)[x4];
+                        ov[0] = o4.x; ov[1] = o4.y; ov[2] = o4.z; ov[3] = o4.w;
                     }
-                    float r = dx * P.inv_hx + dy * P.inv_hy + kn * v + kc * cv[e];
-                    if (P.nu != 0.f) r -= P.nu * (lx * P.inv_hx * P.inv_hx + ly * P.inv_hy * P.inv_hy);
-                    if (BDF2_ && lr >= 1) r += ko * ov[e];
-                    Rv[e] = r;
+                    // D in flux-difference form with each f(v) evaluated once per value:
+                    //   LF: (F_{j+1/2} - F_{j-1/2}) = (f_{j+1} - f_{j-1})/2 - a (v_{j+1} - 2 v_j + v_{j-1})/2
+                    //   upwind: f_j - f_{j-1};  viscous: -nu (v_{j+1} - 2 v_j + v_{j-1}) / h^2
+                    float fx[6], fd[4];
+                    fx[0] = flux(P, lft);
+                    fx[5] = flux(P, rgt);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        fx[e + 1] = flux(P, vr[e + 1]);
+                        fd[e] = flux(P, dv[e]);
+                    }
+                    float Rv[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float v = vr[e + 1];
+                        const float lx = vr[e] - 2.f * v + vr[e + 2], ly = uv[e] - 2.f * v + dv[e];
+                        float dx, dy;
+                        if (lf) {
+                            dx = 0.5f * (fx[e + 2] - fx[e]) - 0.5f * P.lf_a * lx;
+                            dy = 0.5f * (fd[e] - fu[e]) - 0.5f * P.lf_a * ly;
+                        } else {
+                            dx = fx[e + 1] - fx[e];
+                            dy = fx[e + 1] - fu[e];
+                        }
+                        float rv = dx * P.inv_hx + dy * P.inv_hy + kn * v + kc * cv[e];
+                        if (P.nu != 0.f) rv -= P.nu * (lx * P.inv_hx * P.inv_hx + ly * P.inv_hy * P.inv_hy);
+                        if (BDF2_ && lr >= 1) rv += ko * ov[e];
+                        Rv[e] = rv;
+                    }
+                    R[c][q] = make_float4(Rv[0], Rv[1], Rv[2], Rv[3]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) fu[e] = fx[e + 1];
+                    up = v4;
+                    v4 = dn;
                 }
-                R[j] = make_float4(Rv[0], Rv[1], Rv[2], Rv[3]);
             }
             __syncthreads();
             // FFT input in the u slot the residual no longer needs (BE: u^{m-1}, BDF2: u^{m-2})
             float2 *fin2 = reinterpret_cast<float2 *>(const_cast<float *>(BDF2_ ? uold : ucur));
 #pragma unroll
-            for (int j = 0; j < GPT; ++j) {        // z_n = R_{2n} + i R_{2n+1}
-                const int gi = threadIdx.x + j * ATHREADS;
-                if (gi < FH * V) {
-                    const int rr = gi / V, x4 = gi - rr * V;
-                    *reinterpret_cast<float4 *>(fin2 + rr * PN + padx(2 * x4)) = R[j];
-                }
-            }
+            for (int c = 0; c < CPT; ++c)               // z_n = R_{2n} + i R_{2n+1}
+#pragma unroll
+                for (int q = 0; q < RPT; ++q)
+                    *reinterpret_cast<float4 *>(fin2 + (rb + q) * PN + padx(2 * (xb + c * TX))) = R[c][q];
             __syncthreads();
             const float2 *res = stockham<LOG2M, false, FH, ATHREADS, 2>(fin2, scr, twM);
+            // split pairs (k, M-k), k = 0..M/2, both outputs from one pair of loads
             float2 *dst = spec + (int64_t)lr * P.nkx * ny + y0;
-            for (int idx = threadIdx.x; idx < (M + 1) * FH; idx += blockDim.x) {
+            for (int idx = threadIdx.x; idx < (M / 2 + 1) * FH; idx += blockDim.x) {
                 const int k = idx / FH, rr = idx - k * FH;
                 const float2 *row = res + rr * PN;
-                dst[(int64_t)k * ny + rr] =
-                    rfft_split_vals(row[padx(k == M ? 0 : k)], row[padx(k == 0 ? 0 : M - k)], k, twN);
+                float2 xk, xm;
+                rfft_split_pair(row[padx(k)], row[padx(k == 0 ? 0 : M - k)], __ldg(twN + k), xk, xm);
+                dst[(int64_t)k * ny + rr] = xk;
+                if (k != M / 2) dst[(int64_t)(M - k) * ny + rr] = xm;
             }
         }
         __syncthreads();

@@ -1,4 +1,4 @@
-"""GPU parity of the fused 2D path (float32): rows-A / cols / rows-C kernels.
+"""GPU parity of the fused 2D path (float32): primal / rows-R / cols / rows-C kernels.
 
 * small and mid sizes: n iterations element by element against the float64
   oracle and against the plain path (several row blocks, several t-chunks, a
