@@ -427,6 +427,25 @@ static std::vector<float> staged_twiddles(int64_t N) {
     return t;
 }
 
+// Twiddles of the radix-8 Stockham transform of length N: the radix-8 stage of span
+// p (p = P0, 8 P0, ... with P0 = 2^(log2 N mod 3)) owns entries
+// (p - P0) + (q-1) p + k = W_N^{q k N/(8p)}, q = 1..7, k < p.
+static std::vector<float> staged_twiddles8(int64_t N) {
+    std::vector<float> t(2 * N, 0.f);
+    int lg = 0;
+    while ((int64_t(1) << lg) < N) ++lg;
+    const int64_t p0 = int64_t(1) << (lg % 3);
+    for (int64_t p = p0; 8 * p <= N; p *= 8)
+        for (int64_t q = 1; q < 8; ++q)
+            for (int64_t k = 0; k < p; ++k) {
+                const int64_t e = (p - p0) + (q - 1) * p + k;
+                const double a = 2.0 * M_PI * (double)(q * k * (N / (8 * p))) / (double)N;
+                t[2 * e] = (float)std::cos(a);
+                t[2 * e + 1] = (float)(-std::sin(a));
+            }
+    return t;
+}
+
 // Run fn(r0, r1) over [0, nrows) in contiguous chunks on up to 16 host threads when
 // the work (total elements) is large; inline otherwise.  Results do not depend on
 // the split: every element is computed the same way.
@@ -545,6 +564,8 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
         });
         CK(cudaMemcpy(f.twM, tm.data(), tm.size() * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(f.twY, ty.data(), ty.size() * 4, cudaMemcpyHostToDevice));
+        const std::vector<float> t8 = staged_twiddles8(G.nx / 2);
+        CK(cudaMemcpy(f.twM8, t8.data(), t8.size() * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(f.thetaT, tt.data(), tt.size() * 4, cudaMemcpyHostToDevice));
     }
     Params<T> &P = params_of<T>(h);

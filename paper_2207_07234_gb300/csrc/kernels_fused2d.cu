@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_primal2d(Params<float> P, float *__rest
 //   us  [NR][FH+2][NX]  u^m, u^{m-1} (and u^{m-2} for BDF2)
 //   scr [FH][PN]        FFT scratch
 // The FFT input aliases the u slot that the residual no longer needs, so BE
-// takes 69 KB at nx = 1024: three blocks per SM.
+// takes 67 KB at nx = 1024: three blocks per SM.
 // ---------------------------------------------------------------------------
 template <int NX, int N>
 __device__ __forceinline__ void fetch_rows(float4 (&reg)[N], const float *__restrict__ src_slice, int ybase, int ny) {
@@ -166,11 +166,11 @@ __device__ __forceinline__ void store_rows(float *dst, const float4 (&reg)[N]) {
 template <int LOG2M, bool BDF2_>
 __global__ void __launch_bounds__(ATHREADS, (LOG2M >= 10 ? 1 : (BDF2_ ? 2 : 3)))
 k_rowsR(Params<float> P, const float *__restrict__ u, float2 *__restrict__ spec,
-        const float2 *__restrict__ twN, const float2 *__restrict__ twM, int Tc) {
+        const float2 *__restrict__ twN, const float2 *__restrict__ tw8, int Tc) {
     constexpr int M = 1 << LOG2M, NX = 2 * M;
     constexpr int NR = BDF2_ ? 3 : 2;            // u ring slots
     constexpr int RU = FH + 2;                   // u rows: block rows + one halo row each side
-    constexpr int PN = SeqLayout<LOG2M, 2>::PN;  // padded FFT rows (stockham.cuh)
+    constexpr int PN = R8<LOG2M>::PN;            // FFT row stride (radix-8 layout, stockham.cuh)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *us = reinterpret_cast<float *>(smem_raw);                  // [NR][RU][NX]
     float2 *scr = reinterpret_cast<float2 *>(us + NR * RU * NX);     // [FH][PN]
@@ -269,16 +269,16 @@ k_rowsR(Params<float> P, const float *__restrict__ u, float2 *__restrict__ spec,
             for (int c = 0; c < CPT; ++c)               // z_n = R_{2n} + i R_{2n+1}
 #pragma unroll
                 for (int q = 0; q < RPT; ++q)
-                    *reinterpret_cast<float4 *>(fin2 + (rb + q) * PN + padx(2 * (xb + c * TX))) = R[c][q];
+                    *reinterpret_cast<float4 *>(fin2 + (rb + q) * PN + 2 * (xb + c * TX)) = R[c][q];
             __syncthreads();
-            const float2 *res = stockham<LOG2M, false, FH, ATHREADS, 2>(fin2, scr, twM);
+            const float2 *res = stockham8<LOG2M, false, FH, ATHREADS>(fin2, scr, tw8);
             // split pairs (k, M-k), k = 0..M/2, both outputs from one pair of loads
             float2 *dst = spec + (int64_t)lr * P.nkx * ny + y0;
             for (int idx = threadIdx.x; idx < (M / 2 + 1) * FH; idx += blockDim.x) {
                 const int k = idx / FH, rr = idx - k * FH;
                 const float2 *row = res + rr * PN;
                 float2 xk, xm;
-                rfft_split_pair(row[padx(k)], row[padx(k == 0 ? 0 : M - k)], __ldg(twN + k), xk, xm);
+                rfft_split_pair(row[k], row[k == 0 ? 0 : M - k], __ldg(twN + k), xk, xm);
                 dst[(int64_t)k * ny + rr] = xk;
                 if (k != M / 2) dst[(int64_t)(M - k) * ny + rr] = xm;
             }
@@ -706,6 +706,7 @@ size_t fused2d_workspace_bytes(int64_t nx, int64_t ny, int64_t nt) {
     const int64_t nkx = nx / 2 + 1;
     return al(nt * nkx * ny * 8) +             // spectrum [l][kx][y]
            al(nx / 2 * 8) + al(ny * 8) +       // twiddles W_M, W_ny
+           al(nx / 2 * 8) +                    // radix-8 twiddles W_M
            al(nkx * ny * 4);                   // theta [kx][ky]
 }
 
@@ -715,11 +716,12 @@ void fused2d_layout(Fused2D *f, void *ws, int64_t nx, int64_t ny, int64_t nt) {
     f->spec = (float2 *)p; p += al(nt * nkx * ny * 8);
     f->twM = (float2 *)p; p += al(nx / 2 * 8);
     f->twY = (float2 *)p; p += al(ny * 8);
+    f->twM8 = (float2 *)p; p += al(nx / 2 * 8);
     f->thetaT = (float *)p;
 }
 
 static size_t smem_rowsR(int log2m, bool bdf2) {
-    const int M = 1 << log2m, NX = 2 * M, PN = M + M / 4 + 4;     // SeqLayout<log2m, 2>::PN
+    const int M = 1 << log2m, NX = 2 * M, PN = M + M / 8 + 4;     // R8<log2m>::PN
     return (size_t)(bdf2 ? 3 : 2) * (FH + 2) * NX * 4 + (size_t)FH * PN * 8;
 }
 static size_t smem_rowsC(int log2m) {
@@ -760,9 +762,9 @@ template <int L>
 static cudaError_t launch_rowsR(const Fused2D *f, const Params<float> &P, const float *u, cudaStream_t s) {
     dim3 grid((unsigned)(P.ny / FH), (unsigned)((P.nt + f->tc - 1) / f->tc));
     if (P.time == BDF2)
-        k_rowsR<L, true><<<grid, ATHREADS, smem_rowsR(L, true), s>>>(P, u, f->spec, f->twN, f->twM, f->tc);
+        k_rowsR<L, true><<<grid, ATHREADS, smem_rowsR(L, true), s>>>(P, u, f->spec, f->twN, f->twM8, f->tc);
     else
-        k_rowsR<L, false><<<grid, ATHREADS, smem_rowsR(L, false), s>>>(P, u, f->spec, f->twN, f->twM, f->tc);
+        k_rowsR<L, false><<<grid, ATHREADS, smem_rowsR(L, false), s>>>(P, u, f->spec, f->twN, f->twM8, f->tc);
     return cudaGetLastError();
 }
 

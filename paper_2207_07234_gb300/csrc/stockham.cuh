@@ -134,4 +134,136 @@ __device__ __forceinline__ float2 *stockham(float2 *a, float2 *b, const float2 *
     }
 }
 
+// ---------------------------------------------------------------------------
+// Radix-8 Stockham: one leading radix-2 or radix-4 stage when log2 N is not a
+// multiple of 3, then radix-8 stages of span P0, 8 P0, ... (P0 = 2^(log2 N mod 3)),
+// so 512 points take 3 shared-memory passes instead of 5.
+//
+// Twiddles (host-built, N entries): the radix-8 stage of span p reads
+// tw8[(p - P0) + (q - 1) p + k] = W_N^{q k N/(8p)} for q = 1..7, k < p.
+//
+// Layout: sequence stride N + N/8 + 4; inside a sequence, element j of the buffer
+// written by a stage sits at j + c (j >> 4), with c = 1 after a span-1 stage, 2
+// after a span-2..8 stage and 0 after the last stage (span >= 16).  The writes of
+// span-1 stages (stride 8 or 4 or 2 per lane) and of span-2..8 stages (groups of
+// lanes 16..64 elements apart) then hit 16 distinct banks per 16 lanes, and the
+// reads (consecutive lanes at offsets that are multiples of 16) stay contiguous.
+// Input and output use c = 0.
+// ---------------------------------------------------------------------------
+template <int LOG2N>
+struct R8 {
+    static constexpr int N = 1 << LOG2N;
+    static constexpr int R0 = LOG2N % 3;              // leading radix 2^R0 (none when 0)
+    static constexpr int P0 = 1 << R0;                // span of the first radix-8 stage
+    static constexpr int PN = N + N / 8 + 4;          // sequence stride
+};
+
+template <int C>
+__device__ __forceinline__ int padc(int j) { return C ? j + C * (j >> 4) : j; }
+
+// 8-point DFT in registers (forward: W_8 = exp(-i pi/4)), natural order in and out:
+// two 4-point DFTs of the even and odd inputs, combined with W_8^r.
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&x)[8]) {
+    dft4<INV>(x[0], x[2], x[4], x[6]);        // E_r -> x[2r]
+    dft4<INV>(x[1], x[3], x[5], x[7]);        // O_r -> x[2r+1]
+    constexpr float h = 0.70710678118654752f;
+    const float2 o1 = x[3], o2 = x[5], o3 = x[7];
+    float2 t1, t2, t3;                         // W_8^{+-r} O_r
+    if (!INV) {
+        t1 = make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
+        t2 = make_float2(o2.y, -o2.x);
+        t3 = make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+    } else {
+        t1 = make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y));
+        t2 = make_float2(-o2.y, o2.x);
+        t3 = make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y));
+    }
+    const float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6], t0 = x[1];
+    x[0] = cadd(e0, t0); x[4] = csub(e0, t0);
+    x[1] = cadd(e1, t1); x[5] = csub(e1, t1);
+    x[2] = cadd(e2, t2); x[6] = csub(e2, t2);
+    x[3] = cadd(e3, t3); x[7] = csub(e3, t3);
+}
+
+// Leading radix-2^R0 stage (span 1, no twiddles): reads c = 0, writes c = 1.
+template <int LOG2N, bool INV, int BATCH, int NTHR>
+__device__ __forceinline__ void stage_r8_lead(const float2 *a, float2 *b) {
+    constexpr int N = 1 << LOG2N, R = 1 << R8<LOG2N>::R0, Q = N / R, W = BATCH * Q;
+    constexpr int ITERS = (W + NTHR - 1) / NTHR, PN = R8<LOG2N>::PN, LQ = LOG2N - R8<LOG2N>::R0;
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+        const int idx = threadIdx.x + it * NTHR;
+        if (W % NTHR != 0 && idx >= W) break;
+        const int s = idx >> LQ, i = idx & (Q - 1);
+        const float2 *src = a + s * PN;
+        float2 *dst = b + s * PN;
+        if constexpr (R == 2) {
+            const float2 x0 = src[i], x1 = src[i + Q];
+            dst[padc<1>(2 * i)] = cadd(x0, x1);
+            dst[padc<1>(2 * i + 1)] = csub(x0, x1);
+        } else {
+            float2 x0 = src[i], x1 = src[i + Q], x2 = src[i + 2 * Q], x3 = src[i + 3 * Q];
+            dft4<INV>(x0, x1, x2, x3);
+            dst[padc<1>(4 * i)] = x0;
+            dst[padc<1>(4 * i + 1)] = x1;
+            dst[padc<1>(4 * i + 2)] = x2;
+            dst[padc<1>(4 * i + 3)] = x3;
+        }
+    }
+}
+
+template <int LOG2N, bool INV, int P, int CIN, int COUT, int BATCH, int NTHR>
+__device__ __forceinline__ void stage_r8(const float2 *a, float2 *b, const float2 *tw) {
+    constexpr int N = 1 << LOG2N, Q = N >> 3, W = BATCH * Q, ITERS = (W + NTHR - 1) / NTHR;
+    constexpr int PN = R8<LOG2N>::PN;
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+        const int idx = threadIdx.x + it * NTHR;
+        if (W % NTHR != 0 && idx >= W) break;
+        const int s = idx >> (LOG2N - 3), i = idx & (Q - 1);
+        const float2 *src = a + s * PN;
+        float2 *dst = b + s * PN;
+        const int k = i & (P - 1);
+        float2 x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = src[padc<CIN>(i + q * Q)];
+        if (P > 1) {
+            const float2 *tp = tw + (P - R8<LOG2N>::P0) + k;
+#pragma unroll
+            for (int q = 1; q < 8; ++q) x[q] = twmul<INV>(x[q], tp[(q - 1) * P]);
+        }
+        dft8<INV>(x);
+        const int j = ((i - k) << 3) + k;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) dst[padc<COUT>(j + r * P)] = x[r];
+    }
+}
+
+template <int LOG2N, bool INV, int P, int CIN, int BATCH, int NTHR>
+__device__ __forceinline__ float2 *stockham8_range(float2 *a, float2 *b, const float2 *tw) {
+    if constexpr (P >= (1 << LOG2N)) {
+        return a;
+    } else {
+        constexpr int COUT = 8 * P >= (1 << LOG2N) ? 0 : (P == 1 ? 1 : 2);
+        stage_r8<LOG2N, INV, P, CIN, COUT, BATCH, NTHR>(a, b, tw);
+        __syncthreads();
+        return stockham8_range<LOG2N, INV, 8 * P, COUT, BATCH, NTHR>(b, a, tw);
+    }
+}
+
+// Full transform of BATCH sequences (stride R8<LOG2N>::PN, c = 0 layout) by NTHR
+// threads; data starts in a, b is scratch; returns the buffer holding the result
+// (c = 0 layout).  Ends with __syncthreads().
+template <int LOG2N, bool INV, int BATCH, int NTHR>
+__device__ __forceinline__ float2 *stockham8(float2 *a, float2 *b, const float2 *tw8) {
+    if constexpr (R8<LOG2N>::R0 == 0) {
+        return stockham8_range<LOG2N, INV, 1, 0, BATCH, NTHR>(a, b, tw8);
+    } else {
+        stage_r8_lead<LOG2N, INV, BATCH, NTHR>(a, b);
+        __syncthreads();
+        return stockham8_range<LOG2N, INV, R8<LOG2N>::P0, 1, BATCH, NTHR>(b, a, tw8);
+    }
+}
+
 }  // namespace pdhg
