@@ -446,6 +446,26 @@ static std::vector<float> staged_twiddles8(int64_t N) {
     return t;
 }
 
+// Twiddles of the 4 x 8 x 8 x 4 transform of length 1024 along y (fused 2D path):
+// the radix-8 stage of span p (4, 32) owns entries (p - 4) + (q-1) p + k =
+// W^{q k 1024/(8p)}, q = 1..7, k < p; the final radix-4 stage (span 256) owns
+// 252 + (q-1) 256 + k = W^{q k}, q = 1..3, with W = exp(-2 pi i / 1024).
+static std::vector<float> cols1024_twiddles() {
+    const int64_t N = 1024;
+    std::vector<float> t(2 * N, 0.f);
+    auto put = [&](int64_t e, int64_t expo) {
+        const double a = 2.0 * M_PI * (double)expo / (double)N;
+        t[2 * e] = (float)std::cos(a);
+        t[2 * e + 1] = (float)(-std::sin(a));
+    };
+    for (int64_t p : {int64_t(4), int64_t(32)})
+        for (int64_t q = 1; q < 8; ++q)
+            for (int64_t k = 0; k < p; ++k) put((p - 4) + (q - 1) * p + k, q * k * (N / (8 * p)));
+    for (int64_t q = 1; q < 4; ++q)
+        for (int64_t k = 0; k < 256; ++k) put(252 + (q - 1) * 256 + k, q * k);
+    return t;
+}
+
 // Run fn(r0, r1) over [0, nrows) in contiguous chunks on up to 16 host threads when
 // the work (total elements) is large; inline otherwise.  Results do not depend on
 // the split: every element is computed the same way.
@@ -554,10 +574,12 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     }
     if (G.fused) {
         // fused 2D path: staged twiddle tables for the Stockham transforms of length
-        // M = nx/2 (along x) and ny (along y), and theta in [kx][ky] order
+        // M = nx/2 (along x) and ny (along y; ny = 1024 has its own plan), and theta
+        // in [kx][ky] order
         Fused2D &f = h->fused;
         fused2d_layout(&f, h->ws + h->L.fused, G.nx, G.ny, G.nt);
-        std::vector<float> tm = staged_twiddles(G.nx / 2), ty = staged_twiddles(G.ny), tt(G.nkx * G.ny);
+        std::vector<float> tm = staged_twiddles(G.nx / 2), ty = G.ny == 1024 ? cols1024_twiddles() : staged_twiddles(G.ny),
+                           tt(G.nkx * G.ny);
         parallel_rows(G.nkx, G.nkx * G.ny, [&](int64_t x0, int64_t x1) {
             for (int64_t kx = x0; kx < x1; ++kx)
                 for (int64_t ky = 0; ky < G.ny; ++ky) tt[kx * G.ny + ky] = (float)th[ky * G.nkx + kx];

@@ -8,7 +8,7 @@ namespace pdhg {
 struct Fused2D {
     float2 *spec;            // spectrum [l][kx][y]: X, then spill, then K_d^{-1} R, in place
     float2 *twM;             // staged Stockham twiddles of length M = nx/2 (stockham.cuh)
-    float2 *twY;             // staged Stockham twiddles of length ny
+    float2 *twY;             // staged twiddles of length ny (radix 4; ny = 1024: the 4x8x8x4 plan)
     float2 *twM8;            // radix-8 staged twiddles of length M (stockham.cuh)
     float *thetaT;           // theta per mode, [kx][ky]
     const float2 *twN;       // W_nx^k, k <= nx/2 (the plain path's table)

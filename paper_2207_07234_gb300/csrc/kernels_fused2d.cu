@@ -414,14 +414,17 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
     }
 }
 
-// ny = 1024 with 256 threads: thread t owns modes t + 256 q (q = 0..3), which are
-// exactly the inputs of the first radix-4 stage (span 1) and the outputs of the
-// last (span 256).  Those two stages run in registers; only the three middle
-// stages (spans 4, 16, 64) go through shared memory.
-__global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float2 *__restrict__ spec,
+// ny = 1024 with 256 threads as 4 x 8 x 8 x 4: thread t owns modes t + 256 q
+// (q = 0..3), which are exactly the inputs of the first radix-4 stage (span 1) and
+// the outputs of the last radix-4 stage (span 256).  Those two stages run in
+// registers; the two radix-8 stages between them (spans 4 and 32) go through
+// shared memory (radix-8 layout of stockham.cuh: c = 2 after the first two stages,
+// c = 0 after the third).  Twiddles (twY): radix-8 span p at (p - 4) + (q-1) p + k,
+// radix-4 span 256 at 252 + (q-1) 256 + k.
+__global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float2 *__restrict__ spec,
                                                        const float2 *__restrict__ twY,
                                                        const float *__restrict__ thetaT) {
-    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2, PN = SeqLayout<LOG2NY, 1>::PN;
+    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2, PN = R8<LOG2NY>::PN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *ba = reinterpret_cast<float2 *>(smem_raw);              // [TB][PN] (padded)
     float2 *bb = ba + TB * PN;                                      // [TB][PN]
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
         for (int b = 0; b < TB; ++b) {
             float2 x0 = pf[b][0], x1 = pf[b][1], x2 = pf[b][2], x3 = pf[b][3];
             dft4<false>(x0, x1, x2, x3);
-            float4 *d = reinterpret_cast<float4 *>(ba + b * PN + padx(4 * t));
+            float4 *d = reinterpret_cast<float4 *>(ba + b * PN + padc<2>(4 * t));
             d[0] = make_float4(x0.x, x0.y, x1.x, x1.y);
             d[1] = make_float4(x2.x, x2.y, x3.x, x3.y);
         }
@@ -468,16 +471,21 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
                 for (int q = 0; q < 4; ++q) pf[b][q] = l < nt ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham_r4_range<LOG2NY, false, 4, 256, TB, FTHREADS, 1>(ba, bb, tw);
-        // stage 5 (span 256) in registers: inputs t + 256 r with twiddles W^{r t}, outputs t + 256 q
+        stage_r8<LOG2NY, false, 4, 2, 2, TB, FTHREADS, 4>(ba, bb, tw);
+        __syncthreads();
+        stage_r8<LOG2NY, false, 32, 2, 0, TB, FTHREADS, 4>(bb, ba, tw);
+        __syncthreads();
+        const float2 *res = ba;
+        // last stage (radix 4, span 256) in registers: inputs t + 256 r with twiddles W^{r t},
+        // outputs t + 256 q
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = lb + b;
             const float2 *rb = res + b * PN;
-            float2 x0 = rb[padx(t)];
-            float2 x1 = cmul(rb[padx(t + Q)], tw[255 + t]);             // staged block of span 256
-            float2 x2 = cmul(rb[padx(t + 2 * Q)], tw[255 + 256 + t]);
-            float2 x3 = cmul(rb[padx(t + 3 * Q)], tw[255 + 512 + t]);
+            float2 x0 = rb[t];
+            float2 x1 = cmul(rb[t + Q], tw[252 + t]);
+            float2 x2 = cmul(rb[t + 2 * Q], tw[252 + 256 + t]);
+            float2 x3 = cmul(rb[t + 3 * Q], tw[252 + 512 + t]);
             dft4<false>(x0, x1, x2, x3);
             if (l < nt) {
                 float2 y[4] = {x0, x1, x2, x3};
@@ -490,8 +498,8 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
                 }
             }
         }
+        __syncthreads();                 // res (= ba) takes the next batch's first stage
     }
-    __syncthreads();
     // ---- backward sweep (batches from the top) ----
     int hi = nt - 1;
 #pragma unroll
@@ -516,7 +524,7 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
             }
             // inverse stage 1 (span 1) in registers
             dft4<true>(z[0], z[1], z[2], z[3]);
-            float4 *d = reinterpret_cast<float4 *>(ba + b * PN + padx(4 * t));
+            float4 *d = reinterpret_cast<float4 *>(ba + b * PN + padc<2>(4 * t));
             d[0] = make_float4(z[0].x, z[0].y, z[1].x, z[1].y);
             d[1] = make_float4(z[2].x, z[2].y, z[3].x, z[3].y);
         }
@@ -529,15 +537,19 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
                 for (int q = 0; q < 4; ++q) pf[b][q] = l >= 0 ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
             }
         }
-        const float2 *res = stockham_r4_range<LOG2NY, true, 4, 256, TB, FTHREADS, 1>(ba, bb, tw);
+        stage_r8<LOG2NY, true, 4, 2, 2, TB, FTHREADS, 4>(ba, bb, tw);
+        __syncthreads();
+        stage_r8<LOG2NY, true, 32, 2, 0, TB, FTHREADS, 4>(bb, ba, tw);
+        __syncthreads();
+        const float2 *res = ba;
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
             const int l = hi - b;
             const float2 *rb = res + b * PN;
-            float2 x0 = rb[padx(t)];
-            float2 x1 = cmulconj(rb[padx(t + Q)], tw[255 + t]);
-            float2 x2 = cmulconj(rb[padx(t + 2 * Q)], tw[255 + 256 + t]);
-            float2 x3 = cmulconj(rb[padx(t + 3 * Q)], tw[255 + 512 + t]);
+            float2 x0 = rb[t];
+            float2 x1 = cmulconj(rb[t + Q], tw[252 + t]);
+            float2 x2 = cmulconj(rb[t + 2 * Q], tw[252 + 256 + t]);
+            float2 x3 = cmulconj(rb[t + 3 * Q], tw[252 + 512 + t]);
             dft4<true>(x0, x1, x2, x3);
             if (l >= 0) {
                 col[(int64_t)l * cs + t] = x0;
@@ -546,12 +558,13 @@ __global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float
                 col[(int64_t)l * cs + t + 3 * Q] = x3;
             }
         }
+        __syncthreads();                 // res (= ba) takes the next batch's first stage
     }
 }
 
 static size_t smem_cols(int log2ny) {
     const size_t n = (size_t)1 << log2ny;
-    return log2ny == 10 ? (4 * (size_t)SeqLayout<10, 1>::PN + n) * 8 : 5 * n * 8;    // ny = 1024: padded
+    return log2ny == 10 ? (4 * (size_t)R8<10>::PN + n) * 8 : 5 * n * 8;    // ny = 1024: radix-8 layout
 }
 
 // ---------------------------------------------------------------------------

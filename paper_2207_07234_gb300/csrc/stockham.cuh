@@ -213,7 +213,9 @@ __device__ __forceinline__ void stage_r8_lead(const float2 *a, float2 *b) {
     }
 }
 
-template <int LOG2N, bool INV, int P, int CIN, int COUT, int BATCH, int NTHR>
+// One radix-8 stage of span P.  TW0 is the span whose block starts the twiddle
+// table (the span of the first radix-8 stage, unless a custom plan says otherwise).
+template <int LOG2N, bool INV, int P, int CIN, int COUT, int BATCH, int NTHR, int TW0 = R8<LOG2N>::P0>
 __device__ __forceinline__ void stage_r8(const float2 *a, float2 *b, const float2 *tw) {
     constexpr int N = 1 << LOG2N, Q = N >> 3, W = BATCH * Q, ITERS = (W + NTHR - 1) / NTHR;
     constexpr int PN = R8<LOG2N>::PN;
@@ -229,7 +231,7 @@ __device__ __forceinline__ void stage_r8(const float2 *a, float2 *b, const float
 #pragma unroll
         for (int q = 0; q < 8; ++q) x[q] = src[padc<CIN>(i + q * Q)];
         if (P > 1) {
-            const float2 *tp = tw + (P - R8<LOG2N>::P0) + k;
+            const float2 *tp = tw + (P - TW0) + k;
 #pragma unroll
             for (int q = 1; q < 8; ++q) x[q] = twmul<INV>(x[q], tp[(q - 1) * P]);
         }
