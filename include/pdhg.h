@@ -140,7 +140,8 @@ pdhg_status pdhg_set_stream(pdhg_handle *h, void *stream);
  * check_every > 0: every check_every iterations compute Res (Eq. 2.12) and stop
  *   once both entries are <= tol (absolute; relative to ||A(u_init)|| when
  *   relative != 0); synchronises at each check.  Returns NONFINITE/DIVERGED on
- *   a bad residual.
+ *   a bad residual, TIMEOUT when a bounded device wait of the fused path gave
+ *   up since the last check (the state is then invalid).
  * check_every <= 0: enqueue max_iters iterations asynchronously (no host sync).
  * *iters_done (may be NULL) receives the iterations performed by this call. */
 pdhg_status pdhg_iterate(pdhg_handle *h, int64_t max_iters, double tol, int32_t check_every,
@@ -152,7 +153,7 @@ pdhg_status pdhg_iterate(pdhg_handle *h, int64_t max_iters, double tol, int32_t 
  * init LAMBDA), out[2] = ||u^0 - u0||, out[3] = the Lagrangian <phi, R(u)> +
  * <lambda, u^0 - u0> (the duality-gap diagnostic; the objective is 0).
  * Norms are discrete L2 with weights h_t*w_x per equation dof, w_x per
- * initial-row dof (w_x = h_x, or h_x*h_y in 2D). */
+ * initial-row dof (w_x = h_x, or h_x*h_y in 2D).  TIMEOUT as pdhg_iterate. */
 pdhg_status pdhg_residual(pdhg_handle *h, double out[4]);
 
 /* Copy a field (PDHG_FIELD_*) out of / into the state.  dst/src has the

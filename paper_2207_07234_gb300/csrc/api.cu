@@ -613,8 +613,11 @@ static cudaError_t enqueue_check(pdhg_handle *h) {
 
 static pdhg_status read_res(pdhg_handle *h, double out[4]) {
     double acc[6];
+    int err = 0;
     CK(cudaMemcpyAsync(acc, h->ws + h->L.scal, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    if (h->G.fused) CK(cudaMemcpyAsync(&err, h->fused.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (err) return fail(PDHG_ERR_TIMEOUT, "a pipelined spectrum load of the fused rows-C kernel did not arrive");
     double ht = h->ht, wx = h->wx;
     // space-time L2 (weight h_t w_x per equation value), or, for the one-step
     // problems of Algorithm 3, L2 over the domain at one time (weight w_x)

@@ -1,11 +1,15 @@
 // fused2d.h -- the fused four-kernel iteration for 2D finite differences (float32).
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace pdhg {
 
 struct Fused2D {
+    CUtensorMap tmC;         // the spectrum as rows-C's TMA source (nx = 1024), 64-byte aligned
+    int *err;                // device flag: a pipelined rows-C stage wait gave up
     float2 *spec;            // spectrum [l][kx][y]: X, then spill, then K_d^{-1} R, in place
     float2 *twM;             // staged Stockham twiddles of length M = nx/2 (stockham.cuh)
     float2 *twY;             // staged twiddles of length ny (radix 4; ny = 1024: the 4x8x8x4 plan)
@@ -13,6 +17,7 @@ struct Fused2D {
     float *thetaT;           // theta per mode, [kx][ky]
     const float2 *twN;       // W_nx^k, k <= nx/2 (the plain path's table)
     int tc;                  // time slices per rows-R block
+    int nsm;                 // multiprocessors of the device (persistent rows-C grid)
 };
 
 bool fused2d_supported(int dims, int space, int time, int prec, int64_t nx, int64_t ny, int64_t nt, double nu);

@@ -12,9 +12,12 @@
 //           inverse FFT along y, written in place: the x-spectrum of z.
 //   rows-C  (H rows x one slice per block) inverse real FFT along x, dual
 //           step phi^n = phi^{n-1} + tau_phi z and extrapolation phit = phi^n + tau_phi z.
+#include <algorithm>
+
 #include "fused2d.h"
 #include "fft_smem.cuh"
 #include "stockham.cuh"
+#include "tma.cuh"
 
 namespace pdhg {
 
@@ -619,83 +622,131 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC(Params<float> P, const float
     }
 }
 
-// rows-C for nx = 1024 (M = 512 = 2 * 4^4): the inverse split feeds the first
-// (radix-2, span 1) stage directly in registers, three radix-4 stages (spans
-// 2, 8, 32) run in shared memory, and the last (span 128) runs in registers,
-// whose outputs -- complex positions i + 128 q, i.e. x = 2 (i + 128 q) + {0,1} --
-// go straight into the dual step.
-__global__ void __launch_bounds__(FTHREADS) k_rowsC1024(Params<float> P, const float2 *__restrict__ spec,
-                                                        float *__restrict__ phi, float *__restrict__ phit,
-                                                        const float2 *__restrict__ twN,
-                                                        const float2 *__restrict__ twM) {
+// rows-C for nx = 1024 (M = 512 = 2 * 4^4), persistent with a TMA pipeline: a block
+// takes the tiles (4 rows of one slice) blockIdx.x, +gridDim.x, ..., and the spectrum
+// of the tile two ahead is loaded by TMA (three 3D boxes of 172 kx rows x 4 complex,
+// the layout of the spectrum kept: [kx][4]) into the stage buffer the current tile
+// has just released, so the 32-byte gathers are in flight during the transform.
+// The inverse split feeds the first (radix-2, span 1) stage directly in registers,
+// three radix-4 stages (spans 2, 8, 32) run in shared memory, and the last (span
+// 128) runs in registers, whose outputs -- complex positions i + 128 q, i.e.
+// x = 2 (i + 128 q) + {0,1} -- go straight into the dual step.  A stage wait that
+// gives up sets *err and the block returns (after a bounded wait for its copies).
+constexpr int RC_BOX = 172;                    // kx rows per TMA box: 3 boxes >= 513 rows
+constexpr int RC_ROWS = 3 * RC_BOX;            // rows per stage buffer (rows >= nkx are zero-filled)
+constexpr uint32_t RC_TX = RC_ROWS * FH * 8;   // bytes per stage (whole boxes, fill included)
+constexpr int RC_WAIT = 1 << 20;               // polls before a stage wait gives up
+
+__global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, const __grid_constant__ CUtensorMap tmap,
+                                                           float *__restrict__ phi, float *__restrict__ phit,
+                                                           const float2 *__restrict__ twN,
+                                                           const float2 *__restrict__ twM, int *__restrict__ err) {
     constexpr int LOG2M = 9, M = 512, NX = 1024;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *st = reinterpret_cast<float2 *>(smem_raw);      // staging [FH][M+1]
     constexpr int PN = SeqLayout<LOG2M, 2>::PN;           // padded rows (stockham.cuh)
-    float2 *fa = st + FH * (M + 1);                          // [FH][PN]
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // TMA destinations 128-byte aligned (the launch adds 128 bytes of slack)
+    unsigned char *sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    float2 *stg = reinterpret_cast<float2 *>(sm);           // [2][RC_ROWS][FH]
+    float2 *fa = stg + 2 * RC_ROWS * FH;                     // [FH][PN]
     float2 *fb = fa + FH * PN;                               // [FH][PN]
-    const int ny = P.ny;
-    const int y0 = blockIdx.x * FH;
-    const int l = blockIdx.y;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(fb + FH * PN);   // [2]
+    const int nyb = P.ny / FH, ntiles = nyb * P.nt, G = gridDim.x;
     const int t = threadIdx.x;
-    const int64_t base = (int64_t)l * P.S + (int64_t)y0 * NX;
-    // phi at the positions this thread updates: rows 2h, 2h+1 (h = t / 128), x = 2(i + 128 q) + {0, 1}
+    auto issue = [&](int tile, int buf) {                    // one thread
+        const int l = tile / nyb, yb = tile - l * nyb;
+        mbar_arrive_expect_tx(bar + buf, RC_TX);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            tma_load_3d(stg + (buf * RC_ROWS + b * RC_BOX) * FH, &tmap, 2 * FH * yb, b * RC_BOX, l, bar + buf);
+    };
+    if (t == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (t == 0) {
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if ((int)blockIdx.x + G < ntiles) issue(blockIdx.x + G, 1);
+    }
+    // the positions this thread updates: rows 2h, 2h+1 (h = t / 128), x = 2(i + 128 q) + {0, 1}
     const int h = t >> 7, i = t & 127;
-    float2 ph[2][4];
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            ph[rr][q] = __ldg(reinterpret_cast<const float2 *>(phi + base + (int64_t)(2 * h + rr) * NX) + i + 128 * q);
-    // gather [kx][y0..y0+FH)
-    const float4 *src = reinterpret_cast<const float4 *>(spec + (int64_t)l * P.nkx * ny + y0);
-    for (int idx = t; idx < (M + 1) * 2; idx += blockDim.x) {
-        const int k = idx >> 1, hh = idx & 1;
-        const float4 v = __ldg(src + (int64_t)k * (ny / 2) + hh);
-        st[(2 * hh) * (M + 1) + k] = make_float2(v.x, v.y);
-        st[(2 * hh + 1) * (M + 1) + k] = make_float2(v.z, v.w);
-    }
-    __syncthreads();
-    // inverse split (Z_k = E_k + i O_k) for k = t and t + 256, then the radix-2 stage
-    // (span 1: outputs 2t, 2t+1) in registers
-    {
-        const float2 w0 = twN[t], w1 = twN[t + 256];
-#pragma unroll
-        for (int rr = 0; rr < FH; ++rr) {
-            const float2 *X = st + rr * (M + 1);
-            const float2 z0 = irfft_merge(X[t], X[M - t], w0);
-            const float2 z1 = irfft_merge(X[t + 256], X[256 - t], w1);
-            *reinterpret_cast<float4 *>(fa + rr * PN + padx(2 * t)) =
-                make_float4(z0.x + z1.x, z0.y + z1.y, z0.x - z1.x, z0.y - z1.y);
-        }
-    }
-    __syncthreads();
-    const float2 *res = stockham_r4_range<LOG2M, true, 2, 128, FH, FTHREADS, 2>(fa, fb, twM);
     const float s = P.dual_scale;
+    const float2 w0 = twN[t], w1 = twN[t + 256];
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += G, ++it) {
+        const int buf = it & 1;
+        const int l = tile / nyb, y0 = (tile - l * nyb) * FH;
+        const int64_t base = (int64_t)l * P.S + (int64_t)y0 * NX;
+        float2 ph[2][4];
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        const float2 *r = res + (2 * h + rr) * PN;
-        float2 x0 = r[padx(i)];
-        float2 x1 = cmulconj(r[padx(i + 128)], twM[126 + i]);       // staged block of span 128
-        float2 x2 = cmulconj(r[padx(i + 256)], twM[126 + 128 + i]);
-        float2 x3 = cmulconj(r[padx(i + 384)], twM[126 + 256 + i]);
-        dft4<true>(x0, x1, x2, x3);
-        const float2 z[4] = {x0, x1, x2, x3};
-        float2 *p2 = reinterpret_cast<float2 *>(phi + base + (int64_t)(2 * h + rr) * NX);
-        float2 *t2 = reinterpret_cast<float2 *>(phit + base + (int64_t)(2 * h + rr) * NX);
+        for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float2 pn = ph[rr][q];
-            pn.x += s * z[q].x;
-            pn.y += s * z[q].y;
-            p2[i + 128 * q] = pn;
-            t2[i + 128 * q] = make_float2(pn.x + s * z[q].x, pn.y + s * z[q].y);
+            for (int q = 0; q < 4; ++q)
+                ph[rr][q] = __ldg(reinterpret_cast<const float2 *>(phi + base + (int64_t)(2 * h + rr) * NX) + i + 128 * q);
+        const bool ok = mbar_wait_bounded(bar + buf, (it >> 1) & 1, RC_WAIT);
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) {
+                atomicExch(err, 1);
+                // the other stage's copy, if one was issued, before the block leaves
+                if (tile + G < ntiles) mbar_wait_bounded(bar + (buf ^ 1), ((it + 1) >> 1) & 1, RC_WAIT);
+                mbar_wait_bounded(bar + buf, (it >> 1) & 1, RC_WAIT);
+            }
+            return;
+        }
+        // inverse split (Z_k = E_k + i O_k) for k = t and t + 256, then the radix-2 stage
+        // (span 1: outputs 2t, 2t+1) in registers; stage rows are [kx][4 rows]
+        {
+            const float4 *S4 = reinterpret_cast<const float4 *>(stg + buf * RC_ROWS * FH);
+            const float4 xa[2] = {S4[2 * t], S4[2 * t + 1]};
+            const float4 xb[2] = {S4[2 * (M - t)], S4[2 * (M - t) + 1]};
+            const float4 xc[2] = {S4[2 * (t + 256)], S4[2 * (t + 256) + 1]};
+            const float4 xd[2] = {S4[2 * (256 - t)], S4[2 * (256 - t) + 1]};
+#pragma unroll
+            for (int rr = 0; rr < FH; ++rr) {
+                const int hh = rr >> 1;
+                const bool hi = rr & 1;
+                const float2 A = hi ? make_float2(xa[hh].z, xa[hh].w) : make_float2(xa[hh].x, xa[hh].y);
+                const float2 B = hi ? make_float2(xb[hh].z, xb[hh].w) : make_float2(xb[hh].x, xb[hh].y);
+                const float2 C = hi ? make_float2(xc[hh].z, xc[hh].w) : make_float2(xc[hh].x, xc[hh].y);
+                const float2 D = hi ? make_float2(xd[hh].z, xd[hh].w) : make_float2(xd[hh].x, xd[hh].y);
+                const float2 z0 = irfft_merge(A, B, w0);
+                const float2 z1 = irfft_merge(C, D, w1);
+                *reinterpret_cast<float4 *>(fa + rr * PN + padx(2 * t)) =
+                    make_float4(z0.x + z1.x, z0.y + z1.y, z0.x - z1.x, z0.y - z1.y);
+            }
+        }
+        __syncthreads();
+        if (t == 0 && tile + 2 * G < ntiles) {            // the stage buffer is free: next-but-one tile
+            fence_proxy_async_smem();
+            issue(tile + 2 * G, buf);
+        }
+        const float2 *res = stockham_r4_range<LOG2M, true, 2, 128, FH, FTHREADS, 2>(fa, fb, twM);
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const float2 *r = res + (2 * h + rr) * PN;
+            float2 x0 = r[padx(i)];
+            float2 x1 = cmulconj(r[padx(i + 128)], twM[126 + i]);       // staged block of span 128
+            float2 x2 = cmulconj(r[padx(i + 256)], twM[126 + 128 + i]);
+            float2 x3 = cmulconj(r[padx(i + 384)], twM[126 + 256 + i]);
+            dft4<true>(x0, x1, x2, x3);
+            const float2 z[4] = {x0, x1, x2, x3};
+            float2 *p2 = reinterpret_cast<float2 *>(phi + base + (int64_t)(2 * h + rr) * NX);
+            float2 *t2 = reinterpret_cast<float2 *>(phit + base + (int64_t)(2 * h + rr) * NX);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 pn = ph[rr][q];
+                pn.x += s * z[q].x;
+                pn.y += s * z[q].y;
+                p2[i + 128 * q] = pn;
+                t2[i + 128 * q] = make_float2(pn.x + s * z[q].x, pn.y + s * z[q].y);
+            }
         }
     }
 }
 
 static size_t smem_rowsC1024() {
-    return (size_t)FH * (512 + 1) * 8 + 2 * (size_t)FH * SeqLayout<9, 2>::PN * 8;
+    return 128 + (size_t)2 * RC_ROWS * FH * 8 + 2 * (size_t)FH * SeqLayout<9, 2>::PN * 8 + 2 * sizeof(uint64_t);
 }
 
 // ---------------------------------------------------------------------------
@@ -717,7 +768,8 @@ static size_t al(size_t v) { return (v + 255) & ~size_t(255); }
 
 size_t fused2d_workspace_bytes(int64_t nx, int64_t ny, int64_t nt) {
     const int64_t nkx = nx / 2 + 1;
-    return al(nt * nkx * ny * 8) +             // spectrum [l][kx][y]
+    return al(4) +                             // error flag of the pipelined rows-C
+           al(nt * nkx * ny * 8) +             // spectrum [l][kx][y]
            al(nx / 2 * 8) + al(ny * 8) +       // twiddles W_M, W_ny
            al(nx / 2 * 8) +                    // radix-8 twiddles W_M
            al(nkx * ny * 4);                   // theta [kx][ky]
@@ -726,6 +778,7 @@ size_t fused2d_workspace_bytes(int64_t nx, int64_t ny, int64_t nt) {
 void fused2d_layout(Fused2D *f, void *ws, int64_t nx, int64_t ny, int64_t nt) {
     const int64_t nkx = nx / 2 + 1;
     char *p = (char *)ws;
+    f->err = (int *)p; p += al(4);
     f->spec = (float2 *)p; p += al(nt * nkx * ny * 8);
     f->twM = (float2 *)p; p += al(nx / 2 * 8);
     f->twY = (float2 *)p; p += al(ny * 8);
@@ -761,6 +814,33 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
     if (ec != cudaSuccess) return ec;
     fused2d_layout(f, ws, P.nx, P.ny, P.nt);
     f->twN = (const float2 *)twx;
+    {
+        int dev = 0;
+        ec = cudaGetDevice(&dev);
+        if (ec == cudaSuccess) ec = cudaDeviceGetAttribute(&f->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (ec == cudaSuccess) ec = cudaMemset(f->err, 0, sizeof(int));
+        if (ec != cudaSuccess) return ec;
+    }
+    if (P.nx == 1024) {
+        // the spectrum as a 3D float32 tensor [nt][nkx][2 ny] for rows-C's TMA boxes
+        // of 4 complex (8 floats) x RC_BOX kx rows x 1 slice
+        typedef CUresult (*encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                      const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                      CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                      CUtensorMapFloatOOBfill);
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        ec = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (ec != cudaSuccess) return ec;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        const cuuint64_t dims[3] = {(cuuint64_t)(2 * P.ny), (cuuint64_t)P.nkx, (cuuint64_t)P.nt};
+        const cuuint64_t strides[2] = {(cuuint64_t)(2 * P.ny * 4), (cuuint64_t)P.nkx * (cuuint64_t)(2 * P.ny * 4)};
+        const cuuint32_t box[3] = {2 * FH, RC_BOX, 1}, estr[3] = {1, 1, 1};
+        const CUresult r = ((encode_fn)fn)(&f->tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f->spec, dims, strides, box,
+                                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
     f->tc = P.nt >= 64 ? 32 : (P.nt >= 8 ? 8 : 2);
     switch (ilog2i(P.nx / 2)) {
     case 7: return attr_rows<7>();
@@ -832,8 +912,9 @@ cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s) {
 
 cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float *phit, cudaStream_t s) {
     if (P.nx == 1024) {
-        dim3 grid((unsigned)(P.ny / FH), (unsigned)P.nt);
-        k_rowsC1024<<<grid, FTHREADS, smem_rowsC1024(), s>>>(P, f->spec, phi, phit, f->twN, f->twM);
+        const int64_t ntiles = (int64_t)(P.ny / FH) * P.nt;
+        const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)f->nsm * 3);
+        k_rowsC1024<<<grid, FTHREADS, smem_rowsC1024(), s>>>(P, f->tmC, phi, phit, f->twN, f->twM, f->err);
         return cudaGetLastError();
     }
     switch (ilog2i(P.nx / 2)) {
