@@ -187,6 +187,14 @@ pdhg_status pdhg_stage_times(pdhg_handle *h, double ms[PDHG_NUM_STAGES],
  * launches.  enable = 0 turns graphs off; the fused path never uses them. */
 pdhg_status pdhg_set_graphs(pdhg_handle *h, int32_t enable);
 
+/* Budget, in nanoseconds, of each bounded device wait (the TMA stage waits of the
+ * fused path's nx = 1024 rows-C kernel; default 1e9).  A wait that runs out sets a
+ * device flag, its block drains its copies in flight and returns, and the next
+ * residual evaluation returns PDHG_ERR_TIMEOUT (the state is then invalid; the
+ * CUDA context stays usable).  ns = 0 gives up at once: the host-side way to
+ * exercise that path.  No effect on handles without bounded waits. */
+pdhg_status pdhg_set_wait_budget(pdhg_handle *h, uint64_t ns);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *pdhg_last_error(void);
 

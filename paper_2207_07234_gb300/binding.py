@@ -31,7 +31,8 @@ STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_r
 # every symbol include/pdhg.h declares
 EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_stream", "pdhg_iterate",
            "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_info", "pdhg_launch_count",
-           "pdhg_set_profiling", "pdhg_stage_times", "pdhg_set_graphs", "pdhg_last_error",
+           "pdhg_set_profiling", "pdhg_stage_times", "pdhg_set_graphs", "pdhg_set_wait_budget",
+           "pdhg_last_error",
            "pdhg_refine_workspace_size",
            "pdhg_solve_refine", "pdhg_one_step_workspace_size", "pdhg_solve_one_step",
            "pdhg_gradient_workspace_size", "pdhg_solve_gradient", "pdhg_mixed_workspace_size",
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
         "pdhg_set_profiling": [vp, i32],
         "pdhg_stage_times": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
         "pdhg_set_graphs": [vp, i32],
+        "pdhg_set_wait_budget": [vp, ctypes.c_uint64],
         "pdhg_refine_workspace_size": [P, G, S, i32, ctypes.POINTER(ctypes.c_size_t)],
         "pdhg_solve_refine": [P, G, S, i32, ctypes.POINTER(i64), ctypes.c_double, i32, i32, vp, ctypes.c_size_t,
                               vp, ctypes.POINTER(vp), ctypes.POINTER(i64)],
@@ -235,6 +237,10 @@ class Solver:
 
     def set_graphs(self, on=True):
         _check(load().pdhg_set_graphs(self.h, int(bool(on))))
+
+    def set_wait_budget(self, ns):
+        """Budget (ns) of each bounded device wait; 0 forces the timeout path."""
+        _check(load().pdhg_set_wait_budget(self.h, int(ns)))
 
     def stage_times(self):
         ms = (ctypes.c_double * 8)()

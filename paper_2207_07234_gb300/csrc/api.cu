@@ -1567,6 +1567,12 @@ extern "C" pdhg_status pdhg_set_graphs(pdhg_handle *h, int32_t enable) {
     return PDHG_OK;
 }
 
+extern "C" pdhg_status pdhg_set_wait_budget(pdhg_handle *h, uint64_t ns) {
+    if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
+    if (h->G.fused) h->fused.wait_ns = ns;
+    return PDHG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Mixed-precision solve: Algorithm 1 in float32 (the fused path where it applies)
 // until Res reaches tol or stops falling (float32 rounding floor), then the state

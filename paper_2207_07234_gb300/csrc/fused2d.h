@@ -18,7 +18,10 @@ struct Fused2D {
     const float2 *twN;       // W_nx^k, k <= nx/2 (the plain path's table)
     int tc;                  // time slices per rows-R block
     int nsm;                 // multiprocessors of the device (persistent rows-C grid)
+    uint64_t wait_ns;        // budget of each bounded device wait
 };
+
+constexpr uint64_t FUSED2D_WAIT_NS_DEFAULT = 1000000000ull;   // 1 s
 
 bool fused2d_supported(int dims, int space, int time, int prec, int64_t nx, int64_t ny, int64_t nt, double nu);
 size_t fused2d_workspace_bytes(int64_t nx, int64_t ny, int64_t nt);

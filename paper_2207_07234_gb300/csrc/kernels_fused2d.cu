@@ -631,16 +631,18 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC(Params<float> P, const float
 // three radix-4 stages (spans 2, 8, 32) run in shared memory, and the last (span
 // 128) runs in registers, whose outputs -- complex positions i + 128 q, i.e.
 // x = 2 (i + 128 q) + {0,1} -- go straight into the dual step.  A stage wait that
-// gives up sets *err and the block returns (after a bounded wait for its copies).
+// gives up after wait_ns sets *err and the block returns (after a bounded wait for
+// its copies in flight).
 constexpr int RC_BOX = 172;                    // kx rows per TMA box: 3 boxes >= 513 rows
 constexpr int RC_ROWS = 3 * RC_BOX;            // rows per stage buffer (rows >= nkx are zero-filled)
 constexpr uint32_t RC_TX = RC_ROWS * FH * 8;   // bytes per stage (whole boxes, fill included)
-constexpr int RC_WAIT = 1 << 20;               // polls before a stage wait gives up
+constexpr uint64_t RC_DRAIN_NS = 1000000000ull; // budget of the waits for copies in flight on exit
 
 __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, const __grid_constant__ CUtensorMap tmap,
                                                            float *__restrict__ phi, float *__restrict__ phit,
                                                            const float2 *__restrict__ twN,
-                                                           const float2 *__restrict__ twM, int *__restrict__ err) {
+                                                           const float2 *__restrict__ twM, int *__restrict__ err,
+                                                           uint64_t wait_ns) {
     constexpr int LOG2M = 9, M = 512, NX = 1024;
     constexpr int PN = SeqLayout<LOG2M, 2>::PN;           // padded rows (stockham.cuh)
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -684,13 +686,13 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 ph[rr][q] = __ldg(reinterpret_cast<const float2 *>(phi + base + (int64_t)(2 * h + rr) * NX) + i + 128 * q);
-        const bool ok = mbar_wait_bounded(bar + buf, (it >> 1) & 1, RC_WAIT);
+        const bool ok = mbar_wait_bounded(bar + buf, (it >> 1) & 1, wait_ns);
         if (__syncthreads_or(!ok)) {
             if (t == 0) {
                 atomicExch(err, 1);
-                // the other stage's copy, if one was issued, before the block leaves
-                if (tile + G < ntiles) mbar_wait_bounded(bar + (buf ^ 1), ((it + 1) >> 1) & 1, RC_WAIT);
-                mbar_wait_bounded(bar + buf, (it >> 1) & 1, RC_WAIT);
+                // this stage's copy and the other stage's, if one was issued, before the block leaves
+                mbar_wait_bounded(bar + buf, (it >> 1) & 1, RC_DRAIN_NS);
+                if (tile + G < ntiles) mbar_wait_bounded(bar + (buf ^ 1), ((it + 1) >> 1) & 1, RC_DRAIN_NS);
             }
             return;
         }
@@ -814,6 +816,7 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
     if (ec != cudaSuccess) return ec;
     fused2d_layout(f, ws, P.nx, P.ny, P.nt);
     f->twN = (const float2 *)twx;
+    f->wait_ns = FUSED2D_WAIT_NS_DEFAULT;
     {
         int dev = 0;
         ec = cudaGetDevice(&dev);
@@ -914,7 +917,8 @@ cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float 
     if (P.nx == 1024) {
         const int64_t ntiles = (int64_t)(P.ny / FH) * P.nt;
         const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)f->nsm * 3);
-        k_rowsC1024<<<grid, FTHREADS, smem_rowsC1024(), s>>>(P, f->tmC, phi, phit, f->twN, f->twM, f->err);
+        k_rowsC1024<<<grid, FTHREADS, smem_rowsC1024(), s>>>(P, f->tmC, phi, phit, f->twN, f->twM, f->err,
+                                                              f->wait_ns);
         return cudaGetLastError();
     }
     switch (ilog2i(P.nx / 2)) {

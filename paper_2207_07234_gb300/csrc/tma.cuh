@@ -39,12 +39,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Polls the barrier until the phase with the given parity has completed, at most
-// `limit` times; false when it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int limit) {
-    for (int n = 0; n < limit; ++n)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Polls the barrier until the phase with the given parity has completed or
+// budget_ns nanoseconds have passed; false when it gave up.  A budget of 0 gives up
+// at once (the forced tiny budget that exercises the timeout path).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t budget_ns) {
+    if (budget_ns == 0) return false;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > budget_ns) return false;
+    return true;
 }
 
 // Orders this thread's earlier generic-proxy shared-memory accesses before later

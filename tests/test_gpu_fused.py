@@ -148,3 +148,19 @@ def test_full_size_sampled(B):
     r0 = u64[0] - p.u0
     a = np.sqrt(p.ht * p.hx * p.hy * np.sum(R * R) + p.hx * p.hy * np.sum(r0 * r0))
     assert abs(res2[0] - a) <= 1e-4 * a
+
+
+def test_wait_budget_timeout_is_reported(B):
+    """The bounded TMA stage waits of rows-C (nx = 1024): with a zero budget every wait
+    gives up, the blocks drain their copies and return, and the next residual check
+    reports PDHG_ERR_TIMEOUT; the CUDA context stays usable for the next handle."""
+    p = W.burgers_2d(n=1024, nt=3).replace(tau_u=0.4, tau_phi=0.4, tau_u0=0.1, tau_lambda=0.99)
+    with B.Solver(p, precision="fp32", path="fused") as s:
+        s.set_wait_budget(0)
+        with pytest.raises(B.PdhgError) as e:
+            s.iterate(2, tol=0.0, check_every=1)
+        assert e.value.status == -6
+    with B.Solver(p, precision="fp32", path="fused") as s:
+        s.set_wait_budget(10**9)
+        s.iterate(2, tol=0.0, check_every=1)
+        assert np.all(np.isfinite(s.residual()))
