@@ -50,15 +50,59 @@ __device__ void fft_radix2(C *z, int log2n, int batch, int cs, int is, const C *
 // The same in-place DIT transform for one sequence of length n = 2^log2n with
 // twiddles grouped by stage: stage s (half-span hs = 2^s) reads tw[(hs - 1) + pos]
 // = W_n^{pos n / (2 hs)}, so a warp's lanes read consecutive entries.  Stages run
-// in pairs: the elements b, b + hs, b + 2 hs, b + 3 hs of one group pass through
-// stage s (pairs (b, b+hs), (b+2hs, b+3hs), twiddle W_{2hs}^pos) and stage s+1
-// (pairs (b, b+2hs), (b+hs, b+3hs), twiddles W_{4hs}^pos, W_{4hs}^{pos+hs}) in
-// registers, which halves the shared-memory passes and barriers.
+// in threes: the elements b + j hs (j = 0..7) of one group pass through stage s
+// (pairs (j, j+1), j even, twiddle W_{2hs}^pos), stage s+1 (pairs (j, j+2),
+// twiddles W_{4hs}^pos for j = 0, 4 and W_{4hs}^{pos+hs} for j = 1, 5) and stage s+2
+// (pairs (j, j+4), twiddle W_{8hs}^{pos + j hs}) in registers, which cuts the
+// shared-memory passes and barriers to a third; one or two leftover stages run as
+// a pair or alone.
 template <typename C>
 __device__ void fft_radix2_staged(C *z, int log2n, const C *__restrict__ tw, bool inverse) {
     const int n = 1 << log2n;
     int s = 0;
-    for (; s + 1 < log2n; s += 2) {
+    for (; s + 2 < log2n; s += 3) {
+        const int hs = 1 << s;
+        for (int g = threadIdx.x; g < (n >> 3); g += blockDim.x) {
+            const int pos = g & (hs - 1);
+            const int b = ((g >> s) << (s + 3)) + pos;
+            C w1 = tw[(hs - 1) + pos], wa = tw[(2 * hs - 1) + pos], wb = tw[(2 * hs - 1) + pos + hs];
+            C wc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) wc[j] = tw[(4 * hs - 1) + pos + j * hs];
+            if (inverse) {
+                w1.y = -w1.y; wa.y = -wa.y; wb.y = -wb.y;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wc[j].y = -wc[j].y;
+            }
+            C a[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] = z[b + j * hs];
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+                const C t = cmul(w1, a[j + 1]);
+                a[j + 1] = csub(a[j], t);
+                a[j] = cadd(a[j], t);
+            }
+#pragma unroll
+            for (int j0 = 0; j0 < 8; j0 += 4) {
+                const C t0 = cmul(wa, a[j0 + 2]), t1 = cmul(wb, a[j0 + 3]);
+                a[j0 + 2] = csub(a[j0], t0);
+                a[j0] = cadd(a[j0], t0);
+                a[j0 + 3] = csub(a[j0 + 1], t1);
+                a[j0 + 1] = cadd(a[j0 + 1], t1);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const C t = cmul(wc[j], a[j + 4]);
+                a[j + 4] = csub(a[j], t);
+                a[j] = cadd(a[j], t);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) z[b + j * hs] = a[j];
+        }
+        __syncthreads();
+    }
+    if (s + 1 < log2n) {                    // two leftover stages: one pair
         const int hs = 1 << s;
         for (int g = threadIdx.x; g < (n >> 2); g += blockDim.x) {
             const int pos = g & (hs - 1);
@@ -75,8 +119,9 @@ __device__ void fft_radix2_staged(C *z, int log2n, const C *__restrict__ tw, boo
             z[b + 3 * hs] = csub(c1, u3);
         }
         __syncthreads();
+        s += 2;
     }
-    if (s < log2n) {                        // odd log2n: one last single stage
+    if (s < log2n) {                        // one leftover stage
         const int hs = 1 << s;
         for (int k = threadIdx.x; k < (n >> 1); k += blockDim.x) {
             const int pos = k & (hs - 1);
