@@ -118,9 +118,10 @@ __device__ __forceinline__ T time_R(const Params<T> &P, const T *u, int64_t S, i
     return r;
 }
 
-// Bluestein core on z (length L, shared memory): on entry z[bitrev(n)] = a_n; on
-// exit z_k = L conj((a * b)_k), the circular convolution with the chirp filter b,
-// via FFT(a), the product with FFT(b), and a second forward FFT of its conjugate.
+// Bluestein core on z (length L, shared memory, blu_swz layout): on entry
+// z[bitrev(n)] = a_n; on exit z_k = L conj((a * b)_k), the circular convolution
+// with the chirp filter b, via FFT(a), the product with FFT(b), and a second
+// forward FFT of its conjugate.
 template <typename T>
 __device__ __forceinline__ void bluestein_core(const Params<T> &P, typename Cplx<T>::type *z) {
     typedef typename Cplx<T>::type C;
@@ -130,9 +131,10 @@ __device__ __forceinline__ void bluestein_core(const Params<T> &P, typename Cplx
     for (int i = threadIdx.x; i < L; i += blockDim.x) {       // Y = conj(A B^), bit-reversed in place
         const int j = bitrev(i, lgL);
         if (i > j) continue;
-        const C a = cconj(cmul(z[i], bh[i])), b = cconj(cmul(z[j], bh[j]));
-        z[j] = a;
-        z[i] = b;
+        const int si = blu_swz(i, lgL), sj = blu_swz(j, lgL);
+        const C a = cconj(cmul(z[si], bh[i])), b = cconj(cmul(z[sj], bh[j]));
+        z[sj] = a;
+        z[si] = b;
     }
     __syncthreads();
     fft_radix2_staged(z, lgL, tw, false);
@@ -194,7 +196,7 @@ __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T 
                          time_R(P, u + row + x, S, l + 1);
                 v = cmulconj(mk<C, T>(r, r2), cc[x]);
             }
-            z[bitrev(x, lgL)] = v;
+            z[blu_swz(bitrev(x, lgL), lgL)] = v;
         }
         __syncthreads();
         bluestein_core(P, z);
@@ -204,7 +206,7 @@ __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T 
         const T h = T(0.5) / T(L);
         for (int k = threadIdx.x; k < P.nkx; k += blockDim.x) {
             const int km = k == 0 ? 0 : N - k;
-            const C wk = cconj(cmul(cc[k], z[k])), wm = cmul(cc[km], z[km]);     // W_k L, conj(W_{N-k}) L
+            const C wk = cconj(cmul(cc[k], z[blu_swz(k, lgL)])), wm = cmul(cc[km], z[blu_swz(km, lgL)]);     // W_k L, conj(W_{N-k}) L
             out[k] = cscale(cadd(wk, wm), h);
             if (two) {
                 const C d = csub(wk, wm);                                      // (W_k - conj W_{N-k}) L
@@ -389,14 +391,14 @@ __device__ __forceinline__ void dual_irfft_block(const Params<T> &P, const typen
                 }
                 v = cconj(cmul(Wk, cc[k]));
             }
-            z[bitrev(k, lgL)] = v;
+            z[blu_swz(bitrev(k, lgL), lgL)] = v;
         }
         __syncthreads();
         bluestein_core(P, z);
         const T sc = P.blu_scale / (T(L) * T(N));
         const int64_t off = (int64_t)l * P.S + (int64_t)line0 * N;
         for (int x = threadIdx.x; x < N; x += blockDim.x) {
-            const C w = cmul(cc[x], z[x]);
+            const C w = cmul(cc[x], z[blu_swz(x, lgL)]);
             const T dz = sc * w.x;
             const int64_t i = off + x;
             const T pn = phi[i] + dz;
