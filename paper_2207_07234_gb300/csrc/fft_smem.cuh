@@ -18,30 +18,69 @@ __device__ __forceinline__ int bitrev(int i, int log2n) {
 
 // In-place decimation-in-time radix-2 FFT of `batch` sequences of length
 // n = 2^log2n held in shared memory in bit-reversed order.  Element i of
-// sequence c lives at z[c*cs + i*is].  tw[j*tws] = W_n^j (j < n/2).
-// inverse: conjugate twiddles.  Ends with __syncthreads().
+// sequence c lives at z[c*cs + i*is]: contiguous sequences (is = 1) or
+// interleaved ones (cs = 1, is = batch; then consecutive threads take consecutive
+// sequences at the same element, so a warp's accesses stay contiguous).
+// tw[j*tws] = W_n^j (j < n/2); inverse: conjugate twiddles.  Stages run in pairs
+// in registers (the elements b, b + hs, b + 2 hs, b + 3 hs of one group through
+// stages s and s+1), halving the shared-memory passes and barriers; an odd last
+// stage runs alone.  Ends with __syncthreads().
 template <typename C>
 __device__ void fft_radix2(C *z, int log2n, int batch, int cs, int is, const C *__restrict__ tw,
                            int tws, bool inverse) {
-    const int n = 1 << log2n;
-    const int half = n >> 1;
-    const int total = half * batch;
-    for (int s = 0; s < log2n; ++s) {
-        const int hs = 1 << s;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            int c = t / half;
-            int k = t - c * half;
-            int pos = k & (hs - 1);
-            int i0 = ((k >> s) << (s + 1)) + pos;
-            int i1 = i0 + hs;
+    const bool inter = is != 1;
+    const bool pow2b = (batch & (batch - 1)) == 0;
+    const int lb = __ffs(batch) - 1;
+    // thread index t -> (sequence c, group g) with lq = log2(groups per sequence)
+    auto split = [&](int t, int lq, int &c, int &g) {
+        if (!inter) {
+            c = t >> lq;
+            g = t & ((1 << lq) - 1);
+        } else if (pow2b) {
+            c = t & (batch - 1);
+            g = t >> lb;
+        } else {
+            g = t / batch;
+            c = t - g * batch;
+        }
+    };
+    int s = 0;
+    for (; s + 1 < log2n; s += 2) {
+        const int hs = 1 << s, lq = log2n - 2;
+        for (int t = threadIdx.x; t < (batch << lq); t += blockDim.x) {
+            int c, g;
+            split(t, lq, c, g);
+            const int pos = g & (hs - 1);
+            const int b = ((g >> s) << (s + 2)) + pos;
+            C w1 = tw[(pos << (log2n - s - 1)) * tws];
+            C wa = tw[(pos << (log2n - s - 2)) * tws], wb = tw[((pos + hs) << (log2n - s - 2)) * tws];
+            if (inverse) { w1.y = -w1.y; wa.y = -wa.y; wb.y = -wb.y; }
+            C *zc = z + c * cs;
+            const C a0 = zc[b * is], a1 = zc[(b + hs) * is], a2 = zc[(b + 2 * hs) * is], a3 = zc[(b + 3 * hs) * is];
+            const C t1 = cmul(w1, a1), t3 = cmul(w1, a3);
+            const C c0 = cadd(a0, t1), c1 = csub(a0, t1), c2 = cadd(a2, t3), c3 = csub(a2, t3);
+            const C u2 = cmul(wa, c2), u3 = cmul(wb, c3);
+            zc[b * is] = cadd(c0, u2);
+            zc[(b + 2 * hs) * is] = csub(c0, u2);
+            zc[(b + hs) * is] = cadd(c1, u3);
+            zc[(b + 3 * hs) * is] = csub(c1, u3);
+        }
+        __syncthreads();
+    }
+    if (s < log2n) {
+        const int hs = 1 << s, lq = log2n - 1;
+        for (int t = threadIdx.x; t < (batch << lq); t += blockDim.x) {
+            int c, k;
+            split(t, lq, c, k);
+            const int pos = k & (hs - 1);
+            const int i0 = ((k >> s) << (s + 1)) + pos;
             C w = tw[(pos << (log2n - s - 1)) * tws];
             if (inverse) w.y = -w.y;
-            C *a = z + c * cs + i0 * is;
-            C *b = z + c * cs + i1 * is;
-            C tb = cmul(w, *b);
-            C ta = *a;
-            *a = cadd(ta, tb);
-            *b = csub(ta, tb);
+            C *zc = z + c * cs;
+            const C tb = cmul(w, zc[(i0 + hs) * is]);
+            const C ta = zc[i0 * is];
+            zc[i0 * is] = cadd(ta, tb);
+            zc[(i0 + hs) * is] = csub(ta, tb);
         }
         __syncthreads();
     }
