@@ -92,8 +92,8 @@ __device__ void fft_radix2(C *z, int log2n, int batch, int cs, int is, const C *
 // first term spreads the stride-8 accesses of the first stage group and the groups
 // 64 apart of the second over all banks; the second spreads the bit-reversed accesses
 // (a warp's lanes n/32 apart) of the input scatter and the pointwise pass.  A
-// half-warp then meets at most 2 distinct elements per bank where the plain layout
-// gave up to 16 (checked by enumerating every access pattern for n = 2^9 .. 2^13).
+// half-warp then meets at most 2 distinct elements per bank (3 for n = 2^9) where the
+// plain layout gave up to 16 (every access pattern enumerated for n = 2^9 .. 2^13).
 __device__ __forceinline__ int blu_swz(int p, int log2n) {
     const int h = p >> 4;
     const int sh = log2n - 8 > 3 ? log2n - 8 : 3;
