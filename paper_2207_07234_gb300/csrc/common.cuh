@@ -353,4 +353,29 @@ __device__ __forceinline__ void dgx_DT(const Params<T> &P, const T c[3], const T
     else dg1_DT(P, c, pl, pc, pr, out);
 }
 
+// ---------------------------------------------------------------------------
+// residual norms (Eq. 2.12) in double: per-block partial sums, fixed order (block
+// sum of the threads' records by warp shuffles, then over the warps)
+//   acc[0] = sum R^2, acc[1] = sum (J^T phi)^2 over l >= 1, acc[2] = sum phi R,
+//   acc[3] = sum (u^0 - u0)^2, acc[4] = sum (h_t (J^T phi)^0 + lambda)^2,
+//   acc[5] = sum lambda (u^0 - u0)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum6(double acc[6], double *out) {
+    __shared__ double red[32][6];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k) red[wid][k] = acc[k];
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < 6; ++k) {
+            double v = lane < nw ? red[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) out[k] = v;
+        }
+    }
+}
+
 }  // namespace pdhg

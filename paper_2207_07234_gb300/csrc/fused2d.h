@@ -31,6 +31,9 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
 cudaError_t fused2d_primal(const Params<float> &P, float *u, const float *phit, float *lam, float *lamt,
                            const float *u0, cudaStream_t s);
 cudaError_t fused2d_rowsR(Fused2D *f, const Params<float> &P, const float *u, cudaStream_t s);
+// residual norms: gx blocks per slice row, records at partials[(l gx + bx) * 6] (the plain check's layout)
+cudaError_t fused2d_check(const Params<float> &P, const float *u, const float *phi, const float *lam,
+                          const float *u0, double *partials, int gx, cudaStream_t s);
 cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s);
 cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float *phit, cudaStream_t s);
 

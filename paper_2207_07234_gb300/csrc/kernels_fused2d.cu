@@ -752,6 +752,144 @@ static size_t smem_rowsC1024() {
 }
 
 // ---------------------------------------------------------------------------
+// residual norms (Eq. 2.12) for the fused path: the six sums of block_sum6 for
+// slice row l = blockIdx.y, one record per block at partials[(l gx + bx) * 6],
+// the layout of the plain path's check, so the same fixed-order reduction
+// follows.  A thread owns one float4 of x and PRY rows of a tile (tiles
+// blockIdx.x, +gridDim.x, ...), slides three-row windows of u^{l+1} (the
+// equation R^l) and phi^{l-1} (the row l of J(u)^T phi) down them, and folds its
+// float32 sums of the tile's 16 values into float64.
+// ---------------------------------------------------------------------------
+template <int NX>
+__global__ void __launch_bounds__(256) k_check2d(Params<float> P, const float *__restrict__ u,
+                                                 const float *__restrict__ phi, const float *__restrict__ lam,
+                                                 const float *__restrict__ u0, double *__restrict__ partials) {
+    constexpr int V = NX / 4, TX = V < 256 ? V : 256, TY = V < 256 ? 256 / V : 1, XS = V / TX;
+    const int l = blockIdx.y, nt = P.nt, ny = P.ny;
+    const int64_t S = P.S;
+    const int xt = threadIdx.x % TX, yt = threadIdx.x / TX;
+    const int ntile = (ny / (PRY * TY)) * XS;
+    const bool lf = P.space != FD_UPWIND, bdf2 = P.time == BDF2;
+    // R^l = D(u^{l+1}) + kn u^{l+1} + kc u^l + ko u^{l-1}
+    const float kn = l < nt ? coef_new(P, l) : 0.f, kc = l < nt ? coef_cur(P, l) : 0.f;
+    const float ko = (l < nt && bdf2 && l >= 1) ? coef_old(P, l) : 0.f;
+    // (J^T phi)^l = transposed stencil of phi^{l-1} at u^l + cn phi^{l-1} + cc phi^l + co phi^{l+1}
+    const float cn = l >= 1 ? coef_new(P, l - 1) : 0.f, cc = l <= nt - 1 ? coef_cur(P, l) : 0.f;
+    const float co = (bdf2 && l + 1 <= nt - 1) ? coef_old(P, l + 1) : 0.f;
+    auto wrapy = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int x4 = xt + (tile % XS) * TX;
+        const int ya = ((tile / XS) * TY + yt) * PRY;
+        float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (l < nt) {
+            const float *un = u + (int64_t)(l + 1) * S, *uc = u + (int64_t)l * S;
+            const float *uo = u + (int64_t)(l >= 1 ? l - 1 : 0) * S, *ph = phi + (int64_t)l * S;
+            float4 up = __ldg(reinterpret_cast<const float4 *>(un + (int64_t)wrapy(ya - 1) * NX) + x4);
+            float4 v4 = __ldg(reinterpret_cast<const float4 *>(un + (int64_t)ya * NX) + x4);
+#pragma unroll
+            for (int r = 0; r < PRY; ++r) {
+                const int y = ya + r;
+                const float *row = un + (int64_t)y * NX;
+                const float4 dn = __ldg(reinterpret_cast<const float4 *>(un + (int64_t)wrapy(y + 1) * NX) + x4);
+                const float lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
+                const float rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
+                const int64_t i = (int64_t)y * NX + 4 * x4;
+                const float4 cu = __ldg(reinterpret_cast<const float4 *>(uc + i));
+                const float4 p4 = __ldg(reinterpret_cast<const float4 *>(ph + i));
+                float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ko != 0.f) o4 = __ldg(reinterpret_cast<const float4 *>(uo + i));
+                const float vr[6] = {lft, v4.x, v4.y, v4.z, v4.w, rgt};
+                const float uv[4] = {up.x, up.y, up.z, up.w}, dv[4] = {dn.x, dn.y, dn.z, dn.w};
+                const float cv[4] = {cu.x, cu.y, cu.z, cu.w}, ov[4] = {o4.x, o4.y, o4.z, o4.w};
+                const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float v = vr[e + 1];
+                    const float lx = vr[e] - 2.f * v + vr[e + 2], ly = uv[e] - 2.f * v + dv[e];
+                    float dx, dy;
+                    if (lf) {
+                        dx = 0.5f * (flux(P, vr[e + 2]) - flux(P, vr[e])) - 0.5f * P.lf_a * lx;
+                        dy = 0.5f * (flux(P, dv[e]) - flux(P, uv[e])) - 0.5f * P.lf_a * ly;
+                    } else {
+                        dx = flux(P, v) - flux(P, vr[e]);
+                        dy = flux(P, v) - flux(P, uv[e]);
+                    }
+                    float rv = dx * P.inv_hx + dy * P.inv_hy + kn * v + kc * cv[e] + ko * ov[e];
+                    if (P.nu != 0.f) rv -= P.nu * (lx * P.inv_hx * P.inv_hx + ly * P.inv_hy * P.inv_hy);
+                    part[0] += rv * rv;
+                    part[2] += pv[e] * rv;
+                }
+                up = v4;
+                v4 = dn;
+            }
+        }
+        if (l >= 1) {
+            const float *pp = phi + (int64_t)(l - 1) * S, *pc = phi + (int64_t)l * S, *ul = u + (int64_t)l * S;
+            float4 pu = __ldg(reinterpret_cast<const float4 *>(pp + (int64_t)wrapy(ya - 1) * NX) + x4);
+            float4 pm = __ldg(reinterpret_cast<const float4 *>(pp + (int64_t)ya * NX) + x4);
+#pragma unroll
+            for (int r = 0; r < PRY; ++r) {
+                const int y = ya + r;
+                const float *row = pp + (int64_t)y * NX;
+                const float4 pd = __ldg(reinterpret_cast<const float4 *>(pp + (int64_t)wrapy(y + 1) * NX) + x4);
+                const float lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
+                const float rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
+                const int64_t i = (int64_t)y * NX + 4 * x4;
+                const float4 c = __ldg(reinterpret_cast<const float4 *>(ul + i));
+                float4 tc = make_float4(0.f, 0.f, 0.f, 0.f), tn = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (cc != 0.f) tc = __ldg(reinterpret_cast<const float4 *>(pc + i));
+                if (co != 0.f) tn = __ldg(reinterpret_cast<const float4 *>(pc + S + i));
+                const float pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
+                const float uv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
+                const float cv[4] = {c.x, c.y, c.z, c.w};
+                const float gv[4] = {cc * tc.x + co * tn.x, cc * tc.y + co * tn.y, cc * tc.z + co * tn.z,
+                                     cc * tc.w + co * tn.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float p0 = pr[e + 1], df = dflux(P, cv[e]);
+                    const float mx = pr[e], qx = pr[e + 2], my = uv[e], qy = dv[e];
+                    float tx, ty;
+                    if (lf) {
+                        tx = 0.5f * (df * (mx - qx) + P.lf_a * (2.f * p0 - mx - qx));
+                        ty = 0.5f * (df * (my - qy) + P.lf_a * (2.f * p0 - my - qy));
+                    } else {
+                        tx = df * (p0 - qx);
+                        ty = df * (p0 - qy);
+                    }
+                    float g = gv[e] + cn * p0 + tx * P.inv_hx + ty * P.inv_hy;
+                    if (P.nu != 0.f)
+                        g -= P.nu * ((qx - 2.f * p0 + mx) * P.inv_hx * P.inv_hx + (qy - 2.f * p0 + my) * P.inv_hy * P.inv_hy);
+                    part[1] += g * g;
+                }
+                pu = pm;
+                pm = pd;
+            }
+        } else {
+            // the initial row: u^0 - u0, and h_t (J^T phi)^0 + lambda (its time part only)
+#pragma unroll
+            for (int r = 0; r < PRY; ++r) {
+                const int64_t i = (int64_t)(ya + r) * NX + 4 * x4;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const double r0 = (double)u[i + e] - (double)u0[i + e];
+                    part[3] += (float)(r0 * r0);
+                    if (P.init == INIT_LAMBDA) {
+                        const float t0 = cc * phi[i + e] + (co != 0.f ? co * phi[S + i + e] : 0.f);
+                        const double g0 = (double)P.ht * (double)t0 + (double)lam[i + e];
+                        part[4] += (float)(g0 * g0);
+                        part[5] += (float)((double)lam[i + e] * r0);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc[k] += (double)part[k];
+    }
+    block_sum6(acc, partials + ((int64_t)l * gridDim.x + blockIdx.x) * 6);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static int ilog2i(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
@@ -890,6 +1028,19 @@ cudaError_t fused2d_primal(const Params<float> &P, float *u, const float *phit, 
     case 2048: return launch_primal2d<2048>(P, u, phit, lam, lamt, u0, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t fused2d_check(const Params<float> &P, const float *u, const float *phi, const float *lam,
+                          const float *u0, double *partials, int gx, cudaStream_t s) {
+    const dim3 grid((unsigned)gx, (unsigned)(P.nt + 1));
+    switch (P.nx) {
+    case 256: k_check2d<256><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
+    case 512: k_check2d<512><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
+    case 1024: k_check2d<1024><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
+    case 2048: k_check2d<2048><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t fused2d_rowsR(Fused2D *f, const Params<float> &P, const float *u, cudaStream_t s) {

@@ -441,29 +441,8 @@ __global__ void __launch_bounds__(256) k_dual_irfft(Params<T> P, const typename 
 }
 
 // ---------------------------------------------------------------------------
-// residual norms (Eq. 2.12) in double: per-block partial sums, fixed order
-//   acc[0] = sum R^2, acc[1] = sum (J^T phi)^2 over l >= 1, acc[2] = sum phi R,
-//   acc[3] = sum (u^0 - u0)^2, acc[4] = sum (h_t (J^T phi)^0 + lambda)^2,
-//   acc[5] = sum lambda (u^0 - u0)
+// residual norms (Eq. 2.12): the six sums of common.cuh::block_sum6, per block
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void block_sum6(double acc[6], double *out) {
-    __shared__ double red[32][6];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = 0; k < 6; ++k)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-    if (lane == 0)
-        for (int k = 0; k < 6; ++k) red[wid][k] = acc[k];
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-        for (int k = 0; k < 6; ++k) {
-            double v = lane < nw ? red[lane][k] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) out[k] = v;
-        }
-    }
-}
-
 // One thread accumulates many units of one slice (grid-stride over units) into
 // acc (type A).  check_block folds float32 partial sums of at most 16 units into
 // float64 accumulators (GB300's float64 adds would otherwise bound this kernel), so
@@ -647,6 +626,11 @@ template <typename T>
 static int64_t check_grid_x(const Params<T> &P) {
     int64_t units = is_dg(P.space) ? P.nx : P.S;
     return std::min<int64_t>((units + 255) / 256, 32);
+}
+
+cudaError_t launch_reduce6(const double *partials, int64_t nblocks, double *out, cudaStream_t s) {
+    k_reduce6<<<1, 256, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
 }
 
 template <typename T>

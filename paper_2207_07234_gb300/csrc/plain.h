@@ -22,6 +22,8 @@ cudaError_t launch_tsolve(const Params<T> &P, void *spec, const T *theta, const 
 template <typename T>
 cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *phit, const void *twx, cudaStream_t s);
 template <typename T> int64_t check_blocks(const Params<T> &P);
+// sum of nblocks records of 6 partial sums (partials[6 b + k]) into out[0..5], fixed order
+cudaError_t launch_reduce6(const double *partials, int64_t nblocks, double *out, cudaStream_t s);
 // sum_l <phi^l, Lap_h u^{l+1}> (FD) into out[0] (float64), partials as for launch_check
 template <typename T>
 cudaError_t launch_phi_lap(const Params<T> &P, const T *u, const T *phi, double *partials, double *out, cudaStream_t s);
