@@ -18,6 +18,7 @@ struct Fused2D {
     const float2 *twN;       // W_nx^k, k <= nx/2 (the plain path's table)
     int tc;                  // time slices per rows-R block
     int nsm;                 // multiprocessors of the device (persistent rows-C grid)
+    int rows_slots;          // resident rows-R blocks on the device
     uint64_t wait_ns;        // budget of each bounded device wait
 };
 
@@ -35,6 +36,8 @@ cudaError_t fused2d_rowsR(Fused2D *f, const Params<float> &P, const float *u, cu
 cudaError_t fused2d_check(const Params<float> &P, const float *u, const float *phi, const float *lam,
                           const float *u0, double *partials, int gx, cudaStream_t s);
 cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s);
+// time slices per rows-R block for nt slices, `rows` row blocks and `slots` resident blocks
+int rowsR_chunk(int nt, int rows, int slots, bool bdf2);
 cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float *phit, cudaStream_t s);
 
 }  // namespace pdhg

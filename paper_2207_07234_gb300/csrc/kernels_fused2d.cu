@@ -945,6 +945,34 @@ template <int L> static cudaError_t attr_rows() {
     return e;
 }
 
+// Resident rows-R blocks on the whole device (occupancy x multiprocessors).
+template <int L> static cudaError_t rowsR_slots(const Params<float> &P, Fused2D *f) {
+    int per_sm = 0;
+    const bool b2 = P.time == BDF2;
+    cudaError_t e = b2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowsR<L, true>, ATHREADS, smem_rowsR(L, true))
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowsR<L, false>, ATHREADS, smem_rowsR(L, false));
+    f->rows_slots = std::max(1, per_sm) * f->nsm;
+    return e;
+}
+
+// Time slices per rows-R block.  A block of tc slices marches tc + 1 steps (tc + 2
+// for BDF2); nb = rows x ceil(nt / tc) blocks run in ceil(nb / slots) rounds of the
+// resident slots, so the launch takes about rounds x (tc + 1) steps: the chunk
+// minimising that avoids a nearly empty last round (at 1024^2 x 256 on 152 SMs with
+// three blocks each, 32 slices give 4.5 rounds, 37 give 3.9).
+int rowsR_chunk(int nt, int rows, int slots, bool bdf2) {
+    if (nt < 8) return 2;
+    int best = 8;
+    double best_cost = 1e300;
+    for (int tc = 8; tc <= std::min(nt, 64); ++tc) {
+        const int64_t nb = (int64_t)rows * ((nt + tc - 1) / tc);
+        const int64_t rounds = (nb + slots - 1) / slots;
+        const double cost = (double)rounds * (tc + 1 + (bdf2 ? 1 : 0));
+        if (cost <= best_cost) { best_cost = cost; best = tc; }      // ties: the longer chunk
+    }
+    return best;
+}
+
 cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const float *twx, const float *twy,
                          const float *theta) {
     (void)twy; (void)theta;
@@ -982,14 +1010,16 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
                                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
-    f->tc = P.nt >= 64 ? 32 : (P.nt >= 8 ? 8 : 2);
     switch (ilog2i(P.nx / 2)) {
-    case 7: return attr_rows<7>();
-    case 8: return attr_rows<8>();
-    case 9: return attr_rows<9>();
-    case 10: return attr_rows<10>();
+    case 7: ec = attr_rows<7>(); if (ec == cudaSuccess) ec = rowsR_slots<7>(P, f); break;
+    case 8: ec = attr_rows<8>(); if (ec == cudaSuccess) ec = rowsR_slots<8>(P, f); break;
+    case 9: ec = attr_rows<9>(); if (ec == cudaSuccess) ec = rowsR_slots<9>(P, f); break;
+    case 10: ec = attr_rows<10>(); if (ec == cudaSuccess) ec = rowsR_slots<10>(P, f); break;
     default: return cudaErrorInvalidValue;
     }
+    if (ec != cudaSuccess) return ec;
+    f->tc = rowsR_chunk(P.nt, P.ny / FH, f->rows_slots, P.time == BDF2);
+    return cudaSuccess;
 }
 
 template <int L>

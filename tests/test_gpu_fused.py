@@ -36,8 +36,8 @@ def rel(a, b):
 
 def small_cases():
     base = dict(tau_u=0.4, tau_phi=0.4, tau_u0=0.1, tau_lambda=0.99)
-    yield W.burgers_2d(n=256, nt=70).replace(**base)                       # 3 t-chunks, ragged last
-    yield W.burgers_2d(n=256, nt=9).replace(time="bdf2", **base)            # chunks of 8, BDF2
+    yield W.burgers_2d(n=256, nt=71).replace(**base)                       # t-chunks, ragged last (71 prime)
+    yield W.burgers_2d(n=256, nt=9).replace(time="bdf2", **base)            # chunks of 8 and 1, BDF2
     yield W.burgers_2d(n=256, nt=6).replace(init="pinned", nu=0.02, **base)
     p = W.burgers_2d(n=512, nt=5).replace(**base)
     yield p.replace(ny=256, ly=np.pi, u0=np.ascontiguousarray(p.u0[:256]))   # nx != ny
