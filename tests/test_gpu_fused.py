@@ -43,6 +43,8 @@ def small_cases():
     yield p.replace(ny=256, ly=np.pi, u0=np.ascontiguousarray(p.u0[:256]))   # nx != ny
     yield W.burgers_2d(n=256, nt=7).replace(space="fd_upwind", alpha=0.0, beta=1.0, **base)
     yield W.burgers_2d(n=1024, nt=3).replace(**base)                         # the ny = 1024 column kernel
+    p = W.burgers_2d(n=1024, nt=5).replace(**base)                          # TMA rows-C with ny = 512
+    yield p.replace(ny=512, ly=np.pi, u0=np.ascontiguousarray(p.u0[:512]))
     p = W.burgers_2d(n=2048, nt=3).replace(**base)                          # nx = 2048: radix-2 + 3 radix-8
     yield p.replace(ny=256, ly=np.pi / 4, u0=np.ascontiguousarray(p.u0[:256]))
 
