@@ -293,9 +293,9 @@ pdhg_status pdhg_solve_gradient(const pdhg_problem *prob, const pdhg_grid *grid,
  * check_every iterations, or until the larger entry has not fallen by 5% over
  * the last three checks (float32's rounding floor); then the state (u, phi,
  * phit, lambda, lamt) is widened to float64 on the device and Algorithm 1 goes
- * on in float64 on the plain path to tol (checked every max(1, check_every/5)
- * iterations: from the float32 state this phase is short), within max_iters
- * iterations in all.
+ * on in float64 on the plain path to tol (from the float32 state this phase is
+ * short: checked after 1, 2, 3, 4, 6, 9, 13, ... of its iterations, the gaps
+ * growing to at most max(1, check_every/5)), within max_iters iterations in all.
  * scheme->precision is ignored.
  *
  * workspace: device, caller-owned, 256-byte aligned, size from
