@@ -1390,7 +1390,10 @@ static pdhg_status batch_tables(pdhg_batch *b) {
         const int64_t gxp = nb[TAB_PRIMAL] / (G.nt + 1), nlines = nb[TAB_ROWS] / G.nt;
         for (int64_t l = 0; l <= G.nt; ++l)
             for (int64_t x = 0; x < gxp; ++x) t[TAB_PRIMAL].push_back({i, (int32_t)x, (int32_t)l, 0});
-        for (int64_t l = 0; l < G.nt; ++l)
+        // Bluestein rows: the block of an even slice transforms that slice and the next
+        // together, so odd slices get no block
+        const int64_t lstep = G.blu_log2L ? 2 : 1;
+        for (int64_t l = 0; l < G.nt; l += lstep)
             for (int64_t x = 0; x < nlines; ++x) t[TAB_ROWS].push_back({i, (int32_t)x, (int32_t)l, 0});
         for (int64_t x = 0; x < nb[TAB_TSOLVE]; ++x) t[TAB_TSOLVE].push_back({i, (int32_t)x, 0, 0});
         for (int64_t l = 0; l <= G.nt; ++l)
