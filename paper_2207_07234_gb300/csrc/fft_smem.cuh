@@ -87,17 +87,14 @@ __device__ void fft_radix2(C *z, int log2n, int batch, int cs, int is, const C *
 }
 
 // Layout of the Bluestein work buffer (length n = 2^log2n): element p sits at
-// p ^ phi(p >> 4), an XOR within each aligned group of 16 (no extra memory), with
-// phi(h) = ((h & 7) | (bit 2 of h) << 3) ^ (h >> max(log2n - 8, 3)), low 4 bits.  The
-// first term spreads the stride-8 accesses of the first stage group and the groups
-// 64 apart of the second over all banks; the second spreads the bit-reversed accesses
-// (a warp's lanes n/32 apart) of the input scatter and the pointwise pass.  A
-// half-warp then meets at most 2 distinct elements per bank (3 for n = 2^9) where the
-// plain layout gave up to 16 (every access pattern enumerated for n = 2^9 .. 2^13).
+// p ^ (((p >> 4) ^ (p >> (log2n - 4))) & 15), an XOR within each aligned group of 16
+// (no extra memory).  The first term spreads the stride-8 accesses of the first stage
+// group over all banks; the second, the top 4 bits of p, spreads the bit-reversed
+// accesses (a warp's lanes n/32 apart) of the input scatter and the pointwise pass.  A
+// half-warp then meets at most 2 distinct elements per bank where the plain layout
+// gave up to 16 (every access pattern enumerated for n = 2^9 .. 2^13).
 __device__ __forceinline__ int blu_swz(int p, int log2n) {
-    const int h = p >> 4;
-    const int sh = log2n - 8 > 3 ? log2n - 8 : 3;
-    return p ^ ((((h & 7) | ((h & 4) << 1)) ^ (h >> sh)) & 15);
+    return p ^ (((p >> 4) ^ (p >> (log2n - 4))) & 15);
 }
 
 // The same in-place DIT transform for one sequence of length n = 2^log2n, held in

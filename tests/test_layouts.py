@@ -9,7 +9,7 @@ The kernels' index arithmetic is restated here in Python:
   free of shared-memory bank conflicts;
 * the XOR swizzle of the Bluestein work buffer (fft_smem.cuh::blu_swz) keeps the
   bit-reversed and strided accesses of the in-place transform at <= 2 distinct
-  elements per bank and half-warp (3 for L = 2^9).
+  elements per bank and half-warp.
 Banks: 32 four-byte banks; a 64-bit access is served 16 lanes at a time.
 """
 import numpy as np
@@ -165,9 +165,7 @@ def test_radix8_paddings_are_conflict_free(n):
 # --- Bluestein work buffer --------------------------------------------------------
 
 def blu_swz(p, lg):
-    h = p >> 4
-    sh = max(lg - 8, 3)
-    return p ^ ((((h & 7) | ((h & 4) << 1)) ^ (h >> sh)) & 15)
+    return p ^ (((p >> 4) ^ (p >> (lg - 4))) & 15)
 
 
 def bluestein_patterns(lg, n_points):
@@ -214,5 +212,5 @@ def test_bluestein_swizzle(lg, n_points):
             if half:
                 plain = max(plain, multiplicity(half))
                 swz = max(swz, multiplicity([blu_swz(p, lg) for p in half]))
-    assert swz <= (3 if lg == 9 else 2)
+    assert swz <= 2
     assert plain >= 8                                                      # what the swizzle removes
