@@ -606,15 +606,13 @@ template <typename T>
 static cudaError_t enqueue_check(pdhg_handle *h) {
     const Params<T> &P = params_of<T>(h);
     return stage(h, PDHG_STAGE_CHECK, 2, [&] {
-        if constexpr (sizeof(T) == 4) {
-            if (h->G.fused) {
-                const int64_t nb = check_blocks<T>(P);
-                cudaError_t e = fused2d_check(P, F<T>(h, h->u_off), F<T>(h, h->L.phi), F<T>(h, h->L.lam),
+        if (check2d_applies<T>(P)) {
+            const int64_t nb = check_blocks<T>(P);
+            cudaError_t e = launch_check2d<T>(P, F<T>(h, h->u_off), F<T>(h, h->L.phi), F<T>(h, h->L.lam),
                                               F<T>(h, h->L.u0), F<double>(h, h->L.partials),
                                               (int)(nb / (P.nt + 1)), h->stream);
-                if (e != cudaSuccess) return e;
-                return launch_reduce6(F<double>(h, h->L.partials), nb, F<double>(h, h->L.scal), h->stream);
-            }
+            if (e != cudaSuccess) return e;
+            return launch_reduce6(F<double>(h, h->L.partials), nb, F<double>(h, h->L.scal), h->stream);
         }
         return launch_check<T>(P, F<T>(h, h->u_off), F<T>(h, h->L.phi), F<T>(h, h->L.lam), F<T>(h, h->L.u0),
                                F<double>(h, h->L.partials), F<double>(h, h->L.scal), h->stream);

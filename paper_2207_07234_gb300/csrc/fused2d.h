@@ -32,9 +32,12 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
 cudaError_t fused2d_primal(const Params<float> &P, float *u, const float *phit, float *lam, float *lamt,
                            const float *u0, cudaStream_t s);
 cudaError_t fused2d_rowsR(Fused2D *f, const Params<float> &P, const float *u, cudaStream_t s);
-// residual norms: gx blocks per slice row, records at partials[(l gx + bx) * 6] (the plain check's layout)
-cudaError_t fused2d_check(const Params<float> &P, const float *u, const float *phi, const float *lam,
-                          const float *u0, double *partials, int gx, cudaStream_t s);
+// residual norms of a 2D finite-difference state (fused path and plain 2D handles): gx
+// blocks per slice row, records at partials[(l gx + bx) * 6] (the generic check's layout)
+template <typename T> bool check2d_applies(const Params<T> &P);
+template <typename T>
+cudaError_t launch_check2d(const Params<T> &P, const T *u, const T *phi, const T *lam, const T *u0,
+                           double *partials, int gx, cudaStream_t s);
 cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s);
 // time slices per rows-R block for nt slices, `rows` row blocks and `slots` resident blocks
 int rowsR_chunk(int nt, int rows, int slots, bool bdf2);

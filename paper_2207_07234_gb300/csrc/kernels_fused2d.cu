@@ -13,6 +13,7 @@
 //   rows-C  (H rows x one slice per block) inverse real FFT along x, dual
 //           step phi^n = phi^{n-1} + tau_phi z and extrapolation phit = phi^n + tau_phi z.
 #include <algorithm>
+#include <type_traits>
 
 #include "fused2d.h"
 #include "fft_smem.cuh"
@@ -752,115 +753,127 @@ static size_t smem_rowsC1024() {
 }
 
 // ---------------------------------------------------------------------------
-// residual norms (Eq. 2.12) for the fused path: the six sums of block_sum6 for
-// slice row l = blockIdx.y, one record per block at partials[(l gx + bx) * 6],
-// the layout of the plain path's check, so the same fixed-order reduction
-// follows.  A thread owns one float4 of x and PRY rows of a tile (tiles
-// blockIdx.x, +gridDim.x, ...), slides three-row windows of u^{l+1} (the
-// equation R^l) and phi^{l-1} (the row l of J(u)^T phi) down them, and folds its
-// float32 sums of the tile's 16 values into float64.
+// residual norms (Eq. 2.12) of a 2D finite-difference state (the fused path, and
+// the plain path's 2D handles): the six sums of block_sum6 for slice row
+// l = blockIdx.y, one record per block at partials[(l gx + bx) * 6], the layout of
+// the generic check, so the same fixed-order reduction follows.  A thread owns four
+// consecutive x and PRY rows of a tile (tiles blockIdx.x, +gridDim.x, ...), slides
+// three-row windows of u^{l+1} (the equation R^l) and phi^{l-1} (the row l of
+// J(u)^T phi) down them, and sums the tile's 16 values in A (float32 for float32
+// fields, folded into float64 per tile; float64 for float64 fields).
 // ---------------------------------------------------------------------------
-template <int NX>
-__global__ void __launch_bounds__(256) k_check2d(Params<float> P, const float *__restrict__ u,
-                                                 const float *__restrict__ phi, const float *__restrict__ lam,
-                                                 const float *__restrict__ u0, double *__restrict__ partials) {
+template <typename T> struct Q4 { T x, y, z, w; };
+__device__ __forceinline__ Q4<float> ld4(const float *p) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Q4<double> ld4(const double *p) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(256) k_check2d(Params<T> P, const T *__restrict__ u, const T *__restrict__ phi,
+                                                 const T *__restrict__ lam, const T *__restrict__ u0,
+                                                 double *__restrict__ partials) {
+    typedef typename std::conditional<sizeof(T) == 4, float, double>::type A;
     constexpr int V = NX / 4, TX = V < 256 ? V : 256, TY = V < 256 ? 256 / V : 1, XS = V / TX;
     const int l = blockIdx.y, nt = P.nt, ny = P.ny;
     const int64_t S = P.S;
     const int xt = threadIdx.x % TX, yt = threadIdx.x / TX;
     const int ntile = (ny / (PRY * TY)) * XS;
     const bool lf = P.space != FD_UPWIND, bdf2 = P.time == BDF2;
+    const T zero = T(0), half = T(0.5), two = T(2);
     // R^l = D(u^{l+1}) + kn u^{l+1} + kc u^l + ko u^{l-1}
-    const float kn = l < nt ? coef_new(P, l) : 0.f, kc = l < nt ? coef_cur(P, l) : 0.f;
-    const float ko = (l < nt && bdf2 && l >= 1) ? coef_old(P, l) : 0.f;
+    const T kn = l < nt ? coef_new(P, l) : zero, kc = l < nt ? coef_cur(P, l) : zero;
+    const T ko = (l < nt && bdf2 && l >= 1) ? coef_old(P, l) : zero;
     // (J^T phi)^l = transposed stencil of phi^{l-1} at u^l + cn phi^{l-1} + cc phi^l + co phi^{l+1}
-    const float cn = l >= 1 ? coef_new(P, l - 1) : 0.f, cc = l <= nt - 1 ? coef_cur(P, l) : 0.f;
-    const float co = (bdf2 && l + 1 <= nt - 1) ? coef_old(P, l + 1) : 0.f;
+    const T cn = l >= 1 ? coef_new(P, l - 1) : zero, cc = l <= nt - 1 ? coef_cur(P, l) : zero;
+    const T co = (bdf2 && l + 1 <= nt - 1) ? coef_old(P, l + 1) : zero;
     auto wrapy = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const int x4 = xt + (tile % XS) * TX;
         const int ya = ((tile / XS) * TY + yt) * PRY;
-        float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        A part[6] = {0, 0, 0, 0, 0, 0};
         if (l < nt) {
-            const float *un = u + (int64_t)(l + 1) * S, *uc = u + (int64_t)l * S;
-            const float *uo = u + (int64_t)(l >= 1 ? l - 1 : 0) * S, *ph = phi + (int64_t)l * S;
-            float4 up = __ldg(reinterpret_cast<const float4 *>(un + (int64_t)wrapy(ya - 1) * NX) + x4);
-            float4 v4 = __ldg(reinterpret_cast<const float4 *>(un + (int64_t)ya * NX) + x4);
+            const T *un = u + (int64_t)(l + 1) * S, *uc = u + (int64_t)l * S;
+            const T *uo = u + (int64_t)(l >= 1 ? l - 1 : 0) * S, *ph = phi + (int64_t)l * S;
+            Q4<T> up = ld4(un + (int64_t)wrapy(ya - 1) * NX + 4 * x4);
+            Q4<T> v4 = ld4(un + (int64_t)ya * NX + 4 * x4);
 #pragma unroll
             for (int r = 0; r < PRY; ++r) {
                 const int y = ya + r;
-                const float *row = un + (int64_t)y * NX;
-                const float4 dn = __ldg(reinterpret_cast<const float4 *>(un + (int64_t)wrapy(y + 1) * NX) + x4);
-                const float lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
-                const float rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
+                const T *row = un + (int64_t)y * NX;
+                const Q4<T> dn = ld4(un + (int64_t)wrapy(y + 1) * NX + 4 * x4);
+                const T lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
+                const T rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
                 const int64_t i = (int64_t)y * NX + 4 * x4;
-                const float4 cu = __ldg(reinterpret_cast<const float4 *>(uc + i));
-                const float4 p4 = __ldg(reinterpret_cast<const float4 *>(ph + i));
-                float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ko != 0.f) o4 = __ldg(reinterpret_cast<const float4 *>(uo + i));
-                const float vr[6] = {lft, v4.x, v4.y, v4.z, v4.w, rgt};
-                const float uv[4] = {up.x, up.y, up.z, up.w}, dv[4] = {dn.x, dn.y, dn.z, dn.w};
-                const float cv[4] = {cu.x, cu.y, cu.z, cu.w}, ov[4] = {o4.x, o4.y, o4.z, o4.w};
-                const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+                const Q4<T> cu = ld4(uc + i), p4 = ld4(ph + i);
+                Q4<T> o4 = {zero, zero, zero, zero};
+                if (ko != zero) o4 = ld4(uo + i);
+                const T vr[6] = {lft, v4.x, v4.y, v4.z, v4.w, rgt};
+                const T uv[4] = {up.x, up.y, up.z, up.w}, dv[4] = {dn.x, dn.y, dn.z, dn.w};
+                const T cv[4] = {cu.x, cu.y, cu.z, cu.w}, ov[4] = {o4.x, o4.y, o4.z, o4.w};
+                const T pv[4] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float v = vr[e + 1];
-                    const float lx = vr[e] - 2.f * v + vr[e + 2], ly = uv[e] - 2.f * v + dv[e];
-                    float dx, dy;
+                    const T v = vr[e + 1];
+                    const T lx = vr[e] - two * v + vr[e + 2], ly = uv[e] - two * v + dv[e];
+                    T dx, dy;
                     if (lf) {
-                        dx = 0.5f * (flux(P, vr[e + 2]) - flux(P, vr[e])) - 0.5f * P.lf_a * lx;
-                        dy = 0.5f * (flux(P, dv[e]) - flux(P, uv[e])) - 0.5f * P.lf_a * ly;
+                        dx = half * (flux(P, vr[e + 2]) - flux(P, vr[e])) - half * P.lf_a * lx;
+                        dy = half * (flux(P, dv[e]) - flux(P, uv[e])) - half * P.lf_a * ly;
                     } else {
                         dx = flux(P, v) - flux(P, vr[e]);
                         dy = flux(P, v) - flux(P, uv[e]);
                     }
-                    float rv = dx * P.inv_hx + dy * P.inv_hy + kn * v + kc * cv[e] + ko * ov[e];
-                    if (P.nu != 0.f) rv -= P.nu * (lx * P.inv_hx * P.inv_hx + ly * P.inv_hy * P.inv_hy);
-                    part[0] += rv * rv;
-                    part[2] += pv[e] * rv;
+                    T rv = dx * P.inv_hx + dy * P.inv_hy + kn * v + kc * cv[e] + ko * ov[e];
+                    if (P.nu != zero) rv -= P.nu * (lx * P.inv_hx * P.inv_hx + ly * P.inv_hy * P.inv_hy);
+                    part[0] += (A)(rv * rv);
+                    part[2] += (A)(pv[e] * rv);
                 }
                 up = v4;
                 v4 = dn;
             }
         }
         if (l >= 1) {
-            const float *pp = phi + (int64_t)(l - 1) * S, *pc = phi + (int64_t)l * S, *ul = u + (int64_t)l * S;
-            float4 pu = __ldg(reinterpret_cast<const float4 *>(pp + (int64_t)wrapy(ya - 1) * NX) + x4);
-            float4 pm = __ldg(reinterpret_cast<const float4 *>(pp + (int64_t)ya * NX) + x4);
+            const T *pp = phi + (int64_t)(l - 1) * S, *pc = phi + (int64_t)l * S, *ul = u + (int64_t)l * S;
+            Q4<T> pu = ld4(pp + (int64_t)wrapy(ya - 1) * NX + 4 * x4);
+            Q4<T> pm = ld4(pp + (int64_t)ya * NX + 4 * x4);
 #pragma unroll
             for (int r = 0; r < PRY; ++r) {
                 const int y = ya + r;
-                const float *row = pp + (int64_t)y * NX;
-                const float4 pd = __ldg(reinterpret_cast<const float4 *>(pp + (int64_t)wrapy(y + 1) * NX) + x4);
-                const float lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
-                const float rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
+                const T *row = pp + (int64_t)y * NX;
+                const Q4<T> pd = ld4(pp + (int64_t)wrapy(y + 1) * NX + 4 * x4);
+                const T lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
+                const T rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
                 const int64_t i = (int64_t)y * NX + 4 * x4;
-                const float4 c = __ldg(reinterpret_cast<const float4 *>(ul + i));
-                float4 tc = make_float4(0.f, 0.f, 0.f, 0.f), tn = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (cc != 0.f) tc = __ldg(reinterpret_cast<const float4 *>(pc + i));
-                if (co != 0.f) tn = __ldg(reinterpret_cast<const float4 *>(pc + S + i));
-                const float pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
-                const float uv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
-                const float cv[4] = {c.x, c.y, c.z, c.w};
-                const float gv[4] = {cc * tc.x + co * tn.x, cc * tc.y + co * tn.y, cc * tc.z + co * tn.z,
-                                     cc * tc.w + co * tn.w};
+                const Q4<T> c = ld4(ul + i);
+                Q4<T> tc = {zero, zero, zero, zero}, tn = {zero, zero, zero, zero};
+                if (cc != zero) tc = ld4(pc + i);
+                if (co != zero) tn = ld4(pc + S + i);
+                const T pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
+                const T uv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
+                const T cv[4] = {c.x, c.y, c.z, c.w};
+                const T gv[4] = {cc * tc.x + co * tn.x, cc * tc.y + co * tn.y, cc * tc.z + co * tn.z,
+                                 cc * tc.w + co * tn.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float p0 = pr[e + 1], df = dflux(P, cv[e]);
-                    const float mx = pr[e], qx = pr[e + 2], my = uv[e], qy = dv[e];
-                    float tx, ty;
+                    const T p0 = pr[e + 1], df = dflux(P, cv[e]);
+                    const T mx = pr[e], qx = pr[e + 2], my = uv[e], qy = dv[e];
+                    T tx, ty;
                     if (lf) {
-                        tx = 0.5f * (df * (mx - qx) + P.lf_a * (2.f * p0 - mx - qx));
-                        ty = 0.5f * (df * (my - qy) + P.lf_a * (2.f * p0 - my - qy));
+                        tx = half * (df * (mx - qx) + P.lf_a * (two * p0 - mx - qx));
+                        ty = half * (df * (my - qy) + P.lf_a * (two * p0 - my - qy));
                     } else {
                         tx = df * (p0 - qx);
                         ty = df * (p0 - qy);
                     }
-                    float g = gv[e] + cn * p0 + tx * P.inv_hx + ty * P.inv_hy;
-                    if (P.nu != 0.f)
-                        g -= P.nu * ((qx - 2.f * p0 + mx) * P.inv_hx * P.inv_hx + (qy - 2.f * p0 + my) * P.inv_hy * P.inv_hy);
-                    part[1] += g * g;
+                    T g = gv[e] + cn * p0 + tx * P.inv_hx + ty * P.inv_hy;
+                    if (P.nu != zero)
+                        g -= P.nu * ((qx - two * p0 + mx) * P.inv_hx * P.inv_hx + (qy - two * p0 + my) * P.inv_hy * P.inv_hy);
+                    part[1] += (A)(g * g);
                 }
                 pu = pm;
                 pm = pd;
@@ -873,12 +886,12 @@ __global__ void __launch_bounds__(256) k_check2d(Params<float> P, const float *_
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const double r0 = (double)u[i + e] - (double)u0[i + e];
-                    part[3] += (float)(r0 * r0);
+                    part[3] += (A)(r0 * r0);
                     if (P.init == INIT_LAMBDA) {
-                        const float t0 = cc * phi[i + e] + (co != 0.f ? co * phi[S + i + e] : 0.f);
+                        const T t0 = cc * phi[i + e] + (co != zero ? co * phi[S + i + e] : zero);
                         const double g0 = (double)P.ht * (double)t0 + (double)lam[i + e];
-                        part[4] += (float)(g0 * g0);
-                        part[5] += (float)((double)lam[i + e] * r0);
+                        part[4] += (A)(g0 * g0);
+                        part[5] += (A)((double)lam[i + e] * r0);
                     }
                 }
             }
@@ -1060,18 +1073,34 @@ cudaError_t fused2d_primal(const Params<float> &P, float *u, const float *phit, 
     }
 }
 
-cudaError_t fused2d_check(const Params<float> &P, const float *u, const float *phi, const float *lam,
-                          const float *u0, double *partials, int gx, cudaStream_t s) {
+template <typename T>
+bool check2d_applies(const Params<T> &P) {
+    const bool nx_ok = P.nx == 256 || P.nx == 512 || P.nx == 1024 || P.nx == 2048;
+    const int rows_per_tile = PRY * (P.nx / 4 < 256 ? 256 / (P.nx / 4) : 1);
+    return P.dims == 2 && (P.space == FD_UPWIND || P.space == FD_LF) && nx_ok && P.ny % rows_per_tile == 0 &&
+           !P.ulin && !P.tshift && !P.gamma_half;
+}
+
+template <typename T>
+cudaError_t launch_check2d(const Params<T> &P, const T *u, const T *phi, const T *lam, const T *u0,
+                           double *partials, int gx, cudaStream_t s) {
     const dim3 grid((unsigned)gx, (unsigned)(P.nt + 1));
     switch (P.nx) {
-    case 256: k_check2d<256><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
-    case 512: k_check2d<512><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
-    case 1024: k_check2d<1024><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
-    case 2048: k_check2d<2048><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
+    case 256: k_check2d<T, 256><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
+    case 512: k_check2d<T, 512><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
+    case 1024: k_check2d<T, 1024><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
+    case 2048: k_check2d<T, 2048><<<grid, 256, 0, s>>>(P, u, phi, lam, u0, partials); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
+
+template bool check2d_applies<float>(const Params<float> &);
+template bool check2d_applies<double>(const Params<double> &);
+template cudaError_t launch_check2d<float>(const Params<float> &, const float *, const float *, const float *,
+                                           const float *, double *, int, cudaStream_t);
+template cudaError_t launch_check2d<double>(const Params<double> &, const double *, const double *, const double *,
+                                            const double *, double *, int, cudaStream_t);
 
 cudaError_t fused2d_rowsR(Fused2D *f, const Params<float> &P, const float *u, cudaStream_t s) {
     switch (ilog2i(P.nx / 2)) {
