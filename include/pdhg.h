@@ -296,6 +296,9 @@ pdhg_status pdhg_solve_gradient(const pdhg_problem *prob, const pdhg_grid *grid,
  * on in float64 on the plain path to tol (from the float32 state this phase is
  * short: checked after 1, 2, 3, 4, 6, 9, 13, ... of its iterations, the gaps
  * growing to at most max(1, check_every/5)), within max_iters iterations in all.
+ * For finite differences with nx a power of two that phase applies K_d^{-1} in
+ * float32 (residual, u, phi, lambda and Res stay float64): the preconditioner
+ * shapes the iteration, not its fixed point, so the result is the float64 one.
  * scheme->precision is ignored.
  *
  * workspace: device, caller-owned, 256-byte aligned, size from

@@ -50,6 +50,7 @@ namespace {
 struct Layout {
     size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, partials, scal, fused;
     size_t blu_tw, blu_c, blu_b;
+    size_t twx32, twy32, theta32;    // float32 preconditioner tables (Geom::pre32)
     size_t total;
 };
 
@@ -64,9 +65,11 @@ struct Geom {
     bool has_gamma;
     bool fused;
     int blu_log2L;   // > 0: Bluestein x-transform (1D FD, nx not a power of two)
+    bool pre32;      // float64 state with the preconditioner applied in float32 (plain FD path)
 };
 
-pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s, Geom *G) {
+pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s, Geom *G,
+                     bool pre32 = false) {
     if (!p || !g || !s) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
     if (g->dims != 1 && g->dims != 2) return fail(PDHG_ERR_INVALID_ARG, "dims must be 1 or 2");
     if (s->time != PDHG_TIME_BE && s->time != PDHG_TIME_BDF2) return fail(PDHG_ERR_INVALID_ARG, "bad time scheme");
@@ -122,6 +125,7 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
             return fail(PDHG_ERR_UNSUPPORTED, "the fused path needs 2D FD, FP32, nx in [256, 2048], ny in [256, 1024] (powers of two), nt >= 2");
         G->fused = ok;
     }
+    G->pre32 = pre32 && s->precision == PDHG_FP64 && !G->fused && !dg && G->blu_log2L == 0;
     return PDHG_OK;
 }
 
@@ -151,6 +155,9 @@ Layout layout_of(const Geom &G) {
     L.blu_tw = take(lb * 2 * e);
     L.blu_c = take(G.blu_log2L ? G.nx * 2 * e : 0);
     L.blu_b = take(lb * 2 * e);
+    L.twx32 = take(G.pre32 ? G.nkx * 2 * sizeof(float) : 0);
+    L.twy32 = take(G.pre32 && G.dims == 2 ? G.ny * 2 * sizeof(float) : 0);
+    L.theta32 = take(G.pre32 ? G.modes * sizeof(float) : 0);
     L.total = o;
     return L;
 }
@@ -565,6 +572,20 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
         parallel_rows(G.lines, G.lines * G.nkx, rows);
     }
     CK(cudaMemcpy(F<T>(h, h->L.theta), th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (G.pre32) {
+        // float32 copies of the preconditioner's tables (rounded from the float64 values)
+        std::vector<float> t32(tw.begin(), tw.end()), th32(th.begin(), th.end());
+        CK(cudaMemcpy(h->ws + h->L.twx32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->ws + h->L.theta32, th32.data(), th32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        if (G.dims == 2) {
+            std::vector<float> y32(2 * G.ny);
+            for (int64_t k = 0; k < G.ny; ++k) {
+                double a = 2.0 * M_PI * (double)k / (double)G.ny;
+                y32[2 * k] = (float)std::cos(a); y32[2 * k + 1] = (float)(-std::sin(a));
+            }
+            CK(cudaMemcpy(h->ws + h->L.twy32, y32.data(), y32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    }
     if (G.blu_log2L) {
         std::vector<T> btw, bc, bb;
         bluestein_tables<T>(G.nx, G.blu_log2L, btw, bc, bb);
@@ -592,6 +613,7 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     }
     Params<T> &P = params_of<T>(h);
     fill_params(P, G, p, g, lf_a);
+    if (G.pre32) fill_params(h->pf, G, p, g, lf_a);          // the float32 twin for the spectrum stages
     if (G.has_gamma) P.gamma_half = F<T>(h, h->L.gamma);
     if (G.blu_log2L) {
         P.blu_tw = h->ws + h->L.blu_tw;
@@ -599,6 +621,7 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
         P.blu_b = h->ws + h->L.blu_b;
     }
     CK(init_plain_attributes<T>());
+    if (G.pre32) CK(init_plain_attributes<float>());
     return PDHG_OK;
 }
 
@@ -671,10 +694,10 @@ static pdhg_status initial_res_sum(pdhg_handle *h, double *a0) {
     return PDHG_OK;
 }
 
-extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
-                                   void *workspace, size_t bytes, void *stream, pdhg_handle **out) {
+static pdhg_status create_impl(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                               void *workspace, size_t bytes, void *stream, pdhg_handle **out, bool pre32) {
     Geom G;
-    pdhg_status st = validate(prob, grid, scheme, &G);
+    pdhg_status st = validate(prob, grid, scheme, &G, pre32);
     if (st != PDHG_OK) return st;
     if (!out) return fail(PDHG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -717,6 +740,11 @@ extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *gr
     h->launches = 0;
     *out = h;
     return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                   void *workspace, size_t bytes, void *stream, pdhg_handle **out) {
+    return create_impl(prob, grid, scheme, workspace, bytes, stream, out, false);
 }
 
 extern "C" pdhg_status pdhg_destroy(pdhg_handle *h) {
@@ -763,6 +791,28 @@ static cudaError_t enqueue_iteration(pdhg_handle *h) {
     }
     e = stage(h, PDHG_STAGE_PRIMAL, 1, [&] { return launch_primal<T>(P, u, phit, lam, lamt, u0, s); });
     if (e != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 8) {
+        if (h->G.pre32) {
+            // float64 state, K_d^{-1} applied in float32 on a float32 spectrum (in the
+            // float64 spectrum's buffer) with the float32 twin of the parameters
+            const Params<float> &Q = h->pf;
+            const void *tx = h->ws + h->L.twx32, *ty = h->ws + h->L.twy32;
+            const float *th32 = F<float>(h, h->L.theta32);
+            e = stage(h, PDHG_STAGE_RESIDUAL_FFT, 1, [&] { return launch_residual_rfft_p32(P, u, spec, tx, s); });
+            if (e != cudaSuccess) return e;
+            if (h->G.dims == 2) {
+                e = stage(h, PDHG_STAGE_FFT_Y, 1, [&] { return launch_fft_y<float>(Q, spec, ty, 0, s); });
+                if (e != cudaSuccess) return e;
+            }
+            e = stage(h, PDHG_STAGE_TSOLVE, 1, [&] { return launch_tsolve<float>(Q, spec, th32, nullptr, s); });
+            if (e != cudaSuccess) return e;
+            if (h->G.dims == 2) {
+                e = stage(h, PDHG_STAGE_FFT_Y, 1, [&] { return launch_fft_y<float>(Q, spec, ty, 1, s); });
+                if (e != cudaSuccess) return e;
+            }
+            return stage(h, PDHG_STAGE_DUAL, 1, [&] { return launch_dual_irfft_p32(P, spec, phi, phit, tx, s); });
+        }
+    }
     e = stage(h, PDHG_STAGE_RESIDUAL_FFT, 1, [&] { return launch_residual_rfft<T>(P, u, spec, twx, s); });
     if (e != cudaSuccess) return e;
     if (h->G.dims == 2) {
@@ -1599,7 +1649,10 @@ static pdhg_status mixed_schemes(const pdhg_problem *prob, const pdhg_grid *grid
     s64->precision = PDHG_FP64;
     s64->path = PDHG_PATH_PLAIN;
     pdhg_status st = pdhg_workspace_size(prob, grid, s32, b32);
-    if (st == PDHG_OK) st = pdhg_workspace_size(prob, grid, s64, b64);
+    if (st != PDHG_OK) return st;
+    Geom G;
+    st = validate(prob, grid, s64, &G, true);
+    if (st == PDHG_OK) *b64 = layout_of(G).total;
     return st;
 }
 
@@ -1652,7 +1705,7 @@ extern "C" pdhg_status pdhg_solve_mixed(const pdhg_problem *prob, const pdhg_gri
     if (iters) iters[0] = n32;
     if (st != PDHG_OK) { pdhg_destroy(h32); return st; }
     // float64 phase from the widened state
-    st = pdhg_create(prob, grid, &s64, ws + align256(b32), b64, stream, &h64);
+    st = create_impl(prob, grid, &s64, ws + align256(b32), b64, stream, &h64, true);
     if (st != PDHG_OK) { pdhg_destroy(h32); return st; }
     const Geom &G = h32->G;
     const int64_t S = G.S;

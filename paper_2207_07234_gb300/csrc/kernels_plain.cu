@@ -441,6 +441,57 @@ __global__ void __launch_bounds__(256) k_dual_irfft(Params<T> P, const typename 
 }
 
 // ---------------------------------------------------------------------------
+// float64 state with the preconditioner applied in float32 (the float64 phase of
+// the mixed solve; finite differences, x-length a power of two): R^l is formed in
+// float64 and rounded to float32 for the x-transform, and the float32 result of
+// the inverse transform is added to the float64 phi.  K_d^{-1} only shapes the
+// iteration (Sec. 3.3), so the rounding moves the iterates, never the fixed point
+// R(u*) = 0: the stopping test on Res (float64) decides as before.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_residual_rfft_p32(Params<double> P, const double *__restrict__ u,
+                                                           float2 *__restrict__ spec,
+                                                           const float2 *__restrict__ twx) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *z = reinterpret_cast<float2 *>(smem_raw);
+    float *zr = reinterpret_cast<float *>(z);
+    const int line = blockIdx.x, l = blockIdx.y;
+    const int N = P.nx, M = N >> 1, lg = P.log2m;
+    const int64_t S = P.S;
+    const double *un = u + (int64_t)(l + 1) * S;
+    const int64_t row = (int64_t)line * N;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        const double r = fd_D(P, un, line, x) + time_R(P, u + row + x, S, l);
+        zr[bitrev(x >> 1, lg) * 2 + (x & 1)] = (float)r;
+    }
+    __syncthreads();
+    fft_radix2(z, lg, 1, M, 1, twx, 2, false);
+    float2 *out = spec + ((int64_t)l * P.lines + line) * P.nkx;
+    for (int k = threadIdx.x; k <= M; k += blockDim.x) out[k] = rfft_split(z, M, k, twx);
+}
+
+__global__ void __launch_bounds__(256) k_dual_irfft_p32(Params<double> P, const float2 *__restrict__ spec,
+                                                        double *__restrict__ phi, double *__restrict__ phit,
+                                                        const float2 *__restrict__ twx) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *z = reinterpret_cast<float2 *>(smem_raw);
+    const int line = blockIdx.x, l = blockIdx.y;
+    const int N = P.nx, M = N >> 1, lg = P.log2m;
+    const float2 *X = spec + ((int64_t)l * P.lines + line) * P.nkx;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) z[bitrev(k, lg)] = irfft_merge(X[k], X[M - k], twx[k]);
+    __syncthreads();
+    fft_radix2(z, lg, 1, M, 1, twx, 2, true);
+    const float *zr = reinterpret_cast<const float *>(z);
+    const int64_t off = (int64_t)l * P.S + (int64_t)line * N;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        const double dz = P.dual_scale * (double)zr[x];
+        const int64_t i = off + x;
+        const double pn = phi[i] + dz;
+        phi[i] = pn;
+        phit[i] = pn + dz;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // residual norms (Eq. 2.12): the six sums of common.cuh::block_sum6, per block
 // ---------------------------------------------------------------------------
 // One thread accumulates many units of one slice (grid-stride over units) into
@@ -626,6 +677,22 @@ template <typename T>
 static int64_t check_grid_x(const Params<T> &P) {
     int64_t units = is_dg(P.space) ? P.nx : P.S;
     return std::min<int64_t>((units + 255) / 256, 32);
+}
+
+cudaError_t launch_residual_rfft_p32(const Params<double> &P, const double *u, void *spec, const void *twx32,
+                                     cudaStream_t s) {
+    const dim3 grid((unsigned)P.lines, (unsigned)P.nt);
+    k_residual_rfft_p32<<<grid, 256, (size_t)(P.nx / 2) * sizeof(float2), s>>>(P, u, (float2 *)spec,
+                                                                                (const float2 *)twx32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dual_irfft_p32(const Params<double> &P, const void *spec, double *phi, double *phit,
+                                  const void *twx32, cudaStream_t s) {
+    const dim3 grid((unsigned)P.lines, (unsigned)P.nt);
+    k_dual_irfft_p32<<<grid, 256, (size_t)(P.nx / 2) * sizeof(float2), s>>>(P, (const float2 *)spec, phi, phit,
+                                                                             (const float2 *)twx32);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce6(const double *partials, int64_t nblocks, double *out, cudaStream_t s) {

@@ -22,6 +22,12 @@ cudaError_t launch_tsolve(const Params<T> &P, void *spec, const T *theta, const 
 template <typename T>
 cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *phit, const void *twx, cudaStream_t s);
 template <typename T> int64_t check_blocks(const Params<T> &P);
+// float64 state, preconditioner in float32 (FD, nx a power of two): R^l in float64 -> float32
+// x-spectrum; float32 x-spectrum of z -> phi, phit in float64.  twx32: W_nx^k, k <= nx/2, float32.
+cudaError_t launch_residual_rfft_p32(const Params<double> &P, const double *u, void *spec, const void *twx32,
+                                     cudaStream_t s);
+cudaError_t launch_dual_irfft_p32(const Params<double> &P, const void *spec, double *phi, double *phit,
+                                  const void *twx32, cudaStream_t s);
 // sum of nblocks records of 6 partial sums (partials[6 b + k]) into out[0..5], fixed order
 cudaError_t launch_reduce6(const double *partials, int64_t nblocks, double *out, cudaStream_t s);
 // sum_l <phi^l, Lap_h u^{l+1}> (FD) into out[0] (float64), partials as for launch_check
