@@ -239,3 +239,19 @@ def test_traffic_iterations_on_gpu(B):
         it = s.iterate(20000, tol=1e-3, check_every=1)
     assert abs(it - 4573) <= 0.1 * 4573
     assert abs(it - 4715) <= 2
+
+
+@pytest.mark.parametrize("p", [steps(W.burgers_2d(n=256, nt=6), 0.4, 0.4),
+                               steps(W.burgers_2d(n=512, nt=5), 0.4, 0.4).replace(time="bdf2", nu=0.02)],
+                         ids=lambda p: f"{p.name}_{p.time}")
+def test_plain_2d_float64_residual_norms(B, p):
+    """float64 plain 2D handles with nx >= 256 take the thread-column residual-check
+    kernel: after fixed iterations its four norms equal the oracle's (the iterates are
+    the oracle's to rounding)."""
+    n = 5
+    g, res = run_gpu(B, p, "fp64", n)
+    o = run_oracle(p, n)
+    assert rel(g["u"], o["u"]) <= 1e-11
+    ores = opdhg.residual_norms(p, o)
+    assert np.allclose(res[:3], ores[:3], rtol=1e-10, atol=1e-300)
+    assert abs(res[3] - ores[3]) <= 1e-9 * max(abs(ores[3]), 1e-300)
