@@ -171,9 +171,10 @@ pdhg_status pdhg_info(pdhg_handle *h, int64_t *ndof, int64_t *nt, int64_t *itera
 pdhg_status pdhg_launch_count(pdhg_handle *h, int64_t *launches, int32_t reset);
 
 /* Per-stage timing with CUDA events on the handle's stream.  While enabled,
- * pdhg_iterate records an event pair around every stage launch; stage_times
- * returns accumulated milliseconds and launch counts per PDHG_STAGE_* and
- * resets them.  Synchronises the stream. */
+ * pdhg_iterate records an event pair around every stage launch (and marks each
+ * stage's launches with an NVTX range named "pdhg <stage>", for ncu --nvtx);
+ * stage_times returns accumulated milliseconds and launch counts per
+ * PDHG_STAGE_* and resets them.  Synchronises the stream. */
 pdhg_status pdhg_set_profiling(pdhg_handle *h, int32_t enable);
 pdhg_status pdhg_stage_times(pdhg_handle *h, double ms[PDHG_NUM_STAGES],
                              int64_t launches[PDHG_NUM_STAGES]);

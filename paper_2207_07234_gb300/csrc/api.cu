@@ -11,6 +11,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pdhg.h"
 #include "fused2d.h"
 #include "plain.h"
@@ -321,16 +323,24 @@ static cudaEvent_t ev_get(pdhg_handle *h) {
 // run one stage launch, bracketed by events when profiling
 template <typename Fn>
 static cudaError_t stage(pdhg_handle *h, int st, int nlaunch, Fn fn) {
+    // NVTX names of the stages (host ranges around each stage's launches while profiling)
+    static const char *const names[PDHG_NUM_STAGES] = {"pdhg primal", "pdhg residual + x-FFT", "pdhg y-FFT",
+                                                       "pdhg t-solve", "pdhg dual", "pdhg residual norms",
+                                                       "pdhg fused rows", "pdhg fused cols"};
     EvRec r{st, nullptr, nullptr};
     if (h->profiling) {
+        nvtxRangePushA(names[st]);
         r.a = ev_get(h); r.b = ev_get(h);
         if (r.a) cudaEventRecord(r.a, h->stream);
     }
     cudaError_t e = fn();
     h->launches += nlaunch;
-    if (h->profiling && r.b) {
-        cudaEventRecord(r.b, h->stream);
-        h->recs.push_back(r);
+    if (h->profiling) {
+        if (r.b) {
+            cudaEventRecord(r.b, h->stream);
+            h->recs.push_back(r);
+        }
+        nvtxRangePop();
     }
     return e;
 }
