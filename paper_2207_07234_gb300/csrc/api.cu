@@ -510,8 +510,7 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     buf.resize(G.S);
     for (int64_t i = 0; i < G.S; ++i) buf[i] = (T)p->u0[i];
     CK(cudaMemcpyAsync(F<T>(h, h->L.u0), buf.data(), G.S * sizeof(T), cudaMemcpyHostToDevice, s));
-    for (int64_t l = 0; l <= G.nt; ++l)
-        CK(cudaMemcpyAsync(F<T>(h, h->L.u) + l * G.S, F<T>(h, h->L.u0), G.S * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    CK(launch_fill_slices<T>(F<T>(h, h->L.u), F<T>(h, h->L.u0), G.S, G.nt + 1, s));
     CK(cudaMemsetAsync(F<T>(h, h->L.phi), 0, G.nt * G.S * sizeof(T), s));
     CK(cudaMemsetAsync(F<T>(h, h->L.phit), 0, G.nt * G.S * sizeof(T), s));
     CK(cudaMemsetAsync(F<T>(h, h->L.lam), 0, G.S * sizeof(T), s));

@@ -47,6 +47,24 @@ cudaError_t launch_widen(const float *src, double *dst, int64_t n, cudaStream_t 
     return cudaGetLastError();
 }
 
+// u[l S + i] = u0[i] for l < nslices (the initial state: u0 extended in t)
+template <typename T>
+__global__ void k_fill_slices(T *__restrict__ u, const T *__restrict__ u0, int64_t S, int64_t total) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = u0[i % S];
+}
+
+template <typename T>
+cudaError_t launch_fill_slices(T *u, const T *u0, int64_t S, int64_t nslices, cudaStream_t s) {
+    const int64_t total = S * nslices;
+    if (total <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 8);
+    k_fill_slices<T><<<(unsigned)blocks, 256, 0, s>>>(u, u0, S, total);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fill_slices<float>(float *, const float *, int64_t, int64_t, cudaStream_t);
+template cudaError_t launch_fill_slices<double>(double *, const double *, int64_t, int64_t, cudaStream_t);
 template cudaError_t launch_interp_t<float>(const float *, const float *, float *, float *, float *, int64_t, int64_t,
                                             cudaStream_t);
 template cudaError_t launch_interp_t<double>(const double *, const double *, double *, double *, double *, int64_t,

@@ -15,6 +15,10 @@ template <typename T>
 cudaError_t launch_interp_t(const T *uc, const T *phic, T *uf, T *phif, T *phitf, int64_t S, int64_t ntc,
                             cudaStream_t s);
 
+// u[l S + i] = u0[i] for l < nslices, i < S (one launch for the initial state)
+template <typename T>
+cudaError_t launch_fill_slices(T *u, const T *u0, int64_t S, int64_t nslices, cudaStream_t s);
+
 // dst[i] = (double)src[i], i < n (the float32 -> float64 hand-over of a mixed solve)
 cudaError_t launch_widen(const float *src, double *dst, int64_t n, cudaStream_t s);
 
