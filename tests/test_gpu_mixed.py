@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import pdhg_workloads as W
-from oracle import newton
+from oracle import newton, pdhg as opdhg
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +23,15 @@ def B():
     return binding
 
 
+def _bdf2_viscous():
+    """Viscous Burgers, BDF2, the lambda row: tau_u = tau_u0 = tau_phi = sqrt(0.5 / nu_max)."""
+    p = W.viscous_burgers(nx=128, nt=8, nu=0.05).replace(time="bdf2", name="viscous_burgers_bdf2_128x8")
+    t = float(np.sqrt(0.5 / opdhg.power_estimate(p, iters=60)))
+    return p.replace(tau_u=t, tau_u0=t, tau_phi=t)
+
+
 CASES = [W.advection_upwind_be(nx=256, nt=32, tau=(1.4, 0.1, 0.35, 0.99)),
+         _bdf2_viscous(),
          W.burgers_2d(n=256, nt=8).replace(name="transport2d_256x256x8", alpha=0.0, beta=1.0, space="fd_upwind",
                                            lf_a=1.0, c=1.0, tau_u=0.5, tau_phi=0.5, tau_u0=0.1)]
 
@@ -46,7 +54,7 @@ def test_mixed_reaches_scheme_solution(B, p):
 
 def test_mixed_uses_the_fused_path_for_2d(B):
     """On a 2D float32-eligible grid the float32 phase runs the fused kernels."""
-    p = CASES[1]
+    p = CASES[-1]
     with B.Solver(p, precision="fp32") as s32:
         assert s32.info()["path"] == "fused"
     s, its = B.solve_mixed(p, tol=1e-6, relative=True, check_every=10)
