@@ -47,7 +47,8 @@ typedef enum {
     PDHG_ERR_NONFINITE = -4,            /* a residual norm became NaN or Inf */
     PDHG_ERR_DIVERGED = -5,             /* the primal residual grew by more than 1e10 */
     PDHG_ERR_TIMEOUT = -6,              /* a bounded device wait gave up */
-    PDHG_ERR_UNSUPPORTED = -7           /* valid but not implemented (e.g. a 2D nx not a power of two) */
+    PDHG_ERR_UNSUPPORTED = -7,          /* valid but not implemented (e.g. a 2D nx not a power of two) */
+    PDHG_ERR_BOUNDS = -8                /* a debug build (-DPDHG_DEBUG) caught an out-of-range index */
 } pdhg_status;
 
 enum { PDHG_TIME_BE = 0, PDHG_TIME_BDF2 = 1 };

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libpdhg.so")
 OK = 0
 STATUS = {0: "PDHG_OK", -1: "PDHG_ERR_INVALID_ARG", -2: "PDHG_ERR_WORKSPACE_TOO_SMALL",
           -3: "PDHG_ERR_CUDA", -4: "PDHG_ERR_NONFINITE", -5: "PDHG_ERR_DIVERGED",
-          -6: "PDHG_ERR_TIMEOUT", -7: "PDHG_ERR_UNSUPPORTED"}
+          -6: "PDHG_ERR_TIMEOUT", -7: "PDHG_ERR_UNSUPPORTED", -8: "PDHG_ERR_BOUNDS"}
 TIME = {"be": 0, "bdf2": 1}
 SPACE = {"fd_upwind": 0, "fd_lf": 1, "dg_p2_lf": 2, "dg_p1_upwind": 3, "dg_p1_lf": 4}
 PRECISION = {"fp64": 0, "fp32": 1}
@@ -69,11 +69,14 @@ class pdhg_scheme(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libpdhg.so (raises OSError if it has not been built)."""
+def load(path: str | None = None):
+    """Load libpdhg.so (raises OSError if it has not been built).  PDHG_LIBRARY in the
+    environment names another build of the same library (the debug build)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("PDHG_LIBRARY", LIB_PATH)
     if not os.path.exists(path):
         raise OSError(f"{path} not found: run __graft_entry__.build() first")
     lib = ctypes.CDLL(path)

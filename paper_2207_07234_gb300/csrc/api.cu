@@ -50,7 +50,7 @@ void pdhg::set_last_error(const std::string &msg) { g_last_error = msg; }
 namespace {
 
 struct Layout {
-    size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, partials, scal, fused;
+    size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, partials, scal, dbg, fused;
     size_t blu_tw, blu_c, blu_b;
     size_t twx32, twy32, theta32;    // float32 preconditioner tables (Geom::pre32)
     size_t total;
@@ -152,6 +152,7 @@ Layout layout_of(const Geom &G) {
     int64_t nblk = std::min<int64_t>((units + 255) / 256, 32) * (G.nt + 1);    // k_check grid
     L.partials = take(nblk * 6 * sizeof(double));
     L.scal = take(16 * sizeof(double));
+    L.dbg = take(sizeof(int));                  // debug builds: first out-of-range site
     L.fused = take(G.fused ? fused2d_workspace_bytes(G.nx, G.ny, G.nt) : 0);
     const size_t lb = G.blu_log2L ? ((size_t)1 << G.blu_log2L) : 0;
     L.blu_tw = take(lb * 2 * e);
@@ -623,6 +624,9 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     Params<T> &P = params_of<T>(h);
     fill_params(P, G, p, g, lf_a);
     if (G.pre32) fill_params(h->pf, G, p, g, lf_a);          // the float32 twin for the spectrum stages
+    CK(cudaMemset(h->ws + h->L.dbg, 0, sizeof(int)));
+    P.dbg = (int *)(h->ws + h->L.dbg);
+    if (G.pre32) h->pf.dbg = P.dbg;
     if (G.has_gamma) P.gamma_half = F<T>(h, h->L.gamma);
     if (G.blu_log2L) {
         P.blu_tw = h->ws + h->L.blu_tw;
@@ -655,9 +659,12 @@ static pdhg_status read_res(pdhg_handle *h, double out[4]) {
     double acc[6];
     int err = 0;
     CK(cudaMemcpyAsync(acc, h->ws + h->L.scal, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    int bad = 0;
     if (h->G.fused) CK(cudaMemcpyAsync(&err, h->fused.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&bad, h->ws + h->L.dbg, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (err) return fail(PDHG_ERR_TIMEOUT, "a pipelined spectrum load of the fused rows-C kernel did not arrive");
+    if (bad) return fail(PDHG_ERR_BOUNDS, "debug bounds check: out-of-range index at site " + std::to_string(bad));
     double ht = h->ht, wx = h->wx;
     // space-time L2 (weight h_t w_x per equation value), or, for the one-step
     // problems of Algorithm 3, L2 over the domain at one time (weight w_x)

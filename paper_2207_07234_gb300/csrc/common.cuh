@@ -65,7 +65,25 @@ struct Params {
     // slice carries the objective |v - tshift|^2 (tshift = target - u*^nt).
     const T *ulin = nullptr;     // u*, [nt+1][S]; nullptr: forward mode
     const T *tshift = nullptr;   // [S]; nullptr: no terminal objective
+    int *dbg = nullptr;          // debug builds: site code of the first out-of-range index
 };
+
+// Debug builds (-DPDHG_DEBUG): the global indices of the instrumented kernels are checked
+// against their buffer's extent n; the first violation records its site code in *P.dbg
+// (read at the next residual check) and the access goes to element 0 instead, so nothing
+// outside the buffer is touched.  Release builds: the index itself.
+template <typename T>
+__device__ __forceinline__ int64_t dbg_idx(const Params<T> &P, int64_t i, int64_t n, int code) {
+#ifdef PDHG_DEBUG
+    if (i < 0 || i >= n) {
+        if (P.dbg) atomicCAS(P.dbg, 0, code);
+        return 0;
+    }
+#else
+    (void)P; (void)n; (void)code;
+#endif
+    return i;
+}
 
 template <typename T>
 __device__ __forceinline__ T flux(const Params<T> &P, T v) { return v * (P.alpha * v + P.beta); }

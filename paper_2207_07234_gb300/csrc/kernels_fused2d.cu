@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(256) k_primal2d(Params<float> P, float *__rest
     const int ya = (blockIdx.x * blockDim.y + threadIdx.y) * PRY;
     const int m = blockIdx.y;
     const int ny = P.ny, nt = P.nt;
-    const int64_t S = P.S;
+    const int64_t S = P.S, nU = (int64_t)(nt + 1) * S, nF = (int64_t)nt * S;
     float *um = u + (int64_t)m * S;
+    const int64_t nUm = nU - (int64_t)m * S;                // elements from um to the end of u
     const float cc = m <= nt - 1 ? coef_cur(P, m) : 0.f;
     const float co = (P.time == BDF2 && m + 1 <= nt - 1) ? coef_old(P, m + 1) : 0.f;
     if (m == 0) {
@@ -55,48 +56,52 @@ __global__ void __launch_bounds__(256) k_primal2d(Params<float> P, float *__rest
 #pragma unroll
         for (int r = 0; r < PRY; ++r) {
             const int64_t i = (int64_t)(ya + r) * NX + 4 * x4;
-            const float4 c = *reinterpret_cast<const float4 *>(um + i);
-            const float4 tc = __ldg(reinterpret_cast<const float4 *>(phit + i));
+            float4 *up = reinterpret_cast<float4 *>(um + dbg_idx(P, i, nUm - 3, 101));
+            const float4 c = *up;
+            const float4 tc = __ldg(reinterpret_cast<const float4 *>(phit + dbg_idx(P, i, nF - 3, 102)));
             float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (co != 0.f) tn = __ldg(reinterpret_cast<const float4 *>(phit + S + i));
+            if (co != 0.f) tn = __ldg(reinterpret_cast<const float4 *>(phit + dbg_idx(P, S + i, nF - 3, 103)));
             const float cv[4] = {c.x, c.y, c.z, c.w};
             const float gv[4] = {cc * tc.x + co * tn.x, cc * tc.y + co * tn.y, cc * tc.z + co * tn.z,
                                  cc * tc.w + co * tn.w};
             float un[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                un[e] = cv[e] - P.tau_u0 * (P.ht * gv[e] + lamt[i + e]);
-                const float r0 = un[e] - u0[i + e];
-                const float ln = lam[i + e] + P.tau_lambda * r0;
-                lam[i + e] = ln;
-                lamt[i + e] = ln + P.tau_lambda * r0;
+                const int64_t k = dbg_idx(P, i + e, S, 104);
+                un[e] = cv[e] - P.tau_u0 * (P.ht * gv[e] + lamt[k]);
+                const float r0 = un[e] - u0[k];
+                const float ln = lam[k] + P.tau_lambda * r0;
+                lam[k] = ln;
+                lamt[k] = ln + P.tau_lambda * r0;
             }
-            *reinterpret_cast<float4 *>(um + i) = make_float4(un[0], un[1], un[2], un[3]);
+            *up = make_float4(un[0], un[1], un[2], un[3]);
         }
         return;
     }
     const float cn = coef_new(P, m - 1);
     const float *pp = phit + (int64_t)(m - 1) * S;        // phit^{m-1}: transposed stencil
     const float *pc = phit + (int64_t)m * S;              // phit^m: pointwise (m <= nt-1)
+    const int64_t npp = nF - (int64_t)(m - 1) * S, npc = nF - (int64_t)m * S;
     const bool lf = P.space != FD_UPWIND;
-    auto prow = [&](int y) {
+    auto prow = [&](int y) -> int64_t {                  // element offset of row y in pp
         y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-        return pp + (int64_t)y * NX;
+        return (int64_t)y * NX;
     };
-    float4 pu = __ldg(reinterpret_cast<const float4 *>(prow(ya - 1)) + x4);
-    float4 pm = __ldg(reinterpret_cast<const float4 *>(prow(ya)) + x4);
+    float4 pu = __ldg(reinterpret_cast<const float4 *>(pp + dbg_idx(P, prow(ya - 1) + 4 * x4, npp - 3, 105)));
+    float4 pm = __ldg(reinterpret_cast<const float4 *>(pp + dbg_idx(P, prow(ya) + 4 * x4, npp - 3, 105)));
 #pragma unroll
     for (int r = 0; r < PRY; ++r) {
         const int y = ya + r;
-        const float *row = pp + (int64_t)y * NX;
-        const float4 pd = __ldg(reinterpret_cast<const float4 *>(prow(y + 1)) + x4);
-        const float lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
-        const float rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
+        const int64_t row = (int64_t)y * NX;
+        const float4 pd = __ldg(reinterpret_cast<const float4 *>(pp + dbg_idx(P, prow(y + 1) + 4 * x4, npp - 3, 105)));
+        const float lft = __ldg(pp + dbg_idx(P, row + (x4 == 0 ? NX - 1 : 4 * x4 - 1), npp, 106));
+        const float rgt = __ldg(pp + dbg_idx(P, row + (x4 == V - 1 ? 0 : 4 * x4 + 4), npp, 106));
         const int64_t i = (int64_t)y * NX + 4 * x4;
-        const float4 c = *reinterpret_cast<const float4 *>(um + i);
+        float4 *up = reinterpret_cast<float4 *>(um + dbg_idx(P, i, nUm - 3, 107));
+        const float4 c = *up;
         float4 tc = make_float4(0.f, 0.f, 0.f, 0.f), tn = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (cc != 0.f) tc = __ldg(reinterpret_cast<const float4 *>(pc + i));
-        if (co != 0.f) tn = __ldg(reinterpret_cast<const float4 *>(pc + S + i));
+        if (cc != 0.f) tc = __ldg(reinterpret_cast<const float4 *>(pc + dbg_idx(P, i, npc - 3, 108)));
+        if (co != 0.f) tn = __ldg(reinterpret_cast<const float4 *>(pc + dbg_idx(P, S + i, npc - 3, 109)));
         const float pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
         const float uv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
         const float cv[4] = {c.x, c.y, c.z, c.w};
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(256) k_primal2d(Params<float> P, float *__rest
                 ge -= P.nu * ((qx - 2.f * p0 + mx) * P.inv_hx * P.inv_hx + (qy - 2.f * p0 + my) * P.inv_hy * P.inv_hy);
             un[e] = cv[e] - P.tau_u * ge;
         }
-        *reinterpret_cast<float4 *>(um + i) = make_float4(un[0], un[1], un[2], un[3]);
+        *up = make_float4(un[0], un[1], un[2], un[3]);
         pu = pm;
         pm = pd;
     }
@@ -141,8 +146,10 @@ __global__ void __launch_bounds__(256) k_primal2d(Params<float> P, float *__rest
 // takes 67 KB at nx = 1024: three blocks per SM.
 // ---------------------------------------------------------------------------
 template <int NX, int N>
-__device__ __forceinline__ void fetch_rows(float4 (&reg)[N], const float *__restrict__ src_slice, int ybase, int ny) {
+__device__ __forceinline__ void fetch_rows(float4 (&reg)[N], const Params<float> &P, const float *__restrict__ u,
+                                           int64_t slice_off, int ybase, int ny) {
     constexpr int V = NX / 4;
+    const int64_t nU = (int64_t)(P.nt + 1) * P.S;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const int idx = threadIdx.x + j * ATHREADS;
@@ -151,7 +158,7 @@ __device__ __forceinline__ void fetch_rows(float4 (&reg)[N], const float *__rest
             const int r = idx / V, c = idx - r * V;
             int y = ybase + r;
             y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-            v = __ldg(reinterpret_cast<const float4 *>(src_slice + (int64_t)y * NX) + c);
+            v = __ldg(reinterpret_cast<const float4 *>(u + dbg_idx(P, slice_off + (int64_t)y * NX + 4 * c, nU - 3, 201)));
         }
         reg[j] = v;
     }
@@ -187,11 +194,11 @@ k_rowsR(Params<float> P, const float *__restrict__ u, float2 *__restrict__ spec,
     const int mstart = (BDF2_ && l0 > 0) ? l0 - 1 : l0;
     constexpr int UPT = (RU * (NX / 4) + ATHREADS - 1) / ATHREADS;
     float4 ru[UPT];
-    fetch_rows<NX>(ru, u + (int64_t)mstart * S, y0 - 1, ny);
+    fetch_rows<NX>(ru, P, u, (int64_t)mstart * S, y0 - 1, ny);
     for (int m = mstart; m <= l1; ++m) {
         float *uc = us + (m % NR) * RU * NX;             // u^m
         store_rows<NX>(uc, ru);
-        if (m + 1 <= l1) fetch_rows<NX>(ru, u + (int64_t)(m + 1) * S, y0 - 1, ny);
+        if (m + 1 <= l1) fetch_rows<NX>(ru, P, u, (int64_t)(m + 1) * S, y0 - 1, ny);
         __syncthreads();
         const int lr = m - 1;
         if (lr >= l0 && lr < l1) {
@@ -277,14 +284,14 @@ k_rowsR(Params<float> P, const float *__restrict__ u, float2 *__restrict__ spec,
             __syncthreads();
             const float2 *res = stockham8<LOG2M, false, FH, ATHREADS>(fin2, scr, tw8);
             // split pairs (k, M-k), k = 0..M/2, both outputs from one pair of loads
-            float2 *dst = spec + (int64_t)lr * P.nkx * ny + y0;
+            const int64_t dst0 = (int64_t)lr * P.nkx * ny + y0, nX = (int64_t)P.nt * P.nkx * ny;
             for (int idx = threadIdx.x; idx < (M / 2 + 1) * FH; idx += blockDim.x) {
                 const int k = idx / FH, rr = idx - k * FH;
                 const float2 *row = res + rr * PN;
                 float2 xk, xm;
                 rfft_split_pair(row[k], row[k == 0 ? 0 : M - k], __ldg(twN + k), xk, xm);
-                dst[(int64_t)k * ny + rr] = xk;
-                if (k != M / 2) dst[(int64_t)(M - k) * ny + rr] = xm;
+                spec[dbg_idx(P, dst0 + (int64_t)k * ny + rr, nX, 202)] = xk;
+                if (k != M / 2) spec[dbg_idx(P, dst0 + (int64_t)(M - k) * ny + rr, nX, 202)] = xm;
             }
         }
         __syncthreads();
@@ -437,13 +444,14 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
     const int nt = P.nt;
     const int64_t cs = (int64_t)P.nkx * NY;
     float2 *col = spec + (int64_t)kx * NY;
+    const int64_t ncol = (int64_t)nt * P.nkx * NY - (int64_t)kx * NY;     // elements from col to the end
     const int t = threadIdx.x;
     for (int j = t; j < NY; j += FTHREADS) tw[j] = twY[j];
     float th[4], emt[4], q4[4];
     float2 acc[4], pf[TB][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        th[q] = thetaT[(int64_t)kx * NY + t + q * Q];
+        th[q] = thetaT[dbg_idx(P, (int64_t)kx * NY + t + q * Q, (int64_t)P.nkx * NY, 302)];
         emt[q] = expf(-th[q]);
         q4[q] = emt[q] * emt[q];
         acc[q] = make_float2(0.f, 0.f);
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
 #pragma unroll
     for (int b = 0; b < TB; ++b)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) pf[b][q] = b < nt ? col[(int64_t)b * cs + t + q * Q] : make_float2(0.f, 0.f);
+        for (int q = 0; q < 4; ++q) pf[b][q] = b < nt ? col[dbg_idx(P, ((int64_t)b * cs + t + q * Q), ncol, 301)] : make_float2(0.f, 0.f);
     __syncthreads();                                                // twiddles
     for (int g = 0; g < nb; ++g) {
         const int lb = g * TB;
@@ -472,7 +480,7 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
             for (int b = 0; b < TB; ++b) {
                 const int l = lb + TB + b;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) pf[b][q] = l < nt ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
+                for (int q = 0; q < 4; ++q) pf[b][q] = l < nt ? col[dbg_idx(P, ((int64_t)l * cs + t + q * Q), ncol, 301)] : make_float2(0.f, 0.f);
             }
         }
         stage_r8<LOG2NY, false, 4, 2, 2, TB, FTHREADS, 4>(ba, bb, tw);
@@ -498,7 +506,7 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
                     float2 v = y[q];
                     if (l > 0) v = cadd(v, cscale(acc[q], rho_f(th[q], emt[q], q4[q], l - 1)));
                     acc[q] = v;
-                    col[(int64_t)l * cs + t + q * Q] = v;
+                    col[dbg_idx(P, ((int64_t)l * cs + t + q * Q), ncol, 301)] = v;
                 }
             }
         }
@@ -510,7 +518,7 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
     for (int b = 0; b < TB; ++b)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            pf[b][q] = hi - b >= 0 ? col[(int64_t)(hi - b) * cs + t + q * Q] : make_float2(0.f, 0.f);
+            pf[b][q] = hi - b >= 0 ? col[dbg_idx(P, ((int64_t)(hi - b) * cs + t + q * Q), ncol, 301)] : make_float2(0.f, 0.f);
     for (int g = 0; g < nb; ++g, hi -= TB) {
 #pragma unroll
         for (int b = 0; b < TB; ++b) {
@@ -538,7 +546,7 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
             for (int b = 0; b < TB; ++b) {
                 const int l = hi - TB - b;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) pf[b][q] = l >= 0 ? col[(int64_t)l * cs + t + q * Q] : make_float2(0.f, 0.f);
+                for (int q = 0; q < 4; ++q) pf[b][q] = l >= 0 ? col[dbg_idx(P, ((int64_t)l * cs + t + q * Q), ncol, 301)] : make_float2(0.f, 0.f);
             }
         }
         stage_r8<LOG2NY, true, 4, 2, 2, TB, FTHREADS, 4>(ba, bb, tw);
@@ -556,10 +564,10 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
             float2 x3 = cmulconj(rb[t + 3 * Q], tw[252 + 512 + t]);
             dft4<true>(x0, x1, x2, x3);
             if (l >= 0) {
-                col[(int64_t)l * cs + t] = x0;
-                col[(int64_t)l * cs + t + Q] = x1;
-                col[(int64_t)l * cs + t + 2 * Q] = x2;
-                col[(int64_t)l * cs + t + 3 * Q] = x3;
+                col[dbg_idx(P, ((int64_t)l * cs + t), ncol, 301)] = x0;
+                col[dbg_idx(P, ((int64_t)l * cs + t + Q), ncol, 301)] = x1;
+                col[dbg_idx(P, ((int64_t)l * cs + t + 2 * Q), ncol, 301)] = x2;
+                col[dbg_idx(P, ((int64_t)l * cs + t + 3 * Q), ncol, 301)] = x3;
             }
         }
         __syncthreads();                 // res (= ba) takes the next batch's first stage
@@ -654,6 +662,7 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
     float2 *fb = fa + FH * PN;                               // [FH][PN]
     uint64_t *bar = reinterpret_cast<uint64_t *>(fb + FH * PN);   // [2]
     const int nyb = P.ny / FH, ntiles = nyb * P.nt, G = gridDim.x;
+    const int64_t nF = (int64_t)P.nt * P.S;
     const int t = threadIdx.x;
     auto issue = [&](int tile, int buf) {                    // one thread
         const int l = tile / nyb, yb = tile - l * nyb;
@@ -686,7 +695,8 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
         for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                ph[rr][q] = __ldg(reinterpret_cast<const float2 *>(phi + base + (int64_t)(2 * h + rr) * NX) + i + 128 * q);
+                ph[rr][q] = __ldg(reinterpret_cast<const float2 *>(
+                    phi + dbg_idx(P, base + (int64_t)(2 * h + rr) * NX + 2 * (i + 128 * q), nF - 1, 401)));
         const bool ok = mbar_wait_bounded(bar + buf, (it >> 1) & 1, wait_ns);
         if (__syncthreads_or(!ok)) {
             if (t == 0) {
@@ -734,15 +744,15 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
             float2 x3 = cmulconj(r[padx(i + 384)], twM[126 + 256 + i]);
             dft4<true>(x0, x1, x2, x3);
             const float2 z[4] = {x0, x1, x2, x3};
-            float2 *p2 = reinterpret_cast<float2 *>(phi + base + (int64_t)(2 * h + rr) * NX);
-            float2 *t2 = reinterpret_cast<float2 *>(phit + base + (int64_t)(2 * h + rr) * NX);
+            const int64_t rb = base + (int64_t)(2 * h + rr) * NX;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float2 pn = ph[rr][q];
                 pn.x += s * z[q].x;
                 pn.y += s * z[q].y;
-                p2[i + 128 * q] = pn;
-                t2[i + 128 * q] = make_float2(pn.x + s * z[q].x, pn.y + s * z[q].y);
+                const int64_t o = dbg_idx(P, rb + 2 * (i + 128 * q), nF - 1, 402);
+                *reinterpret_cast<float2 *>(phi + o) = pn;
+                *reinterpret_cast<float2 *>(phit + o) = make_float2(pn.x + s * z[q].x, pn.y + s * z[q].y);
             }
         }
     }
@@ -779,7 +789,7 @@ __global__ void __launch_bounds__(256) k_check2d(Params<T> P, const T *__restric
     typedef typename std::conditional<sizeof(T) == 4, float, double>::type A;
     constexpr int V = NX / 4, TX = V < 256 ? V : 256, TY = V < 256 ? 256 / V : 1, XS = V / TX;
     const int l = blockIdx.y, nt = P.nt, ny = P.ny;
-    const int64_t S = P.S;
+    const int64_t S = P.S, nU = (int64_t)(nt + 1) * S, nF = (int64_t)nt * S;
     const int xt = threadIdx.x % TX, yt = threadIdx.x / TX;
     const int ntile = (ny / (PRY * TY)) * XS;
     const bool lf = P.space != FD_UPWIND, bdf2 = P.time == BDF2;
@@ -797,21 +807,20 @@ __global__ void __launch_bounds__(256) k_check2d(Params<T> P, const T *__restric
         const int ya = ((tile / XS) * TY + yt) * PRY;
         A part[6] = {0, 0, 0, 0, 0, 0};
         if (l < nt) {
-            const T *un = u + (int64_t)(l + 1) * S, *uc = u + (int64_t)l * S;
-            const T *uo = u + (int64_t)(l >= 1 ? l - 1 : 0) * S, *ph = phi + (int64_t)l * S;
-            Q4<T> up = ld4(un + (int64_t)wrapy(ya - 1) * NX + 4 * x4);
-            Q4<T> v4 = ld4(un + (int64_t)ya * NX + 4 * x4);
+            const int64_t oN = (int64_t)(l + 1) * S, oC = (int64_t)l * S, oO = (int64_t)(l >= 1 ? l - 1 : 0) * S;
+            Q4<T> up = ld4(u + dbg_idx(P, oN + (int64_t)wrapy(ya - 1) * NX + 4 * x4, nU - 3, 501));
+            Q4<T> v4 = ld4(u + dbg_idx(P, oN + (int64_t)ya * NX + 4 * x4, nU - 3, 501));
 #pragma unroll
             for (int r = 0; r < PRY; ++r) {
                 const int y = ya + r;
-                const T *row = un + (int64_t)y * NX;
-                const Q4<T> dn = ld4(un + (int64_t)wrapy(y + 1) * NX + 4 * x4);
-                const T lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
-                const T rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
+                const int64_t row = oN + (int64_t)y * NX;
+                const Q4<T> dn = ld4(u + dbg_idx(P, oN + (int64_t)wrapy(y + 1) * NX + 4 * x4, nU - 3, 501));
+                const T lft = __ldg(u + dbg_idx(P, row + (x4 == 0 ? NX - 1 : 4 * x4 - 1), nU, 502));
+                const T rgt = __ldg(u + dbg_idx(P, row + (x4 == V - 1 ? 0 : 4 * x4 + 4), nU, 502));
                 const int64_t i = (int64_t)y * NX + 4 * x4;
-                const Q4<T> cu = ld4(uc + i), p4 = ld4(ph + i);
+                const Q4<T> cu = ld4(u + dbg_idx(P, oC + i, nU - 3, 503)), p4 = ld4(phi + dbg_idx(P, oC + i, nF - 3, 504));
                 Q4<T> o4 = {zero, zero, zero, zero};
-                if (ko != zero) o4 = ld4(uo + i);
+                if (ko != zero) o4 = ld4(u + dbg_idx(P, oO + i, nU - 3, 505));
                 const T vr[6] = {lft, v4.x, v4.y, v4.z, v4.w, rgt};
                 const T uv[4] = {up.x, up.y, up.z, up.w}, dv[4] = {dn.x, dn.y, dn.z, dn.w};
                 const T cv[4] = {cu.x, cu.y, cu.z, cu.w}, ov[4] = {o4.x, o4.y, o4.z, o4.w};
@@ -838,21 +847,21 @@ __global__ void __launch_bounds__(256) k_check2d(Params<T> P, const T *__restric
             }
         }
         if (l >= 1) {
-            const T *pp = phi + (int64_t)(l - 1) * S, *pc = phi + (int64_t)l * S, *ul = u + (int64_t)l * S;
-            Q4<T> pu = ld4(pp + (int64_t)wrapy(ya - 1) * NX + 4 * x4);
-            Q4<T> pm = ld4(pp + (int64_t)ya * NX + 4 * x4);
+            const int64_t oP = (int64_t)(l - 1) * S, oL = (int64_t)l * S;
+            Q4<T> pu = ld4(phi + dbg_idx(P, oP + (int64_t)wrapy(ya - 1) * NX + 4 * x4, nF - 3, 506));
+            Q4<T> pm = ld4(phi + dbg_idx(P, oP + (int64_t)ya * NX + 4 * x4, nF - 3, 506));
 #pragma unroll
             for (int r = 0; r < PRY; ++r) {
                 const int y = ya + r;
-                const T *row = pp + (int64_t)y * NX;
-                const Q4<T> pd = ld4(pp + (int64_t)wrapy(y + 1) * NX + 4 * x4);
-                const T lft = __ldg(row + (x4 == 0 ? NX - 1 : 4 * x4 - 1));
-                const T rgt = __ldg(row + (x4 == V - 1 ? 0 : 4 * x4 + 4));
+                const int64_t row = oP + (int64_t)y * NX;
+                const Q4<T> pd = ld4(phi + dbg_idx(P, oP + (int64_t)wrapy(y + 1) * NX + 4 * x4, nF - 3, 506));
+                const T lft = __ldg(phi + dbg_idx(P, row + (x4 == 0 ? NX - 1 : 4 * x4 - 1), nF, 507));
+                const T rgt = __ldg(phi + dbg_idx(P, row + (x4 == V - 1 ? 0 : 4 * x4 + 4), nF, 507));
                 const int64_t i = (int64_t)y * NX + 4 * x4;
-                const Q4<T> c = ld4(ul + i);
+                const Q4<T> c = ld4(u + dbg_idx(P, oL + i, nU - 3, 508));
                 Q4<T> tc = {zero, zero, zero, zero}, tn = {zero, zero, zero, zero};
-                if (cc != zero) tc = ld4(pc + i);
-                if (co != zero) tn = ld4(pc + S + i);
+                if (cc != zero) tc = ld4(phi + dbg_idx(P, oL + i, nF - 3, 509));
+                if (co != zero) tn = ld4(phi + dbg_idx(P, oL + S + i, nF - 3, 510));
                 const T pr[6] = {lft, pm.x, pm.y, pm.z, pm.w, rgt};
                 const T uv[4] = {pu.x, pu.y, pu.z, pu.w}, dv[4] = {pd.x, pd.y, pd.z, pd.w};
                 const T cv[4] = {c.x, c.y, c.z, c.w};
@@ -885,13 +894,14 @@ __global__ void __launch_bounds__(256) k_check2d(Params<T> P, const T *__restric
                 const int64_t i = (int64_t)(ya + r) * NX + 4 * x4;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const double r0 = (double)u[i + e] - (double)u0[i + e];
+                    const int64_t k0 = dbg_idx(P, i + e, S, 511);
+                    const double r0 = (double)u[k0] - (double)u0[k0];
                     part[3] += (A)(r0 * r0);
                     if (P.init == INIT_LAMBDA) {
-                        const T t0 = cc * phi[i + e] + (co != zero ? co * phi[S + i + e] : zero);
-                        const double g0 = (double)P.ht * (double)t0 + (double)lam[i + e];
+                        const T t0 = cc * phi[k0] + (co != zero ? co * phi[dbg_idx(P, S + i + e, nF, 512)] : zero);
+                        const double g0 = (double)P.ht * (double)t0 + (double)lam[k0];
                         part[4] += (A)(g0 * g0);
-                        part[5] += (A)((double)lam[i + e] * r0);
+                        part[5] += (A)((double)lam[k0] * r0);
                     }
                 }
             }

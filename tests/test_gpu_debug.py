@@ -1,0 +1,48 @@
+"""Debug build (-DPDHG_DEBUG): the kernels of the fused 2D iteration and the 2D residual
+check verify every global index against the extent of its buffer; an index out of range is
+recorded (and the access redirected to element 0), and the next residual check returns
+PDHG_ERR_BOUNDS.  The parity cases of the fused path (ragged t-chunks, BDF2 across chunk
+boundaries, both initial rows, nx != ny, the TMA rows-C at nx = 1024, nx = 2048) and their
+float64 plain runs go through that build with checks after every second iteration and
+find no out-of-range index."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SCRIPT = r'''
+import numpy as np
+import pdhg_workloads as W
+from paper_2207_07234_gb300 import binding as B
+base = dict(tau_u=0.4, tau_phi=0.4, tau_u0=0.1, tau_lambda=0.99)
+cases = [W.burgers_2d(n=256, nt=71).replace(**base),
+         W.burgers_2d(n=256, nt=9).replace(time="bdf2", **base),
+         W.burgers_2d(n=256, nt=6).replace(init="pinned", nu=0.02, **base)]
+p = W.burgers_2d(n=1024, nt=5).replace(**base)
+cases.append(p.replace(ny=512, ly=np.pi, u0=np.ascontiguousarray(p.u0[:512])))
+p = W.burgers_2d(n=2048, nt=3).replace(**base)
+cases.append(p.replace(ny=256, ly=np.pi / 4, u0=np.ascontiguousarray(p.u0[:256])))
+for q in cases:
+    for prec, path in (("fp32", "fused"), ("fp64", "plain")):
+        with B.Solver(q, precision=prec, path=path) as s:
+            s.iterate(4, tol=0.0, check_every=2)
+            s.residual()
+print("debug build: no out-of-range index in", len(cases), "cases")
+'''
+
+
+def test_debug_build_finds_no_out_of_range_index():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_07234_gb300 import _build
+    lib = _build.build(debug=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PDHG_LIBRARY=lib)
+    r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
+    assert "no out-of-range index" in r.stdout
