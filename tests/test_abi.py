@@ -118,3 +118,26 @@ def test_non_power_of_two_nx_accepted_only_for_1d_fd(lib):
         with pytest.raises(binding.PdhgError) as e:
             binding.workspace_size(bad, "fp64")
         assert e.value.status == -7
+
+
+def test_mixed_workspace_and_wait_budget_without_device_work(lib):
+    """The mixed solve's workspace holds the float32 handle and the float64 one; for
+    finite differences (nx a power of two) the float64 part adds float32 copies of the
+    preconditioner's tables (x/y twiddles, theta), for DG it does not.  A null handle is
+    rejected by pdhg_set_wait_budget."""
+    from paper_2207_07234_gb300 import binding
+    for p, pre32 in ((W.burgers_2d(n=64, nt=8), True), (W.traffic_dg_p1(ncell=32, nt=4), False)):
+        prob, grid, scheme, keep = binding.structs(p, "fp64", "plain")
+        nb = ctypes.c_size_t(0)
+        assert lib.pdhg_mixed_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                             ctypes.byref(nb)) == 0
+        n32 = _size(p, precision="fp32", path="auto")
+        n64 = _size(p, precision="fp64", path="plain")
+        extra = nb.value - (-(-n32 // 256) * 256 + n64)
+        if pre32:
+            nkx, ny = p.nx // 2 + 1, p.ny
+            tables = nkx * 8 + ny * 8 + nkx * ny * 4           # twx, twy (float2), theta (float)
+            assert tables <= extra <= tables + 3 * 256
+        else:
+            assert extra == 0
+    assert lib.pdhg_set_wait_budget(None, ctypes.c_uint64(0)) == -1
