@@ -69,3 +69,25 @@ def test_thomas_kappa_zero_prefix_sums():
     y = np.cumsum(0.25 * r[:, 0])
     zz = np.cumsum(y[::-1])[::-1]
     assert np.allclose(z[:, 0], zz, atol=1e-14)
+
+
+def test_float32_preconditioner_keeps_the_fixed_point(monkeypatch):
+    """The reading behind the float32 preconditioner of the mixed solve's float64 phase
+    (and of the float32 t-recurrence): K_d^{-1} only shapes the iteration.  Algorithm 1
+    with K_d^{-1} applied to a float32-rounded residual and its result rounded to float32
+    again reaches the same discrete solution (Newton) as the exact preconditioner, to the
+    float64 tolerance, in about the same number of iterations."""
+    from oracle import newton, pdhg as opdhg
+    p = W.advection_upwind_be(nx=64, nt=16, tau=(1.4, 0.1, 0.35, 0.99))
+    _, n_exact, _ = opdhg.solve(p, tol=1e-10, relative=True, check_every=10, max_iters=20000)
+    exact = precond.kd_inverse
+
+    def kd_inverse_f32(q, r):
+        return exact(q, np.asarray(r, np.float32).astype(np.float64)).astype(np.float32).astype(np.float64)
+
+    monkeypatch.setattr(precond, "kd_inverse", kd_inverse_f32)
+    st, n32, _ = opdhg.solve(p, tol=1e-10, relative=True, check_every=10, max_iters=20000)
+    un = newton.solve(p)
+    assert n32 < 20000
+    assert np.max(np.abs(st["u"] - un)) <= 1e-8 * np.max(np.abs(un))
+    assert abs(n32 - n_exact) <= 0.05 * n_exact + 10
