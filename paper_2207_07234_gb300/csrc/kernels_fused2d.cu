@@ -10,8 +10,12 @@
 //           complex FFT along y, forward elimination of (T_t + kappa h_t^2)
 //           per mode with the spill written in place, back substitution, and
 //           inverse FFT along y, written in place: the x-spectrum of z.
-//   rows-C  (H rows x one slice per block) inverse real FFT along x, dual
-//           step phi^n = phi^{n-1} + tau_phi z and extrapolation phit = phi^n + tau_phi z.
+//   rows-C  (tiles of H rows x one slice; at nx = 1024 persistent blocks whose tiles'
+//           spectra arrive by TMA) inverse real FFT along x, dual step
+//           phi^n = phi^{n-1} + tau_phi z and extrapolation phit = phi^n + tau_phi z.
+// Also here: the residual norms of a 2D finite-difference state (k_check2d, float32 and
+// float64).  Debug builds (-DPDHG_DEBUG) check the global indices of these kernels
+// (common.cuh::dbg_idx).
 #include <algorithm>
 #include <type_traits>
 
