@@ -180,13 +180,20 @@ def stage_bytes(p, esz: int):
         "dual": spec + f + 2 * f,                           # read spectrum, phi; write phi, phit
         "fused_rows": u + spec,                             # rows-R: read u; write X
         "fused_cols": spec + spec + 2 * spec,               # read X, write Zx, spill w/r
+        # rows-CP: read the spectrum, phi, u; write phi, u (phit is not stored); lambda row
+        "fused_dual_primal": spec + 2 * f + 2 * u + 5 * lam,
     }
 
+
+# Algorithmic bytes of one pass of the whole path per cell-iteration, by element size:
+# u and phit read, u written (12 B in float32), the t-solve's one spill round trip
+# (8 B), phi read and phi, phit written (12 B).
+ALG_BYTES_PER_CELL = {4: 32, 8: 64}
 
 KERNEL_SOURCES = {"primal": "kernels_plain.cu", "residual_fft": "kernels_plain.cu",
                   "fft_y": "kernels_plain.cu", "tsolve": "kernels_plain.cu",
                   "dual": "kernels_plain.cu", "fused_rows": "kernels_fused2d.cu",
-                  "fused_cols": "kernels_fused2d.cu"}
+                  "fused_cols": "kernels_fused2d.cu", "fused_dual_primal": "kernels_fused2d.cu"}
 # the fused 2D path runs its own primal and dual kernels
 FUSED_SOURCES = dict(KERNEL_SOURCES, primal="kernels_fused2d.cu", dual="kernels_fused2d.cu")
 
@@ -244,32 +251,69 @@ def time_oracle(p, iters=3, warm=1):
     return q.cells_per_iter * iters / dt, q, dt
 
 
+def _oracle_worker(args):
+    """One host process: the oracle on the workload's 8-slice sample (single-threaded
+    numpy), timed between two barriers shared by all processes."""
+    name, iters, warm, bar = args
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    from oracle import pdhg as opdhg
+    q = oracle_sample(workload(name))
+    st = opdhg.initial_state(q)
+    for _ in range(warm):
+        opdhg.step(q, st)
+    bar.wait()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        opdhg.step(q, st)
+    dt = time.perf_counter() - t0
+    return q.cells_per_iter * iters, dt
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle_all_cores(name, iters, warm=1, procs=None):
+    """The oracle on every host core at once: one spawned process per core, each on its
+    own copy of the 8-slice sample; throughput = all processes' cell-iterations / the
+    slowest process's time.  Returns (value, processes, seconds)."""
+    import multiprocessing as mp
+    n = procs or host_cores()
+    ctx = mp.get_context("spawn")             # no fork after CUDA initialisation
+    with ctx.Manager() as m:
+        bar = m.Barrier(n)
+        with ctx.Pool(n) as pool:
+            res = pool.map(_oracle_worker, [(name, iters, warm, bar)] * n)
+    cells = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return cells / dt, n, dt
+
+
 # ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
 
 def run_reference(args):
+    """The oracle (float64 numpy, as it stands) on every host core: one process per
+    core, each on the workload's 8-slice sample, `steps` timed iterations after
+    `warmup` untimed ones."""
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
     p = workload(args.workload)
     q = oracle_sample(p)
-    from oracle import pdhg as opdhg
-    st = opdhg.initial_state(q)
-    for _ in range(args.warmup):
-        opdhg.step(q, st)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        opdhg.step(q, st)
-    dt = time.perf_counter() - t0
-    value = q.cells_per_iter * args.steps / dt
+    value, n, dt = time_oracle_all_cores(args.workload, args.steps, warm=args.warmup)
     sample = (f"{q.name.replace(str(p.nt), str(q.nt))}: the workload cut to its first {q.nt} "
-              f"time slices, {args.steps} oracle iterations")
+              f"time slices, {args.steps} oracle iterations in each of {n} processes (one per host core)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": p.name, "oracle_sample_slices": q.nt},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -319,20 +363,42 @@ def run_ours(args):
     units = p.cells_per_iter * args.steps
     value, max_ms = aggregate(units, local_ms)
 
-    # roofline of the dominant stage
+    # roofline: the whole iteration against the algorithmic bytes of one pass of the
+    # path (32 B per cell-iteration in float32, 64 B in float64: u and phit read and u
+    # written, one spill round trip of the t-solve, phi read and phi, phit written),
+    # timed as ms_per_step; then every stage against its own compulsory bytes
     sb = stage_bytes(p, esz)
     dom = max(stages, key=lambda k: stages[k][0]) if stages else None
     peak, peak_kind = measured_peaks()
     roof = None
     if dom:
-        ms, n = stages[dom]
-        achieved = sb[dom] / (ms / n * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_for(dom, p.name, path == "fused"),
-                "algorithmic_bytes_per_launch": sb[dom], "avg_launch_ms": ms / n,
+        step_bytes = ALG_BYTES_PER_CELL[esz] * p.cells_per_iter
+        step_s = local_ms / args.steps * 1e-3
+        achieved = step_bytes / step_s / 1e9
+        per = {}
+        traffic_sum, traffic_ok = 0.0, True
+        for k, (ms, n) in stages.items():
+            tr = traffic_for(k, p.name, path == "fused")
+            per[k] = {"algorithmic_bytes_per_launch": sb.get(k), "avg_launch_ms": ms / n,
+                      "launches_per_step": n / args.steps,
+                      "achieved_gbs": (sb[k] / (ms / n * 1e-3) / 1e9) if k in sb else None,
+                      "frac": (sb[k] / (ms / n * 1e-3) / 1e9 / peak) if k in sb else None,
+                      "traffic": tr, "ms_share": round(ms / sum(x[0] for x in stages.values()), 4)}
+            if tr is None:
+                traffic_ok = False
+            else:
+                traffic_sum += tr * n / args.steps
+        per_dom = per[dom]
+        roof = {"bound": "hbm", "kernel": "iteration (all kernels of one step)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_sum if traffic_ok else None,
+                "algorithmic_bytes_per_cell": ALG_BYTES_PER_CELL[esz],
+                "algorithmic_bytes_per_step": step_bytes,
+                "measured_dram_bytes_per_cell": (traffic_sum / p.cells_per_iter) if traffic_ok else None,
+                "measured_dram_frac": (traffic_sum / step_s / 1e9 / peak) if traffic_ok else None,
                 "peak_source": peak_kind,
-                "stage_ms_share": {k: round(v[0] / sum(x[0] for x in stages.values()), 4)
-                                   for k, v in stages.items()}}
+                "dominant_kernel": dict(per_dom, kernel=dom),
+                "stages": per}
     solver.close()
     del solver
     torch.cuda.empty_cache()
@@ -366,10 +432,13 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, q, dt = time_oracle(p, iters=CPU_SAMPLE_ITERS)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{p.name} cut to its first {q.nt} time slices, {CPU_SAMPLE_ITERS} oracle iterations "
-                         f"({dt:.1f} s)"}
+        v1, q, dt1 = time_oracle(p, iters=CPU_SAMPLE_ITERS)
+        va, n, dta = time_oracle_all_cores(args.workload, CPU_SAMPLE_ITERS // 2)
+        cpu = {"value": va, "unit": UNIT, "cores": n, "kind": "oracle",
+               "sample": f"{p.name} cut to its first {q.nt} time slices: {CPU_SAMPLE_ITERS // 2} oracle "
+                         f"iterations in each of {n} processes, one per host core ({dta:.1f} s)",
+               "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                               "sample": f"{CPU_SAMPLE_ITERS} oracle iterations in one process ({dt1:.1f} s)"}}
 
     ttr = None
     if args.ttr and rank == 0:

@@ -70,7 +70,11 @@ enum { PDHG_STAGE_PRIMAL = 0,      /* primal step + lambda update (Algorithm 1 s
        PDHG_STAGE_FUSED_ROWS = 6,  /* fused 2D path: residual + x-FFT, spectrum stored transposed
                                       (its primal step is STAGE_PRIMAL, its dual step STAGE_DUAL) */
        PDHG_STAGE_FUSED_COLS = 7,  /* fused 2D path: y-FFT + t-solve + inverse y-FFT */
-       PDHG_NUM_STAGES = 8 };
+       PDHG_STAGE_FUSED_DUAL_PRIMAL = 8, /* fused 2D path, nx = 1024, BE: inverse x-FFT, dual step and the
+                                      next iteration's primal step in one kernel (phit not stored);
+                                      every iteration of a pdhg_iterate call but the last before a
+                                      residual check or the return */
+       PDHG_NUM_STAGES = 9 };
 
 /*
  * The conservation law u_t + f(u)_x - (gamma u_x)_x = 0 on a periodic domain
@@ -367,16 +371,21 @@ pdhg_status pdhg_batch_launch_count(pdhg_batch *b, int64_t *launches, int32_t re
  * pointers in the scheme's element type: u ((nt+1)*ndof), phi (nt*ndof), lambda
  * (ndof; may be NULL with PDHG_INIT_PINNED), u0 (ndof) and gamma_half (nx, or
  * NULL).  prob->u0 and prob->gamma_half are ignored; prob->lf_a must be > 0
- * for the Lax-Friedrichs schemes.  Enqueued on `stream`, then synchronised.
+ * for the Lax-Friedrichs schemes.  The grid, scheme and coefficients pass the
+ * same checks as in pdhg_create (sizes, powers of two, nu >= 0, finite
+ * coefficients; the step sizes and scheme->path are not used):
+ * PDHG_ERR_INVALID_ARG / PDHG_ERR_UNSUPPORTED otherwise, before any device work.
+ * Enqueued on `stream`, then synchronised.
  *
  * Scratch: a fixed 2 MiB array in device memory, part of the library image
  * (held on every GPU that uses it until the process exits).  Problems with
  * min(ceil(units/256), 32)*(nt+1) > 43685 partial blocks (units = ndof, or
  * cells for DG; so nt <= 1364 always fits) are rejected with
  * PDHG_ERR_UNSUPPORTED before any device work.  All calls share the array: calls that overlap on
- * the GPU race; calls ordered on one stream are safe.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make it before any stream capture.
+ * the GPU race; calls ordered on one stream are safe.  The first call in each
+ * CUDA context (a device's primary context; again after cudaDeviceReset) looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make it before any stream capture.
  */
 pdhg_status pdhg_residual_noalloc(const pdhg_problem *prob, const pdhg_grid *grid,
                                   const pdhg_scheme *scheme, const void *u, const void *phi,

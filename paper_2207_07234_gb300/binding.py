@@ -26,7 +26,8 @@ PRECISION = {"fp64": 0, "fp32": 1}
 INIT = {"lambda": 0, "pinned": 1}
 PATH = {"auto": 0, "plain": 1, "fused": 2}
 FIELD = {"u": 0, "phi": 1, "phit": 2, "lambda": 3, "lambdat": 4, "u_terminal": 5}
-STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_rows", "fused_cols"]
+STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_rows", "fused_cols",
+          "fused_dual_primal"]
 
 # every symbol include/pdhg.h declares
 EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_stream", "pdhg_iterate",
@@ -246,10 +247,10 @@ class Solver:
         _check(load().pdhg_set_wait_budget(self.h, int(ns)))
 
     def stage_times(self):
-        ms = (ctypes.c_double * 8)()
-        n = (ctypes.c_int64 * 8)()
+        ms = (ctypes.c_double * len(STAGES))()
+        n = (ctypes.c_int64 * len(STAGES))()
         _check(load().pdhg_stage_times(self.h, ms, n))
-        return {STAGES[i]: (ms[i], n[i]) for i in range(8) if n[i] > 0}
+        return {STAGES[i]: (ms[i], n[i]) for i in range(len(STAGES)) if n[i] > 0}
 
     # ---- fields ----
     def _shape(self, field):

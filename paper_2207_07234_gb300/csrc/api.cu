@@ -70,8 +70,10 @@ struct Geom {
     bool pre32;      // float64 state with the preconditioner applied in float32 (plain FD path)
 };
 
-pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s, Geom *G,
-                     bool pre32 = false) {
+// Checks of the grid, the scheme and the coefficients (everything but u0 and the
+// step sizes); fills G.  Shared with pdhg_residual_noalloc through check_shape().
+pdhg_status validate_shape(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s, Geom *G,
+                           bool pre32) {
     if (!p || !g || !s) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
     if (g->dims != 1 && g->dims != 2) return fail(PDHG_ERR_INVALID_ARG, "dims must be 1 or 2");
     if (s->time != PDHG_TIME_BE && s->time != PDHG_TIME_BDF2) return fail(PDHG_ERR_INVALID_ARG, "bad time scheme");
@@ -84,10 +86,6 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
     if (g->nx < 1 || (g->dims == 2 && g->ny < 1)) return fail(PDHG_ERR_INVALID_ARG, "nx, ny must be positive");
     if (!(g->T > 0) || !(g->lx > 0) || (g->dims == 2 && !(g->ly > 0)))
         return fail(PDHG_ERR_INVALID_ARG, "T, lx, ly must be positive");
-    if (!p->u0) return fail(PDHG_ERR_INVALID_ARG, "u0 is NULL");
-    if (!(p->tau_u > 0) || !(p->tau_phi > 0)) return fail(PDHG_ERR_INVALID_ARG, "tau_u, tau_phi must be > 0");
-    if (s->init == PDHG_INIT_LAMBDA && (!(p->tau_u0 > 0) || !(p->tau_lambda > 0)))
-        return fail(PDHG_ERR_INVALID_ARG, "tau_u0, tau_lambda must be > 0");
     if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !(p->nu >= 0) || !std::isfinite(p->nu) ||
         !std::isfinite(p->c) || !std::isfinite(p->gamma_hat) || !(p->lf_a >= 0) || !std::isfinite(p->lf_a))
         return fail(PDHG_ERR_INVALID_ARG, "non-finite or negative coefficient");
@@ -128,6 +126,17 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
         G->fused = ok;
     }
     G->pre32 = pre32 && s->precision == PDHG_FP64 && !G->fused && !dg && G->blu_log2L == 0;
+    return PDHG_OK;
+}
+
+pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s, Geom *G,
+                     bool pre32 = false) {
+    pdhg_status st = validate_shape(p, g, s, G, pre32);
+    if (st != PDHG_OK) return st;
+    if (!p->u0) return fail(PDHG_ERR_INVALID_ARG, "u0 is NULL");
+    if (!(p->tau_u > 0) || !(p->tau_phi > 0)) return fail(PDHG_ERR_INVALID_ARG, "tau_u, tau_phi must be > 0");
+    if (s->init == PDHG_INIT_LAMBDA && (!(p->tau_u0 > 0) || !(p->tau_lambda > 0)))
+        return fail(PDHG_ERR_INVALID_ARG, "tau_u0, tau_lambda must be > 0");
     return PDHG_OK;
 }
 
@@ -269,6 +278,16 @@ void dg_symbol(double c, double h, double theta, cd S[3][3]) {
 
 }  // namespace
 
+// The grid, scheme and coefficient checks of pdhg_create for a caller that brings
+// its own state (no u0, no step sizes); the path is not part of it.
+pdhg_status pdhg::check_shape(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s) {
+    if (!s) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
+    pdhg_scheme plain = *s;
+    plain.path = PDHG_PATH_PLAIN;
+    Geom G;
+    return validate_shape(p, g, &plain, &G, false);
+}
+
 // ---------------------------------------------------------------------------
 // handle
 // ---------------------------------------------------------------------------
@@ -300,6 +319,11 @@ struct pdhg_handle {
     cudaStream_t gstream;
     int32_t gchunk;
     int64_t glaunches;       // kernel launches per replay
+    // fused path between residual checks (inside one pdhg_iterate call only): the next
+    // iteration's primal step has already been applied to u (ahead), and phi^n sits in the
+    // phit buffer (phi_alt); both are false whenever the state is visible to the caller
+    bool ahead;
+    bool phi_alt;
 };
 
 static void graph_drop(pdhg_handle *h) {
@@ -327,7 +351,8 @@ static cudaError_t stage(pdhg_handle *h, int st, int nlaunch, Fn fn) {
     // NVTX names of the stages (host ranges around each stage's launches while profiling)
     static const char *const names[PDHG_NUM_STAGES] = {"pdhg primal", "pdhg residual + x-FFT", "pdhg y-FFT",
                                                        "pdhg t-solve", "pdhg dual", "pdhg residual norms",
-                                                       "pdhg fused rows", "pdhg fused cols"};
+                                                       "pdhg fused rows", "pdhg fused cols",
+                                                       "pdhg fused dual + primal"};
     EvRec r{st, nullptr, nullptr};
     if (h->profiling) {
         nvtxRangePushA(names[st]);
@@ -734,6 +759,7 @@ static pdhg_status create_impl(const pdhg_problem *prob, const pdhg_grid *grid, 
     h->wx = G.dims == 2 ? hx * (grid->ly / (double)grid->ny) : hx;
     h->iters = 0; h->launches = 0; h->profiling = false;
     h->res_norm = 0;
+    h->ahead = h->phi_alt = false;
     for (int k = 0; k < 4; ++k) h->last_res[k] = NAN;
     h->graphs = !G.fused;
     h->gexec = nullptr; h->gstream = nullptr; h->gchunk = 0; h->glaunches = 0;
@@ -779,8 +805,12 @@ extern "C" pdhg_status pdhg_set_stream(pdhg_handle *h, void *stream) {
     return PDHG_OK;
 }
 
+// One iteration of Algorithm 1.  On the fused path with the dual-primal kernel, an
+// iteration that is not `last` (no residual check or return follows it) ends with that
+// kernel: its dual step and the next iteration's primal step, phit never stored; a
+// `last` one ends with rows-C, so that the caller sees (u^n, phi^n, phit^n) as always.
 template <typename T>
-static cudaError_t enqueue_iteration(pdhg_handle *h) {
+static cudaError_t enqueue_iteration(pdhg_handle *h, bool last) {
     const Params<T> &P = params_of<T>(h);
     cudaStream_t s = h->stream;
     T *u = F<T>(h, h->u_off), *phi = F<T>(h, h->L.phi), *phit = F<T>(h, h->L.phit);
@@ -793,15 +823,30 @@ static cudaError_t enqueue_iteration(pdhg_handle *h) {
         if constexpr (sizeof(T) == 4) {
             Fused2D *f = &h->fused;
             float *uf = F<float>(h, h->u_off);
-            e = stage(h, PDHG_STAGE_PRIMAL, 1, [&] {
-                return fused2d_primal(h->pf, uf, phit, lam, lamt, u0, s);
-            });
-            if (e != cudaSuccess) return e;
+            if (!h->ahead) {
+                e = stage(h, PDHG_STAGE_PRIMAL, 1, [&] {
+                    return fused2d_primal(h->pf, uf, phit, lam, lamt, u0, s);
+                });
+                if (e != cudaSuccess) return e;
+            }
             e = stage(h, PDHG_STAGE_FUSED_ROWS, 1, [&] { return fused2d_rowsR(f, h->pf, uf, s); });
             if (e != cudaSuccess) return e;
             e = stage(h, PDHG_STAGE_FUSED_COLS, 1, [&] { return fused2d_cols(f, h->pf, s); });
             if (e != cudaSuccess) return e;
-            return stage(h, PDHG_STAGE_DUAL, 1, [&] { return fused2d_rowsC(f, h->pf, phi, phit, s); });
+            float *src = h->phi_alt ? phit : phi;
+            if (!last && f->cp) {
+                float *dst = h->phi_alt ? phi : phit;
+                e = stage(h, PDHG_STAGE_FUSED_DUAL_PRIMAL, 1, [&] {
+                    return fused2d_rowsCP(f, h->pf, src, dst, uf, lam, lamt, u0, s);
+                });
+                h->phi_alt = !h->phi_alt;
+                h->ahead = true;
+                return e;
+            }
+            e = stage(h, PDHG_STAGE_DUAL, 1, [&] { return fused2d_rowsC(f, h->pf, src, phi, phit, s); });
+            h->phi_alt = false;
+            h->ahead = false;
+            return e;
         }
         return cudaErrorInvalidValue;
     }
@@ -859,7 +904,7 @@ static cudaError_t graph_build(pdhg_handle *h, int32_t m) {
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int32_t i = 0; i < m && e == cudaSuccess; ++i) e = enqueue_iteration<T>(h);
+        for (int32_t i = 0; i < m && e == cudaSuccess; ++i) e = enqueue_iteration<T>(h, true);
         if (e == cudaSuccess) e = enqueue_check<T>(h);
         cudaError_t e2 = cudaStreamEndCapture(h->gstream, &g);
         if (e == cudaSuccess) e = e2;
@@ -895,8 +940,12 @@ static pdhg_status iterate_T(pdhg_handle *h, int64_t max_iters, double tol, int3
             h->launches += h->glaunches;
             st = read_res(h, r);
         } else {
-            cudaError_t e = enqueue_iteration<T>(h);
-            if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
+            const bool last = n + 1 == max_iters || (check_every > 0 && (n + 1) % check_every == 0);
+            cudaError_t e = enqueue_iteration<T>(h, last);
+            if (e != cudaSuccess) {
+                h->ahead = h->phi_alt = false;
+                return cuda_fail(e, "iteration launch");
+            }
             ++n;
             ++h->iters;
             if (!(check_every > 0 && (n % check_every == 0 || n == max_iters))) continue;

@@ -18,8 +18,12 @@
 //
 // Host code cannot pass the array's name to a kernel (in host code it is only
 // a stand-in for the device symbol), so the device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, by the
-// first call made on it.  Make that first call before any stream capture.
+// cudaGetSymbolAddress, with the device current, by the first call made in its
+// CUDA context.  The address is cached per device together with that
+// context's unique id (cuCtxGetId): after a cudaDeviceReset the device's new
+// primary context has a new id, and the next call looks the address up again.
+// Make the first call in a context before any stream capture.
+#include <cuda.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -44,25 +48,57 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx[kMaxDevices] = {0};    // id of the context g_addr[dev] belongs to
+
+typedef CUresult (*ctx_current_fn)(CUcontext *);
+typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current CUDA context (0: none current, or the
+// driver does not report one, in which case the address is looked up on every call).
+unsigned long long current_context_id() {
+    static ctx_current_fn get_current = nullptr;
+    static ctx_id_fn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (ctx_current_fn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (ctx_id_fn)f;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 pdhg_status err(pdhg_status st, const std::string &m) {
     pdhg::set_last_error(m);
     return st;
 }
 
-// Device address of the scratch array for the current device (set up once per device).
+// Device address of the scratch array for the current device, set up once per
+// device and context (looked up again when the device's context has changed).
 pdhg_status scratch_address(void **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return err(PDHG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return err(PDHG_ERR_UNSUPPORTED, "device index out of range");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return err(PDHG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_addr[dev] = p;
+        g_ctx[dev] = current_context_id();        // the lookup has made the context current
     }
     *out = g_addr[dev];
     return PDHG_OK;
@@ -126,21 +162,16 @@ extern "C" pdhg_status pdhg_residual_noalloc(const pdhg_problem *prob, const pdh
     if (!prob || !grid || !scheme || !u || !phi || !u0 || !out)
         return err(PDHG_ERR_INVALID_ARG, "null argument");
     if (scheme->init == PDHG_INIT_LAMBDA && !lambda) return err(PDHG_ERR_INVALID_ARG, "lambda is NULL");
-    if (grid->dims != 1 && grid->dims != 2) return err(PDHG_ERR_INVALID_ARG, "dims must be 1 or 2");
-    if (grid->nt < 1 || grid->nt > 65534 || grid->nx < 2 || (grid->dims == 2 && grid->ny < 2))
-        return err(PDHG_ERR_INVALID_ARG, "bad grid size");
-    if (!(grid->T > 0) || !(grid->lx > 0) || (grid->dims == 2 && !(grid->ly > 0)))
-        return err(PDHG_ERR_INVALID_ARG, "T, lx, ly must be positive");
-    if (scheme->space < PDHG_SPACE_FD_UPWIND || scheme->space > PDHG_SPACE_DG_P1_LF ||
-        (scheme->time != PDHG_TIME_BE && scheme->time != PDHG_TIME_BDF2) ||
-        (scheme->init != PDHG_INIT_LAMBDA && scheme->init != PDHG_INIT_PINNED))
-        return err(PDHG_ERR_INVALID_ARG, "bad scheme");
-    if (scheme->space >= PDHG_SPACE_DG_P2_LF && (grid->dims != 1 || gamma_half || prob->nu != 0))
-        return err(PDHG_ERR_UNSUPPORTED, "DG is 1D without viscous terms");
+    // pdhg_create's checks of the grid, scheme and coefficients (sizes within the
+    // library's limits, so that every index stays in range), with this call's
+    // gamma_half in place of prob->gamma_half
+    pdhg_problem shape = *prob;
+    shape.gamma_half = (const double *)gamma_half;
+    const pdhg_status vs = check_shape(&shape, grid, scheme);
+    if (vs != PDHG_OK) return vs;
     if ((scheme->space == PDHG_SPACE_FD_LF || scheme->space == PDHG_SPACE_DG_P2_LF ||
          scheme->space == PDHG_SPACE_DG_P1_LF) && !(prob->lf_a > 0))
         return err(PDHG_ERR_INVALID_ARG, "lf_a must be given (> 0) for Lax-Friedrichs schemes");
-    if (gamma_half && grid->dims != 1) return err(PDHG_ERR_UNSUPPORTED, "gamma_half is 1D only");
     cudaStream_t s = (cudaStream_t)stream;
     if (scheme->precision == PDHG_FP64)
         return run<double>(prob, grid, scheme, u, phi, lambda, u0, gamma_half, out, s);

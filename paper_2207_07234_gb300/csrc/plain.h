@@ -3,12 +3,16 @@
 
 #include <string>
 
+#include "../../include/pdhg.h"
 #include "common.cuh"
 
 namespace pdhg {
 
 // sets the message returned by pdhg_last_error() on the calling thread
 void set_last_error(const std::string &msg);
+// pdhg_create's checks of the grid, the scheme and the coefficients (not u0, not the
+// step sizes, not the path); reports through pdhg_last_error()
+pdhg_status check_shape(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s);
 
 template <typename T> cudaError_t init_plain_attributes();
 template <typename T>
