@@ -70,11 +70,7 @@ enum { PDHG_STAGE_PRIMAL = 0,      /* primal step + lambda update (Algorithm 1 s
        PDHG_STAGE_FUSED_ROWS = 6,  /* fused 2D path: residual + x-FFT, spectrum stored transposed
                                       (its primal step is STAGE_PRIMAL, its dual step STAGE_DUAL) */
        PDHG_STAGE_FUSED_COLS = 7,  /* fused 2D path: y-FFT + t-solve + inverse y-FFT */
-       PDHG_STAGE_FUSED_DUAL_PRIMAL = 8, /* fused 2D path, nx = 1024, BE: inverse x-FFT, dual step and the
-                                      next iteration's primal step in one kernel (phit not stored);
-                                      every iteration of a pdhg_iterate call but the last before a
-                                      residual check or the return */
-       PDHG_NUM_STAGES = 9 };
+       PDHG_NUM_STAGES = 8 };
 
 /*
  * The conservation law u_t + f(u)_x - (gamma u_x)_x = 0 on a periodic domain
@@ -83,7 +79,8 @@ enum { PDHG_STAGE_PRIMAL = 0,      /* primal step + lambda update (Algorithm 1 s
  *   nu          constant viscosity: adds -nu * central second difference
  *   gamma_half  host pointer to gamma_{j+1/2}, j = 0..nx-1 (1D FD only) or NULL;
  *               adds -Lap(u) of Sec. 3.2.1.  Copied at create.
- *   u0          host pointer to the initial slice (dof layout above). Copied at create.
+ *   u0          host pointer to the initial slice (dof layout above), or a device pointer
+ *               with PDHG_FLAG_U0_ON_DEVICE.  Copied at create.
  *   lf_a        global Lax-Friedrichs constant for the LF schemes (0: max |f'(u0)|);
  *               the upwind schemes use f(u-) and are monotone where f' >= 0
  *   c, gamma_hat  K = -d_tt - c^2 d_xx + gamma_hat^2 d_xxxx (Eq. 2.8, 2.10);
@@ -116,7 +113,23 @@ typedef struct {
 
 /* time: PDHG_TIME_*; space: PDHG_SPACE_*; precision: PDHG_FP64 / PDHG_FP32;
  * init: PDHG_INIT_LAMBDA (Algorithm 1's multiplier on u^0 = u0) or
- * PDHG_INIT_PINNED (u^0 held at u0); path: PDHG_PATH_*; flags: 0. */
+ * PDHG_INIT_PINNED (u^0 held at u0); path: PDHG_PATH_*; flags: 0 or a combination
+ * of PDHG_FLAG_EXACT_TIME_PRECOND and PDHG_FLAG_U0_ON_DEVICE.
+ *
+ * PDHG_FLAG_EXACT_TIME_PRECOND (an ablation of the preconditioner of Sec. 3.3): the
+ * time part of K_d is the scheme's own h_t^2 D_t D_t^T (D_t the BE or BDF2 time
+ * difference with u^0 held fixed) instead of T_t = tridiag(-1; 1, 2, ..., 2; -1).  For
+ * BE the two are the same matrix; for BDF2 D_t D_t^T is pentadiagonal, applied per
+ * Fourier mode by LDL^T factors computed at create.  Plain path only (PDHG_PATH_AUTO
+ * then chooses it; PDHG_PATH_FUSED gives PDHG_ERR_UNSUPPORTED), at most 2^24
+ * (mode, slice) pairs.  The fixed point does not depend on it. */
+enum { PDHG_FLAG_EXACT_TIME_PRECOND = 1,
+/* PDHG_FLAG_U0_ON_DEVICE: pdhg_problem.u0 is a device pointer (float64, ndof values, kept
+ * by the caller).  The library converts it on the device and takes the finite check and
+ * the Lax-Friedrichs constant (lf_a = 0) from a device scan: u0 is not copied to the
+ * host.  Accepted by pdhg_create and every entry point built on it (mixed, refine,
+ * gradient, batch); PDHG_ERR_UNSUPPORTED for pdhg_solve_one_step. */
+       PDHG_FLAG_U0_ON_DEVICE = 2 };
 typedef struct {
     int32_t time, space, precision, init, path, flags;
 } pdhg_scheme;
@@ -236,7 +249,8 @@ pdhg_status pdhg_solve_refine(const pdhg_problem *prob, const pdhg_grid *grid,
  * Algorithm 1 on the two-slice problem over [l h_t, (l+1) h_t] whose initial
  * data is u*^l (u*^0 = u0), started from [u*^l, u*^l], 0, 0, until both
  * entries of its Res are <= tol, checked every check_every iterations, or
- * max_iters_per_step.  Res here is the L2 norm over the domain at one time
+ * max_iters_per_step (in float32 also once the larger entry has not fallen by 5%
+ * over the step's last three checks: float32's rounding floor).  Res here is the L2 norm over the domain at one time
  * (weight w_x, no h_t), as Sec. 3.5 defines it.  Every input of the full
  * problem is kept (flux, c, step sizes, h_t, and the Lax-Friedrichs constant
  * computed from the full problem's u0 when prob->lf_a is 0), so with tol -> 0

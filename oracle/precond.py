@@ -10,7 +10,9 @@ with the H-norm boundary term at t = 0 only (Sec. 2.2) and phi^{nt} = 0
 T_t = tridiag(-1; 1, 2, ..., 2; -1) of size nt (row l = 0 carries the 1: the
 Neumann end at t = 0; the Dirichlet end sits beyond l = nt-1).  T_t / h_t^2
 equals D_t D_t^T for the backward-Euler difference with u^0 held fixed.
-The same T_t is used for BDF2.
+The same T_t is used for BDF2.  An ablation (p.tprec == "exact") replaces T_t by the
+scheme's own h_t^2 D_t D_t^T = A_t A_t^T (pentadiagonal for BDF2), applied per Fourier
+mode by a dense solve.
 
 K_x for finite differences is diagonal in the discrete Fourier basis with
 symbol kappa(theta) = c^2 L(theta) + ghat^2 L(theta)^2, L(theta) = (2 - 2 cos
@@ -31,7 +33,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import spatial
+from . import spacetime, spatial
 
 
 def symbol_L(n, h):
@@ -114,6 +116,44 @@ def thomas_t(rhs, s, ht):
     return z
 
 
+def time_matrix(p):
+    """A_t: the time part of the scheme's equations as an nt x nt matrix acting on
+    u^1..u^nt (u^0 held fixed), read off the residual's own coefficients
+    (spacetime.time_coefs), times h_t: row m is h_t * coef(m, k+1) in column k."""
+    A = np.zeros((p.nt, p.nt))
+    for m in range(p.nt):
+        for k, c in spacetime.time_coefs(p, m).items():
+            if k >= 1:
+                A[m, k - 1] = c * p.ht
+    return A
+
+
+def exact_Tt(p):
+    """The ablation's time operator, h_t^2 D_t D_t^T = A_t A_t^T (Sec. 3.3 takes K_d as
+    the discrete operator of K; for BE this is T_t, for BDF2 a pentadiagonal matrix)."""
+    A = time_matrix(p)
+    return A @ A.T
+
+
+def exact_t_solve(rhs, s, ht, Tt):
+    """Solve (Tt + s) z = h_t^2 rhs along axis 0 for every trailing index (s broadcast over
+    the trailing axes), by a dense solve per trailing index (numpy.linalg.solve)."""
+    nt = rhs.shape[0]
+    tail = rhs.shape[1:]
+    sb = np.broadcast_to(s, tail).reshape(-1)
+    R = (ht * ht * rhs).reshape(nt, -1).T                       # [n][nt]
+    M = Tt[None, :, :] + sb[:, None, None] * np.eye(nt)[None]    # [n][nt][nt]
+    Z = np.linalg.solve(M, R[..., None])[..., 0]
+    return Z.T.reshape((nt,) + tail)
+
+
+def _t_solve(p, rhs, s):
+    """The time solve of K_d^{-1}: Thomas on T_t, or the exact operator for p.tprec == 'exact'."""
+    if getattr(p, "tprec", "tridiag") == "exact":
+        return exact_t_solve(rhs, s, p.ht, exact_Tt(p))
+    return thomas_t(rhs, s, p.ht)
+
+
 def kd_inverse(p, r):
     """z = K_d^{-1} r for r of shape [nt, *slice] (real)."""
     ht = p.ht
@@ -122,7 +162,7 @@ def kd_inverse(p, r):
         rh = np.moveaxis(rh, -1, 1)                       # [nt][k][nm]
         lam, V = np.linalg.eigh(dg_Kx(p))                 # K_x = V diag(lam) V^H
         w = np.einsum("kmi,tkm->tki", np.conj(V), rh)     # V^H r
-        w = thomas_t(w, lam * ht * ht, ht)
+        w = _t_solve(p, w, lam * ht * ht)
         zh = np.einsum("kmi,tki->tkm", V, w)
         zh = np.moveaxis(zh, 1, -1)
         return np.fft.irfft(zh, n=p.nx, axis=-1)
@@ -130,7 +170,7 @@ def kd_inverse(p, r):
     rh = np.fft.rfft(r, axis=-1)
     if p.dims == 2:
         rh = np.fft.fft(rh, axis=-2)
-    zh = thomas_t(rh, kappa * ht * ht, ht)
+    zh = _t_solve(p, rh, kappa * ht * ht)
     if p.dims == 2:
         zh = np.fft.ifft(zh, axis=-2)
     return np.fft.irfft(zh, n=p.nx, axis=-1)
@@ -176,6 +216,8 @@ def dense_Kx(p):
 
 
 def dense_Kd(p):
-    """K_d = T_t/h_t^2 (x) I + I (x) K_x as an (nt*ndof)^2 matrix."""
+    """K_d = T_t/h_t^2 (x) I + I (x) K_x as an (nt*ndof)^2 matrix (T_t replaced by
+    exact_Tt for p.tprec == 'exact')."""
     n = p.ndof
-    return np.kron(dense_Tt(p.nt) / p.ht ** 2, np.eye(n)) + np.kron(np.eye(p.nt), dense_Kx(p))
+    Tt = exact_Tt(p) if getattr(p, "tprec", "tridiag") == "exact" else dense_Tt(p.nt)
+    return np.kron(Tt / p.ht ** 2, np.eye(n)) + np.kron(np.eye(p.nt), dense_Kx(p))

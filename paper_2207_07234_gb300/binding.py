@@ -26,8 +26,9 @@ PRECISION = {"fp64": 0, "fp32": 1}
 INIT = {"lambda": 0, "pinned": 1}
 PATH = {"auto": 0, "plain": 1, "fused": 2}
 FIELD = {"u": 0, "phi": 1, "phit": 2, "lambda": 3, "lambdat": 4, "u_terminal": 5}
-STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_rows", "fused_cols",
-          "fused_dual_primal"]
+FLAG_EXACT_TIME_PRECOND = 1      # pdhg_scheme.flags: time part of K_d = h_t^2 D_t D_t^T (ablation)
+FLAG_U0_ON_DEVICE = 2            # pdhg_scheme.flags: pdhg_problem.u0 is a device pointer
+STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_rows", "fused_cols"]
 
 # every symbol include/pdhg.h declares
 EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_stream", "pdhg_iterate",
@@ -135,13 +136,22 @@ def _check(status):
         raise PdhgError(status, load().pdhg_last_error().decode())
 
 
-def structs(p, precision="fp32", path="auto"):
-    """C structs for a pdhg_workloads.Problem; returns (prob, grid, scheme, keepalive)."""
-    u0 = np.ascontiguousarray(p.u0, dtype=np.float64).ravel()
-    keep = [u0]
+def structs(p, precision="fp32", path="auto", u0_device=None):
+    """C structs for a pdhg_workloads.Problem; returns (prob, grid, scheme, keepalive).
+    u0_device: a contiguous float64 CUDA tensor holding u0 (PDHG_FLAG_U0_ON_DEVICE), else
+    p.u0 is passed from host memory."""
     prob = pdhg_problem()
     prob.alpha, prob.beta, prob.nu = p.alpha, p.beta, p.nu
-    prob.u0 = u0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if u0_device is not None:
+        import torch
+        assert u0_device.is_cuda and u0_device.dtype == torch.float64 and u0_device.is_contiguous()
+        assert u0_device.numel() == p.ndof
+        keep = [u0_device]
+        prob.u0 = ctypes.cast(ctypes.c_void_p(u0_device.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    else:
+        u0 = np.ascontiguousarray(p.u0, dtype=np.float64).ravel()
+        keep = [u0]
+        prob.u0 = u0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     if p.gamma_half is not None:
         g = np.ascontiguousarray(p.gamma_half, dtype=np.float64)
         keep.append(g)
@@ -149,7 +159,10 @@ def structs(p, precision="fp32", path="auto"):
     prob.lf_a, prob.c, prob.gamma_hat = p.lf_a, p.c, p.gamma_hat
     prob.tau_u, prob.tau_u0, prob.tau_phi, prob.tau_lambda = p.tau_u, p.tau_u0, p.tau_phi, p.tau_lambda
     grid = pdhg_grid(p.dims, p.nx, p.ny if p.dims == 2 else 1, p.lx, p.ly, p.T, p.nt)
-    scheme = pdhg_scheme(TIME[p.time], SPACE[p.space], PRECISION[precision], INIT[p.init], PATH[path], 0)
+    flags = FLAG_EXACT_TIME_PRECOND if getattr(p, "tprec", "tridiag") == "exact" else 0
+    if u0_device is not None:
+        flags |= FLAG_U0_ON_DEVICE
+    scheme = pdhg_scheme(TIME[p.time], SPACE[p.space], PRECISION[precision], INIT[p.init], PATH[path], flags)
     return prob, grid, scheme, keep
 
 
@@ -331,12 +344,13 @@ def solve_one_step(p, tol=1e-3, max_iters_per_step=100000, check_every=1, precis
 
 
 def solve_gradient(p, target, tol=1e-10, max_iters=100000, adj_tol=1e-10, adj_max_iters=100000, check_every=10,
-                   precision="fp64", device=None, stream=None):
+                   precision="fp64", device=None, stream=None, u0_device=None):
     """Loss = w_x |u^nt - target|^2 of the scheme's solution and its gradient through
-    the solve: returns (loss, dLoss/du0 as numpy, dLoss/dnu, [forward, adjoint] iterations)."""
+    the solve: returns (loss, dLoss/du0 as numpy, dLoss/dnu, [forward, adjoint] iterations).
+    u0_device: u0 as a float64 CUDA tensor (used instead of p.u0, not copied to the host)."""
     import torch
     lib = load()
-    prob, grid, scheme, keep = structs(p, precision, "plain")
+    prob, grid, scheme, keep = structs(p, precision, "plain", u0_device=u0_device)
     nbytes = ctypes.c_size_t(0)
     _check(lib.pdhg_gradient_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
                                             ctypes.byref(nbytes)))
@@ -359,15 +373,22 @@ def solve_gradient(p, target, tol=1e-10, max_iters=100000, adj_tol=1e-10, adj_ma
 
 def terminal_loss_fn():
     """A torch.autograd.Function: loss = TerminalLoss.apply(u0, nu, problem, target, opts)
-    with u0 a float64 tensor of the slice shape and nu a 0-d float64 tensor; the
-    backward pass returns dLoss/du0 and dLoss/dnu computed by solve_gradient."""
+    with u0 a float64 tensor of the slice shape (a CUDA tensor is passed to the library as
+    a device pointer) and nu a 0-d float64 tensor; the backward pass returns dLoss/du0
+    and dLoss/dnu computed by solve_gradient (opts may choose precision="fp32")."""
     import torch
 
     class TerminalLoss(torch.autograd.Function):
         @staticmethod
         def forward(ctx, u0, nu, problem, target, opts=None):
-            q = problem.replace(u0=u0.detach().cpu().numpy().astype(np.float64), nu=float(nu))
-            loss, du0, dnu, _ = solve_gradient(q, target, **(opts or {}))
+            # u0 stays in device memory (PDHG_FLAG_U0_ON_DEVICE) when it is a CUDA tensor
+            q = problem.replace(nu=float(nu))
+            if u0.is_cuda:
+                dev_u0 = u0.detach().to(torch.float64).contiguous()
+                loss, du0, dnu, _ = solve_gradient(q, target, device=u0.device, u0_device=dev_u0, **(opts or {}))
+            else:
+                q = q.replace(u0=u0.detach().numpy().astype(np.float64))
+                loss, du0, dnu, _ = solve_gradient(q, target, **(opts or {}))
             ctx.save_for_backward(torch.as_tensor(du0, dtype=u0.dtype, device=u0.device),
                                   torch.as_tensor(dnu, dtype=nu.dtype, device=nu.device))
             return torch.as_tensor(loss, dtype=u0.dtype, device=u0.device)

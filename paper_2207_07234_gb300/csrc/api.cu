@@ -50,7 +50,7 @@ void pdhg::set_last_error(const std::string &msg) { g_last_error = msg; }
 namespace {
 
 struct Layout {
-    size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, partials, scal, dbg, fused;
+    size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, tfac, partials, scal, dbg, fused;
     size_t blu_tw, blu_c, blu_b;
     size_t twx32, twy32, theta32;    // float32 preconditioner tables (Geom::pre32)
     size_t total;
@@ -68,6 +68,7 @@ struct Geom {
     bool fused;
     int blu_log2L;   // > 0: Bluestein x-transform (1D FD, nx not a power of two)
     bool pre32;      // float64 state with the preconditioner applied in float32 (plain FD path)
+    bool exact_t;    // time part of K_d: the scheme's own h_t^2 D_t D_t^T (PDHG_FLAG_EXACT_TIME_PRECOND)
 };
 
 // Checks of the grid, the scheme and the coefficients (everything but u0 and the
@@ -119,13 +120,23 @@ pdhg_status validate_shape(const pdhg_problem *p, const pdhg_grid *g, const pdhg
     G->esz = s->precision == PDHG_FP64 ? 8 : 4;
     G->has_gamma = p->gamma_half != nullptr;
     G->fused = false;
-    if (s->path == PDHG_PATH_FUSED || s->path == PDHG_PATH_AUTO) {
+    if (s->flags & ~(int32_t)(PDHG_FLAG_EXACT_TIME_PRECOND | PDHG_FLAG_U0_ON_DEVICE))
+        return fail(PDHG_ERR_INVALID_ARG, "unknown scheme flag");
+    G->exact_t = (s->flags & PDHG_FLAG_EXACT_TIME_PRECOND) != 0;
+    if (G->exact_t) {
+        if (s->path == PDHG_PATH_FUSED)
+            return fail(PDHG_ERR_UNSUPPORTED, "the exact time preconditioner runs on the plain path");
+        if ((double)G->modes * (double)G->nt > (double)(int64_t(1) << 24))
+            return fail(PDHG_ERR_UNSUPPORTED, "the exact time preconditioner's factor table is limited to "
+                                              "2^24 (mode, slice) pairs");
+    }
+    if (!G->exact_t && (s->path == PDHG_PATH_FUSED || s->path == PDHG_PATH_AUTO)) {
         bool ok = fused2d_supported(g->dims, s->space, s->time, s->precision, g->nx, G->ny, g->nt, p->nu);
         if (s->path == PDHG_PATH_FUSED && !ok)
             return fail(PDHG_ERR_UNSUPPORTED, "the fused path needs 2D FD, FP32, nx in [256, 2048], ny in [256, 1024] (powers of two), nt >= 2");
         G->fused = ok;
     }
-    G->pre32 = pre32 && s->precision == PDHG_FP64 && !G->fused && !dg && G->blu_log2L == 0;
+    G->pre32 = pre32 && s->precision == PDHG_FP64 && !G->fused && !dg && G->blu_log2L == 0 && !G->exact_t;
     return PDHG_OK;
 }
 
@@ -157,6 +168,7 @@ Layout layout_of(const Geom &G) {
     L.twy = take(G.dims == 2 ? G.ny * 2 * e : 0);
     L.theta = take(G.modes * e);
     L.V = take(G.space >= PDHG_SPACE_DG_P2_LF ? G.nkx * 9 * 2 * e : 0);
+    L.tfac = take(G.exact_t ? 3 * G.nt * G.modes * e : 0);
     int64_t units = G.space >= PDHG_SPACE_DG_P2_LF ? G.nx : G.S;
     int64_t nblk = std::min<int64_t>((units + 255) / 256, 32) * (G.nt + 1);    // k_check grid
     L.partials = take(nblk * 6 * sizeof(double));
@@ -181,6 +193,48 @@ typedef std::complex<double> cd;
 
 // theta with cosh(theta) = 1 + s/2, i.e. theta = 2 asinh(sqrt(s)/2), s = kappa h_t^2 >= 0
 double theta_of(double s) { return s <= 0 ? 0.0 : 2.0 * std::asinh(0.5 * std::sqrt(s)); }
+
+// The exact time operator of the ablation: K = A_t A_t^T, A_t the scheme's time
+// differences times h_t acting on u^1..u^nt (u^0 held fixed; row m = equation R^m,
+// entries coef(m, m+1), coef(m, m), coef(m, m-1) in units of 1/h_t), so K is T_t for
+// backward Euler and pentadiagonal for BDF2.  For each mode the LDL^T factors of K + s
+// (L unit lower triangular with sub-diagonals e_l = L_{l,l-1}, f_l = L_{l,l-2}) go to
+// tab[3][nt][modes] as 1/d_l, e_l, f_l.
+template <typename T>
+void exact_t_factors(int time, int64_t nt, const std::vector<double> &s, std::vector<T> &tab) {
+    const int64_t modes = (int64_t)s.size();
+    auto Aj = [&](int64_t m, int j) -> double {           // A_t[m][m - j], column m - j = u^{m+1-j}
+        if (m < 0 || m >= nt || m - j < 0 || j > 2) return 0.0;
+        const bool be = time == PDHG_TIME_BE || m == 0;
+        if (j == 0) return be ? 1.0 : 1.5;
+        if (j == 1) return be ? -1.0 : -2.0;
+        return be ? 0.0 : 0.5;
+    };
+    std::vector<double> a(nt), b(nt), c(nt);                // K[l][l], K[l][l+1], K[l][l+2]
+    for (int64_t l = 0; l < nt; ++l) {
+        a[l] = b[l] = c[l] = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            a[l] += Aj(l, j) * Aj(l, j);
+            b[l] += Aj(l, j) * Aj(l + 1, j + 1);
+            c[l] += Aj(l, j) * Aj(l + 2, j + 2);
+        }
+    }
+    tab.assign(3 * nt * modes, (T)0);
+    for (int64_t k = 0; k < modes; ++k) {
+        double d1 = 1.0, d2 = 1.0, e1 = 0.0;               // d_{l-1}, d_{l-2}, e_{l-1}
+        for (int64_t l = 0; l < nt; ++l) {
+            const double f = l >= 2 ? c[l - 2] / d2 : 0.0;
+            const double e = l >= 1 ? (b[l - 1] - f * e1 * d2) / d1 : 0.0;
+            const double d = a[l] + s[k] - e * e * d1 - f * f * d2;
+            tab[l * modes + k] = (T)(1.0 / d);
+            tab[(nt + l) * modes + k] = (T)e;
+            tab[(2 * nt + l) * modes + k] = (T)f;
+            d2 = d1;
+            d1 = d;
+            e1 = e;
+        }
+    }
+}
 
 // L(theta_k) = (2 - 2 cos(2 pi k/n))/h^2 written as 4 sin^2(pi k/n)/h^2
 double symbol_L(int64_t k, int64_t n, double h) {
@@ -319,11 +373,7 @@ struct pdhg_handle {
     cudaStream_t gstream;
     int32_t gchunk;
     int64_t glaunches;       // kernel launches per replay
-    // fused path between residual checks (inside one pdhg_iterate call only): the next
-    // iteration's primal step has already been applied to u (ahead), and phi^n sits in the
-    // phit buffer (phi_alt); both are false whenever the state is visible to the caller
-    bool ahead;
-    bool phi_alt;
+    bool u0_dev;             // the problem's u0 was given in device memory (PDHG_FLAG_U0_ON_DEVICE)
 };
 
 static void graph_drop(pdhg_handle *h) {
@@ -351,8 +401,7 @@ static cudaError_t stage(pdhg_handle *h, int st, int nlaunch, Fn fn) {
     // NVTX names of the stages (host ranges around each stage's launches while profiling)
     static const char *const names[PDHG_NUM_STAGES] = {"pdhg primal", "pdhg residual + x-FFT", "pdhg y-FFT",
                                                        "pdhg t-solve", "pdhg dual", "pdhg residual norms",
-                                                       "pdhg fused rows", "pdhg fused cols",
-                                                       "pdhg fused dual + primal"};
+                                                       "pdhg fused rows", "pdhg fused cols"};
     EvRec r{st, nullptr, nullptr};
     if (h->profiling) {
         nvtxRangePushA(names[st]);
@@ -527,6 +576,34 @@ static void parallel_rows(int64_t nrows, int64_t total, Fn fn) {
     for (auto &th : pool) th.join();
 }
 
+// u0 in device memory (PDHG_FLAG_U0_ON_DEVICE): the largest |f'(u0)| = |2 alpha u0 + beta|
+// and the number of non-finite values, without copying u0 out.  out[0] holds the bits
+// of the maximum (non-negative doubles order like their bit patterns), out[1] the count.
+__global__ void k_u0_scan(const double *__restrict__ u0, int64_t n, double alpha, double beta,
+                          unsigned long long *out) {
+    double m = 0.0;
+    unsigned long long bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = u0[i];
+        if (!isfinite(v)) ++bad;
+        else m = fmax(m, fabs(2.0 * alpha * v + beta));
+    }
+    for (int o = 16; o; o >>= 1) {
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(m));
+        if (bad) atomicAdd(out + 1, bad);
+    }
+}
+
+template <typename T>
+__global__ void k_u0_convert(const double *__restrict__ src, T *__restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
+}
+
 template <typename T>
 static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pdhg_grid *g, double lf_a) {
     const Geom &G = h->G;
@@ -534,8 +611,14 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     std::vector<T> buf;
     // u0 extended in t; phi = phit = 0; lambda = lambdat = 0 (Sec. 3.3)
     buf.resize(G.S);
-    for (int64_t i = 0; i < G.S; ++i) buf[i] = (T)p->u0[i];
-    CK(cudaMemcpyAsync(F<T>(h, h->L.u0), buf.data(), G.S * sizeof(T), cudaMemcpyHostToDevice, s));
+    if (h->u0_dev) {
+        k_u0_convert<T><<<(unsigned)std::min<int64_t>((G.S + 255) / 256, 1024), 256, 0, s>>>(p->u0, F<T>(h, h->L.u0),
+                                                                                            G.S);
+        CK(cudaGetLastError());
+    } else {
+        for (int64_t i = 0; i < G.S; ++i) buf[i] = (T)p->u0[i];
+        CK(cudaMemcpyAsync(F<T>(h, h->L.u0), buf.data(), G.S * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
     CK(launch_fill_slices<T>(F<T>(h, h->L.u), F<T>(h, h->L.u0), G.S, G.nt + 1, s));
     CK(cudaMemsetAsync(F<T>(h, h->L.phi), 0, G.nt * G.S * sizeof(T), s));
     CK(cudaMemsetAsync(F<T>(h, h->L.phit), 0, G.nt * G.S * sizeof(T), s));
@@ -565,6 +648,7 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     double ht = g->T / (double)g->nt, hx = g->lx / (double)g->nx;
     double hy = G.dims == 2 ? g->ly / (double)g->ny : 1.0;
     std::vector<T> th(G.modes);
+    std::vector<double> sv(G.exact_t ? G.modes : 0);      // s = kappa h_t^2 per mode (exact time operator)
     if (G.space >= PDHG_SPACE_DG_P2_LF) {
         const int nm = (int)G.lines;
         std::vector<T> V(G.nkx * 18, (T)0);
@@ -581,7 +665,10 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
                     A[i][j] = (i < nm && j < nm) ? acc : cd(0.0);
                 }
             jacobi_herm(nm, A, w, Vm);
-            for (int i = 0; i < nm; ++i) th[k * nm + i] = (T)theta_of(std::max(w[i], 0.0) * ht * ht);
+            for (int i = 0; i < nm; ++i) {
+                th[k * nm + i] = (T)theta_of(std::max(w[i], 0.0) * ht * ht);
+                if (G.exact_t) sv[k * nm + i] = std::max(w[i], 0.0) * ht * ht;
+            }
             for (int m = 0; m < 3; ++m)
                 for (int i = 0; i < 3; ++i) {
                     V[(k * 9 + m * 3 + i) * 2] = (T)Vm[m][i].real();
@@ -602,11 +689,17 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
                 for (int64_t kx = 0; kx < G.nkx; ++kx) {
                     const double L = Lx[kx] + Ly[ky];
                     th[ky * G.nkx + kx] = (T)theta_of((c2 * L + g2 * L * L) * ht * ht);
+                    if (G.exact_t) sv[ky * G.nkx + kx] = (c2 * L + g2 * L * L) * ht * ht;
                 }
         };
         parallel_rows(G.lines, G.lines * G.nkx, rows);
     }
     CK(cudaMemcpy(F<T>(h, h->L.theta), th.data(), th.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (G.exact_t) {
+        std::vector<T> tab;
+        exact_t_factors<T>(G.time, G.nt, sv, tab);
+        CK(cudaMemcpy(F<T>(h, h->L.tfac), tab.data(), tab.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
     if (G.pre32) {
         // float32 copies of the preconditioner's tables (rounded from the float64 values)
         std::vector<float> t32(tw.begin(), tw.end()), th32(th.begin(), th.end());
@@ -653,6 +746,7 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     P.dbg = (int *)(h->ws + h->L.dbg);
     if (G.pre32) h->pf.dbg = P.dbg;
     if (G.has_gamma) P.gamma_half = F<T>(h, h->L.gamma);
+    if (G.exact_t) P.tfac = F<T>(h, h->L.tfac);
     if (G.blu_log2L) {
         P.blu_tw = h->ws + h->L.blu_tw;
         P.blu_c = h->ws + h->L.blu_c;
@@ -712,14 +806,36 @@ static pdhg_status compute_res(pdhg_handle *h, double out[4]) {
 }
 
 // Lax-Friedrichs constant: explicit, or max |f'(u0)| when 0 (1 if that is 0 too)
-static double lf_constant(const pdhg_problem *prob, const Geom &G) {
+// The Lax-Friedrichs constant: prob->lf_a, or max |f'(u0)| when that is 0 (maxdf: that
+// maximum when already known, e.g. from the device scan of a u0 in device memory).
+static double lf_constant(const pdhg_problem *prob, const Geom &G, double maxdf = -1.0) {
     double lf_a = prob->lf_a;
     if ((G.space == PDHG_SPACE_FD_LF || G.space == PDHG_SPACE_DG_P2_LF || G.space == PDHG_SPACE_DG_P1_LF) &&
         lf_a == 0.0) {
-        for (int64_t i = 0; i < G.S; ++i) lf_a = std::max(lf_a, std::fabs(2 * prob->alpha * prob->u0[i] + prob->beta));
+        if (maxdf >= 0.0) lf_a = maxdf;
+        else
+            for (int64_t i = 0; i < G.S; ++i)
+                lf_a = std::max(lf_a, std::fabs(2 * prob->alpha * prob->u0[i] + prob->beta));
         if (lf_a == 0.0) lf_a = 1.0;
     }
     return lf_a;
+}
+
+// max |f'(u0)| and the non-finite count of a device u0, through `scratch` (16 bytes of
+// device memory); synchronises the stream.
+static pdhg_status scan_device_u0(const pdhg_problem *p, int64_t n, void *scratch, cudaStream_t s, double *maxdf,
+                                  unsigned long long *bad) {
+    unsigned long long *d = (unsigned long long *)scratch, hv[2];
+    CK(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), s));
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    k_u0_scan<<<blocks, 256, 0, s>>>(p->u0, n, p->alpha, p->beta, d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hv, d, sizeof(hv), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    long long bits = (long long)hv[0];
+    memcpy(maxdf, &bits, sizeof(double));
+    *bad = hv[1];
+    return PDHG_OK;
 }
 
 template <typename T>
@@ -746,20 +862,29 @@ static pdhg_status create_impl(const pdhg_problem *prob, const pdhg_grid *grid, 
     if (!workspace) return fail(PDHG_ERR_INVALID_ARG, "workspace is NULL");
     if (((uintptr_t)workspace & 255) != 0) return fail(PDHG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (bytes < L.total) return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small: need " + std::to_string(L.total));
-    for (int64_t i = 0; i < G.S; ++i)
-        if (!std::isfinite(prob->u0[i])) return fail(PDHG_ERR_INVALID_ARG, "u0 has a non-finite value");
-    const double lf_a = lf_constant(prob, G);
+    const bool u0_dev = (scheme->flags & PDHG_FLAG_U0_ON_DEVICE) != 0;
+    double maxdf = -1.0;
+    if (u0_dev) {
+        unsigned long long bad = 0;
+        st = scan_device_u0(prob, G.S, (char *)workspace + L.scal, (cudaStream_t)stream, &maxdf, &bad);
+        if (st != PDHG_OK) return st;
+        if (bad) return fail(PDHG_ERR_INVALID_ARG, "u0 has a non-finite value");
+    } else {
+        for (int64_t i = 0; i < G.S; ++i)
+            if (!std::isfinite(prob->u0[i])) return fail(PDHG_ERR_INVALID_ARG, "u0 has a non-finite value");
+    }
+    const double lf_a = lf_constant(prob, G, maxdf);
     if (G.has_gamma)
         for (int64_t i = 0; i < G.nx; ++i)
             if (!std::isfinite(prob->gamma_half[i])) return fail(PDHG_ERR_INVALID_ARG, "gamma_half non-finite");
     pdhg_handle *h = new pdhg_handle();
     h->G = G; h->L = L; h->ws = (char *)workspace; h->stream = (cudaStream_t)stream;
+    h->u0_dev = u0_dev;
     h->ht = grid->T / (double)grid->nt;
     double hx = grid->lx / (double)grid->nx;
     h->wx = G.dims == 2 ? hx * (grid->ly / (double)grid->ny) : hx;
     h->iters = 0; h->launches = 0; h->profiling = false;
     h->res_norm = 0;
-    h->ahead = h->phi_alt = false;
     for (int k = 0; k < 4; ++k) h->last_res[k] = NAN;
     h->graphs = !G.fused;
     h->gexec = nullptr; h->gstream = nullptr; h->gchunk = 0; h->glaunches = 0;
@@ -805,12 +930,8 @@ extern "C" pdhg_status pdhg_set_stream(pdhg_handle *h, void *stream) {
     return PDHG_OK;
 }
 
-// One iteration of Algorithm 1.  On the fused path with the dual-primal kernel, an
-// iteration that is not `last` (no residual check or return follows it) ends with that
-// kernel: its dual step and the next iteration's primal step, phit never stored; a
-// `last` one ends with rows-C, so that the caller sees (u^n, phi^n, phit^n) as always.
 template <typename T>
-static cudaError_t enqueue_iteration(pdhg_handle *h, bool last) {
+static cudaError_t enqueue_iteration(pdhg_handle *h) {
     const Params<T> &P = params_of<T>(h);
     cudaStream_t s = h->stream;
     T *u = F<T>(h, h->u_off), *phi = F<T>(h, h->L.phi), *phit = F<T>(h, h->L.phit);
@@ -823,30 +944,15 @@ static cudaError_t enqueue_iteration(pdhg_handle *h, bool last) {
         if constexpr (sizeof(T) == 4) {
             Fused2D *f = &h->fused;
             float *uf = F<float>(h, h->u_off);
-            if (!h->ahead) {
-                e = stage(h, PDHG_STAGE_PRIMAL, 1, [&] {
-                    return fused2d_primal(h->pf, uf, phit, lam, lamt, u0, s);
-                });
-                if (e != cudaSuccess) return e;
-            }
+            e = stage(h, PDHG_STAGE_PRIMAL, 1, [&] {
+                return fused2d_primal(h->pf, uf, phit, lam, lamt, u0, s);
+            });
+            if (e != cudaSuccess) return e;
             e = stage(h, PDHG_STAGE_FUSED_ROWS, 1, [&] { return fused2d_rowsR(f, h->pf, uf, s); });
             if (e != cudaSuccess) return e;
             e = stage(h, PDHG_STAGE_FUSED_COLS, 1, [&] { return fused2d_cols(f, h->pf, s); });
             if (e != cudaSuccess) return e;
-            float *src = h->phi_alt ? phit : phi;
-            if (!last && f->cp) {
-                float *dst = h->phi_alt ? phi : phit;
-                e = stage(h, PDHG_STAGE_FUSED_DUAL_PRIMAL, 1, [&] {
-                    return fused2d_rowsCP(f, h->pf, src, dst, uf, lam, lamt, u0, s);
-                });
-                h->phi_alt = !h->phi_alt;
-                h->ahead = true;
-                return e;
-            }
-            e = stage(h, PDHG_STAGE_DUAL, 1, [&] { return fused2d_rowsC(f, h->pf, src, phi, phit, s); });
-            h->phi_alt = false;
-            h->ahead = false;
-            return e;
+            return stage(h, PDHG_STAGE_DUAL, 1, [&] { return fused2d_rowsC(f, h->pf, phi, phit, s); });
         }
         return cudaErrorInvalidValue;
     }
@@ -904,7 +1010,7 @@ static cudaError_t graph_build(pdhg_handle *h, int32_t m) {
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int32_t i = 0; i < m && e == cudaSuccess; ++i) e = enqueue_iteration<T>(h, true);
+        for (int32_t i = 0; i < m && e == cudaSuccess; ++i) e = enqueue_iteration<T>(h);
         if (e == cudaSuccess) e = enqueue_check<T>(h);
         cudaError_t e2 = cudaStreamEndCapture(h->gstream, &g);
         if (e == cudaSuccess) e = e2;
@@ -940,12 +1046,8 @@ static pdhg_status iterate_T(pdhg_handle *h, int64_t max_iters, double tol, int3
             h->launches += h->glaunches;
             st = read_res(h, r);
         } else {
-            const bool last = n + 1 == max_iters || (check_every > 0 && (n + 1) % check_every == 0);
-            cudaError_t e = enqueue_iteration<T>(h, last);
-            if (e != cudaSuccess) {
-                h->ahead = h->phi_alt = false;
-                return cuda_fail(e, "iteration launch");
-            }
+            cudaError_t e = enqueue_iteration<T>(h);
+            if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
             ++n;
             ++h->iters;
             if (!(check_every > 0 && (n % check_every == 0 || n == max_iters))) continue;
@@ -1165,6 +1267,8 @@ static pdhg_status one_step_inputs(const pdhg_problem *prob, const pdhg_grid *gr
     if (!prob || !grid || !scheme) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
     if (scheme->time != PDHG_TIME_BE)
         return fail(PDHG_ERR_UNSUPPORTED, "the one-step variant is backward Euler only (a BDF2 step needs two past slices)");
+    if (scheme->flags & PDHG_FLAG_U0_ON_DEVICE)
+        return fail(PDHG_ERR_UNSUPPORTED, "the one-step variant takes u0 in host memory");
     Geom G;
     pdhg_status st = validate(prob, grid, scheme, &G);
     if (st != PDHG_OK) return st;
@@ -1222,7 +1326,26 @@ extern "C" pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_
         if (e == cudaSuccess && l > 0) e = restart_step(h, uo + l * sb);
         if (e != cudaSuccess) { st = cuda_fail(e, "one-step restart"); break; }
         int64_t done = 0;
-        st = pdhg_iterate(h, max_iters_per_step, tol, check_every, 0, &done);
+        if (h->G.prec == PDHG_FP64) {
+            st = pdhg_iterate(h, max_iters_per_step, tol, check_every, 0, &done);
+        } else {
+            // float32: a step whose larger Res entry has not fallen by 5% over its last three
+            // checks has met float32's rounding floor and ends there
+            double hist[3] = {INFINITY, INFINITY, INFINITY};
+            while (done < max_iters_per_step) {
+                int64_t d = 0;
+                const int64_t chunk = std::min<int64_t>(check_every, max_iters_per_step - done);
+                st = pdhg_iterate(h, chunk, tol, (int32_t)chunk, 0, &d);
+                done += d;
+                if (st != PDHG_OK) break;
+                if (h->last_res[0] <= tol && h->last_res[1] <= tol) break;
+                const double w = std::max(h->last_res[0], h->last_res[1]);
+                if (w > 0.95 * hist[0]) break;
+                hist[0] = hist[1];
+                hist[1] = hist[2];
+                hist[2] = w;
+            }
+        }
         total += done;
         if (iters_per_step) iters_per_step[l] = done;
         if (st != PDHG_OK) break;

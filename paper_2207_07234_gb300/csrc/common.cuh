@@ -66,6 +66,9 @@ struct Params {
     const T *ulin = nullptr;     // u*, [nt+1][S]; nullptr: forward mode
     const T *tshift = nullptr;   // [S]; nullptr: no terminal objective
     int *dbg = nullptr;          // debug builds: site code of the first out-of-range index
+    // exact time operator (PDHG_FLAG_EXACT_TIME_PRECOND): per mode the LDL^T factors of
+    // h_t^2 D_t D_t^T + s as [3][nt][modes] (1/d_l, e_l, f_l); nullptr: T_t (closed form)
+    const T *tfac = nullptr;
 };
 
 // Debug builds (-DPDHG_DEBUG): the global indices of the instrumented kernels are checked

@@ -9,7 +9,6 @@ namespace pdhg {
 
 struct Fused2D {
     CUtensorMap tmC;         // the spectrum as rows-C's TMA source (nx = 1024), 64-byte aligned
-    CUtensorMap tmC2;        // the same tensor with boxes of 2 complex (halo rows of rows-CP)
     int *err;                // device flag: a pipelined rows-C stage wait gave up
     float2 *spec;            // spectrum [l][kx][y]: X, then spill, then K_d^{-1} R, in place
     float2 *twM;             // staged Stockham twiddles of length M = nx/2 (stockham.cuh)
@@ -20,8 +19,6 @@ struct Fused2D {
     int tc;                  // time slices per rows-R block
     int nsm;                 // multiprocessors of the device (persistent rows-C grid)
     int rows_slots;          // resident rows-R blocks on the device
-    bool cp;                 // the fused dual-primal kernel applies (nx = 1024, backward Euler)
-    int tc_cp;               // time slices per rows-CP block
     uint64_t wait_ns;        // budget of each bounded device wait
 };
 
@@ -44,12 +41,6 @@ cudaError_t launch_check2d(const Params<T> &P, const T *u, const T *phi, const T
 cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s);
 // time slices per rows-R block for nt slices, `rows` row blocks and `slots` resident blocks
 int rowsR_chunk(int nt, int rows, int slots, bool bdf2);
-// phi^{n-1} from phi_src (phi, or at nx = 1024 possibly phit), phi^n to phi, phit to phit
-cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, const float *phi_src, float *phi, float *phit,
-                          cudaStream_t s);
-// dual step of iteration n (phi^{n-1} from phi_src, phi^n to phi_dst) and primal step of
-// iteration n+1 (u, lambda, lamt in place); requires f->cp
-cudaError_t fused2d_rowsCP(Fused2D *f, const Params<float> &P, const float *phi_src, float *phi_dst, float *u,
-                           float *lam, float *lamt, const float *u0, cudaStream_t s);
+cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float *phit, cudaStream_t s);
 
 }  // namespace pdhg

@@ -13,9 +13,6 @@
 //   rows-C  (tiles of H rows x one slice; at nx = 1024 persistent blocks whose tiles'
 //           spectra arrive by TMA) inverse real FFT along x, dual step
 //           phi^n = phi^{n-1} + tau_phi z and extrapolation phit = phi^n + tau_phi z.
-//   rows-CP (nx = 1024, backward Euler) rows-C fused with the next iteration's primal
-//           step: phit is used where it is made and never stored, so between two
-//           residual checks an iteration is rows-R, cols, rows-CP (three kernels).
 // Also here: the residual norms of a 2D finite-difference state (k_check2d, float32 and
 // float64).  Debug builds (-DPDHG_DEBUG) check the global indices of these kernels
 // (common.cuh::dbg_idx).
@@ -48,8 +45,6 @@ constexpr int PRY = 4;          // rows per thread in the primal kernel
 // c = u^m (multipliers mx, p0, qx at x-1, x, x+1 and my, qy at y-1, y+1):
 //   LF: (f'(u) (m - q) + a (2p - m - q)) / 2h;  upwind: f'(u) (p - q) / h;
 //   viscous: -nu (q - 2p + m) / h^2.
-// The primal kernel and the fused dual-primal kernel both call it, so that both
-// paths give the same values.
 __device__ __forceinline__ float primal_g1(const Params<float> &P, bool lf, float c, float cn, float p0, float mx,
                                            float qx, float my, float qy) {
     const float df = dflux(P, c);
@@ -323,7 +318,8 @@ k_rowsR(Params<float> P, const float *__restrict__ u, float2 *__restrict__ spec,
 // rows are loaded after the transform, so they arrive during the split.  The
 // residual rows go to fa, the three radix-8 stages run fa -> fb -> fa -> fb, and the
 // split reads fb while the next step's residual is written to fa: four barriers per
-// step.  The arithmetic of R and of the transform is that of k_rowsR (same values).
+// step.  R is evaluated with the Lax-Friedrichs and viscous second differences folded
+// into per-block coefficients (the same R as k_rowsR up to rounding order).
 template <bool BDF2_>
 __global__ void __launch_bounds__(ATHREADS, 3)
 k_rowsR1024(Params<float> P, const float *__restrict__ u, float2 *__restrict__ spec,
@@ -370,7 +366,14 @@ k_rowsR1024(Params<float> P, const float *__restrict__ u, float2 *__restrict__ s
         const int lr = m - 1;
         const bool act = lr >= l0 && lr < l1;                // block-uniform
         if (act) {
-            const float kn = coef_new(P, lr), kc = coef_cur(P, lr), ko = coef_old(P, lr);
+            const float kc = coef_cur(P, lr), ko = coef_old(P, lr);
+            // R = A1 F1 + A2 F2 - ax (v_{x-1} + v_{x+1}) - ay (v_{y-1} + v_{y+1}) + cv v + kc u^{m-1}
+            //     (+ ko u^{m-2}), with the flux differences F1 (x), F2 (y) of the scheme and the
+            //     Lax-Friedrichs and viscous second differences folded into ax, ay, cv
+            const float ax = (lf ? 0.5f * P.lf_a * P.inv_hx : 0.f) + P.nu * P.inv_hx * P.inv_hx;
+            const float ay = (lf ? 0.5f * P.lf_a * P.inv_hy : 0.f) + P.nu * P.inv_hy * P.inv_hy;
+            const float A1 = lf ? 0.5f * P.inv_hx : P.inv_hx, A2 = lf ? 0.5f * P.inv_hy : P.inv_hy;
+            const float cvc = coef_new(P, lr) + 2.f * (ax + ay);
             float fu[4] = {flux(P, cur[0].x), flux(P, cur[0].y), flux(P, cur[0].z), flux(P, cur[0].w)};
             float fm[4] = {flux(P, cur[1].x), flux(P, cur[1].y), flux(P, cur[1].z), flux(P, cur[1].w)};
 #pragma unroll
@@ -396,17 +399,10 @@ k_rowsR1024(Params<float> P, const float *__restrict__ u, float2 *__restrict__ s
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const float v = vr[e + 1];
-                    const float lx = vr[e] - 2.f * v + vr[e + 2], ly = uv[e] - 2.f * v + dv[e];
-                    float dx, dy;
-                    if (lf) {
-                        dx = 0.5f * (fx[e + 2] - fx[e]) - 0.5f * P.lf_a * lx;
-                        dy = 0.5f * (fd[e] - fu[e]) - 0.5f * P.lf_a * ly;
-                    } else {
-                        dx = fx[e + 1] - fx[e];
-                        dy = fx[e + 1] - fu[e];
-                    }
-                    float rv = dx * P.inv_hx + dy * P.inv_hy + kn * v + kc * cv[e];
-                    if (P.nu != 0.f) rv -= P.nu * (lx * P.inv_hx * P.inv_hx + ly * P.inv_hy * P.inv_hy);
+                    const float F1 = lf ? fx[e + 2] - fx[e] : fx[e + 1] - fx[e];
+                    const float F2 = lf ? fd[e] - fu[e] : fx[e + 1] - fu[e];
+                    float rv = A1 * F1 + A2 * F2 - ax * (vr[e] + vr[e + 2]) - ay * (uv[e] + dv[e]) + cvc * v +
+                               kc * cv[e];
                     if (BDF2_ && lr >= 1) rv += ko * ov[e];
                     Rv[e] = rv;
                 }
@@ -789,16 +785,14 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC(Params<float> P, const float
 // 128) runs in registers, whose outputs -- complex positions i + 128 q, i.e.
 // x = 2 (i + 128 q) + {0,1} -- go straight into the dual step.  A stage wait that
 // gives up after wait_ns sets *err and the block returns (after a bounded wait for
-// its copies in flight).  phi^{n-1} is read from phi_src: phi itself or, after an odd
-// number of fused dual-primal iterations, the phit buffer (each element is read and
-// then overwritten by the same thread, so the two may alias).
+// its copies in flight).
 constexpr int RC_BOX = 172;                    // kx rows per TMA box: 3 boxes >= 513 rows
 constexpr int RC_ROWS = 3 * RC_BOX;            // rows per stage buffer (rows >= nkx are zero-filled)
 constexpr uint32_t RC_TX = RC_ROWS * FH * 8;   // bytes per stage (whole boxes, fill included)
 constexpr uint64_t RC_DRAIN_NS = 1000000000ull; // budget of the waits for copies in flight on exit
 
 __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, const __grid_constant__ CUtensorMap tmap,
-                                                           const float *phi_src, float *__restrict__ phi, float *phit,
+                                                           float *__restrict__ phi, float *__restrict__ phit,
                                                            const float2 *__restrict__ twN,
                                                            const float2 *__restrict__ twM, int *__restrict__ err,
                                                            uint64_t wait_ns) {
@@ -845,8 +839,8 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
         for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                ph[rr][q] = *reinterpret_cast<const float2 *>(
-                    phi_src + dbg_idx(P, base + (int64_t)(2 * h + rr) * NX + 2 * (i + 128 * q), nF - 1, 401));
+                ph[rr][q] = __ldg(reinterpret_cast<const float2 *>(
+                    phi + dbg_idx(P, base + (int64_t)(2 * h + rr) * NX + 2 * (i + 128 * q), nF - 1, 401)));
         const bool ok = mbar_wait_bounded(bar + buf, (it >> 1) & 1, wait_ns);
         if (__syncthreads_or(!ok)) {
             if (t == 0) {
@@ -910,240 +904,6 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
 
 static size_t smem_rowsC1024() {
     return 128 + (size_t)2 * RC_ROWS * FH * 8 + 2 * (size_t)FH * SeqLayout<9, 2>::PN * 8 + 2 * sizeof(uint64_t);
-}
-
-// ---------------------------------------------------------------------------
-// rows-CP (nx = 1024, backward Euler): rows-C fused with the primal step of the next
-// iteration, so that phit is consumed where it is made and never stored.
-//
-// (J(u)^T phit)^m needs phit^{m-1} on the transposed stencil (rows y-1..y+1) and
-// phit^m at the point.  A block owns the rows y0..y0+FH-1 and a chunk of slices
-// [m0, m1), marches in t, and transforms CP_ROWS = FH + 2 rows per slice (a halo row
-// on each side), one row of 128 threads per transformed row.  For slice m:
-//   phi^n = phi^{n-1} + tau_phi z (own rows; read from phi_src, written to phi_dst: the
-//     two buffers swap roles between iterations, so no block reads what another
-//     writes), phit^m = phi^n + tau_phi z (all rows, into shared memory);
-//   u^m (own rows) = u^m - tau_u (g1 + coef(m,m) phit^m), g1 kept from the slice before;
-//   g1 for u^{m+1} = the phit^m part of (J^T phit)^{m+1} (primal_g1, linearised at u^{m+1}).
-// A chunk with m0 > 0 first transforms slice m0-1 for the g1 of u^{m0}; the chunk that
-// ends at nt finishes u^{nt} (phit^{nt} = 0); the one that starts at 0 updates u^0 and
-// lambda as the primal kernel does.  The arithmetic of both steps is that of rows-C and
-// of the primal kernel.  Each slice's spectrum (rows y0-2..y0+5: a 2-complex box, the
-// 4-complex box of rows-C and another 2-complex box, each x-aligned to 16 bytes)
-// arrives by TMA two slices ahead; the stage waits are bounded as in rows-C.
-// ---------------------------------------------------------------------------
-constexpr int CP_ROWS = FH + 2;                        // transformed rows y0-1 .. y0+FH
-constexpr int CP_THREADS = 128 * CP_ROWS;              // 768
-constexpr int CP_A = 352;                              // float2 of a 2-complex box region (2816 B)
-constexpr int CP_B = RC_BOX * FH;                      // float2 of a 4-complex box (5504 B)
-constexpr int CP_GRP = 2 * CP_A + CP_B;                // float2 per kx chunk: boxes A, B, C
-constexpr int CP_STAGE = 3 * CP_GRP;                   // float2 per stage buffer
-constexpr uint32_t CP_TX = 3u * RC_BOX * (2 + FH + 2) * 8;   // bytes one stage receives
-
-// stage element of transformed row rho (0..5 = y0-1..y0+4) at kx k
-__device__ __forceinline__ int cp_sidx(int rho, int k) {
-    const int b = k / RC_BOX, r = k - b * RC_BOX;
-    const int w = rho == 0 ? 2 * r + 1 : (rho <= FH ? CP_A + FH * r + rho - 1 : CP_A + CP_B + 2 * r);
-    return b * CP_GRP + w;
-}
-
-__global__ void __launch_bounds__(CP_THREADS, 1)
-k_rowsCP1024(Params<float> P, const __grid_constant__ CUtensorMap tm2, const __grid_constant__ CUtensorMap tm4,
-             const float *__restrict__ phi_src, float *__restrict__ phi_dst, float *__restrict__ u,
-             float *__restrict__ lam, float *__restrict__ lamt, const float *__restrict__ u0,
-             const float2 *__restrict__ twN, const float2 *__restrict__ twM, int *__restrict__ err,
-             uint64_t wait_ns, int Tc) {
-    constexpr int LOG2M = 9, M = 512, NX = 1024;
-    constexpr int PN = SeqLayout<LOG2M, 2>::PN;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char *sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    float2 *stg = reinterpret_cast<float2 *>(sm);                      // [2][CP_STAGE]
-    float2 *fa = stg + 2 * CP_STAGE;                                    // [CP_ROWS][PN]
-    float2 *fb = fa + CP_ROWS * PN;                                     // [CP_ROWS][PN]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(fb + CP_ROWS * PN);   // [2]
-    float *xb = reinterpret_cast<float *>(fa);                          // [CP_ROWS][NX] phit^m, after the transform
-
-    const int ny = P.ny, nt = P.nt;
-    const int64_t S = P.S, nF = (int64_t)nt * S, nU = (int64_t)(nt + 1) * S;
-    const int t = threadIdx.x, rho = t >> 7, i = t & 127;
-    const int y0 = blockIdx.x * FH;
-    const int m0 = blockIdx.y * Tc, m1 = min(m0 + Tc, nt);
-    const int ms = m0 > 0 ? m0 - 1 : 0;                                  // first slice transformed
-    const int yA = y0 >= 2 ? y0 - 2 : y0 - 2 + ny, yC = y0 + FH < ny ? y0 + FH : y0 + FH - ny;
-    const int yr = y0 - 1 + rho < 0 ? ny - 1 : (y0 - 1 + rho >= ny ? y0 - 1 + rho - ny : y0 - 1 + rho);
-    const int64_t roff = (int64_t)yr * NX;
-    const bool own = rho >= 1 && rho <= FH;
-    const bool lf = P.space != FD_UPWIND;
-    const float s = P.dual_scale;
-    auto issue = [&](int m, int buf) {                                  // one thread
-        float2 *st = stg + buf * CP_STAGE;
-        mbar_arrive_expect_tx(bar + buf, CP_TX);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            tma_load_3d(st + b * CP_GRP, &tm2, 2 * yA, b * RC_BOX, m, bar + buf);
-            tma_load_3d(st + b * CP_GRP + CP_A, &tm4, 2 * y0, b * RC_BOX, m, bar + buf);
-            tma_load_3d(st + b * CP_GRP + CP_A + CP_B, &tm2, 2 * yC, b * RC_BOX, m, bar + buf);
-        }
-    };
-    if (t == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    if (t == 0) {
-        issue(ms, 0);
-        if (ms + 1 < m1) issue(ms + 1, 1);
-    }
-    // own rows, at x = 2 (i + 128 q) + e: g1 of u^m (the phit^{m-1} part of its update)
-    // and u^m itself, both from the slice before
-    float g1[8], uc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) g1[k] = uc[k] = 0.f;
-    int it = 0;
-    for (int m = ms; m < m1; ++m, ++it) {
-        const int buf = it & 1;
-        const bool halo = m < m0;                      // slice m0 - 1: phit only, for g1 of u^{m0}
-        const int64_t pbase = (int64_t)m * S + roff;
-        float2 ph[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            ph[q] = __ldg(reinterpret_cast<const float2 *>(phi_src + dbg_idx(P, pbase + 2 * (i + 128 * q), nF - 1, 601)));
-        const int mn = m + 1;
-        const bool next = own && (mn < m1 || mn == nt);            // g1 of u^{m+1} is this chunk's
-        float2 un[4];
-        if (next) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                un[q] = *reinterpret_cast<const float2 *>(u + dbg_idx(P, (int64_t)mn * S + roff + 2 * (i + 128 * q), nU - 1, 602));
-        }
-        if (m == 0 && own && P.init == INIT_LAMBDA) {              // u^0 (first chunk)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 v = *reinterpret_cast<const float2 *>(u + dbg_idx(P, roff + 2 * (i + 128 * q), nU - 1, 603));
-                uc[2 * q] = v.x;
-                uc[2 * q + 1] = v.y;
-            }
-        }
-        const bool ok = mbar_wait_bounded(bar + buf, (it >> 1) & 1, wait_ns);
-        if (__syncthreads_or(!ok)) {
-            if (t == 0) {
-                atomicExch(err, 1);
-                mbar_wait_bounded(bar + buf, (it >> 1) & 1, RC_DRAIN_NS);
-                if (m + 1 < m1) mbar_wait_bounded(bar + (buf ^ 1), ((it + 1) >> 1) & 1, RC_DRAIN_NS);
-            }
-            return;
-        }
-        // inverse split (Z_j = E_j + i O_j) for j = i and i + 128 of row rho, and the
-        // radix-2 stage of span 1 (outputs 2j, 2j+1) in registers
-        {
-            const float2 *st = stg + buf * CP_STAGE;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = i + 128 * h;
-                const float2 z0 = irfft_merge(st[cp_sidx(rho, j)], st[cp_sidx(rho, M - j)], __ldg(twN + j));
-                const float2 z1 = irfft_merge(st[cp_sidx(rho, j + 256)], st[cp_sidx(rho, 256 - j)], __ldg(twN + j + 256));
-                *reinterpret_cast<float4 *>(fa + rho * PN + padx(2 * j)) =
-                    make_float4(z0.x + z1.x, z0.y + z1.y, z0.x - z1.x, z0.y - z1.y);
-            }
-        }
-        __syncthreads();
-        if (t == 0 && m + 2 < m1) {                    // the stage buffer is free: slice m + 2
-            fence_proxy_async_smem();
-            issue(m + 2, buf);
-        }
-        const float2 *res = stockham_r4_range<LOG2M, true, 2, 128, CP_ROWS, CP_THREADS, 2>(fa, fb, twM);
-        float2 z[4];
-        {
-            const float2 *r = res + rho * PN;
-            float2 x0 = r[padx(i)];
-            float2 x1 = cmulconj(r[padx(i + 128)], twM[126 + i]);
-            float2 x2 = cmulconj(r[padx(i + 256)], twM[126 + 128 + i]);
-            float2 x3 = cmulconj(r[padx(i + 384)], twM[126 + 256 + i]);
-            dft4<true>(x0, x1, x2, x3);
-            z[0] = x0; z[1] = x1; z[2] = x2; z[3] = x3;
-        }
-        // dual step and extrapolation
-        float pt[8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float2 pn = ph[q];
-            pn.x += s * z[q].x;
-            pn.y += s * z[q].y;
-            pt[2 * q] = pn.x + s * z[q].x;
-            pt[2 * q + 1] = pn.y + s * z[q].y;
-            if (own && !halo)
-                *reinterpret_cast<float2 *>(phi_dst + dbg_idx(P, pbase + 2 * (i + 128 * q), nF - 1, 604)) = pn;
-        }
-        // finish u^m (own rows)
-        if (own && !halo) {
-            const float cc = coef_cur(P, m);
-            if (m == 0) {
-                if (P.init == INIT_LAMBDA) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float un0[2];
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int64_t k = dbg_idx(P, roff + 2 * (i + 128 * q) + e, S, 605);
-                            const float gv = __fmul_rn(cc, pt[2 * q + e]);      // as the primal kernel rounds it
-                            un0[e] = uc[2 * q + e] - P.tau_u0 * (P.ht * gv + lamt[k]);
-                            const float r0 = un0[e] - u0[k];
-                            const float ln = lam[k] + P.tau_lambda * r0;
-                            lam[k] = ln;
-                            lamt[k] = ln + P.tau_lambda * r0;
-                        }
-                        *reinterpret_cast<float2 *>(u + dbg_idx(P, roff + 2 * (i + 128 * q), nU - 1, 606)) =
-                            make_float2(un0[0], un0[1]);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float a = uc[2 * q] - P.tau_u * (g1[2 * q] + __fmul_rn(cc, pt[2 * q]));
-                    const float b = uc[2 * q + 1] - P.tau_u * (g1[2 * q + 1] + __fmul_rn(cc, pt[2 * q + 1]));
-                    *reinterpret_cast<float2 *>(u + dbg_idx(P, (int64_t)m * S + roff + 2 * (i + 128 * q), nU - 1, 607)) =
-                        make_float2(a, b);
-                }
-            }
-        }
-        // phit^m of all rows into xb (fa: the last shared-memory stage has read it)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<float2 *>(xb + rho * NX + 2 * (i + 128 * q)) = make_float2(pt[2 * q], pt[2 * q + 1]);
-        __syncthreads();
-        // g1 of u^{m+1}: the phit^m part of (J^T phit)^{m+1}, linearised at u^{m+1}
-        if (next) {
-            const float cn = coef_new(P, m);
-            const float *pr = xb + rho * NX, *pu = pr - NX, *pd = pr + NX;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int x = 2 * (i + 128 * q);
-                const float2 c2 = *reinterpret_cast<const float2 *>(pr + x);
-                const float lft = pr[x == 0 ? NX - 1 : x - 1], rgt = pr[x + 2 == NX ? 0 : x + 2];
-                const float2 up = *reinterpret_cast<const float2 *>(pu + x);
-                const float2 dn = *reinterpret_cast<const float2 *>(pd + x);
-                g1[2 * q] = primal_g1(P, lf, un[q].x, cn, c2.x, lft, c2.y, up.x, dn.x);
-                g1[2 * q + 1] = primal_g1(P, lf, un[q].y, cn, c2.y, c2.x, rgt, up.y, dn.y);
-                uc[2 * q] = un[q].x;
-                uc[2 * q + 1] = un[q].y;
-            }
-            if (mn == nt) {                            // phit^{nt} = 0: u^{nt} is final
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float a = uc[2 * q] - P.tau_u * (g1[2 * q] + 0.f);
-                    const float b = uc[2 * q + 1] - P.tau_u * (g1[2 * q + 1] + 0.f);
-                    *reinterpret_cast<float2 *>(u + dbg_idx(P, (int64_t)nt * S + roff + 2 * (i + 128 * q), nU - 1, 608)) =
-                        make_float2(a, b);
-                }
-            }
-        }
-        __syncthreads();                               // xb (fa) read: the next split writes fa
-    }
-}
-
-static size_t smem_rowsCP1024() {
-    return 128 + (size_t)2 * CP_STAGE * 8 + 2 * (size_t)CP_ROWS * SeqLayout<9, 2>::PN * 8 + 2 * sizeof(uint64_t);
 }
 
 // ---------------------------------------------------------------------------
@@ -1401,8 +1161,6 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
         ec = cudaFuncSetAttribute(k_rowsC1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rowsC1024());
     if (ec != cudaSuccess) return ec;
     fused2d_layout(f, ws, P.nx, P.ny, P.nt);
-    f->cp = false;
-    f->tc_cp = 0;
     f->twN = (const float2 *)twx;
     f->wait_ns = FUSED2D_WAIT_NS_DEFAULT;
     {
@@ -1431,21 +1189,6 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
                                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        // boxes of 2 complex (16 bytes) for the halo rows of the fused dual-primal kernel
-        const cuuint32_t box2[3] = {4, RC_BOX, 1};
-        r = ((encode_fn)fn)(&f->tmC2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f->spec, dims, strides, box2, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-        f->cp = P.time == BE;
-        if (f->cp) {
-            ec = cudaFuncSetAttribute(k_rowsCP1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rowsCP1024());
-            int per_sm = 0;
-            if (ec == cudaSuccess)
-                ec = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowsCP1024, CP_THREADS, smem_rowsCP1024());
-            if (ec != cudaSuccess) return ec;
-            f->tc_cp = rowsR_chunk(P.nt, P.ny / FH, std::max(1, per_sm) * f->nsm, false);
-        }
     }
     switch (ilog2i(P.nx / 2)) {
     case 7: ec = attr_rows<7>(); if (ec == cudaSuccess) ec = rowsR_slots<7>(P, f); break;
@@ -1558,16 +1301,14 @@ cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, const float *phi_src, float *phi, float *phit,
-                          cudaStream_t s) {
+cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, float *phi, float *phit, cudaStream_t s) {
     if (P.nx == 1024) {
         const int64_t ntiles = (int64_t)(P.ny / FH) * P.nt;
         const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)f->nsm * 3);
-        k_rowsC1024<<<grid, FTHREADS, smem_rowsC1024(), s>>>(P, f->tmC, phi_src, phi, phit, f->twN, f->twM, f->err,
+        k_rowsC1024<<<grid, FTHREADS, smem_rowsC1024(), s>>>(P, f->tmC, phi, phit, f->twN, f->twM, f->err,
                                                               f->wait_ns);
         return cudaGetLastError();
     }
-    if (phi_src != phi) return cudaErrorInvalidValue;        // only the nx = 1024 kernels alternate buffers
     switch (ilog2i(P.nx / 2)) {
     case 7: return launch_rowsC<7>(f, P, phi, phit, s);
     case 8: return launch_rowsC<8>(f, P, phi, phit, s);
@@ -1575,15 +1316,6 @@ cudaError_t fused2d_rowsC(Fused2D *f, const Params<float> &P, const float *phi_s
     case 10: return launch_rowsC<10>(f, P, phi, phit, s);
     default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t fused2d_rowsCP(Fused2D *f, const Params<float> &P, const float *phi_src, float *phi_dst, float *u,
-                           float *lam, float *lamt, const float *u0, cudaStream_t s) {
-    if (!f->cp || P.nx != 1024 || P.time != BE) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)(P.ny / FH), (unsigned)((P.nt + f->tc_cp - 1) / f->tc_cp));
-    k_rowsCP1024<<<grid, CP_THREADS, smem_rowsCP1024(), s>>>(P, f->tmC2, f->tmC, phi_src, phi_dst, u, lam, lamt, u0,
-                                                               f->twN, f->twM, f->err, f->wait_ns, f->tc_cp);
-    return cudaGetLastError();
 }
 
 }  // namespace pdhg

@@ -279,6 +279,34 @@ __device__ __forceinline__ T rho_of(T theta, T emt, T q, int l) {
     return emt * (T(1) + w) / (T(1) + q * w);
 }
 
+// (K + s) z = r along t for one mode with the exact time operator (PDHG_FLAG_EXACT_TIME_PRECOND):
+// K + s = L D L^T with the host's factors fac[3][nt][nmodes] at mode id m (1/d_l, e_l =
+// L_{l,l-1}, f_l = L_{l,l-2}); forward y_l = r_l - e_l y_{l-1} - f_l y_{l-2} (stored), then
+// z_l = y_l / d_l - e_{l+1} z_{l+1} - f_{l+2} z_{l+2}.  s points at slice 0 of the mode, stride st.
+template <typename T, typename C>
+__device__ __forceinline__ void tsolve_exact(C *s, int64_t st, const T *__restrict__ fac, int64_t nmodes, int64_t m,
+                                             int nt) {
+    const int64_t ts = (int64_t)nt * nmodes;
+    C y1 = s[0], y2 = mk<C, T>(T(0), T(0));
+    for (int l = 1; l < nt; ++l) {
+        const T e = fac[ts + (int64_t)l * nmodes + m], f = fac[2 * ts + (int64_t)l * nmodes + m];
+        const C y = csub(s[(int64_t)l * st], cadd(cscale(y1, e), cscale(y2, f)));
+        s[(int64_t)l * st] = y;
+        y2 = y1;
+        y1 = y;
+    }
+    C z1 = mk<C, T>(T(0), T(0)), z2 = z1;
+    for (int l = nt - 1; l >= 0; --l) {
+        const C y = l == nt - 1 ? y1 : s[(int64_t)l * st];
+        const T e1 = l + 1 < nt ? fac[ts + (int64_t)(l + 1) * nmodes + m] : T(0);
+        const T f2 = l + 2 < nt ? fac[2 * ts + (int64_t)(l + 2) * nmodes + m] : T(0);
+        const C z = csub(cscale(y, fac[(int64_t)l * nmodes + m]), cadd(cscale(z1, e1), cscale(z2, f2)));
+        s[(int64_t)l * st] = z;
+        z2 = z1;
+        z1 = z;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T>::type *__restrict__ spec,
                                              const T *__restrict__ theta_tab,
@@ -292,6 +320,32 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
         const int64_t ls = nm * (int64_t)P.nkx;      // slice stride
         C v[9];
         for (int i = 0; i < 9; ++i) v[i] = V[(int64_t)k * 9 + i];   // v[m*3+i] = V_{m,i}
+        if (P.tfac) {
+            // w = V^H r in place, the exact time operator per eigen-index (mode id k nm + i), z = V w
+            for (int l = 0; l < nt; ++l) {
+                C r[3], w[3];
+                for (int m = 0; m < nm; ++m) r[m] = spec[l * ls + m * P.nkx + k];
+                for (int i = 0; i < nm; ++i) {
+                    C acc = mk<C, T>(T(0), T(0));
+                    for (int m = 0; m < nm; ++m) acc = cadd(acc, cmulconj(r[m], v[m * 3 + i]));
+                    w[i] = acc;
+                }
+                for (int i = 0; i < nm; ++i) spec[l * ls + i * P.nkx + k] = w[i];
+            }
+            for (int i = 0; i < nm; ++i)
+                tsolve_exact<T, C>(spec + i * P.nkx + k, ls, P.tfac, (int64_t)P.nkx * nm, (int64_t)k * nm + i, nt);
+            for (int l = 0; l < nt; ++l) {
+                C w[3], zz[3];
+                for (int i = 0; i < nm; ++i) w[i] = spec[l * ls + i * P.nkx + k];
+                for (int m = 0; m < nm; ++m) {
+                    C acc = mk<C, T>(T(0), T(0));
+                    for (int i = 0; i < nm; ++i) acc = cadd(acc, cmul(v[m * 3 + i], w[i]));
+                    zz[m] = acc;
+                }
+                for (int m = 0; m < nm; ++m) spec[l * ls + m * P.nkx + k] = zz[m];
+            }
+            return;
+        }
         T th[3], emt[3], q[3];
         for (int i = 0; i < nm; ++i) {
             th[i] = theta_tab[k * nm + i]; emt[i] = expT(-th[i]); q[i] = emt[i] * emt[i];
@@ -331,6 +385,10 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
     const int64_t modes = (int64_t)P.lines * P.nkx;
     const int64_t col = (int64_t)bx * blockDim.x + threadIdx.x;
     if (col >= modes) return;
+    if (P.tfac) {
+        tsolve_exact<T, C>(spec + col, modes, P.tfac, modes, col, nt);
+        return;
+    }
     const T th = theta_tab[col];
     const T emt = expT(-th), q = emt * emt;
     C *s = spec + col;

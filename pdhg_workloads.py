@@ -28,6 +28,7 @@ import numpy as np
 SPACES = ("fd_upwind", "fd_lf", "dg_p2_lf", "dg_p1_upwind", "dg_p1_lf")
 TIMES = ("be", "bdf2")
 INITS = ("lambda", "pinned")
+TPRECS = ("tridiag", "exact")
 
 
 @dataclass
@@ -57,6 +58,8 @@ class Problem:
     tau_lambda: float = 0.99
     init: str = "lambda"        # "lambda": Algorithm 1 multiplier; "pinned": u^0 == u0
     u0: Optional[np.ndarray] = None   # one slice, float64, layout per the conventions above
+    tprec: str = "tridiag"      # time part of K_d: "tridiag" (T_t for BE and BDF2) or "exact"
+                                # (the scheme's own D_t D_t^T: pentadiagonal for BDF2)
 
     # ---- derived sizes (pure bookkeeping) ----
     @property
@@ -99,7 +102,7 @@ class Problem:
         return dataclasses.replace(self, **kw)
 
     def validate(self) -> None:
-        assert self.space in SPACES and self.time in TIMES and self.init in INITS
+        assert self.space in SPACES and self.time in TIMES and self.init in INITS and self.tprec in TPRECS
         assert self.dims in (1, 2)
         assert self.u0 is not None and self.u0.shape == self.slice_shape
         if self.nmodes > 1:

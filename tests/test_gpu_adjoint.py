@@ -73,6 +73,48 @@ def test_adjoint_fixed_iterates(B, p):
     assert abs(dnu_g - dnu_o) <= 1e-9 * max(abs(dnu_o), 1e-3)
 
 
+@pytest.mark.parametrize("p", CASES[:2], ids=lambda p: f"{p.name}_{p.time}")
+def test_gradient_float32_against_float64_oracle(B, p):
+    """The gradient computed in float32 (forward and adjoint Algorithm 1 in float32, run for a
+    fixed budget past float32's rounding floor) against the oracle's float64 sequential
+    adjoint: dLoss/du0 to 1e-4 of its largest value and dLoss/dnu to 1e-4 of its size.
+    The bound comes from the float32 floors of the two solves (relative Res of a few 1e-6
+    each, see the fused converged-parity test) times the conditioning of the linearised
+    problem, which is O(10) here."""
+    p = with_taus(p)
+    g = target_of(p)
+    u = newton.solve(p)
+    _, _, du0, dnu = adjoint.sequential_adjoint(p, u, g)
+    loss, du0_g, dnu_g, iters = B.solve_gradient(p, g, tol=1e-9, max_iters=20000, adj_tol=1e-9,
+                                                 adj_max_iters=20000, check_every=50, precision="fp32")
+    assert abs(loss - adjoint.terminal_loss(p, u, g)) <= 1e-5 * max(1.0, loss)
+    assert np.max(np.abs(du0_g - du0)) <= 1e-4 * np.max(np.abs(du0)), np.max(np.abs(du0_g - du0)) / np.max(np.abs(du0))
+    assert abs(dnu_g - dnu) <= 1e-4 * max(abs(dnu), 1e-3 * np.max(np.abs(du0))), (dnu_g, dnu)
+
+
+def test_autograd_with_u0_on_the_device(B):
+    """TerminalLoss with u0 a CUDA tensor: u0 goes to the library as a device pointer
+    (PDHG_FLAG_U0_ON_DEVICE, no host copy); loss and gradient equal those of the host path,
+    and the Lax-Friedrichs constant taken from the device scan of u0 equals the host's."""
+    import torch
+    p = with_taus(W.viscous_burgers(nx=64, nt=16, T=1.0, nu=0.05).replace(time="be", lf_a=0.0))
+    g = target_of(p)
+    TL = B.terminal_loss_fn()
+    opts = {"tol": 1e-12, "adj_tol": 1e-12, "check_every": 10}
+    out = {}
+    for where in ("cpu", "cuda"):
+        u0 = torch.tensor(p.u0, dtype=torch.float64, device=where, requires_grad=True)
+        nu = torch.tensor(p.nu, dtype=torch.float64, requires_grad=True)
+        loss = TL.apply(u0, nu, p, g, opts)
+        loss.backward()
+        out[where] = (float(loss), u0.grad.detach().cpu().numpy(), float(nu.grad))
+        assert u0.grad.device == u0.device
+    # both solves run to Res 1e-12: equal to that level (bitwise when lf_a rounds alike)
+    assert abs(out["cpu"][0] - out["cuda"][0]) <= 1e-10 * max(1.0, abs(out["cpu"][0]))
+    assert np.max(np.abs(out["cpu"][1] - out["cuda"][1])) <= 1e-9 * np.max(np.abs(out["cpu"][1]))
+    assert abs(out["cpu"][2] - out["cuda"][2]) <= 1e-9 * max(1.0, abs(out["cpu"][2]))
+
+
 def test_autograd_function_matches_gpu_finite_differences(B):
     """TerminalLoss.backward returns the gradient; the objective's own central
     differences (GPU forward solves at u0 +- eps v) agree with <dLoss/du0, v>."""

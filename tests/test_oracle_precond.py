@@ -91,3 +91,48 @@ def test_float32_preconditioner_keeps_the_fixed_point(monkeypatch):
     assert n32 < 20000
     assert np.max(np.abs(st["u"] - un)) <= 1e-8 * np.max(np.abs(un))
     assert abs(n32 - n_exact) <= 0.05 * n_exact + 10
+
+
+# ---------------------------------------------------------------------------
+# ablation: the exact time operator h_t^2 D_t D_t^T in place of T_t
+# ---------------------------------------------------------------------------
+
+def test_exact_time_operator_is_Tt_for_backward_euler():
+    """For BE with u^0 held fixed, h_t^2 D_t D_t^T is the tridiagonal T_t of the reading."""
+    p = W.advection_upwind_be(nx=8, nt=7)
+    assert np.array_equal(precond.exact_Tt(p), precond.dense_Tt(p.nt))
+
+
+def test_exact_time_operator_bdf2_interior_rows_are_the_symbol_autocorrelation():
+    """Away from the first rows, h_t^2 D_t D_t^T for BDF2 is the Toeplitz matrix whose
+    coefficients are those of |a(w)|^2, a(w) = 3/2 - 2 e^{-iw} + 1/2 e^{-2iw} the Fourier
+    symbol of the BDF2 difference (Sec. 3.1): computed here by sampling |a|^2 and an
+    inverse FFT.  The matrix is symmetric positive definite and pentadiagonal."""
+    p = W.advection_upwind_be(nx=8, nt=12).replace(time="bdf2")
+    K = precond.exact_Tt(p)
+    n = 64
+    w = 2.0 * np.pi * np.arange(n) / n
+    a = 1.5 - 2.0 * np.exp(-1j * w) + 0.5 * np.exp(-2j * w)
+    c = np.fft.ifft(np.abs(a) ** 2).real                 # c[k] = coefficient of e^{ikw}
+    for l in range(3, p.nt - 3):
+        for d in range(-3, 4):
+            assert abs(K[l, l + d] - c[d % n]) < 1e-13, (l, d)
+    assert np.allclose(K, K.T, atol=0.0) and np.all(np.linalg.eigvalsh(K) > 0)
+    assert np.all(np.triu(K, 3) == 0.0)
+
+
+@pytest.mark.parametrize("p", [
+    W.advection_upwind_be(nx=10, nt=6).replace(time="bdf2", tprec="exact"),
+    W.burgers_2d(n=4, nt=5).replace(time="bdf2", tprec="exact", ny=6, ly=1.5 * np.pi,
+                                      u0=W.burgers_2d(n=4).u0[:1].repeat(6, 0)),
+    W.burgers_dg_p2(ncell=6, nt=5).replace(c=0.7, tprec="exact"),
+    W.transport_dg_p1(ncell=6, nt=5).replace(tprec="exact"),
+], ids=["fd1d", "fd2d", "dgp2", "dgp1"])
+def test_exact_kd_inverse_equals_dense_solve(p):
+    """K_d^{-1} with the exact time operator (per-mode dense solves after the x/y FFTs)
+    equals a dense solve of the assembled K_d (stencils in real space) to 1e-12."""
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal((p.nt,) + p.slice_shape)
+    z = precond.kd_inverse(p, r)
+    zd = np.linalg.solve(precond.dense_Kd(p), r.ravel()).reshape(r.shape)
+    assert np.max(np.abs(z - zd)) <= 1e-12 * np.max(np.abs(zd))
