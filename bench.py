@@ -541,10 +541,12 @@ def nonlinear_leg(binding, tol=1e-6, device=None, stream=None, alg1_iters=1000):
     torch.cuda.empty_cache()
     q = p.replace(init="pinned", tau_u=0.55, tau_u0=0.55, tau_phi=0.55)
     tol_step = tol * r0 / float(np.sqrt(p.T))
-    for label, prec, chk in (("alg3_fp32", "fp32", 20), ("alg3_fp64_plain", "fp64", 10)):
+    # float32 steps cannot reach the tolerance (float32's rounding floor): they are capped
+    # at 1000 iterations, five times what the float64 steps need at most
+    for label, prec, chk, cap in (("alg3_fp32", "fp32", 20, 1000), ("alg3_fp64_plain", "fp64", 10, 4000)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        u, per = binding.solve_one_step(q, tol=tol_step, max_iters_per_step=4000, check_every=chk, precision=prec,
+        u, per = binding.solve_one_step(q, tol=tol_step, max_iters_per_step=cap, check_every=chk, precision=prec,
                                         device=device, stream=stream)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -561,16 +563,23 @@ def nonlinear_leg(binding, tol=1e-6, device=None, stream=None, alg1_iters=1000):
 
 
 def time_to_residual(binding, p, tol=1e-6, check_every=50, max_iters=20000, device=None, stream=None):
-    """Wall time and iterations to relative Res <= tol for the float32 default path and
-    the plain float64 GPU path (the comparator named by the metric).  Iterates in chunks
+    """Wall time and iterations to relative Res <= tol for the float32 default path, the
+    same with the t-solve recurrence in float64 (fp32_t64: whether float32's floor comes
+    from that recurrence), and the plain float64 GPU path (the comparator named by the
+    metric).  Iterates in chunks
     of 20 checks; a residual that has not dropped by 5% over three chunks is reported as
     the precision's floor instead of running to max_iters.  A third leg times the
     mixed-precision solve (float32, then float64 from the widened state)."""
     import torch
     out = {"workload": p.name, "tol": tol, "relative_to": "||A(u_init)||", "check_every": check_every}
     chunk = 20 * check_every
-    for label, prec, path in (("fp32", "fp32", "auto"), ("fp64_plain", "fp64", "plain")):
-        s = binding.Solver(p, precision=prec, path=path, device=device, stream=stream)
+    legs = [("fp32", "fp32", "auto", False), ("fp32_t64", "fp32", "auto", True), ("fp64_plain", "fp64", "plain", False)]
+    for label, prec, path, t64 in legs:
+        try:
+            s = binding.Solver(p, precision=prec, path=path, device=device, stream=stream, t64=t64)
+        except binding.PdhgError as err:            # e.g. a t-recurrence variant the scheme does not take
+            out[label] = {"status": f"unsupported: {err}"}
+            continue
         r0 = float(s.residual()[0])
         scale0 = r0
         torch.cuda.synchronize()

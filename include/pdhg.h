@@ -114,7 +114,7 @@ typedef struct {
 /* time: PDHG_TIME_*; space: PDHG_SPACE_*; precision: PDHG_FP64 / PDHG_FP32;
  * init: PDHG_INIT_LAMBDA (Algorithm 1's multiplier on u^0 = u0) or
  * PDHG_INIT_PINNED (u^0 held at u0); path: PDHG_PATH_*; flags: 0 or a combination
- * of PDHG_FLAG_EXACT_TIME_PRECOND and PDHG_FLAG_U0_ON_DEVICE.
+ * of PDHG_FLAG_EXACT_TIME_PRECOND, PDHG_FLAG_U0_ON_DEVICE and PDHG_FLAG_T_SOLVE_FP64.
  *
  * PDHG_FLAG_EXACT_TIME_PRECOND (an ablation of the preconditioner of Sec. 3.3): the
  * time part of K_d is the scheme's own h_t^2 D_t D_t^T (D_t the BE or BDF2 time
@@ -129,7 +129,14 @@ enum { PDHG_FLAG_EXACT_TIME_PRECOND = 1,
  * the Lax-Friedrichs constant (lf_a = 0) from a device scan: u0 is not copied to the
  * host.  Accepted by pdhg_create and every entry point built on it (mixed, refine,
  * gradient, batch); PDHG_ERR_UNSUPPORTED for pdhg_solve_one_step. */
-       PDHG_FLAG_U0_ON_DEVICE = 2 };
+       PDHG_FLAG_U0_ON_DEVICE = 2,
+/* PDHG_FLAG_T_SOLVE_FP64 (float32 handles; an ablation of the precision of the t-solve):
+ * the recurrences of the tridiagonal t-solve (the closed-form pivots and the running
+ * forward and backward values) in float64, each stored value rounded to float32 once.
+ * Finite differences with T_t only (PDHG_ERR_UNSUPPORTED with DG or the exact time
+ * operator); on the fused path only for ny = 1024 (PDHG_PATH_AUTO then takes the plain
+ * path for other ny).  No effect on float64 handles. */
+       PDHG_FLAG_T_SOLVE_FP64 = 4 };
 typedef struct {
     int32_t time, space, precision, init, path, flags;
 } pdhg_scheme;
@@ -249,19 +256,20 @@ pdhg_status pdhg_solve_refine(const pdhg_problem *prob, const pdhg_grid *grid,
  * Algorithm 1 on the two-slice problem over [l h_t, (l+1) h_t] whose initial
  * data is u*^l (u*^0 = u0), started from [u*^l, u*^l], 0, 0, until both
  * entries of its Res are <= tol, checked every check_every iterations, or
- * max_iters_per_step (in float32 also once the larger entry has not fallen by 5%
- * over the step's last three checks: float32's rounding floor).  Res here is the L2 norm over the domain at one time
+ * max_iters_per_step.  Res here is the L2 norm over the domain at one time
  * (weight w_x, no h_t), as Sec. 3.5 defines it.  Every input of the full
  * problem is kept (flux, c, step sizes, h_t, and the Lax-Friedrichs constant
  * computed from the full problem's u0 when prob->lf_a is 0), so with tol -> 0
- * the result is the full scheme's solution.  Backward Euler only
- * (PDHG_ERR_UNSUPPORTED for BDF2: its steps need two past slices).
+ * the result is the full scheme's solution.  BDF2: the equation of step l >= 1,
+ * (3 v - 4 u^l + u^{l-1}) / (2 h_t) + D(v) = 0, is the backward-Euler equation of a
+ * step of length 2 h_t / 3 from w = (4 u*^l - u*^{l-1}) / 3, so that step runs as the
+ * two-slice BE problem started from w (step 0 is the scheme's BE start).
  *
  * u_out: device, (nt+1)*ndof values of the scheme's precision, written with
  * u*^0..u*^nt.  iters_per_step (host, nt entries) and iters_total may be NULL.
  * workspace: device, caller-owned, 256-byte aligned, size from
- * pdhg_one_step_workspace_size (one handle with nt = 1).  Synchronises the
- * stream before returning.  A step that fails (NONFINITE, DIVERGED, CUDA)
+ * pdhg_one_step_workspace_size (one handle with nt = 1; two for BDF2, the second
+ * with the step length 2 h_t / 3).  Synchronises the stream before returning.  A step that fails (NONFINITE, DIVERGED, CUDA)
  * returns its status; u_out then holds the steps completed so far.
  */
 pdhg_status pdhg_one_step_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
@@ -373,6 +381,33 @@ pdhg_status pdhg_batch_iterate(pdhg_batch *b, int64_t max_iters, double tol, int
 pdhg_status pdhg_batch_reset(pdhg_batch *b);
 pdhg_status pdhg_batch_instance(pdhg_batch *b, int32_t i, pdhg_handle **h);
 pdhg_status pdhg_batch_launch_count(pdhg_batch *b, int64_t *launches, int32_t reset);
+
+/*
+ * How a batch iteration is launched (an addition of this library).  persistent != 0:
+ * ONE cooperative launch per iteration whose resident blocks take work items from a
+ * queue -- every active instance's primal items, its residual + x-FFT rows, its t-solve
+ * columns, its inverse x-FFT + dual rows; order 0: stage after stage, instances with
+ * most cells first within a stage; order 1: instance after instance (most cells first),
+ * each with its four stages in turn.  An item of a later stage of an
+ * instance starts once that instance's items of the stage before are finished (a wait
+ * bounded by the budget of pdhg_batch_set_wait_budget; one that gives up makes the next
+ * residual check of pdhg_batch_iterate return PDHG_ERR_TIMEOUT and leaves the state
+ * invalid; the context stays usable).  persistent == 0 (the default): one launch per
+ * stage (four per iteration).  Both run the same per-block code, so results are
+ * identical.
+ * blocks_per_sm: resident blocks per multiprocessor of the persistent launch (0: as
+ * many as fit).  tiles (host, 8 entries, may be NULL to keep): row items per queue entry
+ * for each size class c = clamp(log2(row transform length) - 8, 0, 7) (the Bluestein
+ * length L, or nx/2 for the packed real FFT), each in [1, 64]; chosen per class by the
+ * library's autotuner (paper_2207_07234_gb300/autotune.py).  Errors: INVALID_ARG.
+ */
+pdhg_status pdhg_batch_set_launch(pdhg_batch *b, int32_t persistent, int32_t blocks_per_sm, int32_t order,
+                                  const int32_t *tiles);
+
+/* Budget in nanoseconds of each bounded wait of the persistent batch iteration
+ * (default 1e9); 0 gives up at the first wait: the host-side way to exercise the
+ * PDHG_ERR_TIMEOUT path. */
+pdhg_status pdhg_batch_set_wait_budget(pdhg_batch *b, uint64_t ns);
 
 /*
  * Residual norms of a caller-held state, with no handle, no workspace and no

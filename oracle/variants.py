@@ -14,8 +14,9 @@ Readings (the paper leaves these open):
   duals (phit = phi, lamt = lambda), as at a fresh start.
 * Algorithm 3 keeps every input of the full problem (flux, the Lax-Friedrichs
   constant, c, step sizes, h_t) and only shortens the horizon to one step, so its
-  end values are the full scheme's solution when BE is used.  For BDF2 a one-step
-  problem would fall back to its BE start: the variant is BE only.
+  end values are the full scheme's solution.  A BDF2 step (l >= 1) is the BE step of
+  length 2 h_t / 3 from (4 u^l - u^{l-1}) / 3 (the same equation rearranged); step 0
+  is the scheme's BE start.
 * Res of a one-step problem (Sec. 3.5) is the L2 norm over the domain at one time:
   the two entries of Eq. 2.12 on that problem (its equation slice and its initial
   row) with the quadrature weight w_x alone, without the h_t of the space-time norm.
@@ -80,15 +81,23 @@ def slice_residual_norms(p, st):
 
 
 def one_timestep(p, tol, max_iters_per_step=100000, check_every=1):
-    """Algorithm 3 (BE): u*^0 = u0, then each u*^{l+1} from the two-slice problem on
+    """Algorithm 3: u*^0 = u0, then each u*^{l+1} from the two-slice problem on
     [l h_t, (l+1) h_t], iterated until both entries of slice_residual_norms are
-    <= tol.  Returns (u* [nt+1][...], iterations per step)."""
-    assert p.time == "be"
+    <= tol.  Returns (u* [nt+1][...], iterations per step).
+
+    BDF2 (a reading; the paper states Algorithm 3 for one-step schemes): the equation of
+    step l >= 1, (3 v - 4 u^l + u^{l-1}) / (2 h_t) + D(v) = 0, is the backward-Euler
+    equation (v - w) / h' + D(v) = 0 with h' = 2 h_t / 3 and w = (4 u^l - u^{l-1}) / 3, so
+    that step is the two-slice BE problem of length h' started from w; step 0 is the BE
+    start of the scheme (reading 6)."""
     u = np.empty((p.nt + 1,) + p.u0.shape)
     u[0] = p.u0
     counts = []
     for l in range(p.nt):
-        pl = p.replace(nt=1, T=p.ht, u0=u[l].copy())
+        if p.time == "bdf2" and l >= 1:
+            pl = p.replace(time="be", nt=1, T=2.0 * p.ht / 3.0, u0=(4.0 * u[l] - u[l - 1]) / 3.0)
+        else:
+            pl = p.replace(time="be", nt=1, T=p.ht, u0=u[l].copy())
         st = pdhg.initial_state(pl)
         it = 0
         while it < max_iters_per_step:

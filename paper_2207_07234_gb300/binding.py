@@ -28,6 +28,7 @@ PATH = {"auto": 0, "plain": 1, "fused": 2}
 FIELD = {"u": 0, "phi": 1, "phit": 2, "lambda": 3, "lambdat": 4, "u_terminal": 5}
 FLAG_EXACT_TIME_PRECOND = 1      # pdhg_scheme.flags: time part of K_d = h_t^2 D_t D_t^T (ablation)
 FLAG_U0_ON_DEVICE = 2            # pdhg_scheme.flags: pdhg_problem.u0 is a device pointer
+FLAG_T_SOLVE_FP64 = 4            # pdhg_scheme.flags: float32 handle, t-solve recurrence in float64
 STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_rows", "fused_cols"]
 
 # every symbol include/pdhg.h declares
@@ -40,7 +41,8 @@ EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_strea
            "pdhg_gradient_workspace_size", "pdhg_solve_gradient", "pdhg_mixed_workspace_size",
            "pdhg_solve_mixed", "pdhg_batch_workspace_size",
            "pdhg_batch_create", "pdhg_batch_destroy", "pdhg_batch_iterate", "pdhg_batch_reset",
-           "pdhg_batch_instance", "pdhg_batch_launch_count", "pdhg_residual_noalloc"]
+           "pdhg_batch_instance", "pdhg_batch_launch_count", "pdhg_batch_set_launch",
+           "pdhg_batch_set_wait_budget", "pdhg_residual_noalloc"]
 
 
 class PdhgError(RuntimeError):
@@ -115,6 +117,8 @@ def load(path: str | None = None):
         "pdhg_batch_reset": [vp],
         "pdhg_batch_instance": [vp, i32, ctypes.POINTER(vp)],
         "pdhg_batch_launch_count": [vp, ctypes.POINTER(i64), i32],
+        "pdhg_batch_set_launch": [vp, i32, i32, i32, ctypes.POINTER(i32)],
+        "pdhg_batch_set_wait_budget": [vp, ctypes.c_uint64],
         "pdhg_solve_gradient": [P, G, S, ctypes.POINTER(ctypes.c_double), ctypes.c_double, i64, ctypes.c_double, i64,
                                 i32, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
@@ -136,7 +140,7 @@ def _check(status):
         raise PdhgError(status, load().pdhg_last_error().decode())
 
 
-def structs(p, precision="fp32", path="auto", u0_device=None):
+def structs(p, precision="fp32", path="auto", u0_device=None, t64=False):
     """C structs for a pdhg_workloads.Problem; returns (prob, grid, scheme, keepalive).
     u0_device: a contiguous float64 CUDA tensor holding u0 (PDHG_FLAG_U0_ON_DEVICE), else
     p.u0 is passed from host memory."""
@@ -162,6 +166,8 @@ def structs(p, precision="fp32", path="auto", u0_device=None):
     flags = FLAG_EXACT_TIME_PRECOND if getattr(p, "tprec", "tridiag") == "exact" else 0
     if u0_device is not None:
         flags |= FLAG_U0_ON_DEVICE
+    if t64:
+        flags |= FLAG_T_SOLVE_FP64
     scheme = pdhg_scheme(TIME[p.time], SPACE[p.space], PRECISION[precision], INIT[p.init], PATH[path], flags)
     return prob, grid, scheme, keep
 
@@ -177,7 +183,8 @@ def workspace_size(p, precision="fp32", path="auto") -> int:
 class Solver:
     """One space-time problem on the GPU (a pdhg_handle plus its torch-owned workspace)."""
 
-    def __init__(self, p, precision="fp32", path="auto", device=None, stream=None, _adopt=None):
+    def __init__(self, p, precision="fp32", path="auto", device=None, stream=None, _adopt=None, t64=False):
+        """t64: float32 fields with the t-solve recurrence in float64 (PDHG_FLAG_T_SOLVE_FP64)."""
         import torch
         self._torch = torch
         self.p = p
@@ -192,7 +199,7 @@ class Solver:
             self._owned = _adopt[3] if len(_adopt) > 3 else True
             return
         lib = load()
-        prob, grid, scheme, keep = structs(p, precision, path)
+        prob, grid, scheme, keep = structs(p, precision, path, t64=t64)
         nbytes = ctypes.c_size_t(0)
         _check(lib.pdhg_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
                                        ctypes.byref(nbytes)))
@@ -447,6 +454,15 @@ class Batch:
                                      ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(b)))
         self.b = b
         self.count = n
+        # the autotuner's choice of tiles (batch_tiles.json, written by autotune.py), if any
+        tf = os.path.join(os.path.dirname(os.path.abspath(__file__)), "batch_tiles.json")
+        if os.path.exists(tf) and os.environ.get("PDHG_BATCH_TILES") != "none":
+            import json
+            with open(tf) as f:
+                cfg = json.load(f)
+            self.set_launch(persistent=bool(cfg.get("persistent", False)),
+                            blocks_per_sm=int(cfg.get("blocks_per_sm", 0)), order=int(cfg.get("order", 0)),
+                            tiles=cfg.get("tiles", [1] * 8))
 
     def close(self):
         if getattr(self, "b", None) is not None and self.b.value:
@@ -487,3 +503,15 @@ class Batch:
         n = ctypes.c_int64()
         _check(load().pdhg_batch_launch_count(self.b, ctypes.byref(n), int(bool(reset))))
         return n.value
+
+    def set_launch(self, persistent=True, blocks_per_sm=0, order=0, tiles=None):
+        """One persistent launch per iteration or (persistent=False, the library's default)
+        one launch per stage; resident blocks per multiprocessor (0: as many as fit); queue
+        order (0 stage-major, 1 instance-major); tiles: row items per queue entry for the 8
+        size classes (None: keep)."""
+        t = (ctypes.c_int32 * 8)(*[int(v) for v in tiles]) if tiles is not None else None
+        _check(load().pdhg_batch_set_launch(self.b, int(bool(persistent)), int(blocks_per_sm), int(order), t))
+
+    def set_wait_budget(self, ns):
+        """Budget (ns) of each bounded wait of the persistent iteration; 0 forces the timeout path."""
+        _check(load().pdhg_batch_set_wait_budget(self.b, int(ns)))

@@ -69,6 +69,7 @@ struct Geom {
     int blu_log2L;   // > 0: Bluestein x-transform (1D FD, nx not a power of two)
     bool pre32;      // float64 state with the preconditioner applied in float32 (plain FD path)
     bool exact_t;    // time part of K_d: the scheme's own h_t^2 D_t D_t^T (PDHG_FLAG_EXACT_TIME_PRECOND)
+    bool t64;        // float32 fields, t-solve recurrence in float64 (PDHG_FLAG_T_SOLVE_FP64)
 };
 
 // Checks of the grid, the scheme and the coefficients (everything but u0 and the
@@ -120,9 +121,14 @@ pdhg_status validate_shape(const pdhg_problem *p, const pdhg_grid *g, const pdhg
     G->esz = s->precision == PDHG_FP64 ? 8 : 4;
     G->has_gamma = p->gamma_half != nullptr;
     G->fused = false;
-    if (s->flags & ~(int32_t)(PDHG_FLAG_EXACT_TIME_PRECOND | PDHG_FLAG_U0_ON_DEVICE))
+    if (s->flags & ~(int32_t)(PDHG_FLAG_EXACT_TIME_PRECOND | PDHG_FLAG_U0_ON_DEVICE | PDHG_FLAG_T_SOLVE_FP64))
         return fail(PDHG_ERR_INVALID_ARG, "unknown scheme flag");
     G->exact_t = (s->flags & PDHG_FLAG_EXACT_TIME_PRECOND) != 0;
+    G->t64 = (s->flags & PDHG_FLAG_T_SOLVE_FP64) != 0 && s->precision == PDHG_FP32;
+    if (G->t64 && (dg || G->exact_t))
+        return fail(PDHG_ERR_UNSUPPORTED, "the float64 t-recurrence serves the finite-difference schemes with T_t");
+    if (G->t64 && s->path == PDHG_PATH_FUSED && G->ny != 1024)
+        return fail(PDHG_ERR_UNSUPPORTED, "the fused path's float64 t-recurrence needs ny = 1024");
     if (G->exact_t) {
         if (s->path == PDHG_PATH_FUSED)
             return fail(PDHG_ERR_UNSUPPORTED, "the exact time preconditioner runs on the plain path");
@@ -131,7 +137,8 @@ pdhg_status validate_shape(const pdhg_problem *p, const pdhg_grid *g, const pdhg
                                               "2^24 (mode, slice) pairs");
     }
     if (!G->exact_t && (s->path == PDHG_PATH_FUSED || s->path == PDHG_PATH_AUTO)) {
-        bool ok = fused2d_supported(g->dims, s->space, s->time, s->precision, g->nx, G->ny, g->nt, p->nu);
+        bool ok = fused2d_supported(g->dims, s->space, s->time, s->precision, g->nx, G->ny, g->nt, p->nu) &&
+                  !(G->t64 && G->ny != 1024);
         if (s->path == PDHG_PATH_FUSED && !ok)
             return fail(PDHG_ERR_UNSUPPORTED, "the fused path needs 2D FD, FP32, nx in [256, 2048], ny in [256, 1024] (powers of two), nt >= 2");
         G->fused = ok;
@@ -747,6 +754,7 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     if (G.pre32) h->pf.dbg = P.dbg;
     if (G.has_gamma) P.gamma_half = F<T>(h, h->L.gamma);
     if (G.exact_t) P.tfac = F<T>(h, h->L.tfac);
+    P.t64 = G.t64 ? 1 : 0;
     if (G.blu_log2L) {
         P.blu_tw = h->ws + h->L.blu_tw;
         P.blu_c = h->ws + h->L.blu_c;
@@ -1265,8 +1273,6 @@ extern "C" pdhg_status pdhg_solve_refine(const pdhg_problem *prob, const pdhg_gr
 static pdhg_status one_step_inputs(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
                                    pdhg_problem *p1, pdhg_grid *g1) {
     if (!prob || !grid || !scheme) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
-    if (scheme->time != PDHG_TIME_BE)
-        return fail(PDHG_ERR_UNSUPPORTED, "the one-step variant is backward Euler only (a BDF2 step needs two past slices)");
     if (scheme->flags & PDHG_FLAG_U0_ON_DEVICE)
         return fail(PDHG_ERR_UNSUPPORTED, "the one-step variant takes u0 in host memory");
     Geom G;
@@ -1282,6 +1288,14 @@ static pdhg_status one_step_inputs(const pdhg_problem *prob, const pdhg_grid *gr
     return PDHG_OK;
 }
 
+// The one-step problems are backward-Euler problems: with BDF2 the step l >= 1 is the BE
+// step of length 2 h_t / 3 from (4 u^l - u^{l-1}) / 3, on a second handle.
+static pdhg_scheme one_step_scheme(const pdhg_scheme *scheme) {
+    pdhg_scheme s1 = *scheme;
+    s1.time = PDHG_TIME_BE;
+    return s1;
+}
+
 extern "C" pdhg_status pdhg_one_step_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
                                                     const pdhg_scheme *scheme, size_t *bytes) {
     if (!bytes) return fail(PDHG_ERR_INVALID_ARG, "bytes is NULL");
@@ -1289,7 +1303,19 @@ extern "C" pdhg_status pdhg_one_step_workspace_size(const pdhg_problem *prob, co
     pdhg_grid g1;
     pdhg_status st = one_step_inputs(prob, grid, scheme, &p1, &g1);
     if (st != PDHG_OK) return st;
-    return pdhg_workspace_size(&p1, &g1, scheme, bytes);
+    const pdhg_scheme s1 = one_step_scheme(scheme);
+    size_t b1 = 0;
+    st = pdhg_workspace_size(&p1, &g1, &s1, &b1);
+    if (st != PDHG_OK) return st;
+    *bytes = scheme->time == PDHG_TIME_BDF2 ? 2 * align256(b1) : b1;
+    return PDHG_OK;
+}
+
+// w = (4 u^l - u^{l-1}) / 3, the start of a BDF2 step written as a BE step
+template <typename T>
+__global__ void k_bdf2_start(const T *__restrict__ ul, const T *__restrict__ ulm, T *__restrict__ w, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = (T(4) * ul[i] - ulm[i]) / T(3);
 }
 
 static cudaError_t restart_step(pdhg_handle *h, const char *u_start) {
@@ -1314,38 +1340,52 @@ extern "C" pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_
     if (max_iters_per_step < 1 || check_every < 1)
         return fail(PDHG_ERR_INVALID_ARG, "max_iters_per_step and check_every must be >= 1");
     if (iters_total) *iters_total = 0;
-    pdhg_handle *h = nullptr;
-    st = pdhg_create(&p1, &g1, scheme, workspace, bytes, stream, &h);
+    const pdhg_scheme s1 = one_step_scheme(scheme);
+    const bool bdf2 = scheme->time == PDHG_TIME_BDF2;
+    size_t b1 = 0;
+    st = pdhg_workspace_size(&p1, &g1, &s1, &b1);
     if (st != PDHG_OK) return st;
-    h->res_norm = 1;
-    const size_t sb = h->G.S * h->G.esz;
+    if (bytes < (bdf2 ? 2 * align256(b1) : b1)) return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+    pdhg_handle *h1 = nullptr, *h2 = nullptr;
+    st = pdhg_create(&p1, &g1, &s1, workspace, b1, stream, &h1);
+    if (st != PDHG_OK) return st;
+    h1->res_norm = 1;
+    if (bdf2) {
+        pdhg_grid g2 = g1;
+        g2.T = 2.0 * g1.T / 3.0;
+        st = pdhg_create(&p1, &g2, &s1, (char *)workspace + align256(b1), b1, stream, &h2);
+        if (st != PDHG_OK) { pdhg_destroy(h1); return st; }
+        h2->res_norm = 1;
+    }
+    pdhg_handle *h = h1;
+    const size_t sb = h1->G.S * h1->G.esz;
     char *uo = (char *)u_out;
-    cudaError_t e = cudaMemcpyAsync(uo, h->ws + h->L.u0, sb, cudaMemcpyDeviceToDevice, h->stream);
+    cudaError_t e = cudaMemcpyAsync(uo, h1->ws + h1->L.u0, sb, cudaMemcpyDeviceToDevice, h1->stream);
     int64_t total = 0;
     for (int64_t l = 0; l < grid->nt && st == PDHG_OK; ++l) {
-        if (e == cudaSuccess && l > 0) e = restart_step(h, uo + l * sb);
+        if (bdf2 && l >= 1) {
+            // the BDF2 step as a BE step of length 2 h_t / 3 from w, written where u^{l+1} goes
+            h = h2;
+            const int64_t n = h->G.S;
+            const unsigned gb = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+            if (e == cudaSuccess) {
+                if (h->G.prec == PDHG_FP64)
+                    k_bdf2_start<double><<<gb, 256, 0, h->stream>>>((const double *)(uo + l * sb),
+                                                                  (const double *)(uo + (l - 1) * sb),
+                                                                  (double *)(uo + (l + 1) * sb), n);
+                else
+                    k_bdf2_start<float><<<gb, 256, 0, h->stream>>>((const float *)(uo + l * sb),
+                                                                 (const float *)(uo + (l - 1) * sb),
+                                                                 (float *)(uo + (l + 1) * sb), n);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = restart_step(h, uo + (l + 1) * sb);
+        } else if (e == cudaSuccess && l > 0) {
+            e = restart_step(h, uo + l * sb);
+        }
         if (e != cudaSuccess) { st = cuda_fail(e, "one-step restart"); break; }
         int64_t done = 0;
-        if (h->G.prec == PDHG_FP64) {
-            st = pdhg_iterate(h, max_iters_per_step, tol, check_every, 0, &done);
-        } else {
-            // float32: a step whose larger Res entry has not fallen by 5% over its last three
-            // checks has met float32's rounding floor and ends there
-            double hist[3] = {INFINITY, INFINITY, INFINITY};
-            while (done < max_iters_per_step) {
-                int64_t d = 0;
-                const int64_t chunk = std::min<int64_t>(check_every, max_iters_per_step - done);
-                st = pdhg_iterate(h, chunk, tol, (int32_t)chunk, 0, &d);
-                done += d;
-                if (st != PDHG_OK) break;
-                if (h->last_res[0] <= tol && h->last_res[1] <= tol) break;
-                const double w = std::max(h->last_res[0], h->last_res[1]);
-                if (w > 0.95 * hist[0]) break;
-                hist[0] = hist[1];
-                hist[1] = hist[2];
-                hist[2] = w;
-            }
-        }
+        st = pdhg_iterate(h, max_iters_per_step, tol, check_every, 0, &done);
         total += done;
         if (iters_per_step) iters_per_step[l] = done;
         if (st != PDHG_OK) break;
@@ -1354,7 +1394,8 @@ extern "C" pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_
     if (st == PDHG_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (st == PDHG_OK && e != cudaSuccess) st = cuda_fail(e, "one-step copy");
     if (iters_total) *iters_total = total;
-    pdhg_destroy(h);
+    pdhg_destroy(h1);
+    pdhg_destroy(h2);
     return st;
 }
 
@@ -1503,12 +1544,32 @@ struct pdhg_batch {
     std::vector<int32_t> order;          // instance ids, most cells first
     size_t smem;
     int64_t launches;
+    // persistent launch (one cooperative launch per iteration, work queue)
+    bool persistent;
+    BatchEntry *queue;                   // device: the work items, stage | items << 2 in pad
+    int64_t nqueue;
+    int32_t *need;                       // device: items per (instance, stage)
+    unsigned int *cnt;                   // device: dequeue counter, then finished items per (instance, stage)
+    int *err;                            // device: a bounded wait gave up
+    uint64_t wait_ns;
+    int32_t blocks_per_sm;               // resident blocks per multiprocessor (0: as many as fit)
+    int32_t tiles[8];                    // row items per queue entry, by size class
+    int32_t qorder;                      // 0: stage-major queue, 1: instance-major
+    int nsm;
 };
 
 namespace {
 
+// size class of an instance for the tiles: log2 of its row transform length (the
+// Bluestein length, or nx/2 for the packed real FFT) - 8, clamped to [0, 7]
+int batch_class(const Geom &G) {
+    const int lg = G.blu_log2L ? G.blu_log2L : ilog2(std::max<int64_t>(G.nx / 2, 1));
+    return std::min(7, std::max(0, lg - 8));
+}
+
 struct BatchLayout {
     size_t insts, tab[TAB_N], list, partials, out, inst0, total;
+    size_t queue, need, cnt, err;
     int64_t cap[TAB_N];
     std::vector<size_t> inst_off, inst_bytes;
     std::vector<int64_t> part_off;
@@ -1559,6 +1620,12 @@ pdhg_status batch_layout(int32_t count, const pdhg_problem *probs, const pdhg_gr
     B->list = take(count * sizeof(int32_t));
     B->partials = take(parts * 6 * sizeof(double));
     B->out = take(count * 6 * sizeof(double));
+    // persistent queue: at most one entry per primal block, two per row block (residual
+    // and dual), one per 256 t-solve columns (<= the 128-column table's entries)
+    B->queue = take((tabs[TAB_PRIMAL] + 2 * tabs[TAB_ROWS] + tabs[TAB_TSOLVE]) * sizeof(BatchEntry));
+    B->need = take((size_t)count * 4 * sizeof(int32_t));
+    B->cnt = take((1 + (size_t)count * 4) * sizeof(unsigned int));
+    B->err = take(sizeof(int));
     B->inst_off.resize(count);
     for (int32_t i = 0; i < count; ++i) B->inst_off[i] = take(B->inst_bytes[i]);
     B->total = o;
@@ -1636,6 +1703,53 @@ static pdhg_status batch_tables(pdhg_batch *b) {
             for (int64_t x = 0; x < gx; ++x) t[TAB_CHECK].push_back({i, (int32_t)x, (int32_t)l, 0});
         list.push_back(i);
     }
+    // persistent queue: stage after stage (order 0: instances most cells first within a
+    // stage) or instance after instance (order 1: each instance's four stages in turn, so
+    // that the stages of different instances overlap); an entry covers `tiles[class]` row
+    // items (primal slices, row blocks) or one block of 256 t-solve columns
+    std::vector<BatchEntry> q;
+    std::vector<int32_t> need((size_t)b->count * 4, 0);
+    std::vector<std::pair<int, int32_t>> seq;            // (stage, instance) in queue order
+    for (int stage = 0; stage < 4; ++stage)
+        for (int32_t i : b->order) seq.push_back({stage, i});
+    if (b->qorder == 1)
+        std::stable_sort(seq.begin(), seq.end(), [&](const std::pair<int, int32_t> &x, const std::pair<int, int32_t> &y) {
+            const auto px = std::find(b->order.begin(), b->order.end(), x.second) - b->order.begin();
+            const auto py = std::find(b->order.begin(), b->order.end(), y.second) - b->order.begin();
+            return px < py;
+        });
+    for (const auto &si : seq) {
+        {
+            const int stage = si.first;
+            const int32_t i = si.second;
+            if (!b->active[i]) continue;
+            const Geom &G = b->h[i]->G;
+            int64_t nb[TAB_N], gx;
+            batch_blocks(G, nb, &gx);
+            const int64_t g = std::max(1, b->tiles[batch_class(G)]);
+            if (stage == 0) {
+                const int64_t gxp = nb[TAB_PRIMAL] / (G.nt + 1);
+                for (int64_t l = 0; l <= G.nt; l += g)
+                    for (int64_t x = 0; x < gxp; ++x)
+                        q.push_back({i, (int32_t)x, (int32_t)l, (int32_t)(std::min(g, G.nt + 1 - l) << 2)});
+            } else if (stage == 2) {
+                const bool dg = G.space >= PDHG_SPACE_DG_P2_LF;
+                const int64_t cols = dg ? G.nkx : G.lines * G.nkx;
+                for (int64_t x = 0; x < (cols + 255) / 256; ++x) q.push_back({i, (int32_t)x, 0, (int32_t)(2 | (1 << 2))});
+            } else {
+                const int64_t lstep = G.blu_log2L ? 2 : 1, nlines = nb[TAB_ROWS] / G.nt;
+                const int64_t rows = (G.nt + lstep - 1) / lstep;          // row items per line
+                for (int64_t r = 0; r < rows; r += g)
+                    for (int64_t x = 0; x < nlines; ++x)
+                        q.push_back({i, (int32_t)x, (int32_t)(r * lstep), (int32_t)(stage | (std::min(g, rows - r) << 2))});
+            }
+        }
+    }
+    for (const BatchEntry &e : q) ++need[(size_t)e.inst * 4 + (e.pad & 3)];
+    b->nqueue = (int64_t)q.size();
+    if (!q.empty())
+        CK(cudaMemcpyAsync(b->queue, q.data(), q.size() * sizeof(BatchEntry), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->need, need.data(), need.size() * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
     for (int k = 0; k < TAB_N; ++k) {
         b->nblk[k] = (int64_t)t[k].size();
         if (!t[k].empty())
@@ -1673,6 +1787,23 @@ extern "C" pdhg_status pdhg_batch_create(int32_t count, const pdhg_problem *prob
     b->smem = 0;
     b->launches = 0;
     b->active.assign(count, 1);
+    b->persistent = false;
+    b->qorder = 0;
+    b->queue = (BatchEntry *)(ws + B.queue);
+    b->nqueue = 0;
+    b->need = (int32_t *)(ws + B.need);
+    b->cnt = (unsigned int *)(ws + B.cnt);
+    b->err = (int *)(ws + B.err);
+    b->wait_ns = 1000000000ull;
+    b->blocks_per_sm = 0;
+    for (int k = 0; k < 8; ++k) b->tiles[k] = 1;
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
+        if (e != cudaSuccess) { delete b; return cuda_fail(e, "batch create"); }
+    }
     for (int32_t i = 0; i < count; ++i) {
         pdhg_scheme s = schemes[i];
         s.path = PDHG_PATH_PLAIN;
@@ -1696,6 +1827,19 @@ extern "C" pdhg_status pdhg_batch_create(int32_t count, const pdhg_problem *prob
 template <typename T>
 static cudaError_t batch_iteration(pdhg_batch *b) {
     const BatchInst<T> *I = (const BatchInst<T> *)b->insts;
+    if (b->persistent) {
+        int per_sm = 0;
+        cudaError_t e = batch_persistent_occupancy<T>(b->smem, &per_sm);
+        if (e != cudaSuccess) return e;
+        if (b->blocks_per_sm > 0) per_sm = std::min(per_sm, (int)b->blocks_per_sm);
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        e = cudaMemsetAsync(b->cnt, 0, (1 + (size_t)b->count * 4) * sizeof(unsigned int), b->stream);
+        if (e == cudaSuccess)
+            e = launch_batch_persistent<T>(I, b->queue, b->nqueue, b->need, b->cnt, b->err, b->wait_ns,
+                                           per_sm * b->nsm, b->smem, b->stream);
+        b->launches += 1;
+        return e;
+    }
     cudaError_t e = launch_batch<T>(BATCH_PRIMAL, I, b->tab[TAB_PRIMAL], b->nblk[TAB_PRIMAL], 0, nullptr, nullptr,
                                     nullptr, b->stream);
     if (e == cudaSuccess)
@@ -1721,8 +1865,14 @@ static pdhg_status batch_check(pdhg_batch *b, std::vector<double> &acc) {
     b->launches += 2;
     if (e != cudaSuccess) return cuda_fail(e, "batched residual check");
     acc.resize((size_t)b->count * 6);
+    int err = 0;
     CK(cudaMemcpyAsync(acc.data(), b->out, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    if (err) {
+        CK(cudaMemset(b->err, 0, sizeof(int)));
+        return fail(PDHG_ERR_TIMEOUT, "a bounded wait of the persistent batch iteration gave up (the batch state is invalid)");
+    }
     return PDHG_OK;
 }
 
@@ -1806,6 +1956,27 @@ extern "C" pdhg_status pdhg_batch_launch_count(pdhg_batch *b, int64_t *launches,
     if (!b || !launches) return fail(PDHG_ERR_INVALID_ARG, "null batch or out");
     *launches = b->launches;
     if (reset) b->launches = 0;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_batch_set_launch(pdhg_batch *b, int32_t persistent, int32_t blocks_per_sm,
+                                             int32_t order, const int32_t *tiles) {
+    if (!b) return fail(PDHG_ERR_INVALID_ARG, "null batch");
+    if (blocks_per_sm < 0) return fail(PDHG_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
+    if (order != 0 && order != 1) return fail(PDHG_ERR_INVALID_ARG, "order must be 0 or 1");
+    b->qorder = order;
+    if (tiles)
+        for (int k = 0; k < 8; ++k)
+            if (tiles[k] < 1 || tiles[k] > 64) return fail(PDHG_ERR_INVALID_ARG, "tiles must be in [1, 64]");
+    b->persistent = persistent != 0;
+    b->blocks_per_sm = blocks_per_sm;
+    if (tiles) std::copy(tiles, tiles + 8, b->tiles);
+    return batch_tables(b);
+}
+
+extern "C" pdhg_status pdhg_batch_set_wait_budget(pdhg_batch *b, uint64_t ns) {
+    if (!b) return fail(PDHG_ERR_INVALID_ARG, "null batch");
+    b->wait_ns = ns;
     return PDHG_OK;
 }
 

@@ -69,6 +69,8 @@ struct Params {
     // exact time operator (PDHG_FLAG_EXACT_TIME_PRECOND): per mode the LDL^T factors of
     // h_t^2 D_t D_t^T + s as [3][nt][modes] (1/d_l, e_l, f_l); nullptr: T_t (closed form)
     const T *tfac = nullptr;
+    // float32 fields with the t-solve recurrence in float64 (PDHG_FLAG_T_SOLVE_FP64)
+    int32_t t64 = 0;
 };
 
 // Debug builds (-DPDHG_DEBUG): the global indices of the instrumented kernels are checked

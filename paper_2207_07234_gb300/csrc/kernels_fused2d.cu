@@ -576,6 +576,39 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
 // shared memory (radix-8 layout of stockham.cuh: c = 2 after the first two stages,
 // c = 0 after the third).  Twiddles (twY): radix-8 span p at (p - 4) + (q-1) p + k,
 // radix-4 span 256 at 252 + (q-1) 256 + k.
+// The recurrence state of the t-solve: float2 and the float32 pivots, or (T64: the
+// PDHG_FLAG_T_SOLVE_FP64 variant) double2 and pivots in double, each stored value rounded
+// to float once.
+template <bool T64> struct TRec;
+template <> struct TRec<false> {
+    typedef float2 A;
+    typedef float R;
+    __device__ static R rho(R th, R emt, R q, int l) { return rho_f(th, emt, q, l); }
+    __device__ static R ex(R x) { return expf(x); }
+    __device__ static A fwd(float2 v, A acc, R r, bool first) { return first ? v : cadd(v, cscale(acc, r)); }
+    __device__ static A bwd(float2 y, A acc, R r, bool last) { return cscale(last ? y : cadd(y, acc), r); }
+    __device__ static float2 out(A a) { return a; }
+    __device__ static A zero() { return make_float2(0.f, 0.f); }
+};
+template <> struct TRec<true> {
+    typedef double2 A;
+    typedef double R;
+    __device__ static R rho(R th, R emt, R q, int l) {
+        const double w = exp(-(double)(2 * l + 1) * th);
+        return emt * (1.0 + w) / (1.0 + q * w);
+    }
+    __device__ static R ex(R x) { return exp(x); }
+    __device__ static A fwd(float2 v, A acc, R r, bool first) {
+        return first ? make_double2(v.x, v.y) : make_double2((double)v.x + r * acc.x, (double)v.y + r * acc.y);
+    }
+    __device__ static A bwd(float2 y, A acc, R r, bool last) {
+        return last ? make_double2(r * y.x, r * y.y) : make_double2(r * ((double)y.x + acc.x), r * ((double)y.y + acc.y));
+    }
+    __device__ static float2 out(A a) { return make_float2((float)a.x, (float)a.y); }
+    __device__ static A zero() { return make_double2(0.0, 0.0); }
+};
+
+template <bool T64>
 __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float2 *__restrict__ spec,
                                                        const float2 *__restrict__ twY,
                                                        const float *__restrict__ thetaT) {
@@ -591,14 +624,16 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
     const int64_t ncol = (int64_t)nt * P.nkx * NY - (int64_t)kx * NY;     // elements from col to the end
     const int t = threadIdx.x;
     for (int j = t; j < NY; j += FTHREADS) tw[j] = twY[j];
-    float th[4], emt[4], q4[4];
-    float2 acc[4], pf[TB][4];
+    typedef TRec<T64> TR;
+    typename TR::R th[4], emt[4], q4[4];
+    typename TR::A acc[4];
+    float2 pf[TB][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         th[q] = thetaT[dbg_idx(P, (int64_t)kx * NY + t + q * Q, (int64_t)P.nkx * NY, 302)];
-        emt[q] = expf(-th[q]);
+        emt[q] = TR::ex(-th[q]);
         q4[q] = emt[q] * emt[q];
-        acc[q] = make_float2(0.f, 0.f);
+        acc[q] = TR::zero();
     }
     const int nb = (nt + TB - 1) / TB;
     // ---- forward sweep ----
@@ -647,10 +682,8 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
                 float2 y[4] = {x0, x1, x2, x3};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    float2 v = y[q];
-                    if (l > 0) v = cadd(v, cscale(acc[q], rho_f(th[q], emt[q], q4[q], l - 1)));
-                    acc[q] = v;
-                    col[dbg_idx(P, ((int64_t)l * cs + t + q * Q), ncol, 301)] = v;
+                    acc[q] = TR::fwd(y[q], acc[q], l > 0 ? TR::rho(th[q], emt[q], q4[q], l - 1) : 0, l == 0);
+                    col[dbg_idx(P, ((int64_t)l * cs + t + q * Q), ncol, 301)] = TR::out(acc[q]);
                 }
             }
         }
@@ -672,10 +705,8 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
             for (int q = 0; q < 4; ++q) {
                 z[q] = make_float2(0.f, 0.f);
                 if (l >= 0) {
-                    float2 y = pf[b][q];
-                    if (l < nt - 1) y = cadd(y, acc[q]);
-                    acc[q] = cscale(y, rho_f(th[q], emt[q], q4[q], l));
-                    z[q] = acc[q];
+                    acc[q] = TR::bwd(pf[b][q], acc[q], TR::rho(th[q], emt[q], q4[q], l), l == nt - 1);
+                    z[q] = TR::out(acc[q]);
                 }
             }
             // inverse stage 1 (span 1) in registers
@@ -1156,7 +1187,10 @@ int rowsR_chunk(int nt, int rows, int slots, bool bdf2) {
 cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const float *twx, const float *twy,
                          const float *theta) {
     (void)twy; (void)theta;
-    cudaError_t ec = cudaFuncSetAttribute(k_cols1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols(10));
+    cudaError_t ec = cudaFuncSetAttribute(k_cols1024<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_cols(10));
+    if (ec == cudaSuccess)
+        ec = cudaFuncSetAttribute(k_cols1024<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols(10));
     if (ec == cudaSuccess)
         ec = cudaFuncSetAttribute(k_rowsC1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rowsC1024());
     if (ec != cudaSuccess) return ec;
@@ -1295,7 +1329,10 @@ cudaError_t fused2d_cols(Fused2D *f, const Params<float> &P, cudaStream_t s) {
     switch (ilog2i(P.ny)) {
     case 8: k_cols<8><<<grid, FTHREADS, smem_cols(8), s>>>(P, f->spec, f->twY, f->thetaT); break;
     case 9: k_cols<9><<<grid, FTHREADS, smem_cols(9), s>>>(P, f->spec, f->twY, f->thetaT); break;
-    case 10: k_cols1024<<<grid, FTHREADS, smem_cols(10), s>>>(P, f->spec, f->twY, f->thetaT); break;
+    case 10:
+        if (P.t64) k_cols1024<true><<<grid, FTHREADS, smem_cols(10), s>>>(P, f->spec, f->twY, f->thetaT);
+        else k_cols1024<false><<<grid, FTHREADS, smem_cols(10), s>>>(P, f->spec, f->twY, f->thetaT);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -389,6 +389,32 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
         tsolve_exact<T, C>(spec + col, modes, P.tfac, modes, col, nt);
         return;
     }
+    if (sizeof(T) == 4 && P.t64) {
+        // the recurrence in float64 (PDHG_FLAG_T_SOLVE_FP64): pivots and the running y, z
+        // in double; each stored y_l and z_l is rounded to the field's precision once
+        const double th = (double)theta_tab[col];
+        const double emt = exp(-th), q = emt * emt;
+        C *s = spec + col;
+        double yr = (double)s[0].x, yi = (double)s[0].y;
+        for (int l = 1; l < nt; ++l) {
+            const C r = s[(int64_t)l * modes];
+            const double rh = rho_of<double>(th, emt, q, l - 1);
+            yr = (double)r.x + rh * yr;
+            yi = (double)r.y + rh * yi;
+            s[(int64_t)l * modes] = mk<C, T>((T)yr, (T)yi);
+        }
+        const double rl = rho_of<double>(th, emt, q, nt - 1);
+        double zr = rl * yr, zi = rl * yi;
+        s[(int64_t)(nt - 1) * modes] = mk<C, T>((T)zr, (T)zi);
+        for (int l = nt - 2; l >= 0; --l) {
+            const C yl = s[(int64_t)l * modes];
+            const double rh = rho_of<double>(th, emt, q, l);
+            zr = rh * ((double)yl.x + zr);
+            zi = rh * ((double)yl.y + zi);
+            s[(int64_t)l * modes] = mk<C, T>((T)zr, (T)zi);
+        }
+        return;
+    }
     const T th = theta_tab[col];
     const T emt = expT(-th), q = emt * emt;
     C *s = spec + col;
@@ -873,6 +899,99 @@ __global__ void __launch_bounds__(256) k_b_reduce(const BatchInst<T> *__restrict
     block_sum6(acc, out + (int64_t)inst * 6);
 }
 
+// ---------------------------------------------------------------------------
+// One batched iteration in a single persistent launch.  Blocks take work items from
+// a queue (atomic counter cnt[0]) in the queue's order: every instance's primal items,
+// then its residual + x-FFT rows, its t-solve columns and its inverse x-FFT + dual rows,
+// stage after stage, the instances with most cells first within a stage.  An item of
+// stage s > 0 starts once all stage s-1 items of its instance are finished (counter
+// cnt[1 + 4 inst + s-1] = need[4 inst + s-1]); it only waits on items that earlier
+// dequeues have handed to running blocks, and all blocks are resident (cooperative
+// launch), so every wait ends.  Each wait is bounded by wait_ns of %globaltimer (0:
+// gives up at once); a block that gives up sets *err and leaves, and so do the blocks
+// that then wait on it.  A queue entry covers `pad >> 2` consecutive row items (the
+// tiles chosen per size class) and stage `pad & 3`.  Completion: every thread fences
+// its writes, the block synchronises, one thread counts the item; the waiting thread
+// fences after it sees the count, then its block synchronises (the pattern of a grid
+// barrier).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t batch_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_persistent(const BatchInst<T> *__restrict__ I,
+                                                      const BatchEntry *__restrict__ q, int64_t nq,
+                                                      const int32_t *__restrict__ need, unsigned int *cnt, int *err,
+                                                      uint64_t wait_ns) {
+    typedef typename Cplx<T>::type C;
+    __shared__ int64_t s_item;
+    __shared__ int s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(cnt, 1u);
+        __syncthreads();
+        const int64_t it = s_item;
+        if (it >= nq) return;
+        const BatchEntry e = q[it];
+        const int stage = e.pad & 3, span = max(e.pad >> 2, 1), inst = e.inst;
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (stage > 0) {
+                const unsigned int target = (unsigned int)need[4 * inst + stage - 1];
+                volatile unsigned int *c = cnt + 1 + 4 * inst + stage - 1;
+                if (wait_ns == 0) {
+                    ok = 0;
+                } else if (*c < target) {
+                    const uint64_t t0 = batch_ns();
+                    while (*c < target)
+                        if (batch_ns() - t0 > wait_ns) { ok = 0; break; }
+                }
+                __threadfence();
+            }
+            if (!ok) atomicExch(err, 1);
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const BatchInst<T> &b = I[inst];
+        for (int k = 0; k < span; ++k) {
+            switch (stage) {
+            case 0: primal_block(b.P, b.u, b.phit, b.lam, b.lamt, b.u0, e.bx, e.l + k); break;
+            case 1:
+                residual_rfft_block(b.P, b.u, (C *)b.spec, (const C *)b.twx, e.bx,
+                                    e.l + k * (b.P.blu_log2L ? 2 : 1));
+                break;
+            case 2: tsolve_block(b.P, (C *)b.spec, b.theta, (const C *)b.V, e.bx + k); break;
+            default:
+                dual_irfft_block(b.P, (const C *)b.spec, b.phi, b.phit, (const C *)b.twx, e.bx,
+                                 e.l + k * (b.P.blu_log2L ? 2 : 1));
+                break;
+            }
+            __syncthreads();
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(cnt + 1 + 4 * inst + stage, 1u);
+    }
+}
+
+template <typename T>
+cudaError_t launch_batch_persistent(const BatchInst<T> *I, const BatchEntry *q, int64_t nq, const int32_t *need,
+                                    unsigned int *cnt, int *err, uint64_t wait_ns, int grid, size_t smem,
+                                    cudaStream_t s) {
+    void *args[] = {(void *)&I, (void *)&q, (void *)&nq, (void *)&need, (void *)&cnt, (void *)&err, (void *)&wait_ns};
+    return cudaLaunchCooperativeKernel((const void *)k_b_persistent<T>, dim3((unsigned)grid), dim3(256), args, smem, s);
+}
+
+template <typename T>
+cudaError_t batch_persistent_occupancy(size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_b_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_b_persistent<T>, 256, smem);
+    return e;
+}
+
 template <typename T>
 cudaError_t launch_batch(int kind, const BatchInst<T> *I, const BatchEntry *tab, int64_t nblocks, size_t smem,
                          const int32_t *list, double *partials, double *out, cudaStream_t s) {
@@ -913,7 +1032,11 @@ cudaError_t init_plain_attributes() {
                                          double *, cudaStream_t, int);                                        \
     template cudaError_t launch_phi_lap<T>(const Params<T> &, const T *, const T *, double *, double *, cudaStream_t); \
     template cudaError_t launch_batch<T>(int, const BatchInst<T> *, const BatchEntry *, int64_t, size_t,        \
-                                         const int32_t *, double *, double *, cudaStream_t);
+                                         const int32_t *, double *, double *, cudaStream_t);                     \
+    template cudaError_t launch_batch_persistent<T>(const BatchInst<T> *, const BatchEntry *, int64_t,          \
+                                                    const int32_t *, unsigned int *, int *, uint64_t, int, size_t, \
+                                                    cudaStream_t);                                              \
+    template cudaError_t batch_persistent_occupancy<T>(size_t, int *);
 
 PDHG_INSTANTIATE(float)
 PDHG_INSTANTIATE(double)

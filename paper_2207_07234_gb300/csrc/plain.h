@@ -65,5 +65,15 @@ enum { BATCH_PRIMAL, BATCH_RESIDUAL, BATCH_TSOLVE, BATCH_DUAL, BATCH_CHECK, BATC
 template <typename T>
 cudaError_t launch_batch(int kind, const BatchInst<T> *I, const BatchEntry *tab, int64_t nblocks, size_t smem,
                          const int32_t *list, double *partials, double *out, cudaStream_t s);
+// One iteration of every queued instance in one cooperative launch of `grid` blocks of
+// 256 threads: queue q (nq entries, pad = stage | items << 2), need[4 inst + stage] items
+// per instance and stage, counters cnt[1 + 4 count] (zeroed before the launch), *err set
+// when a bounded wait (wait_ns) gives up.
+template <typename T>
+cudaError_t launch_batch_persistent(const BatchInst<T> *I, const BatchEntry *q, int64_t nq, const int32_t *need,
+                                    unsigned int *cnt, int *err, uint64_t wait_ns, int grid, size_t smem,
+                                    cudaStream_t s);
+// resident blocks per multiprocessor of the persistent batch kernel with `smem` bytes
+template <typename T> cudaError_t batch_persistent_occupancy(size_t smem, int *blocks_per_sm);
 
 }  // namespace pdhg

@@ -45,11 +45,21 @@ def mixed():
 FIELDS = ("u", "phi", "phit", "lambda", "lambdat")
 
 
+LAUNCHES = [dict(persistent=True), dict(persistent=False),
+            dict(persistent=True, blocks_per_sm=1, order=1, tiles=[3, 2, 4, 1, 2, 5, 1, 2])]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_batch_equals_lone_instances_bitwise(B, precision):
+@pytest.mark.parametrize("launch", LAUNCHES, ids=["persistent", "per_stage", "persistent_order1_tiles"])
+def test_batch_equals_lone_instances_bitwise(B, precision, launch):
+    """The persistent launch (work queue, any tiles and blocks per multiprocessor) and the
+    per-stage launches run the same per-block code: the iterates equal a lone handle's."""
     probs = mixed()
     with B.Batch(probs, precision=precision) as bt:
+        bt.set_launch(**launch)
+        bt.launches(reset=True)
         its, st = bt.iterate(20)
+        assert bt.launches() == 20 * (1 if launch["persistent"] else 4)
         assert list(its) == [20] * len(probs) and list(st) == [0] * len(probs)
         got = [{f: bt.instance(i).get_host(f) for f in FIELDS} for i in range(len(probs))]
     for p, g in zip(probs, got):
@@ -108,7 +118,7 @@ def test_batch_of_256_sampled(B):
         small_adv = min(adv, key=lambda i: cells[i])
         pick = [int(np.argmax(cells)), int(np.argmin(cells)), int(np.argsort(cells)[len(cells) // 2]), small_adv]
         got = {i: bt.instance(i).get_host("u") for i in pick}
-        assert bt.launches() >= 4 * 5
+        assert bt.launches() >= 5
     for i in pick:
         with B.Solver(probs[i], precision="fp32", path="plain") as s:
             s.iterate(5)
@@ -138,3 +148,21 @@ def test_batch_instances_fp64_vs_oracle(B):
         for _ in range(5):
             opdhg.step(p, st)
         assert np.max(np.abs(u - st["u"])) <= 1e-9 * np.max(np.abs(st["u"])), p.name
+
+
+def test_batch_wait_budget_timeout_is_reported(B):
+    """The bounded waits of the persistent iteration: with a zero budget the first wait
+    gives up, the blocks leave, and the next residual check reports PDHG_ERR_TIMEOUT; the
+    CUDA context stays usable and a new batch runs normally."""
+    probs = mixed()
+    with B.Batch(probs, precision="fp64") as bt:
+        bt.set_launch(persistent=True)
+        bt.set_wait_budget(0)
+        with pytest.raises(B.PdhgError) as e:
+            bt.iterate(2, tol=0.0, check_every=1)
+        assert e.value.status == -6
+    with B.Batch(probs, precision="fp64") as bt:
+        bt.set_launch(persistent=True)
+        its, st = bt.iterate(3, tol=0.0, check_every=1)
+        assert list(its) == [3] * len(probs)
+        assert all(np.all(np.isfinite(bt.instance(i).get_host("u"))) for i in range(len(probs)))

@@ -71,11 +71,21 @@ def test_one_step_fp32_counts_near_fp64(B):
     assert np.all(np.isfinite(u32.cpu().numpy()))
 
 
-def test_one_step_rejects_bdf2(B):
-    p = W.traffic_dg_p1(ncell=16, nt=4, time="bdf2")
-    with pytest.raises(B.PdhgError) as e:
-        B.solve_one_step(p, tol=1e-3)
-    assert e.value.status == -7
+@pytest.mark.parametrize("p", [W.viscous_burgers(nx=64, nt=12, T=0.5, nu=0.02),
+                               W.burgers_dg_p2(ncell=32, nt=10, T=0.5).replace(c=0.5),
+                               W.traffic_dg_p1(ncell=16, nt=4, time="bdf2")],
+                         ids=lambda p: p.name)
+def test_one_step_bdf2_reaches_scheme_solution(B, p):
+    """Algorithm 3 for BDF2 (each step l >= 1 the BE step of length 2 h_t / 3 from
+    (4 u^l - u^{l-1}) / 3) on the GPU, float64: the oracle's per-step counts and the
+    Newton solution of the BDF2 scheme (1e-9)."""
+    t = float(np.sqrt(0.5 / opdhg.power_estimate(p.replace(nt=1, T=p.ht, time="be"), iters=60)))
+    p = p.replace(tau_u=t, tau_u0=t, tau_phi=t)
+    u, counts = B.solve_one_step(p, tol=1e-11, max_iters_per_step=20000, check_every=10, precision="fp64")
+    uo, co = variants.one_timestep(p, 1e-11, max_iters_per_step=20000, check_every=10)
+    assert max(abs(a - b) for a, b in zip(counts, co)) <= 10, (counts, co)
+    un = newton.solve(p)
+    assert np.max(np.abs(u.cpu().numpy() - un)) <= 1e-9 * max(1.0, np.max(np.abs(un)))
 
 
 def test_refine_traffic_counts_and_solution(B):

@@ -50,11 +50,15 @@ def one_step_taus(p, fac=0.5):
 
 
 @pytest.mark.parametrize("p", [W.advection_upwind_be(nx=16, nt=8), W.traffic_dg_p1(ncell=16, nt=4),
-                               W.viscous_burgers(nx=16, nt=6, nu=0.05).replace(time="be")],
-                         ids=lambda p: p.name)
+                               W.viscous_burgers(nx=16, nt=6, nu=0.05).replace(time="be"),
+                               W.viscous_burgers(nx=16, nt=6, nu=0.05),
+                               W.advection_upwind_be(nx=16, nt=8).replace(time="bdf2"),
+                               W.burgers_dg_p2(ncell=8, nt=5, T=0.4).replace(c=0.5)],
+                         ids=lambda p: f"{p.name}_{p.time}")
 def test_one_timestep_reaches_scheme_solution(p):
     """Algorithm 3 to Res <= 1e-12 gives the full scheme's solution slice by slice
-    (the one-step problems keep the full problem's inputs)."""
+    (the one-step problems keep the full problem's inputs), for BE and for BDF2, whose
+    steps l >= 1 are BE steps of length 2 h_t / 3 from (4 u^l - u^{l-1}) / 3."""
     p = one_step_taus(p)
     u, counts = variants.one_timestep(p, 1e-12, max_iters_per_step=5000)
     assert max(counts) < 5000, counts
