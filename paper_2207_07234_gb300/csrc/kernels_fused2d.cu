@@ -427,14 +427,22 @@ k_rowsR1024(Params<float> P, const float *__restrict__ u, float2 *__restrict__ s
         }
         if (m + 1 <= l1) load(m + 1);                         // arrives during the split and the other blocks' work
         if (act) {
+            // split pairs (k, M-k) of two rows 2p, 2p+1 per item: both outputs of each row from
+            // one pair of loads, and the two rows' values at one kx stored as one float4
             const int64_t dst0 = (int64_t)lr * P.nkx * ny + y0, nX = (int64_t)P.nt * P.nkx * ny;
-            for (int idx = t; idx < (M / 2 + 1) * FH; idx += ATHREADS) {
-                const int k = idx / FH, rr = idx - k * FH;
-                const float2 *row = res + rr * PN;
-                float2 xk, xm;
-                rfft_split_pair(row[k], row[k == 0 ? 0 : M - k], __ldg(twN + k), xk, xm);
-                spec[dbg_idx(P, dst0 + (int64_t)k * ny + rr, nX, 202)] = xk;
-                if (k != M / 2) spec[dbg_idx(P, dst0 + (int64_t)(M - k) * ny + rr, nX, 202)] = xm;
+            for (int idx = t; idx < (M / 2 + 1) * 2; idx += ATHREADS) {
+                const int k = idx >> 1, p = idx & 1;
+                const float2 *ra = res + (2 * p) * PN, *rb = ra + PN;
+                const float2 w = __ldg(twN + k);
+                const int km = k == 0 ? 0 : M - k;
+                float2 ak, am, bk, bm;
+                rfft_split_pair(ra[k], ra[km], w, ak, am);
+                rfft_split_pair(rb[k], rb[km], w, bk, bm);
+                *reinterpret_cast<float4 *>(spec + dbg_idx(P, dst0 + (int64_t)k * ny + 2 * p, nX - 1, 202)) =
+                    make_float4(ak.x, ak.y, bk.x, bk.y);
+                if (k != M / 2)
+                    *reinterpret_cast<float4 *>(spec + dbg_idx(P, dst0 + (int64_t)(M - k) * ny + 2 * p, nX - 1, 202)) =
+                        make_float4(am.x, am.y, bm.x, bm.y);
             }
         }
     }
