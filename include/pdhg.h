@@ -114,7 +114,8 @@ typedef struct {
 /* time: PDHG_TIME_*; space: PDHG_SPACE_*; precision: PDHG_FP64 / PDHG_FP32;
  * init: PDHG_INIT_LAMBDA (Algorithm 1's multiplier on u^0 = u0) or
  * PDHG_INIT_PINNED (u^0 held at u0); path: PDHG_PATH_*; flags: 0 or a combination
- * of PDHG_FLAG_EXACT_TIME_PRECOND, PDHG_FLAG_U0_ON_DEVICE and PDHG_FLAG_T_SOLVE_FP64.
+ * of PDHG_FLAG_EXACT_TIME_PRECOND, PDHG_FLAG_U0_ON_DEVICE, PDHG_FLAG_T_SOLVE_FP64 and
+ * PDHG_FLAG_MIXED_STEPS.
  *
  * PDHG_FLAG_EXACT_TIME_PRECOND (an ablation of the preconditioner of Sec. 3.3): the
  * time part of K_d is the scheme's own h_t^2 D_t D_t^T (D_t the BE or BDF2 time
@@ -136,7 +137,15 @@ enum { PDHG_FLAG_EXACT_TIME_PRECOND = 1,
  * Finite differences with T_t only (PDHG_ERR_UNSUPPORTED with DG or the exact time
  * operator); on the fused path only for ny = 1024 (PDHG_PATH_AUTO then takes the plain
  * path for other ny).  No effect on float64 handles. */
-       PDHG_FLAG_T_SOLVE_FP64 = 4 };
+       PDHG_FLAG_T_SOLVE_FP64 = 4,
+/* PDHG_FLAG_MIXED_STEPS (pdhg_one_step_workspace_size / pdhg_solve_one_step only;
+ * scheme->precision is then ignored): each step of Algorithm 3 runs in float32 until its
+ * Res reaches tol or stops falling (the worse entry not 5% lower than three checks
+ * before: float32's rounding floor), then goes on in float64 from the widened state
+ * (K_d^{-1} applied in float32, as the float64 phase of pdhg_solve_mixed) to tol; u_out
+ * holds float64 values and iters_per_step counts both phases.  Other entry points:
+ * PDHG_ERR_INVALID_ARG. */
+       PDHG_FLAG_MIXED_STEPS = 8 };
 typedef struct {
     int32_t time, space, precision, init, path, flags;
 } pdhg_scheme;
@@ -265,11 +274,12 @@ pdhg_status pdhg_solve_refine(const pdhg_problem *prob, const pdhg_grid *grid,
  * step of length 2 h_t / 3 from w = (4 u*^l - u*^{l-1}) / 3, so that step runs as the
  * two-slice BE problem started from w (step 0 is the scheme's BE start).
  *
- * u_out: device, (nt+1)*ndof values of the scheme's precision, written with
- * u*^0..u*^nt.  iters_per_step (host, nt entries) and iters_total may be NULL.
- * workspace: device, caller-owned, 256-byte aligned, size from
- * pdhg_one_step_workspace_size (one handle with nt = 1; two for BDF2, the second
- * with the step length 2 h_t / 3).  Synchronises the stream before returning.  A step that fails (NONFINITE, DIVERGED, CUDA)
+ * u_out: device, (nt+1)*ndof values of the scheme's precision (float64 with
+ * PDHG_FLAG_MIXED_STEPS), written with u*^0..u*^nt.  iters_per_step (host, nt entries)
+ * and iters_total may be NULL.  workspace: device, caller-owned, 256-byte aligned, size
+ * from pdhg_one_step_workspace_size (one handle with nt = 1, or a float32 and a float64
+ * one with PDHG_FLAG_MIXED_STEPS; twice that for BDF2, the second for the step length
+ * 2 h_t / 3).  Synchronises the stream before returning.  A step that fails (NONFINITE, DIVERGED, CUDA)
  * returns its status; u_out then holds the steps completed so far.
  */
 pdhg_status pdhg_one_step_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
@@ -408,6 +418,14 @@ pdhg_status pdhg_batch_set_launch(pdhg_batch *b, int32_t persistent, int32_t blo
  * (default 1e9); 0 gives up at the first wait: the host-side way to exercise the
  * PDHG_ERR_TIMEOUT path. */
 pdhg_status pdhg_batch_set_wait_budget(pdhg_batch *b, uint64_t ns);
+
+/* CUDA graphs for the batch (default on): pdhg_batch_iterate captures check_every
+ * iterations plus the residual check kernels once and replays the graph for each whole
+ * chunk of check_every iterations (a tail shorter than check_every, and runs with
+ * check_every == 0, launch kernel by kernel).  The graph is rebuilt when the active set
+ * or the launch choice changes.  The replayed launches are those of the kernel-by-kernel
+ * run, so results are identical.  enable == 0: no graphs.  Errors: INVALID_ARG. */
+pdhg_status pdhg_batch_set_graphs(pdhg_batch *b, int32_t enable);
 
 /*
  * Residual norms of a caller-held state, with no handle, no workspace and no

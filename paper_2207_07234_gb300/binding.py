@@ -29,6 +29,7 @@ FIELD = {"u": 0, "phi": 1, "phit": 2, "lambda": 3, "lambdat": 4, "u_terminal": 5
 FLAG_EXACT_TIME_PRECOND = 1      # pdhg_scheme.flags: time part of K_d = h_t^2 D_t D_t^T (ablation)
 FLAG_U0_ON_DEVICE = 2            # pdhg_scheme.flags: pdhg_problem.u0 is a device pointer
 FLAG_T_SOLVE_FP64 = 4            # pdhg_scheme.flags: float32 handle, t-solve recurrence in float64
+FLAG_MIXED_STEPS = 8             # pdhg_scheme.flags (one-step solve): float32, then float64 per step
 STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_rows", "fused_cols"]
 
 # every symbol include/pdhg.h declares
@@ -42,7 +43,7 @@ EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_strea
            "pdhg_solve_mixed", "pdhg_batch_workspace_size",
            "pdhg_batch_create", "pdhg_batch_destroy", "pdhg_batch_iterate", "pdhg_batch_reset",
            "pdhg_batch_instance", "pdhg_batch_launch_count", "pdhg_batch_set_launch",
-           "pdhg_batch_set_wait_budget", "pdhg_residual_noalloc"]
+           "pdhg_batch_set_wait_budget", "pdhg_batch_set_graphs", "pdhg_residual_noalloc"]
 
 
 class PdhgError(RuntimeError):
@@ -119,6 +120,7 @@ def load(path: str | None = None):
         "pdhg_batch_launch_count": [vp, ctypes.POINTER(i64), i32],
         "pdhg_batch_set_launch": [vp, i32, i32, i32, ctypes.POINTER(i32)],
         "pdhg_batch_set_wait_budget": [vp, ctypes.c_uint64],
+        "pdhg_batch_set_graphs": [vp, ctypes.c_int32],
         "pdhg_solve_gradient": [P, G, S, ctypes.POINTER(ctypes.c_double), ctypes.c_double, i64, ctypes.c_double, i64,
                                 i32, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
@@ -294,6 +296,9 @@ class Solver:
     def set(self, field, value):
         t = self._torch.as_tensor(value, dtype=self.dtype, device=self.device).contiguous()
         assert tuple(t.shape) == self._shape(field)
+        # the conversion above runs on torch's current stream; the copy runs on the
+        # handle's stream, which must wait for it
+        self._stream.wait_stream(self._torch.cuda.current_stream(self.device))
         _check(load().pdhg_set_field(self.h, FIELD[field], ctypes.c_void_p(t.data_ptr()), 1))
 
 
@@ -329,18 +334,23 @@ def solve_refine(p, levels, iters, tol=1e-3, check_every=1, relative=False, prec
 
 def solve_one_step(p, tol=1e-3, max_iters_per_step=100000, check_every=1, precision="fp64", device=None,
                    stream=None):
-    """Algorithm 3 (Sec. 3.5): returns (u* as a device tensor [nt+1][...], iterations per step)."""
+    """Algorithm 3 (Sec. 3.5): returns (u* as a device tensor [nt+1][...], iterations per step).
+    precision "mixed": each step in float32 to tol or float32's floor, then float64
+    (PDHG_FLAG_MIXED_STEPS; u* in float64)."""
     import torch
     lib = load()
-    prob, grid, scheme, keep = structs(p, precision, "plain")
+    prob, grid, scheme, keep = structs(p, "fp64" if precision == "mixed" else precision, "plain")
+    if precision == "mixed":
+        scheme.flags |= FLAG_MIXED_STEPS
     nbytes = ctypes.c_size_t(0)
     _check(lib.pdhg_one_step_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
                                             ctypes.byref(nbytes)))
     dev = torch.device(device if device is not None else "cuda")
     ws = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
-    dtype = torch.float64 if precision == "fp64" else torch.float32
+    dtype = torch.float32 if precision == "fp32" else torch.float64
     u = torch.empty((p.nt + 1,) + tuple(p.slice_shape), dtype=dtype, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))       # u was allocated on the current stream
     per = (ctypes.c_int64 * p.nt)()
     tot = ctypes.c_int64(0)
     _check(lib.pdhg_solve_one_step(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme), float(tol),
@@ -515,3 +525,7 @@ class Batch:
     def set_wait_budget(self, ns):
         """Budget (ns) of each bounded wait of the persistent iteration; 0 forces the timeout path."""
         _check(load().pdhg_batch_set_wait_budget(self.b, int(ns)))
+
+    def set_graphs(self, enable):
+        """CUDA-graph replay of check_every-iteration chunks (the default) or launches one by one."""
+        _check(load().pdhg_batch_set_graphs(self.b, int(bool(enable))))

@@ -1275,8 +1275,13 @@ static pdhg_status one_step_inputs(const pdhg_problem *prob, const pdhg_grid *gr
     if (!prob || !grid || !scheme) return fail(PDHG_ERR_INVALID_ARG, "null problem/grid/scheme");
     if (scheme->flags & PDHG_FLAG_U0_ON_DEVICE)
         return fail(PDHG_ERR_UNSUPPORTED, "the one-step variant takes u0 in host memory");
+    pdhg_scheme sv = *scheme;
+    if (sv.flags & PDHG_FLAG_MIXED_STEPS) {
+        sv.flags &= ~(int32_t)PDHG_FLAG_MIXED_STEPS;
+        sv.precision = PDHG_FP64;
+    }
     Geom G;
-    pdhg_status st = validate(prob, grid, scheme, &G);
+    pdhg_status st = validate(prob, grid, &sv, &G);
     if (st != PDHG_OK) return st;
     *g1 = *grid;
     g1->nt = 1;
@@ -1293,7 +1298,29 @@ static pdhg_status one_step_inputs(const pdhg_problem *prob, const pdhg_grid *gr
 static pdhg_scheme one_step_scheme(const pdhg_scheme *scheme) {
     pdhg_scheme s1 = *scheme;
     s1.time = PDHG_TIME_BE;
+    s1.flags &= ~(int32_t)PDHG_FLAG_MIXED_STEPS;
     return s1;
+}
+
+static pdhg_status mixed_schemes(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
+                                 pdhg_scheme *s32, pdhg_scheme *s64, size_t *b32, size_t *b64);
+
+// workspace of one step length: one handle, or (mixed steps) a float32 handle and a
+// float64 one; two step lengths for BDF2
+static pdhg_status one_step_region(const pdhg_problem *p1, const pdhg_grid *g1, const pdhg_scheme *scheme,
+                                   size_t *region, size_t *b32, size_t *b64) {
+    const pdhg_scheme s1 = one_step_scheme(scheme);
+    if (scheme->flags & PDHG_FLAG_MIXED_STEPS) {
+        pdhg_scheme s32, s64;
+        pdhg_status st = mixed_schemes(p1, g1, &s1, &s32, &s64, b32, b64);
+        if (st != PDHG_OK) return st;
+        *region = align256(*b32) + align256(*b64);
+        return PDHG_OK;
+    }
+    *b64 = 0;
+    pdhg_status st = pdhg_workspace_size(p1, g1, &s1, b32);
+    *region = align256(*b32);
+    return st;
 }
 
 extern "C" pdhg_status pdhg_one_step_workspace_size(const pdhg_problem *prob, const pdhg_grid *grid,
@@ -1303,11 +1330,10 @@ extern "C" pdhg_status pdhg_one_step_workspace_size(const pdhg_problem *prob, co
     pdhg_grid g1;
     pdhg_status st = one_step_inputs(prob, grid, scheme, &p1, &g1);
     if (st != PDHG_OK) return st;
-    const pdhg_scheme s1 = one_step_scheme(scheme);
-    size_t b1 = 0;
-    st = pdhg_workspace_size(&p1, &g1, &s1, &b1);
+    size_t region, b32, b64;
+    st = one_step_region(&p1, &g1, scheme, &region, &b32, &b64);
     if (st != PDHG_OK) return st;
-    *bytes = scheme->time == PDHG_TIME_BDF2 ? 2 * align256(b1) : b1;
+    *bytes = (scheme->time == PDHG_TIME_BDF2 ? 2 : 1) * region;
     return PDHG_OK;
 }
 
@@ -1328,6 +1354,121 @@ static cudaError_t restart_step(pdhg_handle *h, const char *u_start) {
     return e;
 }
 
+// the float32 handle of a mixed step restarted from a float64 start value
+static cudaError_t restart_step_narrow(pdhg_handle *h, const double *u_start) {
+    const int64_t S = h->G.S;
+    const size_t sb = S * sizeof(float);
+    k_u0_convert<float><<<(unsigned)std::min<int64_t>((S + 255) / 256, 1024), 256, 0, h->stream>>>(
+        u_start, F<float>(h, h->L.u0), S);
+    cudaError_t e = cudaGetLastError();
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(h->ws + h->u_off + k * sb, h->ws + h->L.u0, sb, cudaMemcpyDeviceToDevice, h->stream);
+    const size_t zero[4] = {h->L.phi, h->L.phit, h->L.lam, h->L.lamt};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMemsetAsync(h->ws + zero[i], 0, sb, h->stream);
+    return e;
+}
+
+// one mixed step: float32 iterations until Res <= tol or the float32 floor (the worse
+// entry of Res not 5% lower than three checks before), then the state widened to the
+// float64 handle (u^0 and its initial data the exact float64 start value) and float64
+// iterations to tol, checked after 1, 2, 3, 4, 6, 9, ... of them (as pdhg_solve_mixed)
+static pdhg_status mixed_step(pdhg_handle *hf, pdhg_handle *hd, const double *u_start, double tol, int64_t cap,
+                              int32_t check_every, int64_t *n32_out, int64_t *n64_out) {
+    *n32_out = *n64_out = 0;
+    cudaError_t e = restart_step_narrow(hf, u_start);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed step restart");
+    std::vector<double> hist;
+    int64_t n32 = 0;
+    bool done32 = false;
+    while (n32 < cap && !done32) {
+        int64_t done = 0;
+        pdhg_status st = pdhg_iterate(hf, std::min<int64_t>(check_every, cap - n32), tol, check_every, 0, &done);
+        n32 += done;
+        *n32_out = n32;
+        if (st != PDHG_OK) return st;
+        if (hf->last_res[0] <= tol && hf->last_res[1] <= tol) done32 = true;
+        hist.push_back(std::max(hf->last_res[0], hf->last_res[1]));
+        if (hist.size() >= 4 && hist.back() > 0.95 * hist[hist.size() - 4]) break;
+    }
+    const int64_t S = hf->G.S;
+    struct { size_t src, dst; int64_t n; } parts[5] = {
+        {hf->u_off, hd->u_off, 2 * S}, {hf->L.phi, hd->L.phi, S}, {hf->L.phit, hd->L.phit, S},
+        {hf->L.lam, hd->L.lam, S}, {hf->L.lamt, hd->L.lamt, S}};
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+        e = launch_widen((const float *)(hf->ws + parts[i].src), (double *)(hd->ws + parts[i].dst), parts[i].n,
+                         hd->stream);
+    const size_t sb = S * sizeof(double);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd->ws + hd->L.u0, u_start, sb, cudaMemcpyDeviceToDevice, hd->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd->ws + hd->u_off, u_start, sb, cudaMemcpyDeviceToDevice, hd->stream);
+    hd->launches += 5;
+    if (e != cudaSuccess) return cuda_fail(e, "float32 -> float64 hand-over");
+    int64_t n64 = 0;
+    const int64_t ccap = std::max<int32_t>(1, check_every / 5);
+    while (n64 < cap) {
+        const int64_t chunk = std::min<int64_t>(std::min<int64_t>(std::max<int64_t>(1, n64 / 2), ccap), cap - n64);
+        int64_t done = 0;
+        pdhg_status st = pdhg_iterate(hd, chunk, tol, (int32_t)chunk, 0, &done);
+        n64 += done;
+        *n64_out = n64;
+        if (st != PDHG_OK) return st;
+        if (hd->last_res[0] <= tol && hd->last_res[1] <= tol) break;
+    }
+    return PDHG_OK;
+}
+
+// Algorithm 3 with mixed steps: per step length a float32 and a float64 handle (the
+// float64 one applies K_d^{-1} in float32, as the float64 phase of pdhg_solve_mixed)
+static pdhg_status one_step_mixed(const pdhg_problem *p1, const pdhg_grid *g1, const pdhg_scheme *s1, bool bdf2,
+                                  int64_t nt, double tol, int64_t cap, int32_t check_every, char *ws, size_t region,
+                                  size_t b32, size_t b64, cudaStream_t stream, double *uo, int64_t *iters_per_step,
+                                  int64_t *iters_total) {
+    pdhg_scheme s32, s64;
+    size_t c32, c64;
+    pdhg_status st = mixed_schemes(p1, g1, s1, &s32, &s64, &c32, &c64);
+    if (st != PDHG_OK) return st;
+    pdhg_handle *hf[2] = {nullptr, nullptr}, *hd[2] = {nullptr, nullptr};
+    auto cleanup = [&] {
+        for (int k = 0; k < 2; ++k) { pdhg_destroy(hf[k]); pdhg_destroy(hd[k]); }
+    };
+    for (int k = 0; k < (bdf2 ? 2 : 1); ++k) {
+        pdhg_grid gk = *g1;
+        if (k == 1) gk.T = 2.0 * g1->T / 3.0;
+        char *r = ws + k * region;
+        st = pdhg_create(p1, &gk, &s32, r, b32, stream, &hf[k]);
+        if (st == PDHG_OK) st = create_impl(p1, &gk, &s64, r + align256(b32), b64, stream, &hd[k], true);
+        if (st != PDHG_OK) { cleanup(); return st; }
+        hf[k]->res_norm = 1;
+        hd[k]->res_norm = 1;
+        hd[k]->graphs = false;               // chunks of changing length: launch kernel by kernel
+    }
+    const int64_t S = hf[0]->G.S;
+    cudaError_t e = cudaMemcpyAsync(uo, hd[0]->ws + hd[0]->L.u0, S * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+    int64_t total = 0;
+    for (int64_t l = 0; l < nt && st == PDHG_OK; ++l) {
+        const int k = (bdf2 && l >= 1) ? 1 : 0;
+        const double *start = uo + l * S;
+        if (k == 1 && e == cudaSuccess) {
+            const unsigned gb = (unsigned)std::min<int64_t>((S + 255) / 256, 1024);
+            k_bdf2_start<double><<<gb, 256, 0, stream>>>(uo + l * S, uo + (l - 1) * S, uo + (l + 1) * S, S);
+            e = cudaGetLastError();
+            start = uo + (l + 1) * S;
+        }
+        if (e != cudaSuccess) { st = cuda_fail(e, "one-step restart"); break; }
+        int64_t n32 = 0, n64 = 0;
+        st = mixed_step(hf[k], hd[k], start, tol, cap, check_every, &n32, &n64);
+        total += n32 + n64;
+        if (iters_per_step) iters_per_step[l] = n32 + n64;
+        if (st != PDHG_OK) break;
+        e = cudaMemcpyAsync(uo + (l + 1) * S, hd[k]->ws + hd[k]->u_off + S * sizeof(double), S * sizeof(double),
+                            cudaMemcpyDeviceToDevice, stream);
+    }
+    if (st == PDHG_OK && e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (st == PDHG_OK && e != cudaSuccess) st = cuda_fail(e, "one-step copy");
+    if (iters_total) *iters_total = total;
+    cleanup();
+    return st;
+}
+
 extern "C" pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_grid *grid, const pdhg_scheme *scheme,
                                            double tol, int64_t max_iters_per_step, int32_t check_every,
                                            void *workspace, size_t bytes, void *stream, void *u_out,
@@ -1342,10 +1483,13 @@ extern "C" pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_
     if (iters_total) *iters_total = 0;
     const pdhg_scheme s1 = one_step_scheme(scheme);
     const bool bdf2 = scheme->time == PDHG_TIME_BDF2;
-    size_t b1 = 0;
-    st = pdhg_workspace_size(&p1, &g1, &s1, &b1);
+    size_t region = 0, b1 = 0, b64 = 0;
+    st = one_step_region(&p1, &g1, scheme, &region, &b1, &b64);
     if (st != PDHG_OK) return st;
-    if (bytes < (bdf2 ? 2 * align256(b1) : b1)) return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+    if (bytes < (bdf2 ? 2 : 1) * region) return fail(PDHG_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+    if (scheme->flags & PDHG_FLAG_MIXED_STEPS)
+        return one_step_mixed(&p1, &g1, &s1, bdf2, grid->nt, tol, max_iters_per_step, check_every, (char *)workspace,
+                              region, b1, b64, (cudaStream_t)stream, (double *)u_out, iters_per_step, iters_total);
     pdhg_handle *h1 = nullptr, *h2 = nullptr;
     st = pdhg_create(&p1, &g1, &s1, workspace, b1, stream, &h1);
     if (st != PDHG_OK) return st;
@@ -1353,7 +1497,7 @@ extern "C" pdhg_status pdhg_solve_one_step(const pdhg_problem *prob, const pdhg_
     if (bdf2) {
         pdhg_grid g2 = g1;
         g2.T = 2.0 * g1.T / 3.0;
-        st = pdhg_create(&p1, &g2, &s1, (char *)workspace + align256(b1), b1, stream, &h2);
+        st = pdhg_create(&p1, &g2, &s1, (char *)workspace + region, b1, stream, &h2);
         if (st != PDHG_OK) { pdhg_destroy(h1); return st; }
         h2->res_norm = 1;
     }
@@ -1556,7 +1700,20 @@ struct pdhg_batch {
     int32_t tiles[8];                    // row items per queue entry, by size class
     int32_t qorder;                      // 0: stage-major queue, 1: instance-major
     int nsm;
+    // CUDA graph of check_every iterations and the residual check kernels, replayed while
+    // the active set and the launch choice stay the same (dropped by batch_tables)
+    bool graphs = true;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    int32_t gchunk = 0;
+    int64_t glaunches = 0;
 };
+
+static void batch_graph_drop(pdhg_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->gchunk = 0;
+}
 
 namespace {
 
@@ -1646,6 +1803,8 @@ extern "C" pdhg_status pdhg_batch_workspace_size(int32_t count, const pdhg_probl
 
 extern "C" pdhg_status pdhg_batch_destroy(pdhg_batch *b) {
     if (!b) return PDHG_OK;
+    batch_graph_drop(b);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
     for (auto *h : b->h) pdhg_destroy(h);
     delete b;
     return PDHG_OK;
@@ -1683,6 +1842,7 @@ static pdhg_status batch_upload_insts(pdhg_batch *b, const BatchLayout &B) {
 
 // tables of the active instances, most cells first
 static pdhg_status batch_tables(pdhg_batch *b) {
+    batch_graph_drop(b);                         // its launches have the old grids baked in
     std::vector<BatchEntry> t[TAB_N];
     std::vector<int32_t> list;
     for (int32_t i : b->order) {
@@ -1856,14 +2016,18 @@ static cudaError_t batch_iteration(pdhg_batch *b) {
 }
 
 template <typename T>
-static pdhg_status batch_check(pdhg_batch *b, std::vector<double> &acc) {
+static cudaError_t batch_check_launch(pdhg_batch *b) {
     const BatchInst<T> *I = (const BatchInst<T> *)b->insts;
     cudaError_t e = launch_batch<T>(BATCH_CHECK, I, b->tab[TAB_CHECK], b->nblk[TAB_CHECK], 0, nullptr, b->partials,
                                     nullptr, b->stream);
     if (e == cudaSuccess)
         e = launch_batch<T>(BATCH_REDUCE, I, nullptr, b->nlist, 0, b->list, b->partials, b->out, b->stream);
     b->launches += 2;
-    if (e != cudaSuccess) return cuda_fail(e, "batched residual check");
+    return e;
+}
+
+// the six sums of every instance and the wait flag, after the check kernels
+static pdhg_status batch_read(pdhg_batch *b, std::vector<double> &acc) {
     acc.resize((size_t)b->count * 6);
     int err = 0;
     CK(cudaMemcpyAsync(acc.data(), b->out, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
@@ -1874,6 +2038,42 @@ static pdhg_status batch_check(pdhg_batch *b, std::vector<double> &acc) {
         return fail(PDHG_ERR_TIMEOUT, "a bounded wait of the persistent batch iteration gave up (the batch state is invalid)");
     }
     return PDHG_OK;
+}
+
+template <typename T>
+static pdhg_status batch_check(pdhg_batch *b, std::vector<double> &acc) {
+    cudaError_t e = batch_check_launch<T>(b);
+    if (e != cudaSuccess) return cuda_fail(e, "batched residual check");
+    return batch_read(b, acc);
+}
+
+// capture m iterations and the check kernels on a side stream (the same launches as
+// batch_iteration / batch_check_launch, so replays compute what they would)
+template <typename T>
+static cudaError_t batch_graph_build(pdhg_batch *b, int32_t m) {
+    batch_graph_drop(b);
+    cudaError_t e = cudaSuccess;
+    if (!b->gstream) e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaStream_t user = b->stream;
+    const int64_t l0 = b->launches;
+    b->stream = b->gstream;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int32_t i = 0; i < m && e == cudaSuccess; ++i) e = batch_iteration<T>(b);
+        if (e == cudaSuccess) e = batch_check_launch<T>(b);
+        cudaError_t e2 = cudaStreamEndCapture(b->gstream, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    b->stream = user;
+    b->glaunches = b->launches - l0;
+    b->launches = l0;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e == cudaSuccess) b->gchunk = m;
+    else batch_graph_drop(b);
+    return e;
 }
 
 // Res of one instance from its six sums (as read_res)
@@ -1899,14 +2099,37 @@ static pdhg_status batch_iterate_T(pdhg_batch *b, int64_t max_iters, double tol,
     std::vector<double> acc;
     pdhg_status st = PDHG_OK;
     for (int64_t n = 0; n < max_iters && b->nlist > 0;) {
-        cudaError_t e = batch_iteration<T>(b);
-        if (e != cudaSuccess) { st = cuda_fail(e, "batched iteration"); break; }
-        ++n;
-        for (int32_t i = 0; i < b->count; ++i)
-            if (b->active[i]) { ++it[i]; ++b->h[i]->iters; }
-        if (check_every > 0 && (n % check_every == 0 || n == max_iters)) {
-            st = batch_check<T>(b, acc);
+        // whole chunks of check_every iterations run as one graph replay (iterations and
+        // check kernels); the tail and graph-less runs launch kernel by kernel
+        const bool chunk = b->graphs && check_every > 0 && n % check_every == 0 && max_iters - n >= check_every;
+        if (chunk && b->gchunk != check_every && batch_graph_build<T>(b, check_every) != cudaSuccess) {
+            cudaGetLastError();                          // capture refused: launch kernel by kernel
+            b->graphs = false;
+        }
+        bool checked = false;
+        if (chunk && b->gchunk == check_every) {
+            cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+            if (e != cudaSuccess) { st = cuda_fail(e, "batch graph launch"); break; }
+            n += check_every;
+            b->launches += b->glaunches;
+            for (int32_t i = 0; i < b->count; ++i)
+                if (b->active[i]) { it[i] += check_every; b->h[i]->iters += check_every; }
+            st = batch_read(b, acc);
             if (st != PDHG_OK) break;
+            checked = true;
+        } else {
+            cudaError_t e = batch_iteration<T>(b);
+            if (e != cudaSuccess) { st = cuda_fail(e, "batched iteration"); break; }
+            ++n;
+            for (int32_t i = 0; i < b->count; ++i)
+                if (b->active[i]) { ++it[i]; ++b->h[i]->iters; }
+            if (check_every > 0 && (n % check_every == 0 || n == max_iters)) {
+                st = batch_check<T>(b, acc);
+                if (st != PDHG_OK) break;
+                checked = true;
+            }
+        }
+        if (checked) {
             bool changed = false;
             for (int32_t i = 0; i < b->count; ++i) {
                 if (!b->active[i]) continue;
@@ -1976,7 +2199,15 @@ extern "C" pdhg_status pdhg_batch_set_launch(pdhg_batch *b, int32_t persistent, 
 
 extern "C" pdhg_status pdhg_batch_set_wait_budget(pdhg_batch *b, uint64_t ns) {
     if (!b) return fail(PDHG_ERR_INVALID_ARG, "null batch");
+    batch_graph_drop(b);                         // the budget is a kernel argument
     b->wait_ns = ns;
+    return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_batch_set_graphs(pdhg_batch *b, int32_t enable) {
+    if (!b) return fail(PDHG_ERR_INVALID_ARG, "null batch");
+    batch_graph_drop(b);
+    b->graphs = enable != 0;
     return PDHG_OK;
 }
 

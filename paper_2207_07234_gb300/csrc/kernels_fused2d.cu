@@ -816,18 +816,21 @@ __global__ void __launch_bounds__(FTHREADS) k_rowsC(Params<float> P, const float
 
 // rows-C for nx = 1024 (M = 512 = 2 * 4^4), persistent with a TMA pipeline: a block
 // takes the tiles (4 rows of one slice) blockIdx.x, +gridDim.x, ..., and the spectrum
-// of the tile two ahead is loaded by TMA (three 3D boxes of 172 kx rows x 4 complex,
-// the layout of the spectrum kept: [kx][4]) into the stage buffer the current tile
-// has just released, so the 32-byte gathers are in flight during the transform.
+// of the tile two ahead is loaded by TMA (six 3D boxes of 176 kx rows x 2 complex: rows
+// y0, y0+1 into one half of the stage buffer and rows y0+2, y0+3 into the other, each
+// half [kx][2]) into the stage buffer the current tile has just released, so the
+// 32-byte gathers are in flight during the transform.  A thread reads its kx from both
+// halves as 16-byte words at consecutive addresses across the warp (no bank conflicts;
+// one [kx][4] array read 32 bytes per lane, two wavefronts per quarter warp).
 // The inverse split feeds the first (radix-2, span 1) stage directly in registers,
 // three radix-4 stages (spans 2, 8, 32) run in shared memory, and the last (span
 // 128) runs in registers, whose outputs -- complex positions i + 128 q, i.e.
 // x = 2 (i + 128 q) + {0,1} -- go straight into the dual step.  A stage wait that
 // gives up after wait_ns sets *err and the block returns (after a bounded wait for
 // its copies in flight).
-constexpr int RC_BOX = 172;                    // kx rows per TMA box: 3 boxes >= 513 rows
+constexpr int RC_BOX = 176;                    // kx rows per TMA box: 3 boxes >= 513 rows, 2816 bytes (128 | size)
 constexpr int RC_ROWS = 3 * RC_BOX;            // rows per stage buffer (rows >= nkx are zero-filled)
-constexpr uint32_t RC_TX = RC_ROWS * FH * 8;   // bytes per stage (whole boxes, fill included)
+constexpr uint32_t RC_TX = RC_ROWS * FH * 8;   // bytes per stage, both halves (whole boxes, fill included)
 constexpr uint64_t RC_DRAIN_NS = 1000000000ull; // budget of the waits for copies in flight on exit
 
 __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, const __grid_constant__ CUtensorMap tmap,
@@ -840,7 +843,7 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // TMA destinations 128-byte aligned (the launch adds 128 bytes of slack)
     unsigned char *sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    float2 *stg = reinterpret_cast<float2 *>(sm);           // [2][RC_ROWS][FH]
+    float2 *stg = reinterpret_cast<float2 *>(sm);           // [2 halves][2 stages][RC_ROWS][2]
     float2 *fa = stg + 2 * RC_ROWS * FH;                     // [FH][PN]
     float2 *fb = fa + FH * PN;                               // [FH][PN]
     uint64_t *bar = reinterpret_cast<uint64_t *>(fb + FH * PN);   // [2]
@@ -852,7 +855,10 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
         mbar_arrive_expect_tx(bar + buf, RC_TX);
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            tma_load_3d(stg + (buf * RC_ROWS + b * RC_BOX) * FH, &tmap, 2 * FH * yb, b * RC_BOX, l, bar + buf);
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf)
+                tma_load_3d(stg + ((2 * hf + buf) * RC_ROWS + b * RC_BOX) * 2, &tmap, 2 * FH * yb + 4 * hf,
+                            b * RC_BOX, l, bar + buf);
     };
     if (t == 0) {
         mbar_init(bar, 1);
@@ -891,13 +897,15 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_rowsC1024(Params<float> P, cons
             return;
         }
         // inverse split (Z_k = E_k + i O_k) for k = t and t + 256, then the radix-2 stage
-        // (span 1: outputs 2t, 2t+1) in registers; stage rows are [kx][4 rows]
+        // (span 1: outputs 2t, 2t+1) in registers; stage halves are [kx][rows 0, 1] and
+        // [kx][rows 2, 3]
         {
-            const float4 *S4 = reinterpret_cast<const float4 *>(stg + buf * RC_ROWS * FH);
-            const float4 xa[2] = {S4[2 * t], S4[2 * t + 1]};
-            const float4 xb[2] = {S4[2 * (M - t)], S4[2 * (M - t) + 1]};
-            const float4 xc[2] = {S4[2 * (t + 256)], S4[2 * (t + 256) + 1]};
-            const float4 xd[2] = {S4[2 * (256 - t)], S4[2 * (256 - t) + 1]};
+            const float4 *A4 = reinterpret_cast<const float4 *>(stg + buf * RC_ROWS * 2);
+            const float4 *B4 = reinterpret_cast<const float4 *>(stg + (2 + buf) * RC_ROWS * 2);
+            const float4 xa[2] = {A4[t], B4[t]};
+            const float4 xb[2] = {A4[M - t], B4[M - t]};
+            const float4 xc[2] = {A4[t + 256], B4[t + 256]};
+            const float4 xd[2] = {A4[256 - t], B4[256 - t]};
 #pragma unroll
             for (int rr = 0; rr < FH; ++rr) {
                 const int hh = rr >> 1;
@@ -1214,7 +1222,7 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
     }
     if (P.nx == 1024) {
         // the spectrum as a 3D float32 tensor [nt][nkx][2 ny] for rows-C's TMA boxes
-        // of 4 complex (8 floats) x RC_BOX kx rows x 1 slice
+        // of 2 complex (4 floats, 16 bytes) x RC_BOX kx rows x 1 slice
         typedef CUresult (*encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                       const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -1226,7 +1234,7 @@ cudaError_t fused2d_init(Fused2D *f, const Params<float> &P, void *ws, const flo
         if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         const cuuint64_t dims[3] = {(cuuint64_t)(2 * P.ny), (cuuint64_t)P.nkx, (cuuint64_t)P.nt};
         const cuuint64_t strides[2] = {(cuuint64_t)(2 * P.ny * 4), (cuuint64_t)P.nkx * (cuuint64_t)(2 * P.ny * 4)};
-        const cuuint32_t box[3] = {2 * FH, RC_BOX, 1}, estr[3] = {1, 1, 1};
+        const cuuint32_t box[3] = {4, RC_BOX, 1}, estr[3] = {1, 1, 1};
         CUresult r = ((encode_fn)fn)(&f->tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f->spec, dims, strides, box,
                                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

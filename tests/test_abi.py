@@ -141,3 +141,25 @@ def test_mixed_workspace_and_wait_budget_without_device_work(lib):
         else:
             assert extra == 0
     assert lib.pdhg_set_wait_budget(None, ctypes.c_uint64(0)) == -1
+
+
+def test_mixed_steps_flag_only_for_the_one_step_solve(lib):
+    """PDHG_FLAG_MIXED_STEPS is accepted by the one-step workspace query (a float32 and a
+    float64 handle per step length: more than the float64 one-step workspace) and
+    rejected, before any device work, by the entry points it does not apply to."""
+    from paper_2207_07234_gb300 import binding
+    p = W.burgers_2d(n=64, nt=8)
+    for time in ("be", "bdf2"):
+        q = p.replace(init="pinned", time=time)
+        prob, grid, scheme, keep = binding.structs(q, "fp64", "plain")
+        n64 = ctypes.c_size_t(0)
+        assert lib.pdhg_one_step_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                                ctypes.byref(n64)) == 0
+        scheme.flags |= binding.FLAG_MIXED_STEPS
+        nm = ctypes.c_size_t(0)
+        assert lib.pdhg_one_step_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                                ctypes.byref(nm)) == 0
+        assert nm.value > n64.value
+        nb = ctypes.c_size_t(0)
+        assert lib.pdhg_workspace_size(ctypes.byref(prob), ctypes.byref(grid), ctypes.byref(scheme),
+                                       ctypes.byref(nb)) == -1

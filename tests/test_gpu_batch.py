@@ -97,6 +97,27 @@ def test_batch_convergence_masks_match_lone_counts(B):
     assert len(set(its)) > 1
 
 
+@pytest.mark.parametrize("launch", LAUNCHES[:2], ids=["persistent", "per_stage"])
+def test_batch_graph_replay_equals_launch_by_launch(B, launch):
+    """Chunks of check_every iterations replayed from a CUDA graph (rebuilt whenever an
+    instance leaves the active set) give the same counts, states and fields, bit for bit,
+    as the same run launched kernel by kernel; 23 = 4 chunks of 5 plus a tail of 3."""
+    probs = mixed()
+    out = {}
+    for graphs in (True, False):
+        with B.Batch(probs, precision="fp64") as bt:
+            bt.set_launch(**launch)
+            bt.set_graphs(graphs)
+            bt.launches(reset=True)
+            its, st = bt.iterate(23, tol=0.3, check_every=5, relative=True)
+            out[graphs] = (list(its), list(st), bt.launches(),
+                           [{f: bt.instance(i).get_host(f) for f in FIELDS} for i in range(len(probs))])
+    assert out[True][:3] == out[False][:3]
+    for a, b in zip(out[True][3], out[False][3]):
+        for f in FIELDS:
+            assert np.array_equal(a[f], b[f]), f
+
+
 def test_batch_isolates_a_diverging_instance(B):
     good = W.advection_upwind_be(nx=128, nt=16, tau=(0.5, 0.1, 0.5, 0.99))
     bad = good.replace(tau_u=40.0, tau_phi=40.0, tau_u0=40.0)

@@ -285,3 +285,18 @@ def test_plain_2d_float64_residual_norms(B, p):
     ores = opdhg.residual_norms(p, o)
     assert np.allclose(res[:3], ores[:3], rtol=1e-10, atol=1e-300)
     assert abs(res[3] - ores[3]) <= 1e-9 * max(abs(ores[3]), 1e-300)
+
+
+def test_set_waits_for_the_current_stream(B):
+    """A handle on its own stream: set() converts the value on torch's current stream
+    (here queued behind a ~25 ms spin kernel) and the handle's copy waits for it."""
+    import torch
+    p = W.burgers_2d(n=256, nt=8)
+    side = torch.cuda.Stream()
+    with B.Solver(p, precision="fp32", path="fused", stream=side) as s:
+        u64 = torch.randn((p.nt + 1, p.ny, p.nx), dtype=torch.float64, device="cuda")
+        want = u64.float().cpu().numpy()
+        torch.cuda._sleep(50_000_000)
+        s.set("u", u64)
+        got = s.get_host("u")
+    assert np.array_equal(got, want)

@@ -88,6 +88,23 @@ def test_one_step_bdf2_reaches_scheme_solution(B, p):
     assert np.max(np.abs(u.cpu().numpy() - un)) <= 1e-9 * max(1.0, np.max(np.abs(un)))
 
 
+@pytest.mark.parametrize("p", [W.viscous_burgers(nx=64, nt=12, T=0.5, nu=0.02),
+                               W.viscous_burgers(nx=64, nt=12, T=0.5, nu=0.02).replace(time="bdf2"),
+                               W.burgers_2d(n=32, nt=6, cfl=0.5)],
+                         ids=lambda p: f"{p.name}_{p.time}")
+def test_one_step_mixed_reaches_scheme_solution(B, p):
+    """Mixed steps (float32 to its floor, then float64 from the widened state): with a
+    per-step tolerance far below float32's floor the float64 phase carries every step to
+    the scheme's solution (Newton, 1e-9)."""
+    t = float(np.sqrt(0.5 / opdhg.power_estimate(p.replace(nt=1, T=p.ht, time="be"), iters=60)))
+    p = p.replace(init="pinned", tau_u=t, tau_u0=t, tau_phi=t)
+    um, cm = B.solve_one_step(p, tol=1e-11, max_iters_per_step=20000, check_every=10, precision="mixed")
+    assert um.dtype.is_floating_point and um.element_size() == 8
+    assert max(cm) < 20000
+    un = newton.solve(p)
+    assert np.max(np.abs(um.cpu().numpy() - un)) <= 1e-9 * max(1.0, np.max(np.abs(un)))
+
+
 def test_refine_traffic_counts_and_solution(B):
     """Table 3's mesh-refinement row on the GPU (float64): 1000 + 1000 iterations on
     256 x 8 and 256 x 16, then to Res <= 1e-3 on 256 x 32; counts and the final

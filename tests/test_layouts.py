@@ -214,3 +214,56 @@ def test_bluestein_swizzle(lg, n_points):
                 swz = max(swz, multiplicity([blu_swz(p, lg) for p in half]))
     assert swz <= 2
     assert plain >= 8                                                      # what the swizzle removes
+
+
+# --- rows-C (nx = 1024) TMA stage buffer ------------------------------------------
+
+RC_BOX, M, FH = 176, 512, 4
+
+
+def wavefronts(byte_addrs, width=16):
+    """Shared-memory wavefronts of one 128-bit warp access: served a quarter warp (8
+    lanes) at a time; a phase takes as many wavefronts as the busiest of the 32 four-byte
+    banks has distinct words."""
+    n = 0
+    for q in range(4):
+        banks = {}
+        for a in byte_addrs[8 * q:8 * q + 8]:
+            for w in range(a // 4, (a + width) // 4):
+                banks.setdefault(w % 32, set()).add(w)
+        n += max(len(v) for v in banks.values())
+    return n
+
+
+def test_rows_c_stage_halves():
+    """The six TMA boxes of a rows-C stage (2 complex x 176 kx rows each: rows y0, y0+1
+    into half 0, rows y0+2, y0+3 into half 1) start on 128-byte boundaries, their x
+    coordinates (floats) are 16-byte multiples, they tile each half's [kx][2] rows 0..527
+    with no overlap, and the split's reads of kx = t, M - t, t + 256, 256 - t from both
+    halves take 4 wavefronts per warp access (the single [kx][4] array took 8)."""
+    rows = 3 * RC_BOX
+    assert rows >= M + 1
+    cover = {}
+    for hf in range(2):
+        for buf in range(2):
+            for b in range(3):
+                start = ((2 * hf + buf) * rows + b * RC_BOX) * 2 * 8      # bytes: float2 index * 8
+                assert start % 128 == 0 and (RC_BOX * 16) % 128 == 0
+                for yb in (0, 1, 255):
+                    x = 2 * FH * yb + 4 * hf
+                    assert (x * 4) % 16 == 0
+                for r in range(RC_BOX):
+                    key = (hf, buf, b * RC_BOX + r)
+                    assert key not in cover
+                    cover[key] = start + 16 * r
+    assert len(cover) == 2 * 2 * rows
+    assert max(cover.values()) + 16 <= 2 * rows * FH * 8            # inside the staging area
+    for w in range(8):
+        lanes = [32 * w + j for j in range(32)]
+        for kx in (lambda t: t, lambda t: M - t, lambda t: t + 256, lambda t: 256 - t):
+            for hf in range(2):
+                addrs = [((2 * hf) * rows + kx(t)) * 16 for t in lanes]
+                assert all(0 <= kx(t) <= M for t in lanes)
+                assert wavefronts(addrs) == 4
+            old = [kx(t) * 32 for t in lanes]                        # [kx][4]: 32 bytes per lane
+            assert wavefronts(old) == 8 and wavefronts([a + 16 for a in old]) == 8
