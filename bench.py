@@ -451,6 +451,10 @@ def run_ours(args):
     if not args.no_nonlinear and rank == 0 and args.workload == "burgers2d" and args.precision == "fp32":
         nonlin = nonlinear_leg(binding, device=dev, stream=stream)
 
+    grad = None
+    if not args.no_gradient and rank == 0:
+        grad = gradient_leg(binding, device=dev, stream=stream)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -468,6 +472,8 @@ def run_ours(args):
             line["batch"] = batch
         if nonlin:
             line["nonlinear"] = nonlin
+        if grad:
+            line["gradient"] = grad
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -499,22 +505,70 @@ def batch_leg(binding, steps=10, warmup=3, device=None, stream=None):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         launches = bt.launches() / steps
-        # the same iterations as one CUDA-graph replay with the residual check at its end
-        # (check_every = steps; the first call captures the graph and is not timed)
-        bt.iterate(steps, tol=0.0, check_every=steps)
-        torch.cuda.synchronize()
-        e0.record(s)
-        bt.iterate(steps, tol=0.0, check_every=steps)
-        e1.record(s)
-        torch.cuda.synchronize()
-        ms_graph = e0.elapsed_time(e1) / steps
+    # CUDA-graph replay against launch by launch, with a residual check every `steps`
+    # iterations (instances whose residual stops being finite leave at a check, so both
+    # runs take the same fresh batch through the same sequence: an untimed chunk, which
+    # also captures the graph, then a timed one)
+    graph = {"check_every": steps}
+    for use_graph in (False, True):
+        with binding.Batch(probs, precision="fp32", device=device, stream=s) as bt:
+            bt.set_graphs(use_graph)
+            bt.iterate(steps, tol=0.0, check_every=steps)
+            _, st = bt.iterate(0)
+            torch.cuda.synchronize()
+            e0.record(s)
+            bt.iterate(steps, tol=0.0, check_every=steps)
+            e1.record(s)
+            torch.cuda.synchronize()
+            graph["graph_ms_per_iter" if use_graph else "launch_by_launch_ms_per_iter"] = e0.elapsed_time(e1) / steps
+            graph["active_instances"] = int(np.sum(np.asarray(st) == 0))
     peak, src = measured_peaks()
     gbs = nbytes / (ms * 1e-3) / 1e9
     return {"workload": f"{len(probs)} mixed 1D instances, seed 20723", "instances": len(probs),
             "cells_per_iter": cells, "steps": steps, "ms_per_iter": ms, "value": cells / (ms * 1e-3),
             "unit": UNIT, "launches_per_iter": launches, "algorithmic_bytes_per_iter": nbytes,
             "achieved_gbs": gbs, "frac": gbs / peak, "peak_source": src,
-            "graph": {"ms_per_iter_incl_one_check": ms_graph, "check_every": steps}}
+            "graph": graph}
+
+
+def gradient_leg(binding, iters=200, device=None, stream=None):
+    """Cost per iteration of the forward and the adjoint solve of the gradient at the
+    gradient workload's own shape: viscous Burgers 2048 x 1024, BDF2, nu = 1e-3, float32,
+    plain path.  Algorithm 1 does not converge on that configuration, so fixed iteration
+    counts are timed (small steps tau = 0.05 keep the iterates finite over them; the cost
+    of an iteration does not depend on the steps): the forward iterations alone, then
+    pdhg_solve_gradient with (n, n) and (2n, 2n) forward/adjoint iterations, whose
+    difference is n forward plus n adjoint iterations."""
+    import torch
+    p = W.viscous_burgers().replace(tau_u=0.05, tau_phi=0.05, tau_u0=0.05)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = {"workload": p.name + f"_bdf2_nu{p.nu:g}", "cells_per_iter": p.cells_per_iter, "precision": "fp32",
+           "iterations": iters}
+    try:
+        with binding.Solver(p, precision="fp32", path="plain", device=device, stream=s) as sv:
+            sv.iterate(10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sv.iterate(iters)
+            torch.cuda.synchronize()
+            fwd = (time.perf_counter() - t0) / iters
+        target = np.zeros(p.slice_shape)
+        tg = []
+        for n in (iters, 2 * iters):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            binding.solve_gradient(p, target, tol=0.0, max_iters=n, adj_tol=0.0, adj_max_iters=n, check_every=n,
+                                   precision="fp32", device=device, stream=s)
+            torch.cuda.synchronize()
+            tg.append(time.perf_counter() - t0)
+        both = (tg[1] - tg[0]) / iters
+        adj = both - fwd
+        out.update({"forward_ms_per_iter": fwd * 1e3, "adjoint_ms_per_iter": adj * 1e3,
+                    "forward_value": p.cells_per_iter / fwd, "adjoint_value": p.cells_per_iter / adj,
+                    "unit": UNIT, "gradient_call_seconds": tg})
+    except binding.PdhgError as err:
+        out["status"] = f"stopped: {err}"
+    return out
 
 
 def nonlinear_leg(binding, tol=1e-6, device=None, stream=None, alg1_iters=1000):
@@ -655,6 +709,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch leg")
+    ap.add_argument("--no-gradient", action="store_true", help="skip the gradient-workload timing leg")
     ap.add_argument("--no-nonlinear", action="store_true",
                     help="skip the converged solve of the workload itself (Algorithm 3, float32 and float64)")
     ap.add_argument("--clock-log", default=None, help="also write the raw nvidia-smi clock samples to this CSV")

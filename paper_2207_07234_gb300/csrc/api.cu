@@ -2037,6 +2037,15 @@ static pdhg_status batch_read(pdhg_batch *b, std::vector<double> &acc) {
         CK(cudaMemset(b->err, 0, sizeof(int)));
         return fail(PDHG_ERR_TIMEOUT, "a bounded wait of the persistent batch iteration gave up (the batch state is invalid)");
     }
+#ifdef PDHG_DEBUG
+    // debug builds: the first out-of-range site recorded by any instance's kernels
+    for (int32_t i = 0; i < b->count; ++i) {
+        int bad = 0;
+        CK(cudaMemcpy(&bad, b->h[i]->ws + b->h[i]->L.dbg, sizeof(int), cudaMemcpyDeviceToHost));
+        if (bad) return fail(PDHG_ERR_BOUNDS, "debug bounds check: instance " + std::to_string(i) + ", site " +
+                                                  std::to_string(bad));
+    }
+#endif
     return PDHG_OK;
 }
 

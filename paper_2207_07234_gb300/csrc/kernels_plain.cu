@@ -40,7 +40,7 @@ template <typename T>
 __device__ __forceinline__ void primal_block(const Params<T> &P, T *__restrict__ u, const T *__restrict__ phit,
                                              T *__restrict__ lam, T *__restrict__ lamt, const T *__restrict__ u0,
                                              int bx, int l) {
-    const int64_t S = P.S;
+    const int64_t S = P.S, nU = (int64_t)(P.nt + 1) * S;
     if (is_dg(P.space)) {
         const int N = P.nx, nm = P.lines;
         const int k = bx * blockDim.x + threadIdx.x;
@@ -59,12 +59,13 @@ __device__ __forceinline__ void primal_block(const Params<T> &P, T *__restrict__
                 pl[m] = ps[m * N + km]; pc[m] = ps[m * N + k]; pr[m] = ps[m * N + kp];
             }
             dgx_DT(P, c, pl, pc, pr, d);
-            for (int m = 0; m < nm; ++m) ul[m * N + k] = c[m] - P.tau_u * (g[m] + d[m]);
+            for (int m = 0; m < nm; ++m)
+                u[dbg_idx(P, (int64_t)l * S + m * N + k, nU, 101)] = c[m] - P.tau_u * (g[m] + d[m]);
         } else if (P.init == INIT_LAMBDA) {
             for (int m = 0; m < nm; ++m) {
-                int64_t i = m * N + k;
+                const int64_t i = dbg_idx(P, (int64_t)m * N + k, S, 102);
                 T un = c[m] - P.tau_u0 * (P.ht * g[m] + lamt[i]);
-                ul[i] = un;
+                u[i] = un;
                 T r0 = un - u0[i];
                 T ln = lam[i] + P.tau_lambda * r0;
                 lam[i] = ln;
@@ -87,10 +88,10 @@ __device__ __forceinline__ void primal_block(const Params<T> &P, T *__restrict__
             const T k = T(2) * P.tau_u * P.inv_ht;
             un = (un + k * P.tshift[i]) / (T(1) + k);
         }
-        ul[i] = un;
+        u[dbg_idx(P, (int64_t)l * S + i, nU, 103)] = un;
     } else if (P.init == INIT_LAMBDA) {
         T un = c - P.tau_u0 * (P.ht * g + lamt[i]);
-        ul[i] = un;
+        u[dbg_idx(P, i, nU, 104)] = un;
         T r0 = un - u0[i];
         T ln = lam[i] + P.tau_lambda * r0;
         lam[i] = ln;
@@ -149,7 +150,7 @@ __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T 
     C *z = reinterpret_cast<C *>(smem_raw);      // line: row y (FD); 0 for DG
     const int N = P.nx, M = N >> 1;
     const int lg = P.log2m;
-    const int64_t S = P.S;
+    const int64_t S = P.S, nX = (int64_t)P.nt * P.lines * P.nkx;     // spectrum extent (complex)
     T *zr = reinterpret_cast<T *>(z);
     if (is_dg(P.space)) {
         const int nm = P.lines;
@@ -168,7 +169,7 @@ __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T 
         fft_radix2(z, lg, nm, M, 1, twx, 2, false);
         for (int t = threadIdx.x; t < nm * (M + 1); t += blockDim.x) {
             int m = t / (M + 1), k = t - m * (M + 1);
-            spec[((int64_t)l * nm + m) * P.nkx + k] = rfft_split(z + m * M, M, k, twx);
+            spec[dbg_idx(P, ((int64_t)l * nm + m) * P.nkx + k, nX, 111)] = rfft_split(z + m * M, M, k, twx);
         }
         return;
     }
@@ -201,16 +202,15 @@ __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T 
         __syncthreads();
         bluestein_core(P, z);
         // z_k = L conj((a * b)_k): W_k = conj(c_k z_k) / L
-        C *out = spec + ((int64_t)l * P.lines + line) * P.nkx;
-        C *out2 = spec + ((int64_t)(l + 1) * P.lines + line) * P.nkx;
+        const int64_t o1 = ((int64_t)l * P.lines + line) * P.nkx, o2 = ((int64_t)(l + 1) * P.lines + line) * P.nkx;
         const T h = T(0.5) / T(L);
         for (int k = threadIdx.x; k < P.nkx; k += blockDim.x) {
             const int km = k == 0 ? 0 : N - k;
             const C wk = cconj(cmul(cc[k], z[blu_swz(k, lgL)])), wm = cmul(cc[km], z[blu_swz(km, lgL)]);     // W_k L, conj(W_{N-k}) L
-            out[k] = cscale(cadd(wk, wm), h);
+            spec[dbg_idx(P, o1 + k, nX, 112)] = cscale(cadd(wk, wm), h);
             if (two) {
                 const C d = csub(wk, wm);                                      // (W_k - conj W_{N-k}) L
-                out2[k] = cscale(mk<C, T>(d.y, -d.x), h);                     // / (2i)
+                spec[dbg_idx(P, o2 + k, nX, 113)] = cscale(mk<C, T>(d.y, -d.x), h);   // / (2i)
             }
         }
         return;
@@ -222,8 +222,8 @@ __device__ __forceinline__ void residual_rfft_block(const Params<T> &P, const T 
     }
     __syncthreads();
     fft_radix2(z, lg, 1, M, 1, twx, 2, false);
-    C *out = spec + ((int64_t)l * P.lines + line) * P.nkx;
-    for (int k = threadIdx.x; k <= M; k += blockDim.x) out[k] = rfft_split(z, M, k, twx);
+    const int64_t o = ((int64_t)l * P.lines + line) * P.nkx;
+    for (int k = threadIdx.x; k <= M; k += blockDim.x) spec[dbg_idx(P, o + k, nX, 114)] = rfft_split(z, M, k, twx);
 }
 
 template <typename T>
@@ -254,9 +254,10 @@ __global__ void __launch_bounds__(256) k_fft_y(Params<T> P, typename Cplx<T>::ty
     }
     __syncthreads();
     fft_radix2(z, lg, cb, 1, cb, twy, 1, inverse != 0);
+    const int64_t off = (int64_t)l * ny * P.nkx + k0, nX = (int64_t)P.nt * ny * P.nkx;
     for (int t = threadIdx.x; t < ny * cb; t += blockDim.x) {
         int y = t / cb, c = t - y * cb;
-        base[(int64_t)y * P.nkx + c] = z[y * cb + c];
+        spec[dbg_idx(P, off + (int64_t)y * P.nkx + c, nX, 121)] = z[y * cb + c];
     }
 }
 
@@ -362,7 +363,7 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
             for (int i = 0; i < nm; ++i) {
                 if (l > 0) w[i] = cadd(w[i], cscale(yv[i], rho_of(th[i], emt[i], q[i], l - 1)));
                 yv[i] = w[i];
-                spec[l * ls + i * P.nkx + k] = w[i];
+                spec[dbg_idx(P, l * ls + i * P.nkx + k, nt * ls, 131)] = w[i];
             }
         }
         C zv[3];
@@ -378,7 +379,7 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
                 for (int i = 0; i < nm; ++i) acc = cadd(acc, cmul(v[m * 3 + i], zv[i]));
                 zz[m] = acc;
             }
-            for (int m = 0; m < nm; ++m) spec[l * ls + m * P.nkx + k] = zz[m];
+            for (int m = 0; m < nm; ++m) spec[dbg_idx(P, l * ls + m * P.nkx + k, nt * ls, 132)] = zz[m];
         }
         return;
     }
@@ -417,19 +418,45 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
     }
     const T th = theta_tab[col];
     const T emt = expT(-th), q = emt * emt;
-    C *s = spec + col;
-    C y = s[0];
-    for (int l = 1; l < nt; ++l) {
-        C r = s[(int64_t)l * modes];
-        y = cadd(r, cscale(y, rho_of(th, emt, q, l - 1)));
-        s[(int64_t)l * modes] = y;
+    const int64_t nX = (int64_t)nt * modes;
+    // the right-hand sides do not depend on the recurrence: each sweep loads TU slices
+    // ahead into registers, so a thread has TU loads in flight instead of one (the sweeps
+    // of a few modes per multiprocessor -- 1D problems -- are bound by that latency)
+    constexpr int TU = 8;
+    C y = spec[dbg_idx(P, col, nX, 133)];
+    int l = 1;
+    for (; l + TU <= nt; l += TU) {
+        C r[TU];
+#pragma unroll
+        for (int j = 0; j < TU; ++j) r[j] = spec[dbg_idx(P, col + (int64_t)(l + j) * modes, nX, 133)];
+#pragma unroll
+        for (int j = 0; j < TU; ++j) {
+            y = cadd(r[j], cscale(y, rho_of(th, emt, q, l + j - 1)));
+            spec[dbg_idx(P, col + (int64_t)(l + j) * modes, nX, 133)] = y;
+        }
+    }
+    for (; l < nt; ++l) {
+        const int64_t i = dbg_idx(P, col + (int64_t)l * modes, nX, 133);
+        y = cadd(spec[i], cscale(y, rho_of(th, emt, q, l - 1)));
+        spec[i] = y;
     }
     C z = cscale(y, rho_of(th, emt, q, nt - 1));
-    s[(int64_t)(nt - 1) * modes] = z;
-    for (int l = nt - 2; l >= 0; --l) {
-        C yl = s[(int64_t)l * modes];
-        z = cscale(cadd(yl, z), rho_of(th, emt, q, l));
-        s[(int64_t)l * modes] = z;
+    spec[dbg_idx(P, col + (int64_t)(nt - 1) * modes, nX, 134)] = z;
+    l = nt - 2;
+    for (; l - TU + 1 >= 0; l -= TU) {
+        C r[TU];
+#pragma unroll
+        for (int j = 0; j < TU; ++j) r[j] = spec[dbg_idx(P, col + (int64_t)(l - j) * modes, nX, 134)];
+#pragma unroll
+        for (int j = 0; j < TU; ++j) {
+            z = cscale(cadd(r[j], z), rho_of(th, emt, q, l - j));
+            spec[dbg_idx(P, col + (int64_t)(l - j) * modes, nX, 134)] = z;
+        }
+    }
+    for (; l >= 0; --l) {
+        const int64_t i = dbg_idx(P, col + (int64_t)l * modes, nX, 134);
+        z = cscale(cadd(spec[i], z), rho_of(th, emt, q, l));
+        spec[i] = z;
     }
 }
 
@@ -481,16 +508,17 @@ __device__ __forceinline__ void dual_irfft_block(const Params<T> &P, const typen
         bluestein_core(P, z);
         const T sc = P.blu_scale / (T(L) * T(N));
         const int64_t off = (int64_t)l * P.S + (int64_t)line0 * N;
+        const int64_t nF = (int64_t)P.nt * P.S;
         for (int x = threadIdx.x; x < N; x += blockDim.x) {
             const C w = cmul(cc[x], z[blu_swz(x, lgL)]);
             const T dz = sc * w.x;
-            const int64_t i = off + x;
+            const int64_t i = dbg_idx(P, off + x, nF, 141);
             const T pn = phi[i] + dz;
             phi[i] = pn;
             phit[i] = pn + dz;
             if (two) {
                 const T dz2 = sc * w.y;
-                const int64_t i2 = i + P.S;
+                const int64_t i2 = dbg_idx(P, off + x + P.S, nF, 142);
                 const T pn2 = phi[i2] + dz2;
                 phi[i2] = pn2;
                 phit[i2] = pn2 + dz2;
@@ -510,7 +538,7 @@ __device__ __forceinline__ void dual_irfft_block(const Params<T> &P, const typen
     for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
         int m = t / N, x = t - m * N;
         T dz = P.dual_scale * zr[m * N + x];
-        int64_t i = off + (int64_t)m * N + x;
+        const int64_t i = dbg_idx(P, off + (int64_t)m * N + x, (int64_t)P.nt * P.S, 143);
         T pn = phi[i] + dz;
         phi[i] = pn;
         phit[i] = pn + dz;

@@ -1,10 +1,12 @@
 """Debug build (-DPDHG_DEBUG): the kernels of the fused 2D iteration and the 2D residual
-check verify every global index against the extent of its buffer; an index out of range is
+check verify every global index, and the plain path's per-stage kernels (alone and in
+batches) every global store, against the extent of its buffer; an index out of range is
 recorded (and the access redirected to element 0), and the next residual check returns
 PDHG_ERR_BOUNDS.  The parity cases of the fused path (ragged t-chunks, BDF2 across chunk
 boundaries, both initial rows, nx != ny, the TMA rows-C at nx = 1024, nx = 2048) and their
-float64 plain runs go through that build with checks after every second iteration and
-find no out-of-range index."""
+float64 plain runs, and 1D plain cases (Bluestein lengths, DG P2 / P1, BE and BDF2) alone
+and as a batch, go through that build with checks after every second iteration and find
+no out-of-range index."""
 import os
 import subprocess
 import sys
@@ -30,7 +32,23 @@ for q in cases:
         with B.Solver(q, precision=prec, path=path) as s:
             s.iterate(4, tol=0.0, check_every=2)
             s.residual()
-print("debug build: no out-of-range index in", len(cases), "cases")
+# the plain path's 1D kernels (power-of-two and Bluestein x-lengths, DG P2 and P1, BE and
+# BDF2) alone and as one batch, both precisions
+plain = [W.advection_upwind_be(nx=256, nt=9), W.advection_upwind_be(nx=300, nt=7).replace(time="bdf2"),
+         W.viscous_burgers(nx=333, nt=6, T=0.5, nu=0.01), W.heat_table1(128, 11),
+         W.burgers_dg_p2(ncell=64, nt=5, T=0.5, time="be").replace(c=0.5, tau_u=0.05, tau_u0=0.05, tau_phi=0.05),
+         W.traffic_dg_p1(ncell=32, nt=7, time="bdf2")]
+for q in plain:
+    for prec in ("fp32", "fp64"):
+        with B.Solver(q, precision=prec, path="plain") as s:
+            s.iterate(4, tol=0.0, check_every=2)
+            s.residual()
+for prec in ("fp32", "fp64"):
+    with B.Batch(plain, precision=prec) as bt:
+        bt.iterate(4, tol=0.0, check_every=2)
+        for i in range(len(plain)):
+            bt.instance(i).residual()
+print("debug build: no out-of-range index in", len(cases) + len(plain), "cases")
 '''
 
 
