@@ -456,9 +456,13 @@ static size_t smem_rowsR1024() { return (size_t)2 * FH * R8<9>::PN * 8; }
 // ---------------------------------------------------------------------------
 // The pivots only shape the preconditioner (they change the iterates, never the
 // fixed point R(u*) = 0), so the fast exponential and division intrinsics serve:
-// their relative errors (~1e-6) are far below what the iteration notices.
+// their relative errors (~1e-6) are far below what the iteration notices.  Past
+// (2l+1) theta = 17, w < 2^-24 and 1 + w, 1 + q w round to 1: the pivot is e^{-theta}
+// itself, with no exponential and no division (most steps of most modes).
 __device__ __forceinline__ float rho_f(float th, float emt, float q, int l) {
-    const float w = __expf(-(float)(2 * l + 1) * th);
+    const float x = (float)(2 * l + 1) * th;
+    if (x > 17.f) return emt;
+    const float w = __expf(-x);
     return __fdividef(emt * (1.f + w), 1.f + q * w);
 }
 

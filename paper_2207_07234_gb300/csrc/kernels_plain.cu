@@ -274,9 +274,18 @@ __global__ void __launch_bounds__(256) k_fft_y(Params<T> P, typename Cplx<T>::ty
 __device__ __forceinline__ float expT(float x) { return expf(x); }
 __device__ __forceinline__ double expT(double x) { return exp(x); }
 
+// Past x = (2l+1) theta = 17 (float) or 37 (double), w = e^{-x} is below half an ulp
+// of 1, so 1 + w and 1 + q w round to 1 and the pivot is exactly e^{-theta}: the same
+// value with no exponential and no division (most steps of most modes).
+template <typename T> struct RhoCut;
+template <> struct RhoCut<float> { static constexpr float x = 17.f; };
+template <> struct RhoCut<double> { static constexpr double x = 37.0; };
+
 template <typename T>
 __device__ __forceinline__ T rho_of(T theta, T emt, T q, int l) {
-    T w = expT(-(T)(2 * l + 1) * theta);
+    const T x = (T)(2 * l + 1) * theta;
+    if (x > RhoCut<T>::x) return emt;
+    T w = expT(-x);
     return emt * (T(1) + w) / (T(1) + q * w);
 }
 
@@ -421,8 +430,8 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
     const int64_t nX = (int64_t)nt * modes;
     // the right-hand sides do not depend on the recurrence: each sweep loads TU slices
     // ahead into registers, so a thread has TU loads in flight instead of one (the sweeps
-    // of a few modes per multiprocessor -- 1D problems -- are bound by that latency)
-    constexpr int TU = 8;
+    // of 1D problems, a few modes per multiprocessor, are bound by that latency)
+    constexpr int TU = 16;
     C y = spec[dbg_idx(P, col, nX, 133)];
     int l = 1;
     for (; l + TU <= nt; l += TU) {

@@ -300,7 +300,11 @@ def batch_instances(count: int = 256, seed: int = 20723, nx_range=(256, 4096), n
       log2 nx uniform over the range);
     * nt uniform in nt_range; CFL = c h_t / h_x uniform in cfl_range; BE or BDF2;
     * u0 = sum_{k=1..8} (0.5/k) N(0,1) sin(k x + theta_k) on [0, 2 pi] (plus 0.5 for
-      Burgers), c = a = max |f'(u0)| (1 for advection)."""
+      Burgers), c = a = max |f'(u0)| (1 for advection);
+    * step sizes `tau` for BE; for BDF2 tau_u = tau_phi = sqrt(0.5 / (2.5 + nt / 4)) (tau_u0,
+      tau_lambda as for BE): with the T_t preconditioner the power estimate of the
+      preconditioned operator is about 2 for BE and 2.5 + nt/4 for BDF2 (oracle.pdhg.
+      power_estimate, CFL 1..8), so tau_u tau_phi nu_max stays at or below 1/2 for both."""
     rng = np.random.default_rng(seed)
     lo, hi = int(np.log2(nx_range[0])), int(np.log2(nx_range[1]))
     out = []
@@ -310,6 +314,10 @@ def batch_instances(count: int = 256, seed: int = 20723, nx_range=(256, 4096), n
         nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
         cfl = float(rng.uniform(*cfl_range))
         time = "bdf2" if rng.random() < 0.5 else "be"
+        ts = tau
+        if time == "bdf2":
+            tb = float(np.sqrt(0.5 / (2.5 + nt / 4.0)))
+            ts = (tb, tau[1], tb, tau[3])
         useed = int(rng.integers(0, 2 ** 31 - 1))
         lx = 2.0 * np.pi
         u0 = random_fourier_1d(nx, lx, useed)
@@ -323,6 +331,6 @@ def batch_instances(count: int = 256, seed: int = 20723, nx_range=(256, 4096), n
         T = nt * cfl * hx / c
         out.append(Problem(name=f"batch{i}_{'burgers' if burgers else 'advection'}_{nx}x{nt}", dims=1,
                            space=space, time=time, nx=nx, lx=lx, T=T, nt=nt, alpha=alpha, beta=beta,
-                           lf_a=c, c=c, tau_u=tau[0], tau_u0=tau[1], tau_phi=tau[2],
-                           tau_lambda=tau[3], u0=u0))
+                           lf_a=c, c=c, tau_u=ts[0], tau_u0=ts[1], tau_phi=ts[2],
+                           tau_lambda=ts[3], u0=u0))
     return out

@@ -136,3 +136,18 @@ def test_exact_kd_inverse_equals_dense_solve(p):
     z = precond.kd_inverse(p, r)
     zd = np.linalg.solve(precond.dense_Kd(p), r.ravel()).reshape(r.shape)
     assert np.max(np.abs(z - zd)) <= 1e-12 * np.max(np.abs(zd))
+
+
+def test_bdf2_preconditioned_norm_with_tt_and_exact_operator():
+    """What the T_t reading costs BDF2: the largest eigenvalue of the preconditioned
+    operator (power estimate) grows as 2.5 + nt/4 with T_t, while the exact time operator
+    keeps it at the BE value (about 2) for every nt -- the reason the exact operator cuts
+    BDF2 iteration counts and the T_t step sizes must shrink as nt^{-1/2}."""
+    from oracle import pdhg as opdhg
+    for nt in (16, 32, 64):
+        p = W.advection_upwind_be(nx=32, nt=nt).replace(time="bdf2", T=nt * 2 * (2 * np.pi / 32))
+        tt = opdhg.power_estimate(p, iters=40)
+        ex = opdhg.power_estimate(p.replace(tprec="exact"), iters=40)
+        be = opdhg.power_estimate(p.replace(time="be"), iters=40)
+        assert abs(tt - (2.5 + nt / 4)) <= 0.02 * (2.5 + nt / 4), (nt, tt)
+        assert abs(ex - be) <= 0.05 * be and be < 2.0, (nt, ex, be)
