@@ -50,7 +50,7 @@ void pdhg::set_last_error(const std::string &msg) { g_last_error = msg; }
 namespace {
 
 struct Layout {
-    size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, tfac, partials, scal, dbg, fused;
+    size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, tfac, rtab, partials, scal, dbg, fused;
     size_t blu_tw, blu_c, blu_b;
     size_t twx32, twy32, theta32;    // float32 preconditioner tables (Geom::pre32)
     size_t total;
@@ -70,6 +70,7 @@ struct Geom {
     bool pre32;      // float64 state with the preconditioner applied in float32 (plain FD path)
     bool exact_t;    // time part of K_d: the scheme's own h_t^2 D_t D_t^T (PDHG_FLAG_EXACT_TIME_PRECOND)
     bool t64;        // float32 fields, t-solve recurrence in float64 (PDHG_FLAG_T_SOLVE_FP64)
+    bool rtab;       // t-solve pivots from a [nt][modes] table (1D finite differences, few modes)
 };
 
 // Checks of the grid, the scheme and the coefficients (everything but u0 and the
@@ -144,6 +145,11 @@ pdhg_status validate_shape(const pdhg_problem *p, const pdhg_grid *g, const pdhg
         G->fused = ok;
     }
     G->pre32 = pre32 && s->precision == PDHG_FP64 && !G->fused && !dg && G->blu_log2L == 0 && !G->exact_t;
+    // 1D: a few thousand modes, each swept by one thread, so the sweeps run at the latency
+    // of their per-step pivot evaluation; a table of the same values (computed once at
+    // create, at most 2^23 entries) turns each pivot into one load
+    G->rtab = g->dims == 1 && !dg && !G->fused && !G->exact_t && !G->t64 && !G->pre32 &&
+              (double)G->modes * (double)G->nt <= (double)(int64_t(1) << 23);
     return PDHG_OK;
 }
 
@@ -176,6 +182,7 @@ Layout layout_of(const Geom &G) {
     L.theta = take(G.modes * e);
     L.V = take(G.space >= PDHG_SPACE_DG_P2_LF ? G.nkx * 9 * 2 * e : 0);
     L.tfac = take(G.exact_t ? 3 * G.nt * G.modes * e : 0);
+    L.rtab = take(G.rtab ? G.nt * G.modes * e : 0);
     int64_t units = G.space >= PDHG_SPACE_DG_P2_LF ? G.nx : G.S;
     int64_t nblk = std::min<int64_t>((units + 255) / 256, 32) * (G.nt + 1);    // k_check grid
     L.partials = take(nblk * 6 * sizeof(double));
@@ -755,6 +762,10 @@ static pdhg_status upload_tables(pdhg_handle *h, const pdhg_problem *p, const pd
     if (G.has_gamma) P.gamma_half = F<T>(h, h->L.gamma);
     if (G.exact_t) P.tfac = F<T>(h, h->L.tfac);
     P.t64 = G.t64 ? 1 : 0;
+    if (G.rtab) {
+        P.rtab = F<T>(h, h->L.rtab);
+        CK(launch_rho_table<T>(F<T>(h, h->L.theta), G.modes, (int)G.nt, F<T>(h, h->L.rtab), h->stream));
+    }
     if (G.blu_log2L) {
         P.blu_tw = h->ws + h->L.blu_tw;
         P.blu_c = h->ws + h->L.blu_c;

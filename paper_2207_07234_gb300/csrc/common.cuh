@@ -71,6 +71,8 @@ struct Params {
     const T *tfac = nullptr;
     // float32 fields with the t-solve recurrence in float64 (PDHG_FLAG_T_SOLVE_FP64)
     int32_t t64 = 0;
+    // t-solve pivots rho_l per mode as [nt][modes] (1D finite differences); nullptr: evaluated
+    const T *rtab = nullptr;
 };
 
 // Debug builds (-DPDHG_DEBUG): the global indices of the instrumented kernels are checked

@@ -425,9 +425,59 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
         }
         return;
     }
+    const int64_t nX = (int64_t)nt * modes;
+    if (P.rtab) {
+        // pivots from the handle's [nt][modes] table (the values rho_of gives), loaded with
+        // the right-hand sides, TU slices ahead
+        constexpr int TU = 16;
+        const T *rt = P.rtab;
+        C y = spec[dbg_idx(P, col, nX, 135)];
+        int l = 1;
+        for (; l + TU <= nt; l += TU) {
+            C r[TU];
+            T rh[TU];
+#pragma unroll
+            for (int j = 0; j < TU; ++j) {
+                r[j] = spec[dbg_idx(P, col + (int64_t)(l + j) * modes, nX, 135)];
+                rh[j] = rt[dbg_idx(P, col + (int64_t)(l + j - 1) * modes, nX, 136)];
+            }
+#pragma unroll
+            for (int j = 0; j < TU; ++j) {
+                y = cadd(r[j], cscale(y, rh[j]));
+                spec[dbg_idx(P, col + (int64_t)(l + j) * modes, nX, 135)] = y;
+            }
+        }
+        for (; l < nt; ++l) {
+            const int64_t i = dbg_idx(P, col + (int64_t)l * modes, nX, 135);
+            y = cadd(spec[i], cscale(y, rt[dbg_idx(P, col + (int64_t)(l - 1) * modes, nX, 136)]));
+            spec[i] = y;
+        }
+        C z = cscale(y, rt[dbg_idx(P, col + (int64_t)(nt - 1) * modes, nX, 136)]);
+        spec[dbg_idx(P, col + (int64_t)(nt - 1) * modes, nX, 137)] = z;
+        l = nt - 2;
+        for (; l - TU + 1 >= 0; l -= TU) {
+            C r[TU];
+            T rh[TU];
+#pragma unroll
+            for (int j = 0; j < TU; ++j) {
+                r[j] = spec[dbg_idx(P, col + (int64_t)(l - j) * modes, nX, 137)];
+                rh[j] = rt[dbg_idx(P, col + (int64_t)(l - j) * modes, nX, 136)];
+            }
+#pragma unroll
+            for (int j = 0; j < TU; ++j) {
+                z = cscale(cadd(r[j], z), rh[j]);
+                spec[dbg_idx(P, col + (int64_t)(l - j) * modes, nX, 137)] = z;
+            }
+        }
+        for (; l >= 0; --l) {
+            const int64_t i = dbg_idx(P, col + (int64_t)l * modes, nX, 137);
+            z = cscale(cadd(spec[i], z), rt[dbg_idx(P, col + (int64_t)l * modes, nX, 136)]);
+            spec[i] = z;
+        }
+        return;
+    }
     const T th = theta_tab[col];
     const T emt = expT(-th), q = emt * emt;
-    const int64_t nX = (int64_t)nt * modes;
     // the right-hand sides do not depend on the recurrence: each sweep loads TU slices
     // ahead into registers, so a thread has TU loads in flight instead of one (the sweeps
     // of 1D problems, a few modes per multiprocessor, are bound by that latency)
@@ -467,6 +517,26 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
         z = cscale(cadd(spec[i], z), rho_of(th, emt, q, l));
         spec[i] = z;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rho_table(const T *__restrict__ theta_tab, int64_t modes, int nt,
+                                                   T *__restrict__ tab) {
+    const int64_t n = (int64_t)nt * modes;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(i / modes);
+        const T th = theta_tab[i - (int64_t)l * modes];
+        const T emt = expT(-th), q = emt * emt;
+        tab[i] = rho_of(th, emt, q, l);
+    }
+}
+
+template <typename T>
+cudaError_t launch_rho_table(const T *theta, int64_t modes, int nt, T *tab, cudaStream_t s) {
+    const int64_t n = (int64_t)nt * modes;
+    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    k_rho_table<T><<<g, 256, 0, s>>>(theta, modes, nt, tab);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -1062,6 +1132,7 @@ cudaError_t init_plain_attributes() {
     template cudaError_t launch_residual_rfft<T>(const Params<T> &, const T *, void *, const void *, cudaStream_t); \
     template cudaError_t launch_fft_y<T>(const Params<T> &, void *, const void *, int, cudaStream_t);          \
     template cudaError_t launch_tsolve<T>(const Params<T> &, void *, const T *, const void *, cudaStream_t);   \
+    template cudaError_t launch_rho_table<T>(const T *, int64_t, int, T *, cudaStream_t);                     \
     template cudaError_t launch_dual_irfft<T>(const Params<T> &, const void *, T *, T *, const void *, cudaStream_t); \
     template int64_t check_blocks<T>(const Params<T> &);                                                      \
     template cudaError_t init_plain_attributes<T>();                                                      \

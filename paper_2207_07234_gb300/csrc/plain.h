@@ -23,6 +23,9 @@ template <typename T>
 cudaError_t launch_fft_y(const Params<T> &P, void *spec, const void *twy, int inverse, cudaStream_t s);
 template <typename T>
 cudaError_t launch_tsolve(const Params<T> &P, void *spec, const T *theta, const void *V, cudaStream_t s);
+// tab[l * modes + m] = rho_l of mode m (the t-solve's pivots), l < nt
+template <typename T>
+cudaError_t launch_rho_table(const T *theta, int64_t modes, int nt, T *tab, cudaStream_t s);
 template <typename T>
 cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *phit, const void *twx, cudaStream_t s);
 template <typename T> int64_t check_blocks(const Params<T> &P);
