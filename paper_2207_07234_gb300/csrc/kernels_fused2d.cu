@@ -587,7 +587,10 @@ __global__ void __launch_bounds__(FTHREADS) k_cols(Params<float> P, float2 *__re
 // registers; the two radix-8 stages between them (spans 4 and 32) go through
 // shared memory (radix-8 layout of stockham.cuh: c = 2 after the first two stages,
 // c = 0 after the third).  Twiddles (twY): radix-8 span p at (p - 4) + (q-1) p + k,
-// radix-4 span 256 at 252 + (q-1) 256 + k.
+// radix-4 span 256 at 252 + (q-1) 256 + k.  One slice per step (TB = 1) at 63
+// registers: four blocks per SM, so all 513 kx columns are resident at once on the
+// 152 SMs (three blocks per SM, with two slices per step, left 57 columns for a
+// second wave: 0.898 against 0.857 ms at 1024^2 x 256).
 // The recurrence state of the t-solve: float2 and the float32 pivots, or (T64: the
 // PDHG_FLAG_T_SOLVE_FP64 variant) double2 and pivots in double, each stored value rounded
 // to float once.
@@ -621,10 +624,10 @@ template <> struct TRec<true> {
 };
 
 template <bool T64>
-__global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float2 *__restrict__ spec,
+__global__ void __launch_bounds__(FTHREADS, 4) k_cols1024(Params<float> P, float2 *__restrict__ spec,
                                                        const float2 *__restrict__ twY,
                                                        const float *__restrict__ thetaT) {
-    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 2, PN = R8<LOG2NY>::PN;
+    constexpr int LOG2NY = 10, NY = 1024, Q = 256, TB = 1, PN = R8<LOG2NY>::PN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *ba = reinterpret_cast<float2 *>(smem_raw);              // [TB][PN] (padded)
     float2 *bb = ba + TB * PN;                                      // [TB][PN]
@@ -763,7 +766,7 @@ __global__ void __launch_bounds__(FTHREADS, 3) k_cols1024(Params<float> P, float
 
 static size_t smem_cols(int log2ny) {
     const size_t n = (size_t)1 << log2ny;
-    return log2ny == 10 ? (4 * (size_t)R8<10>::PN + n) * 8 : 5 * n * 8;    // ny = 1024: radix-8 layout
+    return log2ny == 10 ? (2 * (size_t)R8<10>::PN + n) * 8 : 5 * n * 8;    // ny = 1024: radix-8 layout
 }
 
 // ---------------------------------------------------------------------------

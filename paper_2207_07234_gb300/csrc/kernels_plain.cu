@@ -293,27 +293,56 @@ __device__ __forceinline__ T rho_of(T theta, T emt, T q, int l) {
 // K + s = L D L^T with the host's factors fac[3][nt][nmodes] at mode id m (1/d_l, e_l =
 // L_{l,l-1}, f_l = L_{l,l-2}); forward y_l = r_l - e_l y_{l-1} - f_l y_{l-2} (stored), then
 // z_l = y_l / d_l - e_{l+1} z_{l+1} - f_{l+2} z_{l+2}.  s points at slice 0 of the mode, stride st.
+// Both sweeps load TU slices (right-hand sides and factors) ahead of the recurrence.
 template <typename T, typename C>
 __device__ __forceinline__ void tsolve_exact(C *s, int64_t st, const T *__restrict__ fac, int64_t nmodes, int64_t m,
                                              int nt) {
+    constexpr int TU = 8;
     const int64_t ts = (int64_t)nt * nmodes;
     C y1 = s[0], y2 = mk<C, T>(T(0), T(0));
-    for (int l = 1; l < nt; ++l) {
-        const T e = fac[ts + (int64_t)l * nmodes + m], f = fac[2 * ts + (int64_t)l * nmodes + m];
-        const C y = csub(s[(int64_t)l * st], cadd(cscale(y1, e), cscale(y2, f)));
-        s[(int64_t)l * st] = y;
-        y2 = y1;
-        y1 = y;
+    int l = 1;
+    for (; l < nt; l += TU) {
+        const int nb = min(TU, nt - l);
+        C r[TU];
+        T e[TU], f[TU];
+#pragma unroll
+        for (int j = 0; j < TU; ++j)
+            if (j < nb) {
+                r[j] = s[(int64_t)(l + j) * st];
+                e[j] = fac[ts + (int64_t)(l + j) * nmodes + m];
+                f[j] = fac[2 * ts + (int64_t)(l + j) * nmodes + m];
+            }
+#pragma unroll
+        for (int j = 0; j < TU; ++j)
+            if (j < nb) {
+                const C y = csub(r[j], cadd(cscale(y1, e[j]), cscale(y2, f[j])));
+                s[(int64_t)(l + j) * st] = y;
+                y2 = y1;
+                y1 = y;
+            }
     }
     C z1 = mk<C, T>(T(0), T(0)), z2 = z1;
-    for (int l = nt - 1; l >= 0; --l) {
-        const C y = l == nt - 1 ? y1 : s[(int64_t)l * st];
-        const T e1 = l + 1 < nt ? fac[ts + (int64_t)(l + 1) * nmodes + m] : T(0);
-        const T f2 = l + 2 < nt ? fac[2 * ts + (int64_t)(l + 2) * nmodes + m] : T(0);
-        const C z = csub(cscale(y, fac[(int64_t)l * nmodes + m]), cadd(cscale(z1, e1), cscale(z2, f2)));
-        s[(int64_t)l * st] = z;
-        z2 = z1;
-        z1 = z;
+    for (l = nt - 1; l >= 0; l -= TU) {
+        const int nb = min(TU, l + 1);
+        C y[TU];
+        T d[TU], e1[TU], f2[TU];
+#pragma unroll
+        for (int j = 0; j < TU; ++j)
+            if (j < nb) {
+                const int k = l - j;
+                y[j] = k == nt - 1 ? y1 : s[(int64_t)k * st];
+                d[j] = fac[(int64_t)k * nmodes + m];
+                e1[j] = k + 1 < nt ? fac[ts + (int64_t)(k + 1) * nmodes + m] : T(0);
+                f2[j] = k + 2 < nt ? fac[2 * ts + (int64_t)(k + 2) * nmodes + m] : T(0);
+            }
+#pragma unroll
+        for (int j = 0; j < TU; ++j)
+            if (j < nb) {
+                const C z = csub(cscale(y[j], d[j]), cadd(cscale(z1, e1[j]), cscale(z2, f2[j])));
+                s[(int64_t)(l - j) * st] = z;
+                z2 = z1;
+                z1 = z;
+            }
     }
 }
 

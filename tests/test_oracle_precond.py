@@ -151,3 +151,23 @@ def test_bdf2_preconditioned_norm_with_tt_and_exact_operator():
         be = opdhg.power_estimate(p.replace(time="be"), iters=40)
         assert abs(tt - (2.5 + nt / 4)) <= 0.02 * (2.5 + nt / 4), (nt, tt)
         assert abs(ex - be) <= 0.05 * be and be < 2.0, (nt, ex, be)
+
+
+def test_exact_operator_converges_viscous_burgers_bdf2():
+    """Viscous Burgers, BDF2 (the gradient workload's scheme, 64 x 32, nu = 1e-3, T = 0.5),
+    steps from the power estimate of each preconditioner: with the exact time operator
+    Algorithm 1 reaches relative Res 1e-8 within 1000 iterations; with T_t (admissible
+    steps smaller by sqrt(2.5 + nt/4) / sqrt(2)) it is still above 1e-2 after 1500."""
+    from oracle import pdhg as opdhg
+    base = W.viscous_burgers(nx=64, nt=32, T=0.5, nu=1e-3)
+    rel = {}
+    for tprec in ("exact", "tridiag"):
+        p = base.replace(tprec=tprec)
+        t = float(np.sqrt(0.5 / opdhg.power_estimate(p, iters=30)))
+        q = p.replace(tau_u=t, tau_phi=t, tau_u0=t)
+        r0 = opdhg.residual_norms(q, opdhg.initial_state(q))[0]
+        st, its, _ = opdhg.solve(q, max_iters=1500, tol=1e-8, check_every=100, relative=True)
+        r = opdhg.residual_norms(q, st)
+        rel[tprec] = (its, max(r[0], r[1]) / r0)
+    assert rel["exact"][0] <= 1000 and rel["exact"][1] <= 1e-8, rel
+    assert rel["tridiag"][1] > 1e-2, rel
