@@ -568,6 +568,48 @@ def gradient_leg(binding, iters=200, device=None, stream=None):
                     "unit": UNIT, "gradient_call_seconds": tg})
     except binding.PdhgError as err:
         out["status"] = f"stopped: {err}"
+    out["converged"] = gradient_converged(binding, device=device, stream=s)
+    return out
+
+
+def gradient_converged(binding, device=None, stream=None):
+    """The gradient workload's shape and scheme before the shock (T = 0.5 instead of 2),
+    with the exact time operator (PDHG_FLAG_EXACT_TIME_PRECOND; with T_t the admissible
+    BDF2 steps shrink as nt^{-1/2} and Algorithm 1 makes no progress here): forward solve to
+    relative Res 1e-6 in float64 and by the mixed solve, and the float32 gradient (forward
+    and adjoint each to float32's floor, at most 4000 iterations) of |u^nt - target|^2,
+    target = 0.5 + 0.9 sin(x - 1)."""
+    import torch
+    p = W.viscous_burgers(T=0.5).replace(tprec="exact", tau_u=0.45, tau_phi=0.45, tau_u0=0.45)
+    out = {"workload": p.name + f"_bdf2_nu{p.nu:g}_T{p.T:g}_exact_time_operator", "tol": 1e-6}
+    try:
+        with binding.Solver(p, precision="fp64", path="plain", device=device, stream=stream) as s:
+            r0 = float(s.residual()[0])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n = s.iterate(20000, tol=1e-6, check_every=100, relative=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            r = s.residual()
+            out["forward_fp64"] = {"seconds": dt, "iterations": int(n), "rel_res": max(r[0], r[1]) / r0}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sm, its = binding.solve_mixed(p, tol=1e-6, relative=True, check_every=100, max_iters=20000, device=device,
+                                      stream=stream)
+        torch.cuda.synchronize()
+        out["forward_mixed"] = {"seconds": time.perf_counter() - t0, "iterations": [int(v) for v in its]}
+        sm.close()
+        target = 0.5 + 0.9 * np.sin(W.fd_nodes(p.nx, p.lx) - 1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, du0, dnu, its = binding.solve_gradient(p, target, tol=1e-7, max_iters=4000, adj_tol=1e-7,
+                                                     adj_max_iters=4000, check_every=100, precision="fp32",
+                                                     device=device, stream=stream)
+        torch.cuda.synchronize()
+        out["gradient_fp32"] = {"seconds": time.perf_counter() - t0, "iterations": [int(v) for v in its],
+                                "loss": loss, "dloss_dnu": dnu, "dloss_du0_norm": float(np.linalg.norm(du0))}
+    except binding.PdhgError as err:
+        out["status"] = f"stopped: {err}"
     return out
 
 
