@@ -576,9 +576,10 @@ def gradient_converged(binding, device=None, stream=None):
     """The gradient workload's shape and scheme before the shock (T = 0.5 instead of 2),
     with the exact time operator (PDHG_FLAG_EXACT_TIME_PRECOND; with T_t the admissible
     BDF2 steps shrink as nt^{-1/2} and Algorithm 1 makes no progress here): forward solve to
-    relative Res 1e-6 in float64 and by the mixed solve, and the float32 gradient (forward
-    and adjoint each to float32's floor, at most 4000 iterations) of |u^nt - target|^2,
-    target = 0.5 + 0.9 sin(x - 1)."""
+    relative Res 1e-6 in float64 and by the mixed solve, and the float32 gradient of
+    |u^nt - target|^2, target = 0.5 + 0.9 sin(x - 1): forward to float32's floor (at most
+    4000 iterations), adjoint 30,000 iterations (its multipliers converge more slowly than
+    the forward state; at 30,000 the float32 gradient agrees with a float64 one to 1e-5)."""
     import torch
     p = W.viscous_burgers(T=0.5).replace(tprec="exact", tau_u=0.45, tau_phi=0.45, tau_u0=0.45)
     out = {"workload": p.name + f"_bdf2_nu{p.nu:g}_T{p.T:g}_exact_time_operator", "tol": 1e-6}
@@ -602,8 +603,8 @@ def gradient_converged(binding, device=None, stream=None):
         target = 0.5 + 0.9 * np.sin(W.fd_nodes(p.nx, p.lx) - 1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        loss, du0, dnu, its = binding.solve_gradient(p, target, tol=1e-7, max_iters=4000, adj_tol=1e-7,
-                                                     adj_max_iters=4000, check_every=100, precision="fp32",
+        loss, du0, dnu, its = binding.solve_gradient(p, target, tol=1e-7, max_iters=4000, adj_tol=0.0,
+                                                     adj_max_iters=30000, check_every=100, precision="fp32",
                                                      device=device, stream=stream)
         torch.cuda.synchronize()
         out["gradient_fp32"] = {"seconds": time.perf_counter() - t0, "iterations": [int(v) for v in its],

@@ -60,21 +60,24 @@ def test_gradient_workload_scheme_with_the_exact_time_operator(B):
     """The gradient workload's scheme (viscous Burgers, BDF2, nu = 1e-3) before the shock
     (T = 0.5) at 128 x 64, with the exact time operator (with T_t the BDF2 steps must shrink
     as nt^{-1/2} and Algorithm 1 does not converge at this shape): the float64 GPU gradient
-    equals the sequential adjoint of the Newton solution, and the float32 one (forward and
-    adjoint to float32's floor) stays within 1e-3 of it."""
+    after 50,000 adjoint iterations (the adjoint's multipliers converge more slowly than the
+    forward state: 3e-2 after 2000, 5e-8 after 10,000) equals the sequential adjoint of the
+    Newton solution, and the float32 one (forward to float32's floor, 20,000 adjoint
+    iterations) stays within 1e-4 of it."""
     p = W.viscous_burgers(nx=128, nt=64, T=0.5, nu=1e-3).replace(tprec="exact")
     p = with_taus(p, fac=0.4)
     g = target_of(p)
     u = newton.solve(p)
     _, _, du0, dnu = adjoint.sequential_adjoint(p, u, g)
-    loss, du0_g, dnu_g, iters = B.solve_gradient(p, g, tol=1e-12, adj_tol=1e-12, check_every=10)
-    assert iters[0] < 100000 and iters[1] < 100000
-    assert np.max(np.abs(du0_g - du0)) <= 1e-8 * np.max(np.abs(du0))
-    assert abs(dnu_g - dnu) <= 1e-8 * max(abs(dnu), 1e-3 * np.max(np.abs(du0)))
-    loss32, du0_32, dnu_32, _ = B.solve_gradient(p, g, tol=1e-5, max_iters=20000, adj_tol=1e-5,
-                                                 adj_max_iters=20000, check_every=50, precision="fp32")
-    assert np.max(np.abs(du0_32 - du0)) <= 1e-3 * np.max(np.abs(du0))
-    assert abs(dnu_32 - dnu) <= 1e-3 * max(abs(dnu), np.max(np.abs(du0)))
+    loss, du0_g, dnu_g, iters = B.solve_gradient(p, g, tol=1e-12, adj_tol=0.0, adj_max_iters=50000,
+                                                 check_every=100)
+    assert iters[0] < 100000 and iters[1] == 50000
+    assert np.max(np.abs(du0_g - du0)) <= 1e-9 * np.max(np.abs(du0))
+    assert abs(dnu_g - dnu) <= 1e-9 * max(abs(dnu), 1e-3 * np.max(np.abs(du0)))
+    loss32, du0_32, dnu_32, _ = B.solve_gradient(p, g, tol=1e-5, max_iters=20000, adj_tol=0.0,
+                                                 adj_max_iters=20000, check_every=100, precision="fp32")
+    assert np.max(np.abs(du0_32 - du0)) <= 1e-4 * np.max(np.abs(du0))
+    assert abs(dnu_32 - dnu) <= 1e-4 * max(abs(dnu), np.max(np.abs(du0)))
 
 
 @pytest.mark.parametrize("p", CASES[:2] + CASES[3:], ids=lambda p: f"{p.name}_{p.time}")
