@@ -1862,8 +1862,12 @@ static pdhg_status batch_tables(pdhg_batch *b) {
         int64_t nb[TAB_N], gx;
         batch_blocks(G, nb, &gx);
         const int64_t gxp = nb[TAB_PRIMAL] / (G.nt + 1), nlines = nb[TAB_ROWS] / G.nt;
-        for (int64_t l = 0; l <= G.nt; ++l)
-            for (int64_t x = 0; x < gxp; ++x) t[TAB_PRIMAL].push_back({i, (int32_t)x, (int32_t)l, 0});
+        // primal entries cover BATCH_PRIMAL_SPAN slices each (pad = the count): a block of 256
+        // dofs of one slice is too little work for its launch and setup
+        for (int64_t l = 0; l <= G.nt; l += BATCH_PRIMAL_SPAN)
+            for (int64_t x = 0; x < gxp; ++x)
+                t[TAB_PRIMAL].push_back({i, (int32_t)x, (int32_t)l,
+                                         (int32_t)std::min<int64_t>(BATCH_PRIMAL_SPAN, G.nt + 1 - l)});
         // Bluestein rows: the block of an even slice transforms that slice and the next
         // together, so odd slices get no block
         const int64_t lstep = G.blu_log2L ? 2 : 1;

@@ -980,11 +980,24 @@ cudaError_t launch_phi_lap(const Params<T> &P, const T *u, const T *phi, double 
 // the single-instance kernels above; tables list active instances only,
 // largest first.
 // ---------------------------------------------------------------------------
+// The instance's record (its Params and pointers) copied to shared memory by the block,
+// so that the per-block code reads its coefficients there and not through global memory.
+template <typename T>
+__device__ __forceinline__ const BatchInst<T> &batch_inst_shared(const BatchInst<T> *I, int inst) {
+    static_assert(sizeof(BatchInst<T>) % 8 == 0, "8-byte words");
+    constexpr int NW = (int)(sizeof(BatchInst<T>) / 8);
+    __shared__ uint64_t rec[NW];
+    const uint64_t *src = reinterpret_cast<const uint64_t *>(I + inst);
+    for (int w = threadIdx.x; w < NW; w += blockDim.x) rec[w] = src[w];
+    __syncthreads();
+    return *reinterpret_cast<const BatchInst<T> *>(rec);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_b_primal(const BatchInst<T> *__restrict__ I, const BatchEntry *__restrict__ tab) {
     const BatchEntry e = tab[blockIdx.x];
-    const BatchInst<T> &b = I[e.inst];
-    primal_block(b.P, b.u, b.phit, b.lam, b.lamt, b.u0, e.bx, e.l);
+    const BatchInst<T> &b = batch_inst_shared(I, e.inst);
+    for (int k = 0; k < max(e.pad, 1); ++k) primal_block(b.P, b.u, b.phit, b.lam, b.lamt, b.u0, e.bx, e.l + k);
 }
 
 template <typename T>
@@ -992,7 +1005,7 @@ __global__ void __launch_bounds__(256) k_b_residual_rfft(const BatchInst<T> *__r
                                                          const BatchEntry *__restrict__ tab) {
     typedef typename Cplx<T>::type C;
     const BatchEntry e = tab[blockIdx.x];
-    const BatchInst<T> &b = I[e.inst];
+    const BatchInst<T> &b = batch_inst_shared(I, e.inst);
     residual_rfft_block(b.P, b.u, (C *)b.spec, (const C *)b.twx, e.bx, e.l);
 }
 
@@ -1000,7 +1013,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_b_tsolve(const BatchInst<T> *__restrict__ I, const BatchEntry *__restrict__ tab) {
     typedef typename Cplx<T>::type C;
     const BatchEntry e = tab[blockIdx.x];
-    const BatchInst<T> &b = I[e.inst];
+    const BatchInst<T> &b = batch_inst_shared(I, e.inst);
     tsolve_block(b.P, (C *)b.spec, b.theta, (const C *)b.V, e.bx);
 }
 
@@ -1009,7 +1022,7 @@ __global__ void __launch_bounds__(256) k_b_dual_irfft(const BatchInst<T> *__rest
                                                       const BatchEntry *__restrict__ tab) {
     typedef typename Cplx<T>::type C;
     const BatchEntry e = tab[blockIdx.x];
-    const BatchInst<T> &b = I[e.inst];
+    const BatchInst<T> &b = batch_inst_shared(I, e.inst);
     dual_irfft_block(b.P, (const C *)b.spec, b.phi, b.phit, (const C *)b.twx, e.bx, e.l);
 }
 

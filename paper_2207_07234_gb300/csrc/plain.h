@@ -62,6 +62,8 @@ struct BatchInst {
 // one block of a batched launch: instance and the block's coordinates in that
 // instance's own grid (bx = blockIdx.x, l = blockIdx.y of the single launch)
 struct BatchEntry { int32_t inst, bx, l, pad; };
+// slices per primal entry of the per-stage batch launch (k_b_primal loops over them)
+constexpr int BATCH_PRIMAL_SPAN = 16;
 enum { BATCH_PRIMAL, BATCH_RESIDUAL, BATCH_TSOLVE, BATCH_DUAL, BATCH_CHECK, BATCH_REDUCE };
 // kind: one of BATCH_*; nblocks table entries (BATCH_REDUCE: entries of `list`,
 // instance ids, each summing its partial records into out[inst * 6 ..]).
