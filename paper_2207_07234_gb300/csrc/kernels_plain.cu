@@ -297,7 +297,7 @@ __device__ __forceinline__ T rho_of(T theta, T emt, T q, int l) {
 template <typename T, typename C>
 __device__ __forceinline__ void tsolve_exact(C *s, int64_t st, const T *__restrict__ fac, int64_t nmodes, int64_t m,
                                              int nt) {
-    constexpr int TU = 8;
+    constexpr int TU = 4;
     const int64_t ts = (int64_t)nt * nmodes;
     C y1 = s[0], y2 = mk<C, T>(T(0), T(0));
     int l = 1;
@@ -458,7 +458,7 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
     if (P.rtab) {
         // pivots from the handle's [nt][modes] table (the values rho_of gives), loaded with
         // the right-hand sides, TU slices ahead
-        constexpr int TU = 16;
+        constexpr int TU = 8;
         const T *rt = P.rtab;
         C y = spec[dbg_idx(P, col, nX, 135)];
         int l = 1;
@@ -510,7 +510,7 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
     // the right-hand sides do not depend on the recurrence: each sweep loads TU slices
     // ahead into registers, so a thread has TU loads in flight instead of one (the sweeps
     // of 1D problems, a few modes per multiprocessor, are bound by that latency)
-    constexpr int TU = 16;
+    constexpr int TU = 8;
     C y = spec[dbg_idx(P, col, nX, 133)];
     int l = 1;
     for (; l + TU <= nt; l += TU) {
@@ -1071,7 +1071,7 @@ __device__ __forceinline__ uint64_t batch_ns() {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_b_persistent(const BatchInst<T> *__restrict__ I,
+__global__ void __launch_bounds__(256, 3) k_b_persistent(const BatchInst<T> *__restrict__ I,
                                                       const BatchEntry *__restrict__ q, int64_t nq,
                                                       const int32_t *__restrict__ need, unsigned int *cnt, int *err,
                                                       uint64_t wait_ns) {
@@ -1104,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_b_persistent(const BatchInst<T> *__rest
         }
         __syncthreads();
         if (!s_ok) return;
-        const BatchInst<T> &b = I[inst];
+        const BatchInst<T> &b = batch_inst_shared(I, inst);
         for (int k = 0; k < span; ++k) {
             switch (stage) {
             case 0: primal_block(b.P, b.u, b.phit, b.lam, b.lamt, b.u0, e.bx, e.l + k); break;
