@@ -160,9 +160,10 @@ def test_full_size_sampled(B):
     for m in modes:
         err = np.max(np.abs(zg[m] - zr[m]))
         own = np.max(np.abs(zr[m]))
-        assert err <= 1e-4 * Z, (m, err, Z)                 # absent modes stay at rounding level
-        if own > 1e-2 * Z:
-            assert err <= 1e-3 * own, (m, err, own)          # present modes to 1e-3 of themselves
+        # float32 transforms and t-recurrence against the float64 per-mode solve: an absolute
+        # floor of the float32 2D transform of values of size Z (measured 2.1e-5 Z on an
+        # absent mode) plus 1e-4 of the mode itself
+        assert err <= 5e-5 * Z + 1e-4 * own, (m, err, own, Z)
     assert np.array_equal(phit1, 2 * phi1) or rel(phit1, 2 * phi1.astype(np.float64)) <= 1e-6
     # (b) iteration 2: the primal step at sampled points from the GPU's own phit^1
     for _ in range(200):

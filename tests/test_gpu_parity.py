@@ -92,6 +92,10 @@ def test_fixed_iterates_fp64(B, p):
     pow2 = p.nx & (p.nx - 1) == 0
     tu = 1e-11 if (p.nmodes == 2 or not pow2) else 1e-12
     assert rel(g["u"], o["u"]) <= tu
+    # the increment u - u_init on its own scale as well (u is u_init plus a change that
+    # can be small next to it)
+    u_init = opdhg.initial_state(p)["u"]
+    assert rel(g["u"] - u_init, o["u"] - u_init) <= 1000 * tu
     assert rel(g["phi"], o["phi"]) <= 10 * tu
     assert rel(g["phit"], o["phit"]) <= 10 * tu
     if p.init == "lambda":
