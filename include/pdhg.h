@@ -167,7 +167,9 @@ pdhg_status pdhg_create(const pdhg_problem *prob, const pdhg_grid *grid,
 /* Free the host handle (the workspace is the caller's to free). NULL is a no-op. */
 pdhg_status pdhg_destroy(pdhg_handle *h);
 
-/* Change the stream used by later calls. */
+/* Change the stream used by later calls.  Waits for the work already queued on the old
+ * stream first, so later calls on the new stream see a finished state.  Errors:
+ * INVALID_ARG, CUDA. */
 pdhg_status pdhg_set_stream(pdhg_handle *h, void *stream);
 
 /* Run iterations of Algorithm 1.
@@ -196,6 +198,11 @@ pdhg_status pdhg_residual(pdhg_handle *h, double out[4]);
  * LAMBDA/LAMBDAT ndof.  Synchronous. */
 pdhg_status pdhg_get_field(pdhg_handle *h, int32_t field, void *dst, int32_t on_device);
 pdhg_status pdhg_set_field(pdhg_handle *h, int32_t field, const void *src, int32_t on_device);
+
+/* The solution read of Algorithm 1's state: which = PDHG_FIELD_U (all slices u^0..u^nt),
+ * PDHG_FIELD_U_TERMINAL (u^nt), PDHG_FIELD_PHI or PDHG_FIELD_LAMBDA (the multipliers);
+ * the same copy as pdhg_get_field.  Other values: INVALID_ARG. */
+pdhg_status pdhg_solution(pdhg_handle *h, void *dst, int32_t dst_on_device, int32_t which);
 
 /* Element counts and iteration counter of the handle. */
 pdhg_status pdhg_info(pdhg_handle *h, int64_t *ndof, int64_t *nt, int64_t *iterations,

@@ -34,7 +34,8 @@ STAGES = ["primal", "residual_fft", "fft_y", "tsolve", "dual", "check", "fused_r
 
 # every symbol include/pdhg.h declares
 EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_stream", "pdhg_iterate",
-           "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_info", "pdhg_launch_count",
+           "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_solution", "pdhg_info",
+           "pdhg_launch_count",
            "pdhg_set_profiling", "pdhg_stage_times", "pdhg_set_graphs", "pdhg_set_wait_budget",
            "pdhg_last_error",
            "pdhg_refine_workspace_size",
@@ -95,6 +96,7 @@ def load(path: str | None = None):
         "pdhg_iterate": [vp, i64, ctypes.c_double, i32, i32, ctypes.POINTER(i64)],
         "pdhg_residual": [vp, ctypes.POINTER(ctypes.c_double)],
         "pdhg_get_field": [vp, i32, vp, i32],
+        "pdhg_solution": [vp, vp, i32, i32],
         "pdhg_set_field": [vp, i32, vp, i32],
         "pdhg_info": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
                       ctypes.POINTER(i32), ctypes.POINTER(i32)],
@@ -292,6 +294,17 @@ class Solver:
         a = out if out is not None else np.empty(self._shape(field), dtype=np_dtype)
         _check(load().pdhg_get_field(self.h, FIELD[field], ctypes.c_void_p(a.ctypes.data), 0))
         return a
+
+    def solution(self, which="u"):
+        """pdhg_solution: u (all slices), u_terminal, phi or lambda as a device tensor."""
+        t = self._torch.empty(self._shape(which), dtype=self.dtype, device=self.device)
+        _check(load().pdhg_solution(self.h, ctypes.c_void_p(t.data_ptr()), 1, FIELD[which]))
+        return t
+
+    def set_stream(self, stream):
+        """Later calls run on `stream` (a torch.cuda.Stream); the old stream's work finishes first."""
+        _check(load().pdhg_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)))
+        self._stream = stream
 
     def set(self, field, value):
         t = self._torch.as_tensor(value, dtype=self.dtype, device=self.device).contiguous()

@@ -945,6 +945,7 @@ extern "C" pdhg_status pdhg_destroy(pdhg_handle *h) {
 
 extern "C" pdhg_status pdhg_set_stream(pdhg_handle *h, void *stream) {
     if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
+    CK(cudaStreamSynchronize(h->stream));        // the old stream's work on the state is done
     h->stream = (cudaStream_t)stream;
     return PDHG_OK;
 }
@@ -1129,6 +1130,13 @@ extern "C" pdhg_status pdhg_get_field(pdhg_handle *h, int32_t field, void *dst, 
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return PDHG_OK;
+}
+
+extern "C" pdhg_status pdhg_solution(pdhg_handle *h, void *dst, int32_t dst_on_device, int32_t which) {
+    if (which != PDHG_FIELD_U && which != PDHG_FIELD_U_TERMINAL && which != PDHG_FIELD_PHI &&
+        which != PDHG_FIELD_LAMBDA)
+        return fail(PDHG_ERR_INVALID_ARG, "which must be PDHG_FIELD_U, _U_TERMINAL, _PHI or _LAMBDA");
+    return pdhg_get_field(h, which, dst, dst_on_device);
 }
 
 extern "C" pdhg_status pdhg_set_field(pdhg_handle *h, int32_t field, const void *src, int32_t on_device) {

@@ -304,3 +304,26 @@ def test_set_waits_for_the_current_stream(B):
         s.set("u", u64)
         got = s.get_host("u")
     assert np.array_equal(got, want)
+
+
+def test_solution_and_stream_switch(B):
+    """pdhg_solution returns the same values as the field reads, and a handle moved to
+    another stream in mid-run (after queued, unsynchronised iterations) continues from the
+    finished state: 6 + 6 iterations across the switch equal 12 on one stream."""
+    import torch
+    p = steps(W.advection_upwind_be(nx=256, nt=9), 0.6, 0.6)
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    with B.Solver(p, precision="fp64", path="plain", stream=a) as s:
+        s.iterate(6)
+        s.set_stream(b)
+        s.iterate(6)
+        u = s.get_host("u")
+        assert np.array_equal(s.solution("u").cpu().numpy(), u)
+        assert np.array_equal(s.solution("u_terminal").cpu().numpy(), u[-1])
+        assert np.array_equal(s.solution("phi").cpu().numpy(), s.get_host("phi"))
+        assert np.array_equal(s.solution("lambda").cpu().numpy(), s.get_host("lambda"))
+        with pytest.raises(B.PdhgError):
+            s.solution("phit")
+    with B.Solver(p, precision="fp64", path="plain") as s:
+        s.iterate(12)
+        assert np.array_equal(s.get_host("u"), u)
