@@ -76,7 +76,8 @@ __device__ __forceinline__ void primal_block(const Params<T> &P, T *__restrict__
     }
     const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
     if (i >= S) return;
-    const int ii = (int)i, y = ii / P.nx, x = ii - y * P.nx;     // one slice < 2^31 dofs: 32-bit division
+    // one slice < 2^31 dofs: 32-bit division, none in 1D (S == nx)
+    const int ii = (int)i, y = P.S == P.nx ? 0 : ii / P.nx, x = ii - y * P.nx;
     T *ul = u + (int64_t)l * S;
     T c = ul[i];
     T g = time_T(P, phit + i, S, l);
@@ -764,7 +765,8 @@ __device__ __forceinline__ void check_unit(const Params<T> &P, const T *__restri
         return;
     }
     const int64_t i = unit;
-    const int ii = (int)i, y = ii / P.nx, x = ii - y * P.nx;     // one slice < 2^31 dofs: 32-bit division
+    // one slice < 2^31 dofs: 32-bit division, none in 1D (S == nx)
+    const int ii = (int)i, y = P.S == P.nx ? 0 : ii / P.nx, x = ii - y * P.nx;
     if (l < P.nt) {
         const T *un = u + (int64_t)(l + 1) * S;
         const T d = P.ulin ? fd_D_jvp(P, P.ulin + (int64_t)(l + 1) * S, un, y, x) : fd_D(P, un, y, x);
@@ -951,7 +953,8 @@ __global__ void __launch_bounds__(256) k_phi_lap(Params<T> P, const T *__restric
     const T *ul = u + (int64_t)(l + 1) * S;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x) {
-        const int ii = (int)i, y = ii / P.nx, x = ii - y * P.nx;     // one slice < 2^31 dofs: 32-bit division
+        // one slice < 2^31 dofs: 32-bit division, none in 1D (S == nx)
+        const int ii = (int)i, y = P.S == P.nx ? 0 : ii / P.nx, x = ii - y * P.nx;
         const int64_t r = (int64_t)y * P.nx;
         const T c = ul[i];
         T lap = (ul[r + wrapp(x, P.nx)] - T(2) * c + ul[r + wrapm(x, P.nx)]) * P.inv_hx * P.inv_hx;
