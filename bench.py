@@ -536,9 +536,10 @@ def gradient_leg(binding, iters=200, device=None, stream=None):
     gradient workload's own shape: viscous Burgers 2048 x 1024, BDF2, nu = 1e-3, float32,
     plain path.  Algorithm 1 does not converge on that configuration, so fixed iteration
     counts are timed (small steps tau = 0.05 keep the iterates finite over them; the cost
-    of an iteration does not depend on the steps): the forward iterations alone, then
-    pdhg_solve_gradient with (n, n) and (2n, 2n) forward/adjoint iterations, whose
-    difference is n forward plus n adjoint iterations."""
+    of an iteration does not depend on the steps): the forward iterations alone (device
+    time by CUDA events), then pdhg_solve_gradient with (n, n) and (2n, 2n)
+    forward/adjoint iterations, whose difference in wall-clock time is n forward plus n
+    adjoint iterations."""
     import torch
     p = W.viscous_burgers().replace(tau_u=0.05, tau_phi=0.05, tau_u0=0.05)
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -546,12 +547,16 @@ def gradient_leg(binding, iters=200, device=None, stream=None):
            "iterations": iters}
     try:
         with binding.Solver(p, precision="fp32", path="plain", device=device, stream=s) as sv:
-            sv.iterate(10)
+            # device time per iteration: iters iterations plus one residual check replayed
+            # as one CUDA graph (the first call captures it), timed by events on the stream
+            sv.iterate(iters, tol=0.0, check_every=iters)
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            sv.iterate(iters)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            sv.iterate(iters, tol=0.0, check_every=iters)
+            e.record(s)
             torch.cuda.synchronize()
-            fwd = (time.perf_counter() - t0) / iters
+            fwd = a.elapsed_time(e) * 1e-3 / iters
         target = np.zeros(p.slice_shape)
         tg = []
         for n in (iters, 2 * iters):
@@ -654,6 +659,7 @@ def nonlinear_leg(binding, tol=1e-6, device=None, stream=None, alg1_iters=1000):
     # floor, reached in about 60 iterations): they are capped at 200 iterations, about what
     # float64 steps need
     tol_step = tol * r0 / float(np.sqrt(p.T))
+    sols = {}
     for label, prec, chk, cap in (("alg3_fp32", "fp32", 20, 200), ("alg3_mixed", "mixed", 10, 4000),
                                   ("alg3_fp64_plain", "fp64", 10, 4000)):
         torch.cuda.synchronize()
@@ -670,8 +676,14 @@ def nonlinear_leg(binding, tol=1e-6, device=None, stream=None, alg1_iters=1000):
                       "status": "converged" if rel <= tol else "floor", "rel_res": rel,
                       "path": "plain (one time step at a time)" + (
                           ", each step float32 to its floor, then float64" if prec == "mixed" else "")}
-        del u
-        torch.cuda.empty_cache()
+        sols[label] = u
+    # the float32 and mixed solutions against the float64 one (relative L-inf over all slices)
+    ref = sols["alg3_fp64_plain"].to(torch.float64)
+    scale = float(ref.abs().max())
+    for label in ("alg3_fp32", "alg3_mixed"):
+        out[label]["u_rel_linf_vs_fp64"] = float((sols[label].to(torch.float64) - ref).abs().max()) / scale
+    del sols, ref
+    torch.cuda.empty_cache()
     return out
 
 

@@ -894,11 +894,10 @@ cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *p
     return cudaGetLastError();
 }
 
-// blocks per slice of the residual check: at most 32 (grid-stride beyond that)
+// blocks per slice of the residual check (check_blocks_per_row)
 template <typename T>
 static int64_t check_grid_x(const Params<T> &P) {
-    int64_t units = is_dg(P.space) ? P.nx : P.S;
-    return std::min<int64_t>((units + 255) / 256, 32);
+    return check_blocks_per_row(is_dg(P.space) ? P.nx : P.S);
 }
 
 cudaError_t launch_residual_rfft_p32(const Params<double> &P, const double *u, void *spec, const void *twx32,

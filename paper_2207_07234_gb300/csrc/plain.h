@@ -1,6 +1,7 @@
 // plain.h -- launchers of the per-stage kernels (kernels_plain.cu).
 #pragma once
 
+#include <algorithm>
 #include <string>
 
 #include "../../include/pdhg.h"
@@ -64,6 +65,15 @@ struct BatchInst {
 struct BatchEntry { int32_t inst, bx, l, pad; };
 // slices per primal entry of the per-stage batch launch (k_b_primal loops over them)
 constexpr int BATCH_PRIMAL_SPAN = 16;
+// Units (dofs, or DG cells) per block of a slice row in the residual check: 256
+// threads x 16 units, one float32 partial per thread folded into float64 once; at
+// most 32 blocks per slice row (grid-stride beyond).  Fewer, wider blocks keep the
+// float64 block reductions (GB300's float64 rate is a small fraction of float32's)
+// from bounding the check.
+constexpr int64_t CHECK_UNITS_PER_BLOCK = 4096;
+inline int64_t check_blocks_per_row(int64_t units) {
+    return std::min<int64_t>((units + CHECK_UNITS_PER_BLOCK - 1) / CHECK_UNITS_PER_BLOCK, 32);
+}
 enum { BATCH_PRIMAL, BATCH_RESIDUAL, BATCH_TSOLVE, BATCH_DUAL, BATCH_CHECK, BATCH_REDUCE };
 // kind: one of BATCH_*; nblocks table entries (BATCH_REDUCE: entries of `list`,
 // instance ids, each summing its partial records into out[inst * 6 ..]).
