@@ -192,6 +192,19 @@ pdhg_status pdhg_iterate(pdhg_handle *h, int64_t max_iters, double tol, int32_t 
  * initial-row dof (w_x = h_x, or h_x*h_y in 2D).  TIMEOUT as pdhg_iterate. */
 pdhg_status pdhg_residual(pdhg_handle *h, double out[4]);
 
+/* Residual history (a diagnostic of this library; the paper plots Res against the
+ * iteration count, Sec. 4): every check of pdhg_iterate (every check_every iterations,
+ * and the last iteration of a call) -- and every check of pdhg_batch_iterate for the
+ * instance's handle -- records one row of 5 doubles: the handle's iterations so far,
+ * then the four entries of pdhg_residual at that point (absolute values).  The newest
+ * 65536 rows are kept (host memory of the handle; nothing on the device).
+ * max_rows = 0: *rows = the number of rows held (out may be NULL).  max_rows > 0: the
+ * oldest min(max_rows, held) rows are copied to out (host, row-major, 5 doubles per
+ * row) and *rows is that number.  clear != 0 empties the history after the copy (rows
+ * not copied are dropped).  Errors: INVALID_ARG (null handle or rows, max_rows < 0, out
+ * NULL with max_rows > 0). */
+pdhg_status pdhg_residual_history(pdhg_handle *h, double *out, int64_t max_rows, int64_t *rows, int32_t clear);
+
 /* Copy a field (PDHG_FIELD_*) out of / into the state.  dst/src has the
  * handle's element type; on_device != 0 means a device pointer.  Sizes in
  * elements: U (nt+1)*ndof, U_TERMINAL ndof (get only), PHI/PHIT nt*ndof,

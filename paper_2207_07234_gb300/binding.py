@@ -37,7 +37,7 @@ EXPORTS = ["pdhg_workspace_size", "pdhg_create", "pdhg_destroy", "pdhg_set_strea
            "pdhg_residual", "pdhg_get_field", "pdhg_set_field", "pdhg_solution", "pdhg_info",
            "pdhg_launch_count",
            "pdhg_set_profiling", "pdhg_stage_times", "pdhg_set_graphs", "pdhg_set_wait_budget",
-           "pdhg_last_error",
+           "pdhg_residual_history", "pdhg_last_error",
            "pdhg_refine_workspace_size",
            "pdhg_solve_refine", "pdhg_one_step_workspace_size", "pdhg_solve_one_step",
            "pdhg_gradient_workspace_size", "pdhg_solve_gradient", "pdhg_mixed_workspace_size",
@@ -105,6 +105,7 @@ def load(path: str | None = None):
         "pdhg_stage_times": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)],
         "pdhg_set_graphs": [vp, i32],
         "pdhg_set_wait_budget": [vp, ctypes.c_uint64],
+        "pdhg_residual_history": [vp, ctypes.POINTER(ctypes.c_double), i64, ctypes.POINTER(i64), i32],
         "pdhg_refine_workspace_size": [P, G, S, i32, ctypes.POINTER(ctypes.c_size_t)],
         "pdhg_solve_refine": [P, G, S, i32, ctypes.POINTER(i64), ctypes.c_double, i32, i32, vp, ctypes.c_size_t,
                               vp, ctypes.POINTER(vp), ctypes.POINTER(i64)],
@@ -246,6 +247,16 @@ class Solver:
         out = (ctypes.c_double * 4)()
         _check(load().pdhg_residual(self.h, out))
         return np.array(list(out))
+
+    def history(self, clear=False) -> np.ndarray:
+        """Res at every check of iterate(): rows [iterations, Res entries 0..3]."""
+        lib = load()
+        n = ctypes.c_int64(0)
+        _check(lib.pdhg_residual_history(self.h, None, 0, ctypes.byref(n), 0))
+        out = np.zeros((max(n.value, 1), 5))
+        _check(lib.pdhg_residual_history(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         max(n.value, 1), ctypes.byref(n), int(bool(clear))))
+        return out[: n.value]
 
     def info(self):
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

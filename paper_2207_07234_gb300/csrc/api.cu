@@ -49,11 +49,18 @@ void pdhg::set_last_error(const std::string &msg) { g_last_error = msg; }
 // ---------------------------------------------------------------------------
 namespace {
 
+constexpr int kMaxCanaries = 32;
+constexpr unsigned char kCanaryByte = 0xA5;
 struct Layout {
     size_t u, phi, phit, lam, lamt, u0, gamma, spec, twx, twy, theta, V, tfac, rtab, partials, scal, dbg, fused;
     size_t blu_tw, blu_c, blu_b;
     size_t twx32, twy32, theta32;    // float32 preconditioner tables (Geom::pre32)
     size_t total;
+    // debug builds: the bytes after each sub-buffer up to the next 256-byte boundary plus
+    // 256 more, filled with kCanaryByte at create and verified at every residual read
+    int ncan;
+    size_t can_off[kMaxCanaries];
+    uint32_t can_len[kMaxCanaries];
 };
 
 inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -166,8 +173,21 @@ pdhg_status validate(const pdhg_problem *p, const pdhg_grid *g, const pdhg_schem
 
 Layout layout_of(const Geom &G) {
     Layout L;
+    L.ncan = 0;
     size_t o = 0;
-    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+#ifdef PDHG_DEBUG
+        if (L.ncan < kMaxCanaries) {
+            L.can_off[L.ncan] = at + bytes;
+            L.can_len[L.ncan] = (uint32_t)(o + 256 - (at + bytes));
+            ++L.ncan;
+        }
+        o += 256;
+#endif
+        return at;
+    };
     const size_t e = G.esz;
     L.u = take((G.nt + 1) * G.S * e);
     L.phi = take(G.nt * G.S * e);
@@ -388,7 +408,23 @@ struct pdhg_handle {
     int32_t gchunk;
     int64_t glaunches;       // kernel launches per replay
     bool u0_dev;             // the problem's u0 was given in device memory (PDHG_FLAG_U0_ON_DEVICE)
+    // Res at every check of pdhg_iterate: rows [iterations done, Res entries 0..3], the
+    // newest kHistoryRows kept (a ring: hist_next is the next row to write)
+    std::vector<double> hist;
+    int64_t hist_next;
+    int64_t hist_count;
 };
+
+constexpr int64_t kHistoryRows = 65536;
+
+static void history_push(pdhg_handle *h, const double r[4]) {
+    if (h->hist.empty()) h->hist.assign((size_t)kHistoryRows * 5, 0.0);
+    double *row = h->hist.data() + (size_t)(h->hist_next % kHistoryRows) * 5;
+    row[0] = (double)h->iters;
+    for (int k = 0; k < 4; ++k) row[1 + k] = r[k];
+    ++h->hist_next;
+    h->hist_count = std::min<int64_t>(h->hist_count + 1, kHistoryRows);
+}
 
 static void graph_drop(pdhg_handle *h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -793,16 +829,67 @@ static cudaError_t enqueue_check(pdhg_handle *h) {
     });
 }
 
+#ifdef PDHG_DEBUG
+// Debug builds: one block per canary region of the handle's workspace; a changed byte
+// records site 900 + region in the debug flag (the first site recorded is kept).
+struct CanaryList {
+    int n;
+    unsigned long long off[kMaxCanaries];
+    unsigned len[kMaxCanaries];
+};
+
+__global__ void k_canary_check(const unsigned char *__restrict__ ws, CanaryList c, int *dbg) {
+    const int r = blockIdx.x;
+    if (r >= c.n) return;
+    const unsigned char *q = ws + c.off[r];
+    bool bad = false;
+    for (unsigned i = threadIdx.x; i < c.len[r]; i += blockDim.x) bad |= q[i] != kCanaryByte;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(dbg, 0, 900 + r);
+}
+
+static CanaryList canaries_of(const pdhg_handle *h) {
+    CanaryList c;
+    c.n = h->L.ncan;
+    for (int i = 0; i < c.n; ++i) { c.off[i] = h->L.can_off[i]; c.len[i] = h->L.can_len[i]; }
+    return c;
+}
+
+static cudaError_t canary_fill(pdhg_handle *h) {
+    for (int i = 0; i < h->L.ncan; ++i) {
+        cudaError_t e = cudaMemsetAsync(h->ws + h->L.can_off[i], kCanaryByte, h->L.can_len[i], h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t canary_check(pdhg_handle *h, cudaStream_t s) {
+    if (h->L.ncan == 0) return cudaSuccess;
+    k_canary_check<<<h->L.ncan, 256, 0, s>>>((const unsigned char *)h->ws, canaries_of(h), (int *)(h->ws + h->L.dbg));
+    return cudaGetLastError();
+}
+#endif
+
+// message of a recorded debug site: a canary region (900 + region) or an index check
+static std::string debug_site_message(int bad) {
+    if (bad >= 900 && bad < 900 + kMaxCanaries)
+        return "debug canary check: the bytes after workspace buffer " + std::to_string(bad - 900) +
+               " (in layout order) were overwritten";
+    return "debug bounds check: out-of-range index at site " + std::to_string(bad);
+}
+
 static pdhg_status read_res(pdhg_handle *h, double out[4]) {
     double acc[6];
     int err = 0;
+#ifdef PDHG_DEBUG
+    CK(canary_check(h, h->stream));
+#endif
     CK(cudaMemcpyAsync(acc, h->ws + h->L.scal, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
     int bad = 0;
     if (h->G.fused) CK(cudaMemcpyAsync(&err, h->fused.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&bad, h->ws + h->L.dbg, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (err) return fail(PDHG_ERR_TIMEOUT, "a pipelined spectrum load of the fused rows-C kernel did not arrive");
-    if (bad) return fail(PDHG_ERR_BOUNDS, "debug bounds check: out-of-range index at site " + std::to_string(bad));
+    if (bad) return fail(PDHG_ERR_BOUNDS, debug_site_message(bad));
     double ht = h->ht, wx = h->wx;
     // space-time L2 (weight h_t w_x per equation value), or, for the one-step
     // problems of Algorithm 3, L2 over the domain at one time (weight w_x)
@@ -908,6 +995,9 @@ static pdhg_status create_impl(const pdhg_problem *prob, const pdhg_grid *grid, 
     h->graphs = !G.fused;
     h->gexec = nullptr; h->gstream = nullptr; h->gchunk = 0; h->glaunches = 0;
     h->u_off = L.u;
+#ifdef PDHG_DEBUG
+    if (cudaError_t e = canary_fill(h); e != cudaSuccess) { delete h; return cuda_fail(e, "canary fill"); }
+#endif
     memset(h->stage_ms, 0, sizeof(h->stage_ms));
     memset(h->stage_n, 0, sizeof(h->stage_n));
     st = (G.prec == PDHG_FP64) ? upload_tables<double>(h, prob, grid, lf_a) : upload_tables<float>(h, prob, grid, lf_a);
@@ -1075,6 +1165,7 @@ static pdhg_status iterate_T(pdhg_handle *h, int64_t max_iters, double tol, int3
         }
         {
             if (st != PDHG_OK) { if (done) *done = n; return st; }
+            history_push(h, r);
             if (!std::isfinite(r[0]) || !std::isfinite(r[1])) {
                 if (done) *done = n;
                 return fail(PDHG_ERR_NONFINITE, "residual is not finite after " + std::to_string(h->iters) + " iterations");
@@ -1098,6 +1189,22 @@ extern "C" pdhg_status pdhg_iterate(pdhg_handle *h, int64_t max_iters, double to
     if (iters_done) *iters_done = 0;
     return h->G.prec == PDHG_FP64 ? iterate_T<double>(h, max_iters, tol, check_every, relative, iters_done)
                                   : iterate_T<float>(h, max_iters, tol, check_every, relative, iters_done);
+}
+
+extern "C" pdhg_status pdhg_residual_history(pdhg_handle *h, double *out, int64_t max_rows, int64_t *rows,
+                                             int32_t clear) {
+    if (!h || !rows) return fail(PDHG_ERR_INVALID_ARG, "null handle or rows");
+    if (max_rows < 0 || (max_rows > 0 && !out)) return fail(PDHG_ERR_INVALID_ARG, "out is NULL or max_rows < 0");
+    const int64_t n = std::min(h->hist_count, max_rows);
+    // the oldest kept row is hist_next - hist_count; copy the oldest n of the kept rows
+    const int64_t first = h->hist_next - h->hist_count;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *row = h->hist.data() + (size_t)((first + i) % kHistoryRows) * 5;
+        std::copy(row, row + 5, out + i * 5);
+    }
+    *rows = max_rows > 0 ? n : h->hist_count;
+    if (clear) h->hist_count = 0;
+    return PDHG_OK;
 }
 
 extern "C" pdhg_status pdhg_residual(pdhg_handle *h, double out[4]) {
@@ -2062,11 +2169,12 @@ static pdhg_status batch_read(pdhg_batch *b, std::vector<double> &acc) {
     }
 #ifdef PDHG_DEBUG
     // debug builds: the first out-of-range site recorded by any instance's kernels
+    for (int32_t i = 0; i < b->count; ++i) CK(canary_check(b->h[i], b->stream));
+    CK(cudaStreamSynchronize(b->stream));
     for (int32_t i = 0; i < b->count; ++i) {
         int bad = 0;
         CK(cudaMemcpy(&bad, b->h[i]->ws + b->h[i]->L.dbg, sizeof(int), cudaMemcpyDeviceToHost));
-        if (bad) return fail(PDHG_ERR_BOUNDS, "debug bounds check: instance " + std::to_string(i) + ", site " +
-                                                  std::to_string(bad));
+        if (bad) return fail(PDHG_ERR_BOUNDS, "instance " + std::to_string(i) + ": " + debug_site_message(bad));
     }
 #endif
     return PDHG_OK;
@@ -2167,6 +2275,7 @@ static pdhg_status batch_iterate_T(pdhg_batch *b, int64_t max_iters, double tol,
                 if (!b->active[i]) continue;
                 double r[4];
                 res_from_sums(b->h[i], &acc[(size_t)i * 6], r);
+                history_push(b->h[i], r);
                 const double scale = relative ? b->h[i]->res_init : 1.0;
                 if (!std::isfinite(r[0]) || !std::isfinite(r[1]) ||
                     r[0] > 1e10 * std::max(b->h[i]->res_init, 1e-300)) {

@@ -141,6 +141,8 @@ def test_mixed_workspace_and_wait_budget_without_device_work(lib):
         else:
             assert extra == 0
     assert lib.pdhg_set_wait_budget(None, ctypes.c_uint64(0)) == -1
+    n = ctypes.c_int64(0)
+    assert lib.pdhg_residual_history(None, None, ctypes.c_int64(0), ctypes.byref(n), 0) == -1
 
 
 def test_mixed_steps_flag_only_for_the_one_step_solve(lib):

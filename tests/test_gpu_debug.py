@@ -64,3 +64,43 @@ def test_debug_build_finds_no_out_of_range_index():
                        timeout=900)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
     assert "no out-of-range index" in r.stdout
+
+
+CANARY_SCRIPT = r'''
+import numpy as np
+import torch
+import pdhg_workloads as W
+from paper_2207_07234_gb300 import binding as B
+p = W.advection_upwind_be(nx=64, nt=8)
+with B.Solver(p, precision="fp64", path="plain") as s:
+    s.iterate(2, tol=0.0, check_every=1)             # canaries intact: no error
+    # u is the first buffer of the workspace ((nt + 1) x nx doubles); the byte after it
+    # starts its canary region.  Overwrite it from the host, as a kernel writing one
+    # element past u would.
+    off = (p.nt + 1) * p.nx * 8
+    s.workspace[off] = 0
+    torch.cuda.synchronize()
+    try:
+        s.iterate(1, tol=0.0, check_every=1)
+        print("not detected")
+    except B.PdhgError as e:
+        print("status", e.status, str(e))
+'''
+
+
+def test_debug_canary_overwrite_is_reported():
+    """Debug builds surround every sub-buffer of the workspace with canary bytes, filled
+    at create and verified at every residual read: a byte overwritten after the u buffer
+    (here from the host; no kernel misbehaves and the GPU sees no fault) makes the next
+    check return PDHG_ERR_BOUNDS naming the canary."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_07234_gb300 import _build
+    lib = _build.build(debug=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PDHG_LIBRARY=lib)
+    r = subprocess.run([sys.executable, "-c", CANARY_SCRIPT], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
+    assert "status -8" in r.stdout and "canary" in r.stdout and "buffer 0" in r.stdout, r.stdout

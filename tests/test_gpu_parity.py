@@ -327,3 +327,34 @@ def test_solution_and_stream_switch(B):
     with B.Solver(p, precision="fp64", path="plain") as s:
         s.iterate(12)
         assert np.array_equal(s.get_host("u"), u)
+
+
+def test_residual_history(B):
+    """Every check of pdhg_iterate records [iterations, Res]: checks every 10 of 100
+    iterations, then a call of 25 (checked at 10, 20 and its last iteration); the rows
+    equal the oracle's Res at those iterations and the last row pdhg_residual on the same
+    state; clear empties the history; a batch's checks are recorded on each instance's
+    handle."""
+    p = steps(W.advection_upwind_be(nx=128, nt=16), 0.6, 0.6)
+    with B.Solver(p, precision="fp64", path="plain") as s:
+        s.iterate(100, tol=0.0, check_every=10)
+        s.iterate(25, tol=0.0, check_every=10)
+        h = s.history()
+        assert h.shape == (13, 5)
+        assert list(h[:, 0]) == [10, 20, 30, 40, 50, 60, 70, 80, 90, 100, 110, 120, 125]
+        assert np.array_equal(h[-1, 1:], s.residual())
+        st, ores = opdhg.initial_state(p), []
+        for i in range(1, 126):
+            opdhg.step(p, st)
+            if i in h[:, 0]:
+                ores.append(opdhg.residual_norms(p, st)[:3])
+        assert np.allclose(h[:, 1:4], np.array(ores), rtol=1e-9, atol=0.0)
+        assert s.history(clear=True).shape == (13, 5)
+        assert s.history().shape == (0, 5)
+    probs = [p, W.heat_table1(64, 16)]
+    with B.Batch(probs, precision="fp64") as bt:
+        bt.iterate(20, tol=0.0, check_every=10)
+        for i, q in enumerate(probs):
+            h = bt.instance(i).history()
+            assert list(h[:, 0]) == [10, 20]
+            assert np.array_equal(h[-1, 1:], bt.instance(i).residual())
