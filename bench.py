@@ -674,8 +674,10 @@ def nonlinear_leg(binding, tol=1e-6, device=None, stream=None, alg1_iters=1000):
         rel = float(r[0]) / r0
         out[label] = {"seconds": dt, "iterations": int(sum(per)), "max_per_step": int(max(per)),
                       "status": "converged" if rel <= tol else "floor", "rel_res": rel,
-                      "path": "plain (one time step at a time)" + (
-                          ", each step float32 to its floor, then float64" if prec == "mixed" else "")}
+                      "path": {"fp32": "fused float32 steps (one time step at a time)",
+                               "mixed": "one time step at a time, each step float32 on the fused path to its "
+                                        "floor, then float64 on the plain path",
+                               "fp64": "plain (one time step at a time)"}[prec]}
         sols[label] = u
     # the float32 and mixed solutions against the float64 one (relative L-inf over all slices)
     ref = sols["alg3_fp64_plain"].to(torch.float64)

@@ -293,6 +293,10 @@ pdhg_status pdhg_solve_refine(const pdhg_problem *prob, const pdhg_grid *grid,
  * (3 v - 4 u^l + u^{l-1}) / (2 h_t) + D(v) = 0, is the backward-Euler equation of a
  * step of length 2 h_t / 3 from w = (4 u*^l - u*^{l-1}) / 3, so that step runs as the
  * two-slice BE problem started from w (step 0 is the scheme's BE start).
+ * The step handles take scheme->path: float32 2D finite-difference steps (and the
+ * float32 phase of PDHG_FLAG_MIXED_STEPS) run on the fused path with PDHG_PATH_AUTO or
+ * PDHG_PATH_FUSED where it applies (nx in [256, 2048], ny in [256, 1024]); float64
+ * steps run on the plain path.
  *
  * u_out: device, (nt+1)*ndof values of the scheme's precision (float64 with
  * PDHG_FLAG_MIXED_STEPS), written with u*^0..u*^nt.  iters_per_step (host, nt entries)

@@ -357,13 +357,15 @@ def solve_refine(p, levels, iters, tol=1e-3, check_every=1, relative=False, prec
 
 
 def solve_one_step(p, tol=1e-3, max_iters_per_step=100000, check_every=1, precision="fp64", device=None,
-                   stream=None):
+                   stream=None, path="auto"):
     """Algorithm 3 (Sec. 3.5): returns (u* as a device tensor [nt+1][...], iterations per step).
     precision "mixed": each step in float32 to tol or float32's floor, then float64
-    (PDHG_FLAG_MIXED_STEPS; u* in float64)."""
+    (PDHG_FLAG_MIXED_STEPS; u* in float64).  path: of the float32 step handles ("auto":
+    the fused path for 2D finite differences where it applies; float64 steps run plain)."""
     import torch
     lib = load()
-    prob, grid, scheme, keep = structs(p, "fp64" if precision == "mixed" else precision, "plain")
+    prob, grid, scheme, keep = structs(p, "fp64" if precision == "mixed" else precision,
+                                       "plain" if precision == "fp64" else path)
     if precision == "mixed":
         scheme.flags |= FLAG_MIXED_STEPS
     nbytes = ctypes.c_size_t(0)

@@ -148,7 +148,7 @@ pdhg_status validate_shape(const pdhg_problem *p, const pdhg_grid *g, const pdhg
         bool ok = fused2d_supported(g->dims, s->space, s->time, s->precision, g->nx, G->ny, g->nt, p->nu) &&
                   !(G->t64 && G->ny != 1024);
         if (s->path == PDHG_PATH_FUSED && !ok)
-            return fail(PDHG_ERR_UNSUPPORTED, "the fused path needs 2D FD, FP32, nx in [256, 2048], ny in [256, 1024] (powers of two), nt >= 2");
+            return fail(PDHG_ERR_UNSUPPORTED, "the fused path needs 2D FD, FP32, nx in [256, 2048], ny in [256, 1024] (powers of two)");
         G->fused = ok;
     }
     G->pre32 = pre32 && s->precision == PDHG_FP64 && !G->fused && !dg && G->blu_log2L == 0 && !G->exact_t;

@@ -1119,7 +1119,7 @@ bool fused2d_supported(int dims, int space, int time, int prec, int64_t nx, int6
     (void)nu;
     if (dims != 2 || prec != 1) return false;
     if (space != FD_UPWIND && space != FD_LF) return false;
-    if (nt < 2) return false;
+    if (nt < 1) return false;
     auto p2 = [](int64_t v) { return v > 0 && (v & (v - 1)) == 0; };
     if (time == BDF2 && nx > 1024) return false;     // three u slots no longer fit shared memory
     return p2(nx) && p2(ny) && nx >= 256 && nx <= 2048 && ny >= 256 && ny <= 1024;

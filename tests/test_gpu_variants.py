@@ -105,6 +105,28 @@ def test_one_step_mixed_reaches_scheme_solution(B, p):
     assert np.max(np.abs(um.cpu().numpy() - un)) <= 1e-9 * max(1.0, np.max(np.abs(un)))
 
 
+def test_one_step_fused_float32_phase(B):
+    """2D finite differences with nx, ny >= 256: the float32 step handles of Algorithm 3
+    run on the fused path (path "auto").  Mixed steps to a per-step tolerance far below
+    float32's floor give the same solution as with float32 steps on the plain path (both
+    are the scheme's solution, 1e-9), and float32 steps alone stop at the plain path's
+    per-step counts (within 10%), both within 1e-4 of that solution (the oracle's steps at
+    this tolerance stop 1.8e-5 from it)."""
+    p = W.burgers_2d(n=256, nt=4, cfl=0.5)
+    t = float(np.sqrt(0.5 / opdhg.power_estimate(p.replace(nt=1, T=p.ht, time="be"), iters=60)))
+    p = p.replace(init="pinned", tau_u=t, tau_u0=t, tau_phi=t)
+    up, cp = B.solve_one_step(p, tol=1e-11, max_iters_per_step=20000, check_every=10, precision="mixed",
+                              path="plain")
+    uf, cf = B.solve_one_step(p, tol=1e-11, max_iters_per_step=20000, check_every=10, precision="mixed")
+    up, uf = up.cpu().numpy(), uf.cpu().numpy()
+    assert np.max(np.abs(uf - up)) <= 1e-9 * max(1.0, np.max(np.abs(up)))
+    r0 = 1e-3                            # about 4e-4 of a step's initial Res: above float32's floor
+    sp, kp = B.solve_one_step(p, tol=r0, max_iters_per_step=20000, check_every=10, precision="fp32", path="plain")
+    sf, kf = B.solve_one_step(p, tol=r0, max_iters_per_step=20000, check_every=10, precision="fp32")
+    assert all(abs(a - b) <= max(10, 0.1 * b) for a, b in zip(kf, kp)), (kf, kp)
+    assert rel(sf.cpu().numpy(), up) <= 1e-4 and rel(sp.cpu().numpy(), up) <= 1e-4
+
+
 def test_refine_traffic_counts_and_solution(B):
     """Table 3's mesh-refinement row on the GPU (float64): 1000 + 1000 iterations on
     256 x 8 and 256 x 16, then to Res <= 1e-3 on 256 x 32; counts and the final
