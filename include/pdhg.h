@@ -233,13 +233,15 @@ pdhg_status pdhg_set_profiling(pdhg_handle *h, int32_t enable);
 pdhg_status pdhg_stage_times(pdhg_handle *h, double ms[PDHG_NUM_STAGES],
                              int64_t launches[PDHG_NUM_STAGES]);
 
-/* CUDA graphs (plain path; on by default, not used while profiling): with
- * check_every = m > 0, pdhg_iterate captures m iterations plus the residual
- * check as one graph on first use and replays it on the handle's stream for
- * every full chunk of m iterations (fewer launches for small, launch-bound
- * problems; the kernels and their order are unchanged, so results are
- * identical).  A capture the driver refuses falls back to kernel-by-kernel
- * launches.  enable = 0 turns graphs off; the fused path never uses them. */
+/* CUDA graphs (not used while profiling): with check_every = m > 0, pdhg_iterate
+ * captures m iterations plus the residual check as one graph on first use and
+ * replays it on the handle's stream for every full chunk of m iterations (fewer
+ * launches for small, launch-bound problems; the kernels and their order are
+ * unchanged, so results are identical).  A capture the driver refuses falls back
+ * to kernel-by-kernel launches.  Default: on for the plain path and for fused
+ * problems of at most 2^23 cell-iterations (nt x ndof), off for larger fused ones;
+ * enable = 0 turns graphs off, enable = 1 on.  pdhg_set_wait_budget drops a
+ * captured graph (the budget is a launch argument of the fused rows-C kernel). */
 pdhg_status pdhg_set_graphs(pdhg_handle *h, int32_t enable);
 
 /* Budget, in nanoseconds, of each bounded device wait (the TMA stage waits of the

@@ -992,7 +992,9 @@ static pdhg_status create_impl(const pdhg_problem *prob, const pdhg_grid *grid, 
     h->iters = 0; h->launches = 0; h->profiling = false;
     h->res_norm = 0;
     for (int k = 0; k < 4; ++k) h->last_res[k] = NAN;
-    h->graphs = !G.fused;
+    // CUDA graphs of m iterations and the check: the plain path, and fused problems small
+    // enough (<= 2^23 cell-iterations) for launch gaps to matter
+    h->graphs = !G.fused || (double)G.nt * (double)G.S <= (double)(int64_t(1) << 23);
     h->gexec = nullptr; h->gstream = nullptr; h->gchunk = 0; h->glaunches = 0;
     h->u_off = L.u;
 #ifdef PDHG_DEBUG
@@ -1529,10 +1531,14 @@ static pdhg_status mixed_step(pdhg_handle *hf, pdhg_handle *hd, const double *u_
     hd->launches += 5;
     if (e != cudaSuccess) return cuda_fail(e, "float32 -> float64 hand-over");
     int64_t n64 = 0;
-    const int64_t ccap = std::max<int32_t>(1, check_every / 5);
+    // a step's float64 phase takes about as many iterations as a float64 step (its start
+    // is the float32 floor, not the solution): checks after 1, 2, 3, 4, 6, 9, ... of them,
+    // then every check_every, whose full chunks replay one CUDA graph
+    const int64_t ccap = std::max<int32_t>(1, check_every);
     while (n64 < cap) {
         const int64_t chunk = std::min<int64_t>(std::min<int64_t>(std::max<int64_t>(1, n64 / 2), ccap), cap - n64);
         int64_t done = 0;
+        hd->graphs = chunk == ccap;
         pdhg_status st = pdhg_iterate(hd, chunk, tol, (int32_t)chunk, 0, &done);
         n64 += done;
         *n64_out = n64;
@@ -1565,7 +1571,7 @@ static pdhg_status one_step_mixed(const pdhg_problem *p1, const pdhg_grid *g1, c
         if (st != PDHG_OK) { cleanup(); return st; }
         hf[k]->res_norm = 1;
         hd[k]->res_norm = 1;
-        hd[k]->graphs = false;               // chunks of changing length: launch kernel by kernel
+        hd[k]->graphs = false;               // set per chunk in mixed_step: graphs for full chunks only
     }
     const int64_t S = hf[0]->G.S;
     cudaError_t e = cudaMemcpyAsync(uo, hd[0]->ws + hd[0]->L.u0, S * sizeof(double), cudaMemcpyDeviceToDevice, stream);
@@ -2355,13 +2361,16 @@ extern "C" pdhg_status pdhg_batch_set_graphs(pdhg_batch *b, int32_t enable) {
 extern "C" pdhg_status pdhg_set_graphs(pdhg_handle *h, int32_t enable) {
     if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
     graph_drop(h);
-    h->graphs = enable != 0 && !h->G.fused;
+    h->graphs = enable != 0;
     return PDHG_OK;
 }
 
 extern "C" pdhg_status pdhg_set_wait_budget(pdhg_handle *h, uint64_t ns) {
     if (!h) return fail(PDHG_ERR_INVALID_ARG, "null handle");
-    if (h->G.fused) h->fused.wait_ns = ns;
+    if (h->G.fused) {
+        h->fused.wait_ns = ns;
+        graph_drop(h);                   // a captured rows-C launch holds the old budget
+    }
     return PDHG_OK;
 }
 

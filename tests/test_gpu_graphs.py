@@ -49,3 +49,40 @@ def test_profiling_bypasses_graphs(B):
         s.iterate(30, check_every=10)
         t = s.stage_times()
         assert t["primal"][1] == 30 and t["check"][1] == 3      # one record per stage call
+
+
+FUSED = [W.burgers_2d(n=256, nt=16).replace(tau_u=0.4, tau_phi=0.4, tau_u0=0.1),
+         W.burgers_2d(n=1024, nt=4).replace(tau_u=0.4, tau_phi=0.4, tau_u0=0.1, init="pinned"),
+         W.burgers_2d(n=1024, nt=1).replace(tau_u=0.4, tau_phi=0.4, tau_u0=0.1, init="pinned")]
+
+
+@pytest.mark.parametrize("p", FUSED, ids=lambda p: f"{p.name}_{p.init}")
+def test_fused_graphs_change_nothing(B, p):
+    """Fused problems of at most 2^23 cell-iterations replay chunks from a graph by
+    default (Algorithm 3's two-slice steps among them): iterates, residuals, stopping
+    iteration and launch count as launched kernel by kernel, bit for bit."""
+    out = []
+    for graphs in (True, False):
+        with B.Solver(p, precision="fp32", path="fused") as s:
+            s.set_graphs(graphs)
+            n1 = s.iterate(23, tol=0.0, check_every=5)
+            n2 = s.iterate(400, tol=1e-3, check_every=10, relative=True)
+            out.append((n1, n2, s.get_host("u"), s.get_host("phi"), s.residual(), s.launches()))
+    (a1, a2, au, ap, ar, al), (b1, b2, bu, bp, br, bl) = out
+    assert a1 == b1 == 23 and a2 == b2
+    assert np.array_equal(au, bu) and np.array_equal(ap, bp)
+    assert np.array_equal(ar, br)
+    assert al == bl
+
+
+def test_wait_budget_drops_a_captured_graph(B):
+    """The bounded waits' budget is a launch argument of the nx = 1024 rows-C kernel: a
+    budget set after a chunk was captured takes effect (the graph is dropped and
+    captured again), so a zero budget is reported as PDHG_ERR_TIMEOUT at the next check."""
+    p = FUSED[2]
+    with B.Solver(p, precision="fp32", path="fused") as s:
+        s.iterate(10, tol=0.0, check_every=5)
+        s.set_wait_budget(0)
+        with pytest.raises(B.PdhgError) as e:
+            s.iterate(5, tol=0.0, check_every=5)
+        assert e.value.status == -6
