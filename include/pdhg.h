@@ -472,7 +472,7 @@ pdhg_status pdhg_batch_set_graphs(pdhg_batch *b, int32_t enable);
  *
  * Scratch: a fixed 2 MiB array in device memory, part of the library image
  * (held on every GPU that uses it until the process exits).  Problems with
- * min(ceil(units/4096), 32)*(nt+1) > 43685 partial blocks (units = ndof, or
+ * min(ceil(units/4096), max(32, 1216/(nt+1)))*(nt+1) > 43685 partial blocks (units = ndof, or
  * cells for DG; so nt <= 1364 always fits) are rejected with
  * PDHG_ERR_UNSUPPORTED before any device work.  All calls share the array: calls that overlap on
  * the GPU race; calls ordered on one stream are safe.  The first call in each

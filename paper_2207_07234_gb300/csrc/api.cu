@@ -204,7 +204,7 @@ Layout layout_of(const Geom &G) {
     L.tfac = take(G.exact_t ? 3 * G.nt * G.modes * e : 0);
     L.rtab = take(G.rtab ? G.nt * G.modes * e : 0);
     int64_t units = G.space >= PDHG_SPACE_DG_P2_LF ? G.nx : G.S;
-    int64_t nblk = check_blocks_per_row(units) * (G.nt + 1);    // k_check grid
+    int64_t nblk = check_blocks_per_row(units, G.nt) * (G.nt + 1);    // k_check grid
     L.partials = take(nblk * 6 * sizeof(double));
     L.scal = take(16 * sizeof(double));
     L.dbg = take(sizeof(int));                  // debug builds: first out-of-range site
@@ -1871,7 +1871,7 @@ void batch_blocks(const Geom &G, int64_t out[TAB_N], int64_t *gx) {
     const int64_t units = dg ? G.nx : G.S;
     const int64_t nlines = dg ? 1 : G.lines;
     const int64_t cols = dg ? G.nkx : G.lines * G.nkx;
-    *gx = check_blocks_per_row(units);
+    *gx = check_blocks_per_row(units, G.nt);
     out[TAB_PRIMAL] = ((units + 255) / 256) * (G.nt + 1);
     out[TAB_ROWS] = nlines * G.nt;
     out[TAB_TSOLVE] = (cols + 127) / 128;

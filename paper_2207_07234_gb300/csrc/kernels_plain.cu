@@ -897,7 +897,7 @@ cudaError_t launch_dual_irfft(const Params<T> &P, const void *spec, T *phi, T *p
 // blocks per slice of the residual check (check_blocks_per_row)
 template <typename T>
 static int64_t check_grid_x(const Params<T> &P) {
-    return check_blocks_per_row(is_dg(P.space) ? P.nx : P.S);
+    return check_blocks_per_row(is_dg(P.space) ? P.nx : P.S, P.nt);
 }
 
 cudaError_t launch_residual_rfft_p32(const Params<double> &P, const double *u, void *spec, const void *twx32,

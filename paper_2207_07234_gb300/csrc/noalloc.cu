@@ -125,7 +125,7 @@ pdhg_status run(const pdhg_problem *p, const pdhg_grid *g, const pdhg_scheme *s,
     int64_t nblocks = check_blocks<T>(P);
     if (nblocks > kMaxPartialBlocks)
         return err(PDHG_ERR_UNSUPPORTED,
-                   "problem too large for the fixed scratch: min(ceil(units/4096), 32)*(nt+1) = " +
+                   "problem too large for the fixed scratch: min(ceil(units/4096), max(32, 1216/(nt+1)))*(nt+1) = " +
                        std::to_string(nblocks) + " > " + std::to_string(kMaxPartialBlocks) +
                        " partial blocks (units = dofs, or cells for DG)");
     void *base = nullptr;

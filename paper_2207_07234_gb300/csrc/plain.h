@@ -66,13 +66,16 @@ struct BatchEntry { int32_t inst, bx, l, pad; };
 // slices per primal entry of the per-stage batch launch (k_b_primal loops over them)
 constexpr int BATCH_PRIMAL_SPAN = 16;
 // Units (dofs, or DG cells) per block of a slice row in the residual check: 256
-// threads x 16 units, one float32 partial per thread folded into float64 once; at
-// most 32 blocks per slice row (grid-stride beyond).  Fewer, wider blocks keep the
-// float64 block reductions (GB300's float64 rate is a small fraction of float32's)
-// from bounding the check.
+// threads x 16 units, one float32 partial per thread folded into float64 once.  Fewer,
+// wider blocks keep the float64 block reductions (GB300's float64 rate is a small
+// fraction of float32's) from bounding the check.  At most 32 blocks per slice row
+// (grid-stride beyond), or 1216 / (nt + 1) when there are few rows (1216 = 8 blocks
+// on each of 152 multiprocessors), so that a check of a one- or two-slice problem
+// still fills the GPU.
 constexpr int64_t CHECK_UNITS_PER_BLOCK = 4096;
-inline int64_t check_blocks_per_row(int64_t units) {
-    return std::min<int64_t>((units + CHECK_UNITS_PER_BLOCK - 1) / CHECK_UNITS_PER_BLOCK, 32);
+inline int64_t check_blocks_per_row(int64_t units, int64_t nt) {
+    const int64_t cap = std::max<int64_t>(32, 1216 / (nt + 1));
+    return std::min<int64_t>((units + CHECK_UNITS_PER_BLOCK - 1) / CHECK_UNITS_PER_BLOCK, cap);
 }
 enum { BATCH_PRIMAL, BATCH_RESIDUAL, BATCH_TSOLVE, BATCH_DUAL, BATCH_CHECK, BATCH_REDUCE };
 // kind: one of BATCH_*; nblocks table entries (BATCH_REDUCE: entries of `list`,
