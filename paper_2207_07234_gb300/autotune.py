@@ -44,6 +44,40 @@ def time_iterations(bt, iters, stream):
     return e0.elapsed_time(e1) / iters
 
 
+def search(measure, present, candidates=(1, 2, 4, 8), blocks=(0, 1, 2, 3), orders=(0, 1), unsupported=()):
+    """Coordinate descent over the launch choices, given measure(persistent,
+    blocks_per_sm, order, tiles) -> ms per batch iteration: the per-stage launches
+    once, then every (order, blocks per multiprocessor) of the persistent launch with
+    untiled queue entries (a choice whose measure raises one of `unsupported` is
+    skipped), then, at the best of those, each present size class's tile in turn,
+    kept where it is faster.  Returns the choice dict without the timings."""
+    tiles = [1] * 8
+    per_stage = measure(False, 0, 0, tiles)
+    best, best_bps, best_order = None, 0, 0
+    for order in orders:
+        for bps in blocks:
+            try:
+                ms = measure(True, bps, order, tiles)
+            except unsupported:
+                continue
+            if best is None or ms < best:
+                best, best_bps, best_order = ms, bps, order
+    if best is None:                                       # no persistent form fits
+        return {"persistent": False, "blocks_per_sm": 0, "order": 0, "tiles": tiles,
+                "persistent_ms": None, "per_stage_ms": per_stage, "classes_present": list(present)}
+    for c in present:
+        for g in candidates:
+            if g == tiles[c]:
+                continue
+            trial = list(tiles)
+            trial[c] = g
+            ms = measure(True, best_bps, best_order, trial)
+            if ms < best:
+                best, tiles = ms, trial
+    return {"persistent": bool(best < per_stage), "blocks_per_sm": best_bps, "order": best_order, "tiles": tiles,
+            "persistent_ms": best, "per_stage_ms": per_stage, "classes_present": list(present)}
+
+
 def tune(problems, precision="fp32", iters=3, candidates=(1, 2, 4, 8), blocks=(0, 1, 2, 3), orders=(0, 1)):
     """Returns the chosen launch (the persistent one with its best blocks per
     multiprocessor, queue order and tiles, or the per-stage launches when those are
@@ -60,28 +94,9 @@ def tune(problems, precision="fp32", iters=3, candidates=(1, 2, 4, 8), blocks=(0
             log.append({"persistent": persistent, "blocks_per_sm": bps, "order": order, "tiles": list(tiles),
                         "ms": ms})
             return ms
-        tiles = [1] * 8
-        per_stage = run(False, 0, 0, tiles)
-        best, best_bps, best_order = None, 0, 0
-        for order in orders:
-            for bps in blocks:
-                try:
-                    ms = run(True, bps, order, tiles)
-                except binding.PdhgError:
-                    continue
-                if best is None or ms < best:
-                    best, best_bps, best_order = ms, bps, order
-        for c in present:
-            for g in candidates:
-                if g == tiles[c]:
-                    continue
-                trial = list(tiles)
-                trial[c] = g
-                ms = run(True, best_bps, best_order, trial)
-                if ms < best:
-                    best, tiles = ms, trial
-    return {"persistent": bool(best < per_stage), "blocks_per_sm": best_bps, "order": best_order, "tiles": tiles,
-            "persistent_ms": best, "per_stage_ms": per_stage, "classes_present": present, "timings": log}
+        res = search(run, present, candidates, blocks, orders, unsupported=(binding.PdhgError,))
+    res["timings"] = log
+    return res
 
 
 def main(argv=None):
