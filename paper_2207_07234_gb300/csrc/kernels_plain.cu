@@ -295,12 +295,16 @@ __device__ __forceinline__ T rho_of(T theta, T emt, T q, int l) {
 // L_{l,l-1}, f_l = L_{l,l-2}); forward y_l = r_l - e_l y_{l-1} - f_l y_{l-2} (stored), then
 // z_l = y_l / d_l - e_{l+1} z_{l+1} - f_{l+2} z_{l+2}.  s points at slice 0 of the mode, stride st.
 // Both sweeps load TU slices (right-hand sides and factors) ahead of the recurrence.
+// Debug builds check every access against the spectrum (s = spec + base, nX elements)
+// and the factor table (3 nt nmodes).
 template <typename T, typename C>
-__device__ __forceinline__ void tsolve_exact(C *s, int64_t st, const T *__restrict__ fac, int64_t nmodes, int64_t m,
-                                             int nt) {
+__device__ __forceinline__ void tsolve_exact(const Params<T> &P, C *s, int64_t base, int64_t nX, int64_t st,
+                                             const T *__restrict__ fac, int64_t nmodes, int64_t m, int nt) {
     constexpr int TU = 4;
-    const int64_t ts = (int64_t)nt * nmodes;
-    C y1 = s[0], y2 = mk<C, T>(T(0), T(0));
+    const int64_t ts = (int64_t)nt * nmodes, nF = 3 * ts;
+    auto si = [&](int64_t off, int code) { return dbg_idx(P, base + off, nX, code) - base; };
+    auto fi = [&](int64_t off, int code) { return dbg_idx(P, off, nF, code); };
+    C y1 = s[si(0, 140)], y2 = mk<C, T>(T(0), T(0));
     int l = 1;
     for (; l < nt; l += TU) {
         const int nb = min(TU, nt - l);
@@ -309,15 +313,15 @@ __device__ __forceinline__ void tsolve_exact(C *s, int64_t st, const T *__restri
 #pragma unroll
         for (int j = 0; j < TU; ++j)
             if (j < nb) {
-                r[j] = s[(int64_t)(l + j) * st];
-                e[j] = fac[ts + (int64_t)(l + j) * nmodes + m];
-                f[j] = fac[2 * ts + (int64_t)(l + j) * nmodes + m];
+                r[j] = s[si((int64_t)(l + j) * st, 140)];
+                e[j] = fac[fi(ts + (int64_t)(l + j) * nmodes + m, 141)];
+                f[j] = fac[fi(2 * ts + (int64_t)(l + j) * nmodes + m, 141)];
             }
 #pragma unroll
         for (int j = 0; j < TU; ++j)
             if (j < nb) {
                 const C y = csub(r[j], cadd(cscale(y1, e[j]), cscale(y2, f[j])));
-                s[(int64_t)(l + j) * st] = y;
+                s[si((int64_t)(l + j) * st, 142)] = y;
                 y2 = y1;
                 y1 = y;
             }
@@ -331,16 +335,16 @@ __device__ __forceinline__ void tsolve_exact(C *s, int64_t st, const T *__restri
         for (int j = 0; j < TU; ++j)
             if (j < nb) {
                 const int k = l - j;
-                y[j] = k == nt - 1 ? y1 : s[(int64_t)k * st];
-                d[j] = fac[(int64_t)k * nmodes + m];
-                e1[j] = k + 1 < nt ? fac[ts + (int64_t)(k + 1) * nmodes + m] : T(0);
-                f2[j] = k + 2 < nt ? fac[2 * ts + (int64_t)(k + 2) * nmodes + m] : T(0);
+                y[j] = k == nt - 1 ? y1 : s[si((int64_t)k * st, 140)];
+                d[j] = fac[fi((int64_t)k * nmodes + m, 141)];
+                e1[j] = k + 1 < nt ? fac[fi(ts + (int64_t)(k + 1) * nmodes + m, 141)] : T(0);
+                f2[j] = k + 2 < nt ? fac[fi(2 * ts + (int64_t)(k + 2) * nmodes + m, 141)] : T(0);
             }
 #pragma unroll
         for (int j = 0; j < TU; ++j)
             if (j < nb) {
                 const C z = csub(cscale(y[j], d[j]), cadd(cscale(z1, e1[j]), cscale(z2, f2[j])));
-                s[(int64_t)(l - j) * st] = z;
+                s[si((int64_t)(l - j) * st, 142)] = z;
                 z2 = z1;
                 z1 = z;
             }
@@ -364,25 +368,26 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
             // w = V^H r in place, the exact time operator per eigen-index (mode id k nm + i), z = V w
             for (int l = 0; l < nt; ++l) {
                 C r[3], w[3];
-                for (int m = 0; m < nm; ++m) r[m] = spec[l * ls + m * P.nkx + k];
+                for (int m = 0; m < nm; ++m) r[m] = spec[dbg_idx(P, l * ls + m * P.nkx + k, nt * ls, 143)];
                 for (int i = 0; i < nm; ++i) {
                     C acc = mk<C, T>(T(0), T(0));
                     for (int m = 0; m < nm; ++m) acc = cadd(acc, cmulconj(r[m], v[m * 3 + i]));
                     w[i] = acc;
                 }
-                for (int i = 0; i < nm; ++i) spec[l * ls + i * P.nkx + k] = w[i];
+                for (int i = 0; i < nm; ++i) spec[dbg_idx(P, l * ls + i * P.nkx + k, nt * ls, 143)] = w[i];
             }
             for (int i = 0; i < nm; ++i)
-                tsolve_exact<T, C>(spec + i * P.nkx + k, ls, P.tfac, (int64_t)P.nkx * nm, (int64_t)k * nm + i, nt);
+                tsolve_exact<T, C>(P, spec + i * P.nkx + k, i * P.nkx + k, nt * ls, ls, P.tfac, (int64_t)P.nkx * nm,
+                                   (int64_t)k * nm + i, nt);
             for (int l = 0; l < nt; ++l) {
                 C w[3], zz[3];
-                for (int i = 0; i < nm; ++i) w[i] = spec[l * ls + i * P.nkx + k];
+                for (int i = 0; i < nm; ++i) w[i] = spec[dbg_idx(P, l * ls + i * P.nkx + k, nt * ls, 143)];
                 for (int m = 0; m < nm; ++m) {
                     C acc = mk<C, T>(T(0), T(0));
                     for (int i = 0; i < nm; ++i) acc = cadd(acc, cmul(v[m * 3 + i], w[i]));
                     zz[m] = acc;
                 }
-                for (int m = 0; m < nm; ++m) spec[l * ls + m * P.nkx + k] = zz[m];
+                for (int m = 0; m < nm; ++m) spec[dbg_idx(P, l * ls + m * P.nkx + k, nt * ls, 143)] = zz[m];
             }
             return;
         }
@@ -426,7 +431,7 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
     const int64_t col = (int64_t)bx * blockDim.x + threadIdx.x;
     if (col >= modes) return;
     if (P.tfac) {
-        tsolve_exact<T, C>(spec + col, modes, P.tfac, modes, col, nt);
+        tsolve_exact<T, C>(P, spec + col, col, (int64_t)nt * modes, modes, P.tfac, modes, col, nt);
         return;
     }
     if (sizeof(T) == 4 && P.t64) {
@@ -434,24 +439,25 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
         // in double; each stored y_l and z_l is rounded to the field's precision once
         const double th = (double)theta_tab[col];
         const double emt = exp(-th), q = emt * emt;
-        C *s = spec + col;
-        double yr = (double)s[0].x, yi = (double)s[0].y;
+        const int64_t nS = (int64_t)nt * modes;
+        auto si = [&](int l) { return dbg_idx(P, col + (int64_t)l * modes, nS, 144); };
+        double yr = (double)spec[si(0)].x, yi = (double)spec[si(0)].y;
         for (int l = 1; l < nt; ++l) {
-            const C r = s[(int64_t)l * modes];
+            const C r = spec[si(l)];
             const double rh = rho_of<double>(th, emt, q, l - 1);
             yr = (double)r.x + rh * yr;
             yi = (double)r.y + rh * yi;
-            s[(int64_t)l * modes] = mk<C, T>((T)yr, (T)yi);
+            spec[si(l)] = mk<C, T>((T)yr, (T)yi);
         }
         const double rl = rho_of<double>(th, emt, q, nt - 1);
         double zr = rl * yr, zi = rl * yi;
-        s[(int64_t)(nt - 1) * modes] = mk<C, T>((T)zr, (T)zi);
+        spec[si(nt - 1)] = mk<C, T>((T)zr, (T)zi);
         for (int l = nt - 2; l >= 0; --l) {
-            const C yl = s[(int64_t)l * modes];
+            const C yl = spec[si(l)];
             const double rh = rho_of<double>(th, emt, q, l);
             zr = rh * ((double)yl.x + zr);
             zi = rh * ((double)yl.y + zi);
-            s[(int64_t)l * modes] = mk<C, T>((T)zr, (T)zi);
+            spec[si(l)] = mk<C, T>((T)zr, (T)zi);
         }
         return;
     }
@@ -686,8 +692,8 @@ __global__ void __launch_bounds__(256) k_residual_rfft_p32(Params<double> P, con
     }
     __syncthreads();
     fft_radix2(z, lg, 1, M, 1, twx, 2, false);
-    float2 *out = spec + ((int64_t)l * P.lines + line) * P.nkx;
-    for (int k = threadIdx.x; k <= M; k += blockDim.x) out[k] = rfft_split(z, M, k, twx);
+    const int64_t o = ((int64_t)l * P.lines + line) * P.nkx, nX = (int64_t)P.nt * P.lines * P.nkx;
+    for (int k = threadIdx.x; k <= M; k += blockDim.x) spec[dbg_idx(P, o + k, nX, 145)] = rfft_split(z, M, k, twx);
 }
 
 __global__ void __launch_bounds__(256) k_dual_irfft_p32(Params<double> P, const float2 *__restrict__ spec,
@@ -705,7 +711,7 @@ __global__ void __launch_bounds__(256) k_dual_irfft_p32(Params<double> P, const 
     const int64_t off = (int64_t)l * P.S + (int64_t)line * N;
     for (int x = threadIdx.x; x < N; x += blockDim.x) {
         const double dz = P.dual_scale * (double)zr[x];
-        const int64_t i = off + x;
+        const int64_t i = dbg_idx(P, off + x, (int64_t)P.nt * P.S, 146);
         const double pn = phi[i] + dz;
         phi[i] = pn;
         phit[i] = pn + dz;

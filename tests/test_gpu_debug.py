@@ -4,8 +4,9 @@ batches) every global store, against the extent of its buffer; an index out of r
 recorded (and the access redirected to element 0), and the next residual check returns
 PDHG_ERR_BOUNDS.  The parity cases of the fused path (ragged t-chunks, BDF2 across chunk
 boundaries, both initial rows, nx != ny, the TMA rows-C at nx = 1024, nx = 2048) and their
-float64 plain runs, and 1D plain cases (Bluestein lengths, DG P2 / P1, BE and BDF2) alone
-and as a batch, go through that build with checks after every second iteration and find
+float64 plain runs, 1D plain cases (Bluestein lengths, DG P2 / P1, BE and BDF2) alone
+and as a batch, the t-solve variants (the exact time operator, the float64 recurrence) and
+the mixed solve go through that build with checks after every second iteration and find
 no out-of-range index."""
 import os
 import subprocess
@@ -48,7 +49,35 @@ for prec in ("fp32", "fp64"):
         bt.iterate(4, tol=0.0, check_every=2)
         for i in range(len(plain)):
             bt.instance(i).residual()
-print("debug build: no out-of-range index in", len(cases) + len(plain), "cases")
+# the exact time operator (1D finite differences with BDF2, DG P1 and P2, 2D plain), the
+# float64 t-recurrence (1D and 2D plain, the fused columns at ny = 1024) and the mixed
+# solve, whose float64 phase applies K_d^{-1} in float32
+exact = [W.advection_upwind_be(nx=256, nt=9).replace(time="bdf2", tprec="exact"),
+         W.transport_dg_p1(ncell=64, nt=7).replace(tprec="exact"),
+         W.burgers_dg_p2(ncell=32, nt=5, T=0.5).replace(c=0.5, tprec="exact", tau_u=0.05, tau_u0=0.05,
+                                                       tau_phi=0.05),
+         W.burgers_2d(n=32, nt=6).replace(time="bdf2", tprec="exact", **base)]
+for q in exact:
+    for prec in ("fp32", "fp64"):
+        with B.Solver(q, precision=prec, path="plain") as s:
+            s.iterate(4, tol=0.0, check_every=2)
+            s.residual()
+t64 = [(W.advection_upwind_be(nx=256, nt=9), "plain"), (W.burgers_2d(n=64, nt=5).replace(**base), "plain"),
+       (W.burgers_2d(n=1024, nt=3).replace(**base), "fused")]
+for q, path in t64:
+    with B.Solver(q, precision="fp32", path=path, t64=True) as s:
+        s.iterate(4, tol=0.0, check_every=2)
+        s.residual()
+mixed = [W.advection_upwind_be(nx=256, nt=32, tau=(1.4, 0.1, 0.35, 0.99)),
+         W.burgers_2d(n=64, nt=8).replace(alpha=0.0, beta=1.0, space="fd_upwind", lf_a=1.0, c=1.0, tau_u=0.5,
+                                          tau_phi=0.5, tau_u0=0.1)]
+for q in mixed:
+    s, its = B.solve_mixed(q, tol=1e-9, relative=True, check_every=10, max_iters=50000)
+    with s:
+        assert its[1] > 0, its                              # the float64 phase ran
+        s.residual()
+print("debug build: no out-of-range index in", len(cases) + len(plain) + len(exact) + len(t64) + len(mixed),
+      "cases")
 '''
 
 

@@ -13,6 +13,10 @@ from the float64 oracle on the same seeded input, bounds it, and prints it
 * DG P2 Burgers 512 cells x 256 slices, BDF2, T = 2: 20 fixed iterates at the BDF2
   step sizes sqrt(0.5 / (2.5 + nt/4)) (Algorithm 1 does not converge past the shock),
   the increments u - u_init and phi on their own scales;
+* viscous Burgers 2048 x 1024, BDF2, nu = 1e-3 (the gradient workload's forward problem
+  at its own size, in the benchmark's launch configuration): 20 fixed iterates, u to the
+  float32 forward-error bound of its update stencil (large cancelling coefficients at
+  nt = 1024; see the test), phi as above;
 * 2D Burgers 1024 x 1024 (BE + global LF; the nx = ny = 1024 fused kernels) on 6
   slices: 4 fixed iterates, as above;
 * the batch: two BE and two BDF2 instances of the 256-instance draw (the smallest
@@ -22,8 +26,9 @@ from the float64 oracle on the same seeded input, bounds it, and prints it
   with the exact time operator at 128 x 64: the float32 gradient (dLoss/du0,
   dLoss/dnu) against the oracle's sequential adjoint of the Newton solution.
 
-Fixed-iterate bounds are 1e-5 of each field's own largest value (the benchmark spec's float32
-tolerance), for u plus the float32 rounding of u itself over the iterations; the floor solution's, 1e-5 relative L-inf; the gradient's, 1e-4 of the
+Fixed-iterate bounds are 1e-5 of each field's own largest value (the stated float32
+tolerance), for u plus the float32 rounding of u itself over the iterations; the floor
+solution's, 1e-5 relative L-inf; the gradient's, 1e-4 of the
 largest dLoss/du0 (the product of the float32 floors of two solves and the
 conditioning of the linearised problem, see tests/test_gpu_adjoint.py).
 """
@@ -103,6 +108,55 @@ def test_dg_p2_burgers_512x256_fixed_iterates(B):
         s.iterate(20)
         gu, gphi = s.get_host("u"), s.get_host("phi")
     increments("dg_p2_burgers_512x256_bdf2", gu, gphi, p, 20)
+
+
+def test_viscous_burgers_2048x1024_fixed_iterates(B):
+    """The gradient workload's forward problem at its own size (viscous Burgers 2048 x 1024,
+    BDF2, nu = 1e-3, T = 2), in the launch configuration the benchmark's gradient leg times
+    (plain path, steps 0.05): 20 fixed iterates in float32 and in float64 against the
+    oracle's.
+
+    At nt = 1024 the stencil of J^T phit has large coefficients of both signs (the BDF2
+    time part 4/h_t = 2048, the space part max|u|/h_x + 2a/h_x + 4 nu/h_x^2 ~ 2000) whose
+    terms cancel, so float32 rounding of the primal update is not small next to the
+    increment as it is on the short grids above.  Its bound is the forward error of a
+    k-term float32 sum (Higham's gamma_k = k u / (1 - k u), u = 2^-24, k = 16) applied
+    to each iteration's update: sum over iterations of gamma_16 tau_u C_T max|phit|,
+    C_T the sum of the stencil's absolute coefficients; plus the rounding of the stored
+    u (n 2^-24 max|u|) and the stated float32 tolerance, 1e-5 of the increment.  (A
+    root-sum-square model of the same roundings, sqrt(n k) u tau_u C_T max|phit|, gives
+    3.0e-5 absolute; the measured error is 2.8e-5, 1.5e-5 of max|u|.)  phi keeps the 1e-5
+    bound.  In float64, 1e-11 of the increment."""
+    p = W.viscous_burgers().replace(tau_u=0.05, tau_phi=0.05, tau_u0=0.05)
+    n = 20
+    o = opdhg.initial_state(p)
+    u_init = o["u"].copy()
+    phit_max = 0.0
+    for _ in range(n):
+        opdhg.step(p, o)
+        phit_max += float(np.max(np.abs(o["phit"])))
+    hx, ht = p.lx / p.nx, p.T / p.nt
+    c_t = 4.0 / ht + np.max(np.abs(o["u"])) / hx + 2.0 * p.lf_a / hx + 4.0 * p.nu / hx ** 2
+    u32 = 2.0 ** -24
+    gamma16 = 16 * u32 / (1 - 16 * u32)
+    du_o = o["u"] - u_init
+    with B.Solver(p, precision="fp32", path="plain") as s:
+        s.iterate(n)
+        gu, gphi = s.get_host("u"), s.get_host("phi")
+    err_u = float(np.max(np.abs(np.asarray(gu, np.float64) - o["u"])))
+    ep = rel(gphi, o["phi"])
+    report("viscous_burgers_2048x1024_bdf2", f"u-u_init_after_{n}_rel_to_increment", err_u / np.max(np.abs(du_o)))
+    report("viscous_burgers_2048x1024_bdf2", f"u_after_{n}_rel_to_u", err_u / np.max(np.abs(o["u"])))
+    report("viscous_burgers_2048x1024_bdf2", f"phi_after_{n}", ep)
+    bound = (1e-5 * np.max(np.abs(du_o)) + n * u32 * np.max(np.abs(o["u"])) +
+             gamma16 * p.tau_u * c_t * phit_max)
+    assert err_u <= bound, (err_u, bound)
+    assert ep <= 1e-5, ep
+    with B.Solver(p, precision="fp64", path="plain") as s:
+        s.iterate(n)
+        gu, gphi = s.get_host("u"), s.get_host("phi")
+    assert np.max(np.abs(gu - o["u"])) <= 1e-11 * np.max(np.abs(du_o))
+    assert rel(gphi, o["phi"]) <= 1e-11
 
 
 def test_burgers2d_1024_fused_fixed_iterates(B):
