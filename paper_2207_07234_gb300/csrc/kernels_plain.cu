@@ -8,7 +8,8 @@
 //                   lambda, lambdat (Algorithm 1 steps 1 and the lambda update)
 //   k_residual_rfft R^l(u^n) and its forward real FFT along x
 //   k_fft_y         2D: complex FFT along y (forward, and later inverse)
-//   k_tsolve        (T_t + kappa h_t^2) z = r per Fourier mode (Thomas, closed-form pivots)
+//   k_tsolve        (T_t + kappa h_t^2) z = r per Fourier mode (Thomas, closed-form pivots;
+//                   k_tsolve_rtab: 1D handles with a pivot table, deeper prefetch)
 //   k_dual_irfft    inverse FFT along x, phi <- phi + tau_phi z, phit = 2 phi^n - phi^{n-1}
 // plus k_check / k_reduce for Res (Eq. 2.12).
 #include <algorithm>
@@ -351,7 +352,12 @@ __device__ __forceinline__ void tsolve_exact(const Params<T> &P, C *s, int64_t b
     }
 }
 
-template <typename T>
+// TUR: slices in flight per sweep on the pivot-table path (1D finite differences).  The
+// batch kernels keep 8 (16 raised the persistent kernel's registers past one block per
+// multiprocessor); the single-instance t-solve of a 1D problem, about a thousand mode
+// columns on a few multiprocessors and bound by load latency, takes 16.  The arithmetic,
+// and so every value, is the same for any depth.
+template <typename T, int TUR = 8>
 __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T>::type *__restrict__ spec,
                                              const T *__restrict__ theta_tab,
                                              const typename Cplx<T>::type *__restrict__ V, int bx) {
@@ -465,7 +471,7 @@ __device__ __forceinline__ void tsolve_block(const Params<T> &P, typename Cplx<T
     if (P.rtab) {
         // pivots from the handle's [nt][modes] table (the values rho_of gives), loaded with
         // the right-hand sides, TU slices ahead
-        constexpr int TU = 8;
+        constexpr int TU = TUR;
         const T *rt = P.rtab;
         C y = spec[dbg_idx(P, col, nX, 135)];
         int l = 1;
@@ -580,6 +586,14 @@ __global__ void __launch_bounds__(128) k_tsolve(Params<T> P, typename Cplx<T>::t
                                                 const T *__restrict__ theta_tab,
                                                 const typename Cplx<T>::type *__restrict__ V) {
     tsolve_block(P, spec, theta_tab, V, blockIdx.x);
+}
+
+// the same for a handle with a pivot table (1D finite differences): 16 slices in flight
+template <typename T>
+__global__ void __launch_bounds__(128) k_tsolve_rtab(Params<T> P, typename Cplx<T>::type *__restrict__ spec,
+                                                     const T *__restrict__ theta_tab,
+                                                     const typename Cplx<T>::type *__restrict__ V) {
+    tsolve_block<T, 16>(P, spec, theta_tab, V, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -886,7 +900,10 @@ template <typename T>
 cudaError_t launch_tsolve(const Params<T> &P, void *spec, const T *theta, const void *V, cudaStream_t s) {
     typedef typename Cplx<T>::type C;
     int64_t cols = is_dg(P.space) ? P.nkx : (int64_t)P.lines * P.nkx;
-    k_tsolve<T><<<(unsigned)((cols + 127) / 128), 128, 0, s>>>(P, (C *)spec, theta, (const C *)V);
+    if (P.rtab)
+        k_tsolve_rtab<T><<<(unsigned)((cols + 127) / 128), 128, 0, s>>>(P, (C *)spec, theta, (const C *)V);
+    else
+        k_tsolve<T><<<(unsigned)((cols + 127) / 128), 128, 0, s>>>(P, (C *)spec, theta, (const C *)V);
     return cudaGetLastError();
 }
 
