@@ -317,6 +317,16 @@ def run_reference(args):
     return 0
 
 
+def optional_leg(name, fn):
+    """Runs one of the legs that follow the timed iterations; an exception there is
+    recorded in the result line (and on stderr) instead of costing the line itself."""
+    try:
+        return fn()
+    except Exception as err:                      # noqa: BLE001 - any failure of the leg
+        print(f"bench: the {name} leg failed: {type(err).__name__}: {err}", file=sys.stderr)
+        return {"error": f"{type(err).__name__}: {err}"}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -428,32 +438,36 @@ def run_ours(args):
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                "d2h_bytes_per_step": d2h / args.steps}
 
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
+    def cpu_leg():
         v1, q, dt1 = time_oracle(p, iters=CPU_SAMPLE_ITERS)
         va, n, dta = time_oracle_all_cores(args.workload, CPU_SAMPLE_ITERS // 2)
-        cpu = {"value": va, "unit": UNIT, "cores": n, "kind": "oracle",
-               "sample": f"{p.name} cut to its first {q.nt} time slices: {CPU_SAMPLE_ITERS // 2} oracle "
-                         f"iterations in each of {n} processes, one per host core ({dta:.1f} s)",
-               "single_core": {"value": v1, "unit": UNIT, "cores": 1,
-                               "sample": f"{CPU_SAMPLE_ITERS} oracle iterations in one process ({dt1:.1f} s)"}}
+        return {"value": va, "unit": UNIT, "cores": n, "kind": "oracle",
+                "sample": f"{p.name} cut to its first {q.nt} time slices: {CPU_SAMPLE_ITERS // 2} oracle "
+                          f"iterations in each of {n} processes, one per host core ({dta:.1f} s)",
+                "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                                "sample": f"{CPU_SAMPLE_ITERS} oracle iterations in one process ({dt1:.1f} s)"}}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = optional_leg("cpu_baseline", cpu_leg)
 
     ttr = None
     if args.ttr and rank == 0:
-        ttr = [time_to_residual(binding, workload(w), device=dev, stream=stream)
+        ttr = [optional_leg(f"time_to_residual {w}",
+                            lambda w=w: time_to_residual(binding, workload(w), device=dev, stream=stream))
                for w in args.ttr.split(",") if w]
 
     batch = None
     if not args.no_batch and rank == 0:
-        batch = batch_leg(binding, device=dev, stream=stream)
+        batch = optional_leg("batch", lambda: batch_leg(binding, device=dev, stream=stream))
 
     nonlin = None
     if not args.no_nonlinear and rank == 0 and args.workload == "burgers2d" and args.precision == "fp32":
-        nonlin = nonlinear_leg(binding, device=dev, stream=stream)
+        nonlin = optional_leg("nonlinear", lambda: nonlinear_leg(binding, device=dev, stream=stream))
 
     grad = None
     if not args.no_gradient and rank == 0:
-        grad = gradient_leg(binding, device=dev, stream=stream)
+        grad = optional_leg("gradient", lambda: gradient_leg(binding, device=dev, stream=stream))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -71,3 +71,15 @@ def test_traffic_lookup_follows_the_kernel_source(tmp_path, monkeypatch):
         assert bench.traffic_for(s, name, fused=True) is None
         if same[s] is not None:
             assert same[s] == db[name][s]["dram_bytes_per_launch"]
+
+
+def test_a_failing_optional_leg_is_recorded_not_raised(capsys):
+    assert bench.optional_leg("ok", lambda: {"value": 1.0}) == {"value": 1.0}
+
+    def broken():
+        raise RuntimeError("device lost")
+    out = bench.optional_leg("batch", broken)
+    assert out == {"error": "RuntimeError: device lost"}
+    assert "batch leg failed" in capsys.readouterr().err
+    # the result line keeps such an entry (a dict with content is truthy)
+    assert out
