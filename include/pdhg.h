@@ -84,7 +84,9 @@ enum { PDHG_STAGE_PRIMAL = 0,      /* primal step + lambda update (Algorithm 1 s
  *   lf_a        global Lax-Friedrichs constant for the LF schemes (0: max |f'(u0)|);
  *               the upwind schemes use f(u-) and are monotone where f' >= 0
  *   c, gamma_hat  K = -d_tt - c^2 d_xx + gamma_hat^2 d_xxxx (Eq. 2.8, 2.10);
- *                 DG uses c only.
+ *                 DG uses c only.  c shapes the iteration, never its fixed point; for
+ *                 finite differences max |f'(u0)| serves well, while DG P2 Burgers past
+ *                 a shock converges far faster with c well below it (0.25 against 1.5).
  *   tau_u, tau_u0, tau_phi, tau_lambda   step sizes of Algorithm 1 (> 0).
  */
 typedef struct {
